@@ -1,0 +1,266 @@
+"""Pins of the FP64 oracle's whole step: exact streaming, conservation, momentum
+balance, Poiseuille flow, the Laplace law, near-contact merging behaviour, and
+symmetries. Thresholds are the ones the method fixes (conservation to round-off,
+Poiseuille within 1 %, Laplace within 3 %), except where a measured limit of the
+discretisation is stated beside the check.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mini
+from paper_2005_12764_gb300 import inputs
+
+C, W, OPP, B = oracle.lattice()
+
+
+def _lattice(shape, fields=None, **kw):
+    nz, ny, nx = shape
+    lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **kw))
+    if fields is not None:
+        lat.set_fields(*fields)
+    return lat
+
+
+# ------------------------------------------------------------------ streaming
+def test_streaming_is_exact_permutation_periodic():
+    # streaming alone for lcm(nx, ny, nz) steps returns every population bitwise
+    shape = (5, 3, 4)
+    lat = _lattice(shape)
+    r = np.random.default_rng(1)
+    fr, fb = r.random((19,) + shape), r.random((19,) + shape)
+    lat.set_pops(fr, fb)
+    lat.stream_only(1)
+    gr, gb = lat.get_pops()
+    for i in range(19):        # one step equals a periodic shift by c_i (brute force)
+        want = np.roll(fr[i], shift=(C[i][2], C[i][1], C[i][0]), axis=(0, 1, 2))
+        assert np.array_equal(gr[i], want)
+    lat.stream_only(60 - 1)
+    gr, gb = lat.get_pops()
+    assert np.array_equal(gr, fr) and np.array_equal(gb, fb)
+
+
+def test_streaming_with_walls_is_exact_permutation():
+    # halfway bounce-back keeps streaming a permutation: period lcm(nx, 2 ny, 2 nz)
+    shape = (5, 3, 4)
+    lat = _lattice(shape, wall_y=1, wall_z=1)
+    r = np.random.default_rng(2)
+    fr, fb = r.random((19,) + shape), r.random((19,) + shape)
+    lat.set_pops(fr, fb)
+    lat.stream_only(1)
+    gr, _ = lat.get_pops()
+    assert np.array_equal(np.sort(gr.ravel()), np.sort(fr.ravel()))
+    # a population at y = 0 moving towards the wall comes back reversed, in place
+    i_down = [i for i in range(19) if tuple(C[i]) == (0, -1, 0)][0]
+    i_up = OPP[i_down]
+    assert np.array_equal(gr[i_up][:, 0, :], fr[i_down][:, 0, :])
+    lat.stream_only(60 - 1)
+    gr, gb = lat.get_pops()
+    assert np.array_equal(gr, fr) and np.array_equal(gb, fb)
+
+
+# ------------------------------------------------------------------ conservation
+def test_conservation_static_droplet_500_steps():
+    w = inputs.static_droplet(L=32, R=8.0)
+    lat = _lattice(w.shape, (w.rho_r, w.rho_b), **w.params)
+    t0 = lat.totals()
+    lat.step(500)
+    t = lat.totals()
+    M = t0[0] + t0[1]
+    assert abs(t[0] - t0[0]) / t0[0] < 1e-12
+    assert abs(t[1] - t0[1]) / t0[1] < 1e-12
+    assert np.abs(t[2:]).max() / M < 1e-12
+
+
+def test_momentum_changes_by_total_force():
+    # periodic box, body + Kolmogorov + near-contact forces: P(t+1) - P(t) = sum_x F
+    shape = (16, 16, 24)
+    drops = [(7.0, 8.0, 8.0, 5.0), (17.0, 8.0, 8.0, 5.0)]
+    rr, rb = inputs.paint_droplets(shape, drops)
+    lat = _lattice(shape, (rr, rb), sigma=0.01, A_nc=0.05, g=(2e-5, -1e-5, 3e-6),
+                   kolmogorov_amp=1e-4)
+    P0 = lat.totals()[2:]
+    nc_seen = 0.0
+    for _ in range(20):
+        lat.step(1)
+        P1 = lat.totals()[2:]
+        F = lat.get_forces()
+        dP = F.reshape(3, -1).sum(1)
+        assert np.allclose(P1 - P0, dP, rtol=0, atol=1e-13)
+        body = np.array([2e-5, -1e-5, 3e-6]) * rr.size
+        nc_seen = max(nc_seen, np.abs(dP - body).max())
+        P0 = P1
+    assert nc_seen > 1e-6     # the near-contact force did act and is balanced too
+
+
+# ------------------------------------------------------------------ Poiseuille
+def test_poiseuille_profile_within_one_percent():
+    ny, g = 32, 1e-6
+    shape = (2, ny, 2)
+    lat = _lattice(shape, (np.ones(shape), np.zeros(shape)), wall_y=1, tau_r=1.0,
+                   g=(g, 0, 0))
+    lat.step(12000)
+    u = lat.get_fields()["u"][0][0, :, 0]
+    nu = (1.0 - 0.5) / 3
+    y = np.arange(ny)
+    exact = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.abs(u - exact).max() / exact.max() < 0.01
+
+
+# ------------------------------------------------------------------ Laplace law
+def _laplace_ratio(L, R, steps):
+    w = inputs.static_droplet(L=L, R=R)
+    lat = _lattice(w.shape, (w.rho_r, w.rho_b), **w.params)
+    lat.step(steps)
+    lap = lat.laplace((L / 2, L / 2, L / 2))
+    return lap["dp"] / (2 * w.params["sigma"] / lap["R_eff"]), lap
+
+
+def test_laplace_static_droplet_R8_32cube():
+    # The static-droplet workload itself: 32^3, R = 8, sigma = 0.01, 500 steps.
+    # Measured: dp / (2 sigma / R_eff) = 1.042 (1.055 when fully relaxed). The excess
+    # is the finite interface width (~4 lu) against R = 8: it falls as R^-2 (next test).
+    ratio, lap = _laplace_ratio(32, 8.0, 500)
+    assert abs(ratio - 1.0) < 0.06, lap
+    assert 7.5 < lap["R_eff"] < 8.2
+
+
+@pytest.mark.slow
+def test_laplace_R12_within_three_percent():
+    ratio, lap = _laplace_ratio(48, 12.0, 1500)
+    assert abs(ratio - 1.0) < 0.03, lap
+
+
+# ------------------------------------------------------------------ near contact
+def _components(phi):
+    from scipy import ndimage
+    return ndimage.label(phi > 0)[1]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("A_nc,expect", [(0.0, 1), (0.05, 2)])
+def test_near_contact_inhibits_merging(A_nc, expect):
+    # Two R = 8 droplets 2 lu apart (sigma = 0.01). Without the near-contact force the
+    # film drains and they merge (N_c = 0); with A = 0.05 (N_c = A dx / sigma = 5) the
+    # film survives. (With this reading the transition lies between N_c = 3 and 5.)
+    shape = (32, 32, 48)
+    drops = [(14.0, 16.0, 16.0, 8.0), (34.0, 16.0, 16.0, 8.0)]
+    rr, rb = inputs.paint_droplets(shape, drops)
+    lat = _lattice(shape, (rr, rb), sigma=0.01, A_nc=A_nc, h_min=3.0)
+    lat.step(500)
+    assert _components(lat.get_fields()["phi"]) == expect
+
+
+def test_near_contact_film_thickness_flat_films():
+    # Brute force in 1-D: for a profile varying along x only, the ray samples a
+    # piecewise-linear interpolant exactly, so h is the distance between its zeros.
+    nx = 40
+    x = np.arange(nx)
+    prof = np.where((x >= 8) & (x < 16) | (x >= 16 + 4) & (x < 30), 1.0, -1.0)
+    prof = np.convolve(np.pad(prof, 2, mode="wrap"), np.ones(3) / 3, mode="same")[2:-2]
+    phi = np.broadcast_to(prof, (4, 4, nx)).copy()
+    p = oracle.make_params(nx, 4, 4, A_nc=0.02, h_min=3.0, h_cut=6.0)
+    G = oracle.gradient(p, phi)
+    checked = 0
+    for xi in range(nx):
+        g = G[:, 1, 1, xi]
+        if np.linalg.norm(g) < 1e-3:
+            continue
+        F = oracle.nc_force_node(p, phi, xi, 1, 1, g)
+        s = -np.sign(g[0])                        # ray direction along x
+        ts = -1 + 0.5 * np.arange(19)
+        vals = np.interp((xi + s * ts) % nx, np.arange(nx + 1), np.append(prof, prof[0]))
+        zs = []
+        for k in range(len(ts) - 1):
+            v0, v1 = vals[k], vals[k + 1]
+            if (not zs and v0 > 0 >= v1) or (zs and v0 <= 0 < v1):
+                zs.append(ts[k] + 0.5 * v0 / (v0 - v1))
+                if len(zs) == 2:
+                    break
+        want = oracle.A_h(zs[1] - zs[0], 0.02, 3.0, 6.0) * g if len(zs) == 2 else 0 * g
+        assert np.allclose(F, want, atol=1e-15)
+        checked += int(len(zs) == 2 and np.abs(want).max() > 0)
+    assert checked >= 4
+
+
+# ------------------------------------------------------------------ symmetries
+@pytest.mark.parametrize("A_nc", [0.0, 0.01])
+def test_translation_invariance(A_nc):
+    # Shifting the initial state by a lattice vector shifts the result: bitwise
+    # without the near-contact force; with it, the ray's sample points x + t n round
+    # differently at different x, so agreement is to round-off.
+    shape = (10, 9, 12)
+    rr, rb, u = inputs.random_state(shape, seed=11)
+    kw = dict(sigma=0.02, A_nc=A_nc, g=(1e-5, 0, 0), tau_r=0.9, tau_b=1.2)
+    a = _lattice(shape, (rr, rb, u), **kw)
+    a.step(6)
+    s = (3, 0, 5)   # shift in (z, y, x); y kept because nothing here depends on y
+    roll = lambda f: np.roll(f, s, axis=(-3, -2, -1))
+    b = _lattice(shape, (roll(rr), roll(rb), roll(u)), **kw)
+    b.step(6)
+    fa, fb_ = a.get_pops(), b.get_pops()
+    if A_nc == 0.0:
+        assert np.array_equal(roll(fa[0]), fb_[0]) and np.array_equal(roll(fa[1]), fb_[1])
+    else:
+        assert np.allclose(roll(fa[0]), fb_[0], rtol=0, atol=1e-14)
+        assert np.allclose(roll(fa[1]), fb_[1], rtol=0, atol=1e-14)
+
+
+def test_mirror_symmetry_x():
+    shape = (8, 9, 10)
+    rr, rb, u = inputs.random_state(shape, seed=12)
+    kw = dict(sigma=0.02, A_nc=0.01, wall_y=1)
+    a = _lattice(shape, (rr, rb, u), **kw)
+    a.step(5)
+    mir = lambda f: np.roll(f[..., ::-1], 1, axis=-1)   # x -> -x (mod nx)
+    um = np.stack([-mir(u[0]), mir(u[1]), mir(u[2])])
+    b = _lattice(shape, (mir(rr), mir(rb), um), **kw)
+    b.step(5)
+    fa, fb_ = a.get_fields(), b.get_fields()
+    assert np.allclose(mir(fa["rho_r"]), fb_["rho_r"], atol=1e-14)
+    assert np.allclose(-mir(fa["u"][0]), fb_["u"][0], atol=1e-15)
+    assert np.allclose(mir(fa["u"][1]), fb_["u"][1], atol=1e-15)
+
+
+# ------------------------------------------------------------------ cross-checks
+@pytest.mark.parametrize("case", [
+    dict(shape=(4, 4, 4)),
+    dict(shape=(5, 6, 7), wall_y=1, g=(1e-4, 2e-5, 0), tau_b=1.3),
+    dict(shape=(8, 6, 7), wall_z=1, wall_y=1, A_nc=0.02, kolmogorov_amp=1e-3, tau_r=0.8),
+    dict(shape=(8, 8, 8), A_nc=0.05, h_min=2.0),
+])
+def test_numpy_mini_oracle_agrees(case):
+    case = dict(case)
+    shape = case.pop("shape")
+    nz, ny, nx = shape
+    rr, rb, u = inputs.random_state(shape, seed=sum(shape))
+    kw = dict(sigma=0.02, beta=0.7, **case)
+    lat = _lattice(shape, (rr, rb, u), **kw)
+    m = mini.MiniLattice(nx, ny, nz, **kw)
+    m.set_fields(rr, rb, u)
+    lat.step(4)
+    m.step(4)
+    f = lat.get_fields()
+    for k in ("rho_r", "rho_b", "phi"):
+        assert np.allclose(f[k], m.last[k], rtol=0, atol=1e-13), k
+    assert np.allclose(f["u"], m.last["u"], rtol=0, atol=1e-13)
+    assert np.allclose(lat.get_forces(), m.last["F"], rtol=0, atol=1e-13)
+
+
+def test_step_nodes_matches_full_step():
+    w = inputs.channel_droplets(nx=64, ny=40, nz=24, n_grid=(2, 2, 1), r_range=(4, 6),
+                                seed=5)
+    shape = w.shape
+    lat = _lattice(shape, (w.rho_r, w.rho_b), **w.params)
+    lat.step(3)
+    fr, fb = lat.get_pops()
+    lag = lat.get_phi_lag()
+    nodes = np.random.default_rng(3).choice(fr[0].size, 300, replace=False)
+    lat.step(1)
+    gr, gb = lat.get_pops()
+    p = oracle.make_params(shape[2], shape[1], shape[0], **w.params)
+    oa, ob, F = oracle.step_nodes(p, fr.reshape(19, -1), fb.reshape(19, -1), lag.ravel(), nodes)
+    assert np.array_equal(oa, gr.reshape(19, -1)[:, nodes].T)
+    assert np.array_equal(ob, gb.reshape(19, -1)[:, nodes].T)
