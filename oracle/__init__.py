@@ -73,7 +73,7 @@ def _load():
                 "or_perturb": (None, [_D, C.c_double, C.c_double, _D, _D]),
                 "or_recolour": (None, [_D, C.c_double, C.c_double, C.c_double, _D, _D, _D]),
                 "or_A_h": (C.c_double, [C.c_double] * 4),
-                "or_nc_force_node": (None, [P, _D, _U8, C.c_long, C.c_long, C.c_long, _D, _D]),
+                "or_nc_strength_node": (C.c_double, [P, _D, _U8, C.c_long, C.c_long, C.c_long]),
                 "or_gradient": (None, [P, _D, _D, _D, _D]),
                 "or_create": (C.c_void_p, [P]),
                 "or_destroy": (None, [C.c_void_p]),
@@ -189,16 +189,15 @@ def gradient(params: Params, phi):
     return G.reshape((3,) + phi.shape)
 
 
-def nc_force_node(params: Params, phi_ray, x, y, z, G, pin=None):
+def nc_strength_node(params: Params, phi_ray, x, y, z, pin=None):
+    """Near-contact strength A_h at one node, measured on the field phi_ray."""
     phi_ray = _f64(phi_ray)
-    F = np.zeros(3)
     pin_p = None
     if pin is not None:
         pin = np.ascontiguousarray(pin, dtype=np.uint8)
         pin_p = pin.ctypes.data_as(_U8)
-    _load().or_nc_force_node(C.byref(params), _d(phi_ray), pin_p, int(x), int(y), int(z),
-                             _d(_f64(G)), _d(F))
-    return F
+    return _load().or_nc_strength_node(C.byref(params), _d(phi_ray), pin_p, int(x), int(y),
+                                       int(z))
 
 
 def step_nodes(params: Params, fr, fb, phi_lag, nodes, pin=None):

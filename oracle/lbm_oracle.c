@@ -17,7 +17,9 @@
  *   1. pull streaming with halfway bounce-back walls        Eq. (1), streaming text
  *   2. moments rho_r, rho_b, j, phi                          Eq. (3)
  *   3. isotropic colour gradient                             stencil form of Eq. (10)
- *   4. forces: body + Kolmogorov + near-contact              Eq. (11)
+ *   4. forces: body + Kolmogorov + near-contact              Eq. (11); the film
+ *      thickness of the near-contact force is measured on the previous step's
+ *      colour field
  *   5. BGK collision of the total population + EDM source    Eqs. (1), (2), (5)-(9)
  *   6. colour-gradient perturbation (surface tension)        reading: generalised
  *                                                            perturbation operator
@@ -182,13 +184,15 @@ void or_bgk_edm(const double f[Q], double omega, const double F[3], double out[Q
  * population. It conserves mass and momentum and adds the capillary stress
  * (A/9)|G| (n n - I) to the second moment, so the surface tension is
  * sigma = 2A/(9 omega) for a colour field phi running from -1 to +1.
- * Skipped where |G| < 1e-8 (reading: zero-gradient tie-break).                 */
+ * Skipped where |G| < 1e-6 (reading: zero-gradient tie-break; the threshold sits
+ * above the rounding level of a single-precision evaluation of the stencil on an
+ * O(1) colour field, so that FP32 implementations take the same branch).       */
 void or_perturb(const double f[Q], double omega, double sigma, const double G[3],
                 double out[Q]) {
     lattice_init();
     double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     double gm = sqrt(g2);
-    if (gm < 1e-8) {
+    if (gm < 1e-6) {
         for (int i = 0; i < Q; ++i) out[i] = f[i];
         return;
     }
@@ -203,7 +207,7 @@ void or_perturb(const double f[Q], double omega, double sigma, const double G[3]
  *   f_i^r = (rho_r/rho) f_i + beta (rho_r rho_b / rho) w_i cos(theta_i)
  *   f_i^b = (rho_b/rho) f_i - beta (rho_r rho_b / rho) w_i cos(theta_i)
  * cos(theta_i) = c_i.G / (|c_i| |G|), cos(theta_0) = 0; the beta term is
- * skipped where |G| < 1e-8.                                                    */
+ * skipped where |G| < 1e-6 (same tie-break as the perturbation).              */
 void or_recolour(const double f[Q], double rho_r, double rho_b, double beta,
                  const double G[3], double out_r[Q], double out_b[Q]) {
     lattice_init();
@@ -211,7 +215,7 @@ void or_recolour(const double f[Q], double rho_r, double rho_b, double beta,
     double gm = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
     for (int i = 0; i < Q; ++i) {
         double seg = 0.0;
-        if (gm >= 1e-8 && i != 0) {
+        if (gm >= 1e-6 && i != 0) {
             double cn = sqrt((double)(CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i]));
             double cosv = (CX[i] * G[0] + CY[i] * G[1] + CZ[i] * G[2]) / (cn * gm);
             seg = beta * (rho_r * rho_b / rho) * W[i] * cosv;
@@ -272,27 +276,53 @@ static int interp(const or_params* p, const double* fld, double px, double py,
     return 1;
 }
 
+/* Colour gradient of a node field at one node: G = 3 sum_i w_i c_i phi(x + c_i),
+ * a neighbour beyond a wall taking phi(x) (see or_gradient).                   */
+static void gradient_node(const or_params* p, const double* phi, long x, long y, long z,
+                          double G[3]) {
+    long id = nidx(p, x, y, z);
+    double g[3] = {0, 0, 0};
+    for (int i = 1; i < Q; ++i) {
+        long xs = x + CX[i], ys = y + CY[i], zs = z + CZ[i];
+        double v;
+        if ((p->wall_y && (ys < 0 || ys >= p->ny)) || (p->wall_z && (zs < 0 || zs >= p->nz)))
+            v = phi[id];
+        else
+            v = phi[nidx(p, wrap(xs, p->nx), wrap(ys, p->ny), wrap(zs, p->nz))];
+        g[0] += W[i] * CX[i] * v;
+        g[1] += W[i] * CY[i] * v;
+        g[2] += W[i] * CZ[i] * v;
+    }
+    G[0] = 3.0 * g[0];
+    G[1] = 3.0 * g[1];
+    G[2] = 3.0 * g[2];
+}
+
 /* Near-contact repulsive force, Eq. (11): F_rep = -A_h[h] n delta_I.
  * The paper does not say how h, n and delta_I are evaluated. Reading:
- *  - n = -G/|G| is the outward normal of the red (phi > 0) phase and
- *    delta_I = |G|, so F_rep = A_h[h] G (pushes the interface back into its own
- *    droplet; repulsive for both members of a close pair);
- *  - h is the film thickness along n: phi (of the field phi_ray) is sampled by
- *    trilinear interpolation at x + t n for t = -1, -1/2, 0, ..., h_cut + 2; t_d is
- *    the first downward zero crossing (red to blue), t_u the first upward crossing
- *    after it, both located by linear interpolation between samples; h = t_u - t_d;
- *  - no force if |G| < 1e-3, if there is no such pair of crossings, or if the ray
+ *  - delta_I = |G| and n = -G/|G| (outward normal of the red, phi > 0, phase), so
+ *    F_rep = A_h[h] G with G the colour gradient of the current step: the force
+ *    pushes each interface back into its own droplet, repulsive for both members of
+ *    a close pair;
+ *  - the strength A_h[h] is a property of the film around the node, measured on the
+ *    colour field phi_ray of the previous step (lag 1): with G' its gradient at the
+ *    node and n' = -G'/|G'|, phi_ray is sampled by trilinear interpolation at
+ *    x + t n' for t = -1, -1/2, 0, ..., h_cut + 2; t_d is the first downward zero
+ *    crossing (red to blue), t_u the first upward crossing after it, both located by
+ *    linear interpolation between samples; h = t_u - t_d;
+ *  - A_h = 0 if |G'| < 1e-3, if there is no such pair of crossings, or if the ray
  *    leaves the fluid through a wall before both are found;
  *  - pinning sites (if a mask is given) act as another interface: a node with
- *    |G| >= 1e-3 whose nearest pin (within the cube of half-width ceil(h_cut)) lies
- *    at distance d gets an added A_h[d] G.                                       */
-void or_nc_force_node(const or_params* p, const double* phi_ray,
-                      const unsigned char* pin, long x, long y, long z, const double G[3],
-                      double F[3]) {
-    F[0] = F[1] = F[2] = 0.0;
-    if (p->A_nc == 0.0) return;
+ *    |G'| >= 1e-3 whose nearest pin (within the cube of half-width ceil(h_cut))
+ *    lies at distance d gets A_h[d] added.
+ * This routine returns the strength A_h at node (x, y, z).                       */
+double or_nc_strength_node(const or_params* p, const double* phi_ray,
+                           const unsigned char* pin, long x, long y, long z) {
+    if (p->A_nc == 0.0) return 0.0;
+    double G[3];
+    gradient_node(p, phi_ray, x, y, z, G);
     double gm = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-    if (gm < 1e-3) return;
+    if (gm < 1e-3) return 0.0;
     double n[3] = {-G[0] / gm, -G[1] / gm, -G[2] / gm};
     int nsamp = (int)floor(2.0 * (p->h_cut + 3.0)) + 1; /* t = -1 ... h_cut + 2 */
     double t_prev = 0, v_prev = 0, t_d = 0, t_u = 0;
@@ -334,9 +364,7 @@ void or_nc_force_node(const or_params* p, const double* phi_ray,
                 }
         if (best >= 0) Ah += or_A_h(best, p->A_nc, p->h_min, p->h_cut);
     }
-    F[0] = Ah * G[0];
-    F[1] = Ah * G[1];
-    F[2] = Ah * G[2];
+    return Ah;
 }
 
 /* Isotropic colour gradient G(x) = 3 sum_i w_i c_i phi(x + c_i), the stencil form
@@ -566,7 +594,8 @@ void or_step(or_state* s, int nsteps) {
                     double Fb[3], Fn[3];
                     double G[3] = {s->Gx[id], s->Gy[id], s->Gz[id]};
                     body_force(p, y, Fb);
-                    or_nc_force_node(p, phi_ray, s->pin, x, y, z, G, Fn);
+                    double ah = or_nc_strength_node(p, phi_ray, s->pin, x, y, z);
+                    for (int a = 0; a < 3; ++a) Fn[a] = ah * G[a];
                     s->Fx[id] = Fb[0] + Fn[0];
                     s->Fy[id] = Fb[1] + Fn[1];
                     s->Fz[id] = Fb[2] + Fn[2];
@@ -693,7 +722,8 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
         double G[3] = {3.0 * g[0], 3.0 * g[1], 3.0 * g[2]};
         double Fb[3], Fn[3], F[3];
         body_force(p, y, Fb);
-        or_nc_force_node(p, phi_lag, pin, x, y, z, G, Fn);
+        double ah = or_nc_strength_node(p, phi_lag, pin, x, y, z);
+        for (int a = 0; a < 3; ++a) Fn[a] = ah * G[a];
         for (int a = 0; a < 3; ++a) F[a] = Fb[a] + Fn[a];
         collide_node(p, gr, gb, rr, rb, G, F, out_r + k * Q, out_b + k * Q);
         if (Fout)

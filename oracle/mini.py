@@ -13,9 +13,10 @@ Readings (identical to the C oracle, where the paper is silent):
   * Colour gradient 3 sum w c phi(x+c), wall neighbour -> phi(x).
   * Perturbation (A/2)|G|(w (c.n)^2 - B), A = 9 omega sigma / 2,
     B = -2/9, 1/54, 1/27; recolouring with beta (Latva-Kokko & Rothman);
-    both skipped where |G| < 1e-8.
-  * Near-contact force A_h[h] G (Eq. 11) with h measured along -G/|G| on the lagged
-    colour field by linear zero-crossing location on half-unit samples.
+    both skipped where |G| < 1e-6.
+  * Near-contact force A_h[h] G (Eq. 11); h is measured on the lagged colour field,
+    along minus its own gradient, by linear zero-crossing location on half-unit
+    samples.
 """
 from __future__ import annotations
 
@@ -143,13 +144,15 @@ class MiniLattice:
             1 - (self.h_min / self.h_cut) ** 3)
 
     def nc_force(self, phi_ray, G):
+        """A_h measured on phi_ray (its own gradient gives the ray direction) times G."""
         F = np.zeros((3,) + self.n)
         if self.A_nc == 0:
             return F
-        gm = np.sqrt((G * G).sum(0))
+        Gr = self.grad(phi_ray)
+        gm = np.sqrt((Gr * Gr).sum(0))
         ts = [-1 + 0.5 * s for s in range(int(math.floor(2 * (self.h_cut + 3))) + 1)]
         for z, y, x in zip(*np.nonzero(gm >= 1e-3)):
-            nrm = -G[:, z, y, x] / gm[z, y, x]
+            nrm = -Gr[:, z, y, x] / gm[z, y, x]
             vals = []
             for t in ts:
                 v = self._interp(phi_ray, (x + t * nrm[0], y + t * nrm[1], z + t * nrm[2]))
@@ -191,7 +194,7 @@ class MiniLattice:
             S = equilibrium(rho, u + F / rho) - fe
             f1 = f - om * (f - fe) + S
             gm = np.sqrt((G * G).sum(0))
-            ok = gm >= 1e-8
+            ok = gm >= 1e-6
             safe = np.where(ok, gm, 1.0)
             cg = np.einsum("ia,a...->i...", Cf, G)
             A = 4.5 * om * self.sigma

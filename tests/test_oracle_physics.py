@@ -168,7 +168,7 @@ def test_near_contact_film_thickness_flat_films():
         g = G[:, 1, 1, xi]
         if np.linalg.norm(g) < 1e-3:
             continue
-        F = oracle.nc_force_node(p, phi, xi, 1, 1, g)
+        F = oracle.nc_strength_node(p, phi, xi, 1, 1) * g
         s = -np.sign(g[0])                        # ray direction along x
         ts = -1 + 0.5 * np.arange(19)
         vals = np.interp((xi + s * ts) % nx, np.arange(nx + 1), np.append(prof, prof[0]))

@@ -151,7 +151,7 @@ def test_perturbation_moments(seed):
 
 def test_perturbation_skipped_at_zero_gradient():
     f = W * 1.1
-    assert np.array_equal(oracle.perturb(f, 1.0, 0.02, np.array([0.0, 0.0, 1e-9])), f)
+    assert np.array_equal(oracle.perturb(f, 1.0, 0.02, np.array([0.0, 0.0, 5e-7])), f)
 
 
 def test_perturbation_flat_interface_surface_tension():
