@@ -236,30 +236,41 @@ double or_A_h(double h, double A, double h_min, double h_cut) {
     return A * (a * a * a - b * b * b) / (1.0 - b * b * b);
 }
 
-/* Trilinear interpolation of a node field at a point; returns 0 and leaves *v
- * unset if the point lies outside the fluid along a walled axis.             */
-static int interp(const or_params* p, const double* fld, double px, double py,
-                  double pz, double* v) {
-    double pc[3] = {px, py, pz};
+/* Trilinear interpolation of a node field at the point (x + ox, y + oy, z + oz),
+ * (x, y, z) a node and o an offset; returns 0 and leaves *v unset if the point lies
+ * outside the fluid along a walled axis. The cell and the weights are taken from
+ * the offset alone (floor and fraction of o), so a single-precision evaluation
+ * locates the point to the precision of o rather than of x + o.                */
+static int interp(const or_params* p, const double* fld, long x, long y, long z, double ox,
+                  double oy, double oz, double* v) {
+    long base[3] = {x, y, z};
+    double off[3] = {ox, oy, oz};
     int n[3] = {p->nx, p->ny, p->nz};
     int walled[3] = {0, p->wall_y, p->wall_z};
     long i0[3], i1[3];
     double fr[3];
     for (int a = 0; a < 3; ++a) {
-        double q = pc[a];
+        double fl = floor(off[a]);
+        long b = base[a] + (long)fl;
+        double f = off[a] - fl;
         if (walled[a]) {
-            if (q < 0.0 || q > (double)(n[a] - 1)) return 0;
-            long b = (long)floor(q);
-            if (b > n[a] - 2) b = n[a] - 2;
-            if (b < 0) b = 0;
+            if (b < 0 || b > n[a] - 1 || (b == n[a] - 1 && f > 0.0)) return 0;
+            if (n[a] == 1) {
+                i0[a] = i1[a] = 0;
+                fr[a] = 0.0;
+                continue;
+            }
+            if (b == n[a] - 1) { /* exactly on the last node */
+                b = n[a] - 2;
+                f = 1.0;
+            }
             i0[a] = b;
-            i1[a] = (n[a] > 1) ? b + 1 : b;
-            fr[a] = q - (double)b;
+            i1[a] = b + 1;
+            fr[a] = f;
         } else {
-            double fl = floor(q);
-            fr[a] = q - fl;
-            i0[a] = wrap((long)fl, n[a]);
-            i1[a] = wrap((long)fl + 1, n[a]);
+            i0[a] = wrap(b, n[a]);
+            i1[a] = wrap(b + 1, n[a]);
+            fr[a] = f;
         }
     }
     double s = 0.0;
@@ -307,9 +318,10 @@ static void gradient_node(const or_params* p, const double* phi, long x, long y,
  *  - the strength A_h[h] is a property of the film around the node, measured on the
  *    colour field phi_ray of the previous step (lag 1): with G' its gradient at the
  *    node and n' = -G'/|G'|, phi_ray is sampled by trilinear interpolation at
- *    x + t n' for t = -1, -1/2, 0, ..., h_cut + 2; t_d is the first downward zero
- *    crossing (red to blue), t_u the first upward crossing after it, both located by
- *    linear interpolation between samples; h = t_u - t_d;
+ *    x + t n' for t = -1, -1/2, 0, ..., h_cut + 2; samples with |phi| <= 1e-5
+ *    carry no sign; t_d is the first downward zero crossing (red to blue) between
+ *    consecutive signed samples, t_u the first upward crossing after it, both
+ *    located by linear interpolation between those samples; h = t_u - t_d;
  *  - A_h = 0 if |G'| < 1e-3, if there is no such pair of crossings, or if the ray
  *    leaves the fluid through a wall before both are found;
  *  - pinning sites (if a mask is given) act as another interface: a node with
@@ -325,24 +337,29 @@ double or_nc_strength_node(const or_params* p, const double* phi_ray,
     if (gm < 1e-3) return 0.0;
     double n[3] = {-G[0] / gm, -G[1] / gm, -G[2] / gm};
     int nsamp = (int)floor(2.0 * (p->h_cut + 3.0)) + 1; /* t = -1 ... h_cut + 2 */
-    double t_prev = 0, v_prev = 0, t_d = 0, t_u = 0;
-    int have_prev = 0, have_d = 0, have_u = 0;
+    /* A sample carries a sign only if |phi| > 1e-5 (samples at rounding level of
+     * zero are skipped); a crossing lies between the last signed sample and the
+     * next one of opposite sign, located by linear interpolation between them.  */
+    const double band = 1e-5;
+    double t_a = 0, v_a = 0, t_d = 0, t_u = 0;
+    int have_a = 0, have_d = 0, have_u = 0;
     for (int s = 0; s < nsamp && !have_u; ++s) {
         double t = -1.0 + 0.5 * s;
         double v;
-        if (!interp(p, phi_ray, x + t * n[0], y + t * n[1], z + t * n[2], &v)) break;
-        if (have_prev) {
-            if (!have_d && v_prev > 0.0 && v <= 0.0) {
-                t_d = t_prev + 0.5 * v_prev / (v_prev - v);
+        if (!interp(p, phi_ray, x, y, z, t * n[0], t * n[1], t * n[2], &v)) break;
+        if (fabs(v) <= band) continue;
+        if (have_a) {
+            if (!have_d && v_a > 0.0 && v < 0.0) {
+                t_d = t_a + (t - t_a) * v_a / (v_a - v);
                 have_d = 1;
-            } else if (have_d && v_prev <= 0.0 && v > 0.0) {
-                t_u = t_prev + 0.5 * v_prev / (v_prev - v);
+            } else if (have_d && v_a < 0.0 && v > 0.0) {
+                t_u = t_a + (t - t_a) * v_a / (v_a - v);
                 have_u = 1;
             }
         }
-        t_prev = t;
-        v_prev = v;
-        have_prev = 1;
+        t_a = t;
+        v_a = v;
+        have_a = 1;
     }
     double Ah = 0.0;
     if (have_d && have_u) Ah = or_A_h(t_u - t_d, p->A_nc, p->h_min, p->h_cut);

@@ -15,8 +15,8 @@ Readings (identical to the C oracle, where the paper is silent):
     B = -2/9, 1/54, 1/27; recolouring with beta (Latva-Kokko & Rothman);
     both skipped where |G| < 1e-6.
   * Near-contact force A_h[h] G (Eq. 11); h is measured on the lagged colour field,
-    along minus its own gradient, by linear zero-crossing location on half-unit
-    samples.
+    along minus its own gradient, by linear zero-crossing location between
+    consecutive half-unit samples that carry a sign (|phi| > 1e-5).
 """
 from __future__ import annotations
 
@@ -106,25 +106,25 @@ class MiniLattice:
         return G
 
     # --- near contact ----------------------------------------------------------
-    def _interp(self, fld, p):
+    def _interp(self, fld, node, off):
+        """trilinear value at node + off (cell and weights from the offset)."""
         nz, ny, nx = self.n
         dims = [(nx, False), (ny, self.wall_y), (nz, self.wall_z)]
         lo, hi, fr = [], [], []
         for a, (n, walled) in enumerate(dims):
-            q = p[a]
+            fl = math.floor(off[a])
+            b, f = node[a] + fl, off[a] - fl
             if walled:
-                if q < 0 or q > n - 1:
+                if b < 0 or b > n - 1 or (b == n - 1 and f > 0):
                     return None
-                b = min(int(math.floor(q)), n - 2)
-                b = max(b, 0)
-                lo.append(b)
-                hi.append(b + 1 if n > 1 else b)
-                fr.append(q - b)
+                if n == 1:
+                    lo.append(0); hi.append(0); fr.append(0.0)
+                    continue
+                if b == n - 1:
+                    b, f = n - 2, 1.0
+                lo.append(b); hi.append(b + 1); fr.append(f)
             else:
-                fl = math.floor(q)
-                lo.append(int(fl) % n)
-                hi.append((int(fl) + 1) % n)
-                fr.append(q - fl)
+                lo.append(b % n); hi.append((b + 1) % n); fr.append(f)
         v = 0.0
         for cz in (0, 1):
             for cy in (0, 1):
@@ -155,16 +155,17 @@ class MiniLattice:
             nrm = -Gr[:, z, y, x] / gm[z, y, x]
             vals = []
             for t in ts:
-                v = self._interp(phi_ray, (x + t * nrm[0], y + t * nrm[1], z + t * nrm[2]))
+                v = self._interp(phi_ray, (x, y, z), (t * nrm[0], t * nrm[1], t * nrm[2]))
                 if v is None:
                     break
-                vals.append((t, v))
+                if abs(v) > 1e-5:          # samples within 1e-5 of zero carry no sign
+                    vals.append((t, v))
             t_d = t_u = None
             for (t0, v0), (t1, v1) in zip(vals, vals[1:]):
-                if t_d is None and v0 > 0 >= v1:
-                    t_d = t0 + 0.5 * v0 / (v0 - v1)
-                elif t_d is not None and v0 <= 0 < v1:
-                    t_u = t0 + 0.5 * v0 / (v0 - v1)
+                if t_d is None and v0 > 0 > v1:
+                    t_d = t0 + (t1 - t0) * v0 / (v0 - v1)
+                elif t_d is not None and v0 < 0 < v1:
+                    t_u = t0 + (t1 - t0) * v0 / (v0 - v1)
                     break
             if t_d is not None and t_u is not None:
                 F[:, z, y, x] = self._Ah(t_u - t_d) * G[:, z, y, x]
