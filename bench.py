@@ -1,0 +1,315 @@
+"""Benchmark of the fused colour-gradient LB step on GB300.
+
+Default workload: the microfluidic-crystal channel, 256 x 128 x 64 D3Q19 nodes with
+bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigma =
+0.02, beta = 0.7, near-contact force A = 0.01 within 3 lu, g_x = 1e-6, FP32 storage.
+One step = one lattice update of every node (one launch of the fused kernel).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16]
+                  [--impl ours|reference]
+
+Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second)
+over all ranks; ``e2e`` times the same job through the public C-ABI with host
+buffers (set fields from pinned host memory, K steps, fields back to the host);
+``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations
+per node, read once and written once) to the measured HBM bandwidth;
+``cpu_baseline`` times the FP64 oracle on the host cores. ``--impl reference``
+times the oracle itself on the same workload (the method has no other reference
+implementation). Multi-GPU runs are independent replicas (one lattice per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % HBM roofline, FP32 vs FP16-store; served-run p50/p99 latency"
+WORKLOAD = "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, NC on"
+Q, C = 19, 2
+
+
+def kernel_source_hash() -> str:
+    d = os.path.join(ROOT, "paper_2005_12764_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(storage: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == want and parts[1] == storage:
+            return float(parts[2])
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in a thread."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(workload, steps, warm=1):
+    """Oracle lattice updates per second on this host (all cores) over `steps` steps."""
+    import oracle
+    nz, ny, nx = workload.shape
+    lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **workload.params))
+    lat.set_fields(workload.rho_r, workload.rho_b)
+    lat.step(warm)
+    t0 = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t0
+    lat.close()
+    return nx * ny * nz * steps / dt, dt
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores, on the same workload and metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2005_12764_gb300 import inputs
+    w = inputs.channel_droplets()
+    N = w.rho_r.size
+    import oracle
+    nz, ny, nx = w.shape
+    lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **w.params))
+    lat.set_fields(w.rho_r, w.rho_b)
+    lat.step(args.warmup)
+    t0 = time.perf_counter()
+    lat.step(args.steps)
+    dt = time.perf_counter() - t0
+    glups = N * args.steps / dt / 1e9
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": N, "storage": "f64 (oracle)"},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full steps of the {nx}x{ny}x{nz} channel"},
+            "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_12764_gb300 import build_lib, inputs, lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build_lib.build()
+    w = inputs.channel_droplets()
+    nz, ny, nx = w.shape
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    P = lbm.make_params(nx, ny, nz, storage=args.storage, stream=stream.cuda_stream, **w.params)
+    lat = lbm.Lattice(P)
+    dev_rr = torch.from_numpy(w.rho_r).to(f"cuda:{local}")
+    dev_rb = torch.from_numpy(w.rho_b).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    lat.set_fields(dev_rr, dev_rb)
+    lat.step(args.warmup)
+    lat.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing: K steps queued back to back, CUDA events on the
+    # stream the kernels run on
+    barrier()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        lat.step(args.steps)
+        t_end.record(stream)
+        stream.synchronize()
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    glups = world * N * args.steps / (total_ms * 1e-3) / 1e9
+    # per-kernel durations (events around each launch, inside the library)
+    kt = max(5, min(args.steps, 50))
+    nc_ms, step_ms = lat.step_timed(kt)
+    kern_ms = [step_ms / kt]
+    nc_avg_ms = nc_ms / kt
+    # ---- end to end through the public API with pinned host buffers
+    host_rr = torch.from_numpy(w.rho_r).pin_memory()
+    host_rb = torch.from_numpy(w.rho_b).pin_memory()
+    outs = {"rho_r": torch.empty(w.shape, dtype=torch.float64).pin_memory(),
+            "rho_b": torch.empty(w.shape, dtype=torch.float64).pin_memory(),
+            "u": torch.empty((3,) + w.shape, dtype=torch.float64).pin_memory(),
+            "phi": torch.empty(w.shape, dtype=torch.float64).pin_memory()}
+    barrier()
+    t0 = time.perf_counter()
+    lat.set_fields(host_rr, host_rb)
+    lat.step(args.steps)
+    lat.get_fields(outs)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * N * args.steps / e2e_s / 1e9
+    h2d = 2 * N * 8
+    d2h = 6 * N * 8
+
+    # ---- roofline of the step kernel
+    elem = 4 if args.storage == "fp32" else 2
+    alg_bytes = 2 * Q * C * elem * N
+    k_avg = statistics.mean(kern_ms) * 1e-3
+    achieved = alg_bytes / k_avg / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic(args.storage)
+
+    obs = lat.observables()
+    finite = bool(np.isfinite(obs[:5]).all())
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, dt = cpu_oracle_rate(w, args.cpu_steps)
+            cpu = {"value": rate / 1e9, "unit": "GLUPS", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"{args.cpu_steps} full FP64 steps of the {nx}x{ny}x{nz} channel "
+                             f"({dt:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": N, "storage": args.storage,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
+                             % (2 * Q * C * elem * N / 2 / 1e6)},
+            "e2e": {"value": e2e, "unit": "GLUPS",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "job": "set_fields(host) + K steps + get_fields(host)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "kernel": "step_kernel (fused stream/collide/perturb/recolour)",
+                         "kernel_ms": statistics.mean(kern_ms),
+                         "near_contact_pass_ms": nc_avg_ms,
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "gpu_launches": args.steps * lat.launches_per_step,
+            "clocks": clk.summary(),
+            "finite": finite,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * lbm.h -- C-ABI of the GB300 (sm_103a) library liblbm.so: one time step of the
+ * two-component colour-gradient lattice Boltzmann method on the D3Q19 lattice
+ * (Succi et al., "Towards Exascale Design of Soft Mesoscale Materials",
+ * arXiv:2005.12764, Secs. "Basics of Lattice Boltzmann Method", "Multi-component
+ * flows" and "LB method for microfluidic crystals").
+ *
+ * One step (lbm_step) is, for every node, in this order:
+ *   pull streaming with halfway bounce-back walls       Eq. (1) and the streaming text
+ *   moments rho_r, rho_b, j, colour field phi            Eq. (3)
+ *   isotropic colour gradient G = 3 sum_i w_i c_i phi(x+c_i)   stencil form of Eq. (10)
+ *   force F = body + Kolmogorov + near-contact            Eq. (11)
+ *   BGK of the total population + EDM source              Eqs. (1), (2), (5)-(9)
+ *   colour-gradient perturbation (surface tension sigma)  generalised perturbation
+ *   recolouring of the two species (segregation beta)     Latva-Kokko & Rothman
+ * The last two steps are not written in the paper; the library implements the
+ * published colour-gradient method it cites, as documented below.
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice nx*ny*nz nodes, node index n = (z*ny + y)*nx + x (x fastest).
+ *  - Fields passed in or out are float64 arrays: scalar fields [N], vector fields
+ *    [3][N] (component-major). Host pointers when on_device == 0; CUDA device
+ *    pointers (e.g. torch.Tensor.data_ptr()) on the same device when on_device == 1.
+ *    The caller owns every array; the library copies what it needs.
+ *  - Work is queued on the context's CUDA stream (params.cuda_stream, NULL = the
+ *    legacy default stream). Calls that return data to the host synchronise that
+ *    stream; lbm_step does not.
+ *  - Errors are reported by return code, never by exceptions or aborts.
+ *    lbm_last_error() gives a message. After LBM_ECUDA the context should be
+ *    destroyed; after any other error it stays usable.
+ *  - A context is not thread-safe: use one context per host thread and stream.
+ *  - All arithmetic of the step is FP32; FP64 is used only for the set/get
+ *    conversions and the conservation / Laplace reductions.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,   /* bad argument or parameter; nothing was changed          */
+    LBM_ENOMEM = -2,   /* device or host allocation failed                         */
+    LBM_ECUDA = -3,    /* a CUDA call failed; destroy the context                  */
+    LBM_ESTATE = -4,   /* call out of order (e.g. lbm_step before lbm_set_fields)  */
+    LBM_ETIMEOUT = -5  /* a bounded device-side wait gave up                       */
+} lbm_status;
+
+/* Storage of the populations in device memory. Arithmetic is FP32 in all cases.
+ * FP16/BF16 store the deviation f_i^k - w_i rho0/2 rounded to nearest even.    */
+typedef enum {
+    LBM_STORE_FP32 = 0,
+    LBM_STORE_FP16_DEV = 1,
+    LBM_STORE_BF16_DEV = 2
+} lbm_storage;
+
+typedef struct {
+    int nx, ny, nz;          /* lattice size, each >= 1                                  */
+    int wall_y, wall_z;      /* 1 = halfway bounce-back walls at y (z) = -1/2 and n-1/2;
+                                0 = periodic. x is always periodic.                      */
+    double tau_r, tau_b;     /* relaxation times (> 1/2) of the red and blue species;
+                                nu_k = (tau_k - 1/2)/3, Eq. (4). The mixture relaxes at
+                                omega = 2c_s^2/(2 nu + c_s^2) with 1/nu the density-
+                                weighted mean of 1/nu_k, Eqs. (7)-(8) (Eq. (7) read with
+                                a plus sign, consistent with Eq. (4)).                   */
+    double sigma;            /* surface tension; perturbation amplitude A = 9 omega sigma/2 */
+    double beta;             /* recolouring segregation parameter in [0, 1]               */
+    double A_nc;             /* near-contact amplitude A of Eq. (11); 0 = off             */
+    double h_min;            /* plateau length of A_h[h] (lattice units), e.g. 3          */
+    double h_cut;            /* cutoff of A_h[h]; <= 0 means 2*h_min                      */
+    double g[3];             /* uniform body-force density                                */
+    double kolmogorov_amp;   /* adds F_x = amp * sin(2 pi y / ny); 0 = off                */
+    double rho0;             /* reference density of the FP16/BF16 deviation storage (1)  */
+    int storage;             /* lbm_storage                                               */
+    void* cuda_stream;       /* cudaStream_t to run on, or NULL                           */
+} lbm_params;
+
+/* Number of directions and the velocity set used by lbm_get_pops/lbm_set_pops:
+ * c[i] for i = 0..18, lexicographic in (c_z, c_y, c_x); the opposite of i is 18-i
+ * and the rest velocity is i = 9. Writes 57 ints (c_x, c_y, c_z per direction).  */
+#define LBM_Q 19
+void lbm_velocity_set(int c[LBM_Q * 3]);
+
+/* Allocates a context and all its device memory (two population copies, two
+ * colour-field buffers). Returns LBM_EINVAL for nx/ny/nz < 1, tau <= 1/2,
+ * beta outside [0,1], negative A_nc or h_min, unknown storage. *out is set to
+ * NULL on failure.                                                              */
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out);
+
+/* Initial state: f_i^k = f_i^eq(rho_k, u) of Eq. (2) per species, with u the
+ * common velocity ([3][N], NULL = 0); both colour-field buffers are set to
+ * (rho_r - rho_b)/(rho_r + rho_b). rho_r + rho_b must be > 0 at every node.
+ * Resets the step counter.                                                     */
+lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho_r, const double* rho_b,
+                          const double* u, int on_device);
+
+/* Pinning sites ([N] bytes, nonzero = pin; NULL clears): a pin acts as another
+ * interface on the nodes whose previous-step colour gradient is >= 1e-3 and that
+ * lie within the cube of half-width ceil(h_cut) <= 9 around it, adding A_h[d] to
+ * their near-contact strength (d = distance to the nearest pin).               */
+lbm_status lbm_set_pin_mask(lbm_ctx* ctx, const uint8_t* mask, int on_device);
+
+/* Advances n >= 0 time steps (asynchronous on the context stream). With A_nc > 0
+ * each step first measures the near-contact strength A_h[h] of every node on the
+ * colour field of the previous step (film thickness h along minus its gradient,
+ * lag 1), then runs the fused step, where F_rep = A_h G with the current G.     */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* As lbm_step, but synchronising after every step and timing its kernels with CUDA
+ * events on the context stream: out_ms[0] += time of the near-contact pass (0 when
+ * A_nc == 0), out_ms[1] += time of the fused step kernel, summed over the n steps.
+ * For measurement; it serialises the host with the device.                      */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[2]);
+
+/* Kernel launches one lbm_step makes per time step (1, or 2 when A_nc > 0).      */
+int lbm_launches_per_step(const lbm_ctx* ctx);
+
+/* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the
+ * physical velocity u = (j + F/2)/rho of the EDM scheme, [3][N]. Before the first
+ * step, the fields that were set. Synchronises the stream.                      */
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u,
+                          double* phi, int on_device);
+
+/* Raw populations as float64 [19][N] per species, in the order of
+ * lbm_velocity_set, plus the colour field of the previous step (lag buffer, [N];
+ * may be NULL). get synchronises; set replaces the state (step counter kept).   */
+lbm_status lbm_get_pops(lbm_ctx* ctx, double* f_r, double* f_b, double* phi_lag,
+                        int on_device);
+lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f_r, const double* f_b,
+                        const double* phi_lag, int on_device);
+
+/* FP64 conserved totals of the current state, summed on the device in a fixed
+ * order: out = {sum f^r, sum f^b, P_x, P_y, P_z, steps, 0, 0}, P = sum_i c_i f_i.
+ * Synchronises the stream.                                                      */
+lbm_status lbm_observables(lbm_ctx* ctx, double out[8]);
+
+/* Laplace-law measurement of a static droplet centred at c (FP64 on the device):
+ * V = sum (1+phi)/2, R_eff = (3V/4pi)^(1/3), p = rho/3, p_in = mean p over
+ * r < R_eff-3, p_out = mean p over r > R_eff+5 (minimum image on periodic axes).
+ * out = {p_in - p_out, R_eff, p_in, p_out, V}. Synchronises the stream.         */
+lbm_status lbm_laplace(lbm_ctx* ctx, const double centre[3], double out[5]);
+
+/* Checkpoint: lbm_state_bytes() bytes hold the populations in their storage
+ * format, both colour-field buffers and the step counter. Restoring into a
+ * context with the same parameters continues bitwise identically.              */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf);
+
+/* Blocks until the context's queued work is done.                               */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Bytes of device memory held by a context with these parameters (admission).  */
+size_t lbm_footprint_bytes(const lbm_params* p);
+
+/* Number of steps taken since the last lbm_set_fields.                          */
+long long lbm_steps_taken(const lbm_ctx* ctx);
+
+/* Releases the context and its device memory. NULL is a no-op.                  */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failed call on this context (or of lbm_create when ctx is
+ * NULL). Valid until the next call on the same context.                          */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,913 @@
+// lbm_api.cu -- C-ABI of liblbm.so (declared in include/lbm.h): context and device
+// memory management, field set/get conversions, FP64 reductions and the launch of
+// the fused step kernel (lbm_step.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+cudaError_t launch_step(const StepParams& p, int storage, int grid, cudaStream_t s);
+cudaError_t launch_nc(const StepParams& p, int num_sms, cudaStream_t s);
+int step_tile_x();
+int step_tile_y();
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p{};
+    size_t N = 0;
+    size_t elem = 4;            // bytes per stored population
+    void* f[2] = {nullptr, nullptr};
+    float* phi[2] = {nullptr, nullptr};
+    float* fx_row = nullptr;
+    uint8_t* pin_d2 = nullptr;
+    uint8_t* pin_mask = nullptr;
+    float* ah = nullptr;        // near-contact strength per node (A_nc > 0)
+    int* cand[2] = {nullptr, nullptr};  // candidate lists (ping-pong) and counters
+    int* cand_count = nullptr;          // [2]
+    int cw = 0;                 // list the next step kernel writes
+    bool nc_scan = true;        // next near-contact pass must scan every node
+    double* stage = nullptr;    // device FP64 staging, 6N doubles
+    double* red = nullptr;      // reduction partials
+    double* red_host = nullptr; // pinned host copy of reduction results
+    int red_blocks = 0;
+    int cur = 0;                // population copy holding the current state
+    int pc = 0;                 // phi buffer of the last step (the other one = its lag)
+    long long steps = 0;
+    bool fields_set = false;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int grid = 1;               // CTAs of the step kernel (one per SM at most)
+    int* err_word = nullptr;    // device error word (bounded waits)
+    StepParams sp{};
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+    if (c) c->err = msg; else g_create_err = msg;
+    return s;
+}
+static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(ctx, call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+    } while (0)
+
+// ---------------------------------------------------------------- aux kernels
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline size_t nidx(const lbm_params& p, int x, int y, int z) {
+    return ((size_t)z * p.ny + y) * p.nx + x;
+}
+
+// f_i^k = f_i^eq(rho_k, u), Eq. (2); both colour-field buffers get phi.
+template <class St>
+__global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
+                                   const double* rho_r, const double* rho_b, const double* u,
+                                   size_t N, float ref_half) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const double rr = rho_r[n], rb = rho_b[n];
+        double ux = 0, uy = 0, uz = 0;
+        if (u) {
+            ux = u[n];
+            uy = u[N + n];
+            uz = u[2 * N + n];
+        }
+        const double usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+            const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+            const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            const float ref = wgt(i) * ref_half;
+            St::store(f, (size_t)i * N + n, (float)(rr * e), ref);
+            St::store(f, (size_t)(Q + i) * N + n, (float)(rb * e), ref);
+        }
+        const float ph = (float)((rr - rb) / (rr + rb));
+        phi0[n] = ph;
+        phi1[n] = ph;
+    }
+}
+
+template <class St>
+__device__ inline float ldpop(const typename St::T* f, size_t idx, int i, float ref_half) {
+    return St::load(f, idx, wgt(i) * ref_half);
+}
+
+// Fields of the current state. rho_k = sum_i f_i^k of the stored (post-collision)
+// populations, which equals the post-stream density of the last step; the stored
+// momentum is j + F, so u = (sum_i c_i f_i - F/2)/rho; F is re-evaluated from the
+// two colour-field buffers exactly as the step did (have_force = 0 before a step).
+template <class St>
+__global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int have_force,
+                                     const float* phi_now, double* rho_r, double* rho_b,
+                                     double* u, double* phi) {
+    const size_t N = sp.N;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float a = ldpop<St>(f, (size_t)i * N + n, i, sp.ref_half);
+            const float b = ldpop<St>(f, (size_t)(Q + i) * N + n, i, sp.ref_half);
+            rr += a;
+            rb += b;
+            jx += cx(i) * (a + b);
+            jy += cy(i) * (a + b);
+            jz += cz(i) * (a + b);
+        }
+        const int x = (int)(n % sp.nx), y = (int)((n / sp.nx) % sp.ny), z = (int)(n / ((size_t)sp.nx * sp.ny));
+        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+        if (have_force) {
+            Fx = sp.fx_row[y];
+            Fy = sp.gy;
+            Fz = sp.gz;
+            if (sp.A_nc > 0.0f) {
+                // A_h of the last step (re-measured on its lag field before this kernel)
+                // times the gradient of the last step's colour field
+                float Gx, Gy, Gz;
+                gradient_global(sp, phi_now, x, y, z, Gx, Gy, Gz);
+                const float ah = sp.ah[n];
+                Fx += ah * Gx;
+                Fy += ah * Gy;
+                Fz += ah * Gz;
+            }
+        }
+        const double rho = (double)rr + (double)rb;
+        if (rho_r) rho_r[n] = rr;
+        if (rho_b) rho_b[n] = rb;
+        if (u) {
+            u[n] = ((double)jx - 0.5 * Fx) / rho;
+            u[N + n] = ((double)jy - 0.5 * Fy) / rho;
+            u[2 * N + n] = ((double)jz - 0.5 * Fz) / rho;
+        }
+        if (phi) phi[n] = phi_now[n];
+    }
+}
+
+template <class St>
+__global__ void pops_to_f64_kernel(const typename St::T* f, size_t N, float ref_half, double* fr,
+                                   double* fb) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * N + n, i, ref_half);
+            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+        }
+    }
+}
+
+template <class St>
+__global__ void f64_to_pops_kernel(typename St::T* f, size_t N, float ref_half, const double* fr,
+                                   const double* fb) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float ref = wgt(i) * ref_half;
+            St::store(f, (size_t)i * N + n, (float)fr[(size_t)i * N + n], ref);
+            St::store(f, (size_t)(Q + i) * N + n, (float)fb[(size_t)i * N + n], ref);
+        }
+    }
+}
+
+__global__ void f64_to_f32_kernel(float* dst, const double* src, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (float)src[k];
+}
+__global__ void f32_to_f64_kernel(double* dst, const float* src, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (double)src[k];
+}
+
+// Block-level FP64 sum of NV values per thread into out[blockIdx.x * NV + v]:
+// warp shuffles, then the warps of the block in index order (deterministic).
+template <int NV>
+__device__ inline void block_sum(double (&v)[NV], double* out) {
+    __shared__ double sh[kThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sh[w][threadIdx.x];
+        out[blockIdx.x * NV + threadIdx.x] = s;
+    }
+}
+
+// Second pass: one block sums the per-block partials in index order.
+template <int NV>
+__global__ void finish_sum_kernel(const double* part, int nblocks, double* out) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += part[b * NV + k];
+    block_sum<NV>(v, out);
+}
+
+// Conserved totals (FP64): sum f^r, sum f^b, P.
+template <class St>
+__global__ void totals_kernel(const typename St::T* f, size_t N, float ref_half, double* part) {
+    double v[5] = {0, 0, 0, 0, 0};
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double a = ldpop<St>(f, (size_t)i * N + n, i, ref_half);
+            const double b = ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+            v[0] += a;
+            v[1] += b;
+            v[2] += cx(i) * (a + b);
+            v[3] += cy(i) * (a + b);
+            v[4] += cz(i) * (a + b);
+        }
+    }
+    block_sum<5>(v, part);
+}
+
+// Laplace measurement, pass 1: V = sum (1 + phi)/2 with phi from the populations.
+template <class St>
+__global__ void volume_kernel(const typename St::T* f, size_t N, float ref_half, double* part) {
+    double v[1] = {0};
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        double rr = 0, rb = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            rr += ldpop<St>(f, (size_t)i * N + n, i, ref_half);
+            rb += ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+        }
+        v[0] += 0.5 * (1.0 + (rr - rb) / (rr + rb));
+    }
+    block_sum<1>(v, part);
+}
+
+// Pass 2: pressure sums and node counts inside r < R-3 and outside r > R+5.
+template <class St>
+__global__ void pressure_kernel(const typename St::T* f, lbm_params p, size_t N, float ref_half,
+                                double c0, double c1, double c2, double R, double* part) {
+    double v[4] = {0, 0, 0, 0};
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((size_t)p.nx * p.ny));
+        double d[3] = {x - c0, y - c1, z - c2};
+        const int nn[3] = {p.nx, p.ny, p.nz};
+        const int per[3] = {1, !p.wall_y, !p.wall_z};
+        for (int a = 0; a < 3; ++a)
+            if (per[a]) {
+                if (d[a] > 0.5 * nn[a]) d[a] -= nn[a];
+                if (d[a] < -0.5 * nn[a]) d[a] += nn[a];
+            }
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (r < R - 3.0 || r > R + 5.0) {
+            double rho = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                rho += (double)ldpop<St>(f, (size_t)i * N + n, i, ref_half) +
+                       (double)ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+            if (r < R - 3.0) {
+                v[0] += rho / 3.0;
+                v[1] += 1;
+            } else {
+                v[2] += rho / 3.0;
+                v[3] += 1;
+            }
+        }
+    }
+    block_sum<4>(v, part);
+}
+
+// Pin distance field, three separable min-plus passes over the cube of
+// half-width r: d2 = min over pins in the cube of dx^2 + dy^2 + dz^2 (255 = none).
+// Pass along one axis; src codes 255 as "no pin in range".
+__global__ void pin_pass_kernel(const uint8_t* src, uint8_t* dst, lbm_params p, int axis, int r,
+                                int first) {
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        int c[3] = {(int)(n % p.nx), (int)((n / p.nx) % p.ny), (int)(n / ((size_t)p.nx * p.ny))};
+        const int nn[3] = {p.nx, p.ny, p.nz};
+        const int walled = axis == 1 ? p.wall_y : (axis == 2 ? p.wall_z : 0);
+        int best = 255;
+        for (int d = -r; d <= r; ++d) {
+            int q[3] = {c[0], c[1], c[2]};
+            q[axis] += d;
+            if (walled && (q[axis] < 0 || q[axis] >= nn[axis])) continue;
+            q[axis] = wrapi(q[axis], nn[axis]);
+            const uint8_t s = src[((size_t)q[2] * p.ny + q[1]) * p.nx + q[0]];
+            int val;
+            if (first) val = s ? 0 : 255;
+            else val = s;
+            if (val == 255) continue;
+            val += d * d;
+            if (val < best) best = val;
+        }
+        dst[n] = (uint8_t)best;
+    }
+}
+
+int grid_for(size_t n, int num_sms) {
+    size_t b = (n + kThreads - 1) / kThreads;
+    size_t cap = (size_t)num_sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- helpers
+static size_t elem_bytes(int storage) { return storage == 0 ? 4 : 2; }
+
+static lbm_status validate(const lbm_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return LBM_EINVAL; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_EINVAL; }
+    if ((double)p->nx * p->ny * p->nz > 2147483647.0) { why = "lattice larger than 2^31-1 nodes"; return LBM_EINVAL; }
+    if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) { why = "tau_r and tau_b must be > 1/2"; return LBM_EINVAL; }
+    if (!(p->beta >= 0.0 && p->beta <= 1.0)) { why = "beta must be in [0, 1]"; return LBM_EINVAL; }
+    if (!(p->sigma >= 0.0)) { why = "sigma must be >= 0"; return LBM_EINVAL; }
+    if (!(p->A_nc >= 0.0) || !(p->h_min >= 0.0)) { why = "A_nc and h_min must be >= 0"; return LBM_EINVAL; }
+    if (p->A_nc > 0.0 && !(p->h_min > 0.0)) { why = "h_min must be > 0 when A_nc > 0"; return LBM_EINVAL; }
+    double hcut = p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min;
+    if (p->A_nc > 0.0 && !(hcut > p->h_min)) { why = "h_cut must exceed h_min"; return LBM_EINVAL; }
+    if (p->A_nc > 0.0 && hcut > 64.0) { why = "h_cut must be <= 64"; return LBM_EINVAL; }
+    if (p->storage < 0 || p->storage > 2) { why = "unknown storage"; return LBM_EINVAL; }
+    if ((p->storage != 0) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
+    if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
+    if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
+    return LBM_OK;
+}
+
+extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
+    if (!p) return 0;
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    return 2 * 2 * Q * N * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
+}
+
+extern "C" void lbm_velocity_set(int c[LBM_Q * 3]) {
+    for (int i = 0; i < Q; ++i) {
+        c[3 * i + 0] = cx(i);
+        c[3 * i + 1] = cy(i);
+        c[3 * i + 2] = cz(i);
+    }
+}
+
+static void fill_step_params(lbm_ctx* c) {
+    const lbm_params& p = c->p;
+    StepParams& s = c->sp;
+    s.fx_row = c->fx_row;
+    s.pin_d2 = c->pin_d2;
+    s.gy = (float)p.g[1];
+    s.gz = (float)p.g[2];
+    s.nx = p.nx;
+    s.ny = p.ny;
+    s.nz = p.nz;
+    s.N = c->N;
+    s.wall_y = p.wall_y ? 1 : 0;
+    s.wall_z = p.wall_z ? 1 : 0;
+    s.var_tau = p.tau_r != p.tau_b;
+    s.omega0 = (float)(1.0 / p.tau_r);
+    s.inv_nu_r = (float)(3.0 / (p.tau_r - 0.5));
+    s.inv_nu_b = (float)(3.0 / (p.tau_b - 0.5));
+    s.sigma = (float)p.sigma;
+    s.beta = (float)p.beta;
+    const double hcut = p.h_cut > 0 ? p.h_cut : 2.0 * p.h_min;
+    s.A_nc = (float)p.A_nc;
+    s.h_min = (float)p.h_min;
+    s.h_cut = (float)hcut;
+    const double b3 = p.A_nc > 0 ? std::pow(p.h_min / hcut, 3.0) : 0.0;
+    s.ah_b3 = (float)b3;
+    s.ah_inv = (float)(1.0 / (1.0 - b3));
+    s.nsamp = (int)std::floor(2.0 * (hcut + 3.0)) + 1;
+    s.ref_half = p.storage == 0 ? 0.0f : (float)(0.5 * p.rho0);
+    const int tx = step_tile_x(), ty = step_tile_y();
+    s.tiles_x = (p.nx + tx - 1) / tx;
+    s.tiles_y = (p.ny + ty - 1) / ty;
+    s.bulk_ok = (p.nx % 32 == 0) ? 1 : 0;
+    s.err = c->err_word;
+    s.ah = c->ah;
+    // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
+    // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
+    // pipeline fill), the cost of a part-major launch.
+    const long long tiles = (long long)s.tiles_x * s.tiles_y;
+    const int S = c->num_sms > 0 ? c->num_sms : 1;
+    int best_k = 1;
+    double best = 1e300;
+    for (int k = 1; k <= p.nz && k <= 4096; ++k) {
+        const long long ctas = tiles * k;
+        const long long waves = (ctas + S - 1) / S;
+        const double cost = (double)waves * ((double)p.nz / k + 4.0);
+        if (cost < best * 0.999) {
+            best = cost;
+            best_k = k;
+        }
+    }
+    s.zparts = best_k;
+    c->grid = (int)(tiles * best_k);
+}
+
+// The step kernel's bounded waits record a give-up in a device word; report it.
+static lbm_status check_err_word(lbm_ctx* c) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->err_word, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h) return fail(c, LBM_ETIMEOUT, "a bounded wait in the step kernel gave up");
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- API
+extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (validate(p, why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->N = (size_t)p->nx * p->ny * p->nz;
+    c->elem = elem_bytes(p->storage);
+    c->stream = (cudaStream_t)p->cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, LBM_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    const size_t pop_bytes = 2 * Q * c->N * c->elem;
+    auto alloc = [&](void** ptr, size_t bytes) -> bool {
+        return cudaMalloc(ptr, bytes) == cudaSuccess;
+    };
+    bool ok = alloc(&c->f[0], pop_bytes) && alloc(&c->f[1], pop_bytes) &&
+              alloc((void**)&c->phi[0], c->N * sizeof(float)) &&
+              alloc((void**)&c->phi[1], c->N * sizeof(float)) &&
+              alloc((void**)&c->fx_row, p->ny * sizeof(float)) &&
+              alloc((void**)&c->err_word, sizeof(int)) &&
+              (p->A_nc > 0.0 ? alloc((void**)&c->ah, c->N * sizeof(float)) &&
+                                   alloc((void**)&c->cand[0], c->N * sizeof(int)) &&
+                                   alloc((void**)&c->cand[1], c->N * sizeof(int)) &&
+                                   alloc((void**)&c->cand_count, 2 * sizeof(int))
+                               : true);
+    c->red_blocks = c->num_sms * 8;
+    ok = ok && alloc((void**)&c->red, (size_t)(c->red_blocks + 1) * 8 * sizeof(double));
+    ok = ok && cudaMallocHost((void**)&c->red_host, 8 * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ENOMEM, "device allocation failed");
+    }
+    // body force per row, evaluated in FP64 on the host
+    float* row = new (std::nothrow) float[p->ny];
+    if (!row) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    }
+    for (int y = 0; y < p->ny; ++y)
+        row[y] = (float)(p->g[0] + p->kolmogorov_amp * std::sin(2.0 * M_PI * (double)y / (double)p->ny));
+    e = cudaMemcpy(c->fx_row, row, p->ny * sizeof(float), cudaMemcpyHostToDevice);
+    delete[] row;
+    if (e == cudaSuccess) e = cudaMemset(c->err_word, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    fill_step_params(c);
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->phi[0]);
+    cudaFree(c->phi[1]);
+    cudaFree(c->fx_row);
+    cudaFree(c->pin_d2);
+    cudaFree(c->pin_mask);
+    cudaFree(c->stage);
+    cudaFree(c->red);
+    cudaFree(c->err_word);
+    cudaFree(c->ah);
+    cudaFree(c->cand[0]);
+    cudaFree(c->cand[1]);
+    cudaFree(c->cand_count);
+    if (c->red_host) cudaFreeHost(c->red_host);
+    delete c;
+}
+
+extern "C" const char* lbm_last_error(const lbm_ctx* c) {
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+static lbm_status ensure_stage(lbm_ctx* c) {
+    if (c->stage) return LBM_OK;
+    if (cudaMalloc((void**)&c->stage, 2 * Q * c->N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LBM_ENOMEM, "staging allocation failed");
+    }
+    return LBM_OK;
+}
+
+template <class F>
+static void dispatch(int storage, F&& fn) {
+    if (storage == 0) fn(StoreF32{});
+    else if (storage == 1) fn(StoreF16{});
+    else fn(StoreBF16{});
+}
+
+extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const double* rho_b,
+                                     const double* u, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!rho_r || !rho_b) return fail(c, LBM_EINVAL, "rho_r and rho_b are required");
+    const size_t N = c->N;
+    const double *dr = rho_r, *db = rho_b, *du = u;
+    if (!on_device) {
+        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        CK(c, cudaMemcpyAsync(c->stage, rho_r, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->stage + N, rho_b, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        dr = c->stage;
+        db = c->stage + N;
+        if (u) {
+            CK(c, cudaMemcpyAsync(c->stage + 2 * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            du = c->stage + 2 * N;
+        }
+    }
+    const int grid = grid_for(N, c->num_sms);
+    c->cur = 0;
+    c->pc = 0;
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        init_fields_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (typename St::T*)c->f[0], c->phi[0], c->phi[1], dr, db, du, N, c->sp.ref_half);
+    });
+    CK(c, cudaGetLastError());
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed
+    c->steps = 0;
+    c->fields_set = true;
+    c->nc_scan = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_pin_mask(lbm_ctx* c, const uint8_t* mask, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!mask) {
+        cudaFree(c->pin_d2);
+        c->pin_d2 = nullptr;
+        fill_step_params(c);
+        return LBM_OK;
+    }
+    const size_t N = c->N;
+    if (!c->pin_d2) {
+        if (cudaMalloc((void**)&c->pin_d2, N) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LBM_ENOMEM, "pin allocation failed");
+        }
+    }
+    if (!c->pin_mask) {
+        if (cudaMalloc((void**)&c->pin_mask, N) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LBM_ENOMEM, "pin allocation failed");
+        }
+    }
+    CK(c, cudaMemcpyAsync(c->pin_mask, mask, N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    const double hcut = c->p.h_cut > 0 ? c->p.h_cut : 2.0 * c->p.h_min;
+    const int r = (int)std::ceil(hcut);
+    if (3 * r * r >= 255) return fail(c, LBM_EINVAL, "h_cut too large for pinning sites (<= 9)");
+    const int grid = grid_for(N, c->num_sms);
+    // x pass: mask -> d2 ; y pass: d2 -> mask buffer ; z pass: mask buffer -> d2
+    pin_pass_kernel<<<grid, kThreads, 0, c->stream>>>(c->pin_mask, c->pin_d2, c->p, 0, r, 1);
+    pin_pass_kernel<<<grid, kThreads, 0, c->stream>>>(c->pin_d2, c->pin_mask, c->p, 1, r, 0);
+    pin_pass_kernel<<<grid, kThreads, 0, c->stream>>>(c->pin_mask, c->pin_d2, c->p, 2, r, 0);
+    CK(c, cudaGetLastError());
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->pin_mask);
+    c->pin_mask = nullptr;
+    fill_step_params(c);
+    c->nc_scan = true;
+    return LBM_OK;
+}
+
+// Launches of one time step: the near-contact pass (A_nc > 0) and the step kernel.
+// Near-contact bookkeeping: the step kernel of step t lists candidates in cand[cw]
+// and consumes (zeroes) the A_h entries it reads; the pass of step t+1 reads that
+// list and writes A_h only at those nodes. After any change of state the pass scans
+// every node once instead. Events (optional) bracket the two launches.
+static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+    StepParams s = c->sp;
+    s.fin = c->f[c->cur];
+    s.fout = c->f[1 - c->cur];
+    s.phi_lag = c->phi[c->pc];
+    s.phi_out = c->phi[1 - c->pc];
+    cudaError_t e = cudaSuccess;
+    if (e0) e = cudaEventRecord(e0, c->stream);
+    if (c->p.A_nc > 0.0) {
+        if (e == cudaSuccess) {
+            if (c->nc_scan) {
+                s.nc_list = nullptr;
+                s.nc_count = nullptr;
+            } else {
+                s.nc_list = c->cand[1 - c->cw];
+                s.nc_count = c->cand_count + (1 - c->cw);
+            }
+            e = launch_nc(s, c->num_sms, c->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->cand_count + c->cw, 0, sizeof(int), c->stream);
+        s.cand = c->cand[c->cw];
+        s.cand_count = c->cand_count + c->cw;
+    }
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = launch_step(s, c->p.storage, c->grid, c->stream);
+    if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
+    if (e != cudaSuccess) return e;
+    c->nc_scan = false;
+    c->cw ^= 1;
+    c->cur ^= 1;
+    c->pc ^= 1;
+    c->steps++;
+    return cudaSuccess;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
+    if (!c) return LBM_EINVAL;
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    for (int t = 0; t < n; ++t) {
+        cudaError_t e = launch_one_step(c, nullptr, nullptr, nullptr);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[2]) {
+    if (!c || !out_ms) return LBM_EINVAL;
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    out_ms[0] = out_ms[1] = 0.0;
+    cudaEvent_t ev[3];
+    for (int k = 0; k < 3; ++k) CK(c, cudaEventCreate(&ev[k]));
+    lbm_status st = LBM_OK;
+    for (int t = 0; t < n && st == LBM_OK; ++t) {
+        cudaError_t e = launch_one_step(c, ev[0], ev[1], ev[2]);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        float a = 0.f, b = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "timed step");
+            break;
+        }
+        out_ms[0] += a;
+        out_ms[1] += b;
+    }
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    if (st != LBM_OK) return st;
+    return check_err_word(c);
+}
+
+extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, double* u,
+                                     double* phi, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    const size_t N = c->N;
+    double *dr = rho_r, *db = rho_b, *du = u, *dp = phi;
+    if (!on_device) {
+        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        dr = rho_r ? c->stage : nullptr;
+        db = rho_b ? c->stage + N : nullptr;
+        du = u ? c->stage + 2 * N : nullptr;
+        dp = phi ? c->stage + 5 * N : nullptr;
+    }
+    StepParams s = c->sp;
+    s.phi_lag = c->phi[1 - c->pc];   // the lag field the last step's rays read
+    const int grid = grid_for(N, c->num_sms);
+    if (c->steps > 0 && c->p.A_nc > 0.0) {
+        // A_h of the last step, re-measured on its lag field in scan mode into scratch
+        // space after the staged fields (the live A_h buffer is left untouched)
+        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
+        s.nc_list = nullptr;
+        s.nc_count = nullptr;
+        CK(c, launch_nc(s, c->num_sms, c->stream));
+    }
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        export_fields_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (const typename St::T*)c->f[c->cur], s, c->steps > 0 ? 1 : 0, c->phi[c->pc], dr, db,
+            du, dp);
+    });
+    CK(c, cudaGetLastError());
+    if (!on_device) {
+        if (rho_r) CK(c, cudaMemcpyAsync(rho_r, dr, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (rho_b) CK(c, cudaMemcpyAsync(rho_b, db, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (u) CK(c, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (phi) CK(c, cudaMemcpyAsync(phi, dp, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double* phi_lag,
+                                   int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (!f_r || !f_b) return fail(c, LBM_EINVAL, "f_r and f_b are required");
+    const size_t N = c->N;
+    double *dr = f_r, *db = f_b;
+    if (!on_device) {
+        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        dr = c->stage;
+        db = c->stage + Q * N;
+    }
+    const int grid = grid_for(N, c->num_sms);
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        pops_to_f64_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (const typename St::T*)c->f[c->cur], N, c->sp.ref_half, dr, db);
+    });
+    CK(c, cudaGetLastError());
+    if (!on_device) {
+        CK(c, cudaMemcpyAsync(f_r, dr, Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(f_b, db, Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (phi_lag) {
+        // the lag buffer of the next step is the colour field of the last step
+        if (on_device) {
+            f32_to_f64_kernel<<<grid, kThreads, 0, c->stream>>>(phi_lag, c->phi[c->pc], N);
+            CK(c, cudaGetLastError());
+        } else {
+            CK(c, cudaStreamSynchronize(c->stream));
+            f32_to_f64_kernel<<<grid, kThreads, 0, c->stream>>>(c->stage, c->phi[c->pc], N);
+            CK(c, cudaGetLastError());
+            CK(c, cudaMemcpyAsync(phi_lag, c->stage, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* f_b,
+                                   const double* phi_lag, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!f_r || !f_b) return fail(c, LBM_EINVAL, "f_r and f_b are required");
+    const size_t N = c->N;
+    const double *dr = f_r, *db = f_b;
+    if (!on_device) {
+        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        CK(c, cudaMemcpyAsync(c->stage, f_r, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->stage + Q * N, f_b, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        dr = c->stage;
+        db = c->stage + Q * N;
+    }
+    const int grid = grid_for(N, c->num_sms);
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        f64_to_pops_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (typename St::T*)c->f[c->cur], N, c->sp.ref_half, dr, db);
+    });
+    CK(c, cudaGetLastError());
+    if (phi_lag) {
+        const double* src = phi_lag;
+        if (!on_device) {
+            CK(c, cudaStreamSynchronize(c->stream));
+            CK(c, cudaMemcpyAsync(c->stage, phi_lag, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            src = c->stage;
+        }
+        f64_to_f32_kernel<<<grid, kThreads, 0, c->stream>>>(c->phi[c->pc], src, N);
+        CK(c, cudaGetLastError());
+    }
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    c->fields_set = true;
+    c->nc_scan = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_observables(lbm_ctx* c, double out[8]) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    const int grid = c->red_blocks;
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        totals_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
+                                                            c->N, c->sp.ref_half, c->red);
+    });
+    finish_sum_kernel<5><<<1, kThreads, 0, c->stream>>>(c->red, grid, c->red + (size_t)grid * 8);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(c->red_host, c->red + (size_t)grid * 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 5; ++k) out[k] = c->red_host[k];
+    out[5] = (double)c->steps;
+    out[6] = out[7] = 0.0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out[5]) {
+    if (!c || !centre || !out) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    const int grid = c->red_blocks;
+    double* fin = c->red + (size_t)grid * 8;
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        volume_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
+                                                             c->N, c->sp.ref_half, c->red);
+    });
+    finish_sum_kernel<1><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(c->red_host, fin, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double V = c->red_host[0];
+    const double R = std::cbrt(3.0 * V / (4.0 * M_PI));
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        pressure_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (const typename St::T*)c->f[c->cur], c->p, c->N, c->sp.ref_half, centre[0], centre[1],
+            centre[2], R, c->red);
+    });
+    finish_sum_kernel<4><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(c->red_host, fin, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double* h = c->red_host;
+    const double pin = h[1] > 0 ? h[0] / h[1] : NAN, pout = h[3] > 0 ? h[2] / h[3] : NAN;
+    out[0] = pin - pout;
+    out[1] = R;
+    out[2] = pin;
+    out[3] = pout;
+    out[4] = V;
+    return LBM_OK;
+}
+
+extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
+    if (!c) return 0;
+    return 2 * Q * c->N * c->elem + 2 * c->N * sizeof(float) + sizeof(long long);
+}
+
+extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
+    if (!c || !host_buf) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    char* b = (char*)host_buf;
+    const size_t pb = 2 * Q * c->N * c->elem, fb = c->N * sizeof(float);
+    CK(c, cudaMemcpyAsync(b, c->f[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(b + pb, c->phi[c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(b + pb + fb, c->phi[1 - c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(b + pb + 2 * fb, &c->steps, sizeof(long long));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf) {
+    if (!c || !host_buf) return LBM_EINVAL;
+    const char* b = (const char*)host_buf;
+    const size_t pb = 2 * Q * c->N * c->elem, fb = c->N * sizeof(float);
+    c->cur = 0;
+    c->pc = 0;
+    CK(c, cudaMemcpyAsync(c->f[0], b, pb, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->phi[0], b + pb, fb, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->phi[1], b + pb + fb, fb, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(&c->steps, b + pb + 2 * fb, sizeof(long long));
+    c->fields_set = true;
+    c->nc_scan = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_err_word(c);
+}
+
+extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
+    if (!c) return 0;
+    return c->p.A_nc > 0.0 ? 2 : 1;
+}

@@ -1,0 +1,379 @@
+// lbm_device.cuh -- device-side building blocks of the GB300 colour-gradient LB step.
+//
+// D3Q19 velocity set, population storage formats, and the per-node pieces of one
+// time step (Succi et al., arXiv:2005.12764): pull streaming with halfway
+// bounce-back, moments (Eq. 3), near-contact force (Eq. 11), total-population BGK
+// with the EDM source (Eqs. 1, 2, 5-9), colour-gradient perturbation and
+// recolouring (the published colour-gradient method the paper cites).
+// All arithmetic is FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Velocity set ordered lexicographically in (c_z, c_y, c_x): directions 0-4 have
+// c_z = -1, 5-13 have c_z = 0 (9 is the rest velocity), 14-18 have c_z = +1. With
+// this order the opposite of direction i is 18 - i.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8 || i == 11 || i == 15) ? -1
+         : (i == 3 || i == 7 || i == 10 || i == 13 || i == 17) ? 1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 0 || i == 5 || i == 6 || i == 7 || i == 14) ? -1
+         : (i == 4 || i == 11 || i == 12 || i == 13 || i == 18) ? 1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) { return i <= 4 ? -1 : (i >= 14 ? 1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return 18 - i; }
+__host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+// Weights of the second-order equilibrium, Eq. (2): 1/3, 1/18, 1/36. The FP32
+// constants are the nearest single-precision values whose exact sum
+// w_0 + 6 w_f + 12 w_e is 1 (0x3EAAAAAC, 0x3D638E38, 0x3CE38E38 = w_f / 2), so that
+// sum_i w_i rho reproduces rho without a systematic per-step mass gain.
+__host__ __device__ constexpr float wgt(int i) {
+    return csq(i) == 0 ? 0.3333333730697632f : (csq(i) == 1 ? 0.0555555522441864f : 0.0277777761220932f);
+}
+// Isotropy constants B_i of the perturbation operator: -2/9, 1/54, 1/27.
+__host__ __device__ constexpr float bpert(int i) {
+    return csq(i) == 0 ? -2.0f / 9.0f : (csq(i) == 1 ? 1.0f / 54.0f : 1.0f / 27.0f);
+}
+// 1/|c_i| for the recolouring angle (0 for the rest velocity).
+__host__ __device__ constexpr float inv_clen(int i) {
+    return csq(i) == 0 ? 0.0f : (csq(i) == 1 ? 1.0f : 0.70710678118654752f);
+}
+
+// ---------------------------------------------------------------- storage formats
+// Populations live in [2 species][19 directions][N nodes] arrays. FP32 stores the
+// value; FP16/BF16 store the deviation f - ref with ref = w_i rho0 / 2, rounded to
+// nearest even.
+struct StoreF32 {
+    using T = float;
+    static constexpr int kind = 0;
+    __device__ __forceinline__ static float load(const T* p, size_t i, float) { return __ldg(p + i); }
+    __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
+    __device__ __forceinline__ static float cvt(T v, float) { return v; }
+};
+struct StoreF16 {
+    using T = __half;
+    static constexpr int kind = 1;
+    __device__ __forceinline__ static float load(const T* p, size_t i, float ref) {
+        return __half2float(__ldg(p + i)) + ref;
+    }
+    __device__ __forceinline__ static void store(T* p, size_t i, float v, float ref) {
+        p[i] = __float2half_rn(v - ref);
+    }
+    __device__ __forceinline__ static float cvt(T v, float ref) { return __half2float(v) + ref; }
+};
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    static constexpr int kind = 2;
+    __device__ __forceinline__ static float load(const T* p, size_t i, float ref) {
+        return __bfloat162float(__ldg(p + i)) + ref;
+    }
+    __device__ __forceinline__ static void store(T* p, size_t i, float v, float ref) {
+        p[i] = __float2bfloat16_rn(v - ref);
+    }
+    __device__ __forceinline__ static float cvt(T v, float ref) { return __bfloat162float(v) + ref; }
+};
+
+// ---------------------------------------------------------------- parameters
+struct StepParams {
+    const void* fin;        // populations at the start of the step (post-collision)
+    void* fout;             // populations after the step
+    const float* phi_lag;   // colour field of the previous step (near-contact rays)
+    float* phi_out;         // colour field of this step
+    const float* fx_row;    // [ny] x body force per row: g_x + Kolmogorov profile
+    const uint8_t* pin_d2;  // [N] squared distance to the nearest pin, 255 = none; or null
+    float* ah;              // [N] near-contact strength A_h of this step (A_nc > 0)
+    int* cand;              // candidate list written by the step kernel: nodes with |G| >= 0.9e-3
+    int* cand_count;        // its length (reset before the step kernel)
+    const int* nc_list;     // list the near-contact pass works on (null: scan every node)
+    const int* nc_count;
+    float gy, gz;
+    int nx, ny, nz;
+    size_t N;
+    int wall_y, wall_z;
+    int var_tau;            // 0: omega0 everywhere; 1: mixture rule per node
+    float omega0;
+    float inv_nu_r, inv_nu_b;
+    float sigma, beta;
+    float A_nc, h_min, h_cut, ah_b3, ah_inv;  // A_h tail: b3 = (h_min/h_cut)^3, inv = 1/(1-b3)
+    int nsamp;              // ray samples t = -1, -1/2, ..., h_cut + 2
+    float ref_half;         // rho0/2: deviation reference per species (FP16/BF16)
+    int tiles_x, tiles_y;   // xy tiles of the step kernel
+    int bulk_ok;            // rows can be staged with 16-byte bulk copies (nx % 32 == 0)
+    int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
+    int* err;               // device error word: 1 = a bounded wait gave up
+};
+
+// ---------------------------------------------------------------- near-contact force
+__device__ __forceinline__ float A_h(const StepParams& p, float h) {
+    if (h <= p.h_min) return p.A_nc;
+    if (h >= p.h_cut) return 0.0f;
+    float a = p.h_min / h;
+    return p.A_nc * (a * a * a - p.ah_b3) * p.ah_inv;
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+// Wrap of an index that lies within a few periods of [0, n): no integer division.
+__device__ __forceinline__ int wrap_near(int a, int n) {
+    while (a < 0) a += n;
+    while (a >= n) a -= n;
+    return a;
+}
+
+// Trilinear sample of the lagged colour field at node (x, y, z) + offset o; false if
+// the point lies outside the fluid along a walled axis. The cell and the weights come
+// from the offset alone (|o| is small), so the point is located to the precision of
+// o, not of x + o.
+__device__ __forceinline__ bool axis_cell(int base, float o, int n, bool walled, int& i0, int& i1,
+                                          float& fr) {
+    const float fl = floorf(o);
+    int b = base + (int)fl;
+    float f = o - fl;
+    if (walled) {
+        if (b < 0 || b > n - 1 || (b == n - 1 && f > 0.0f)) return false;
+        if (n == 1) {
+            i0 = i1 = 0;
+            fr = 0.0f;
+            return true;
+        }
+        if (b == n - 1) {
+            b = n - 2;
+            f = 1.0f;
+        }
+        i0 = b;
+        i1 = b + 1;
+        fr = f;
+        return true;
+    }
+    i0 = wrap_near(b, n);
+    i1 = i0 + 1 == n ? 0 : i0 + 1;
+    fr = f;
+    return true;
+}
+
+__device__ __forceinline__ bool sample_phi(const StepParams& p, int x, int y, int z, float ox,
+                                           float oy, float oz, float& v) {
+    int ix0, ix1, iy0, iy1, iz0, iz1;
+    float fx, fy, fz;
+    if (!axis_cell(x, ox, p.nx, false, ix0, ix1, fx)) return false;
+    if (!axis_cell(y, oy, p.ny, p.wall_y, iy0, iy1, fy)) return false;
+    if (!axis_cell(z, oz, p.nz, p.wall_z, iz0, iz1, fz)) return false;
+    const float* f = p.phi_lag;
+    const size_t r00 = ((size_t)iz0 * p.ny + iy0) * p.nx, r01 = ((size_t)iz0 * p.ny + iy1) * p.nx;
+    const size_t r10 = ((size_t)iz1 * p.ny + iy0) * p.nx, r11 = ((size_t)iz1 * p.ny + iy1) * p.nx;
+    const float c00 = (1.0f - fx) * __ldg(f + r00 + ix0) + fx * __ldg(f + r00 + ix1);
+    const float c01 = (1.0f - fx) * __ldg(f + r01 + ix0) + fx * __ldg(f + r01 + ix1);
+    const float c10 = (1.0f - fx) * __ldg(f + r10 + ix0) + fx * __ldg(f + r10 + ix1);
+    const float c11 = (1.0f - fx) * __ldg(f + r11 + ix0) + fx * __ldg(f + r11 + ix1);
+    const float c0 = (1.0f - fy) * c00 + fy * c01;
+    const float c1 = (1.0f - fy) * c10 + fy * c11;
+    v = (1.0f - fz) * c0 + fz * c1;
+    return true;
+}
+
+// Isotropic colour gradient of a node field at (x, y, z): 3 w_i = 1/6 (faces), 1/12
+// (edges); a neighbour beyond a wall takes the centre value.
+__device__ __forceinline__ void gradient_global(const StepParams& p, const float* phi, int x, int y,
+                                                int z, float& Gx, float& Gy, float& Gz) {
+    const size_t self = ((size_t)z * p.ny + y) * p.nx + x;
+    const float phic = __ldg(phi + self);
+    Gx = Gy = Gz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (i == 9) continue;
+        const int yy = y + cy(i), zz = z + cz(i);
+        const bool wall = (p.wall_y && (yy < 0 || yy >= p.ny)) || (p.wall_z && (zz < 0 || zz >= p.nz));
+        float v = phic;
+        if (!wall)
+            v = __ldg(phi + ((size_t)wrap_near(zz, p.nz) * p.ny + wrap_near(yy, p.ny)) * p.nx +
+                      wrap_near(x + cx(i), p.nx));
+        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
+        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
+        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
+        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+    }
+}
+
+// Near-contact strength A_h[h] at a node (Eq. 11, F = A_h[h] G with G the current
+// colour gradient). The film is measured on the colour field of the previous step:
+// with G' its gradient at the node (|G'| >= 1e-3, else 0) the ray runs along
+// n' = -G'/|G'|, sampled every half lattice unit from t = -1 to h_cut + 2. Samples
+// within 1e-5 of zero carry no sign; h is the distance between the first downward
+// zero crossing and the next upward one, each located by linear interpolation
+// between consecutive signed samples. Pinning sites add A_h[d], d the distance to
+// the nearest pin. Samples are fetched four at a time so their loads overlap.
+constexpr float kSignBand = 1e-5f;
+
+__device__ inline float nc_strength(const StepParams& p, size_t node, int x, int y, int z) {
+    float Gx, Gy, Gz;
+    gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
+    const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
+    if (!(gm >= 1e-3f)) return 0.0f;
+    const float inv = 1.0f / gm;
+    const float nx_ = -Gx * inv, ny_ = -Gy * inv, nz_ = -Gz * inv;
+    float t_a = 0.0f, v_a = 0.0f, t_d = 0.0f, t_u = 0.0f;
+    bool have_a = false, have_d = false, have_u = false, stop = false;
+    for (int s0 = 0; s0 < p.nsamp && !stop; s0 += 4) {
+        float val[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float t = -1.0f + 0.5f * (float)(s0 + k);
+            ok[k] = (s0 + k < p.nsamp) && sample_phi(p, x, y, z, t * nx_, t * ny_, t * nz_, val[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (stop) break;
+            if (!ok[k]) {
+                stop = true;
+                break;
+            }
+            const float t = -1.0f + 0.5f * (float)(s0 + k);
+            const float v = val[k];
+            if (fabsf(v) <= kSignBand) continue;
+            if (have_a) {
+                if (!have_d && v_a > 0.0f && v < 0.0f) {
+                    t_d = t_a + (t - t_a) * v_a / (v_a - v);
+                    have_d = true;
+                } else if (have_d && v_a < 0.0f && v > 0.0f) {
+                    t_u = t_a + (t - t_a) * v_a / (v_a - v);
+                    have_u = true;
+                    stop = true;
+                    break;
+                }
+            }
+            // any upward crossing after this sample gives h >= h_cut, where A_h vanishes
+            if (have_d && t - t_d >= p.h_cut) {
+                stop = true;
+                break;
+            }
+            t_a = t;
+            v_a = v;
+            have_a = true;
+        }
+    }
+    float ah = (have_d && have_u) ? A_h(p, t_u - t_d) : 0.0f;
+    if (p.pin_d2) {
+        const unsigned d2 = __ldg(p.pin_d2 + node);
+        if (d2 != 255u) ah += A_h(p, sqrtf((float)d2));
+    }
+    return ah;
+}
+
+// ---------------------------------------------------------------- collision
+// Index of the direction opposite to one of the 9 "positive" directions used in
+// the pair loop (directions 10..18 are opposite to 8..0).
+__host__ __device__ constexpr int pair_dir(int k) { return k < 9 ? k : k + 1; }
+
+// Pairwise (fixed-tree) sum of 19 values; every caller sums the same node's
+// populations in the same order, so a node's density is bitwise the same whichever
+// thread computes it.
+__device__ __forceinline__ float sum19(const float (&v)[Q]) {
+    float a = (v[0] + v[1]) + (v[2] + v[3]);
+    float b = (v[4] + v[5]) + (v[6] + v[7]);
+    float c = (v[8] + v[9]) + (v[10] + v[11]);
+    float d = (v[12] + v[13]) + (v[14] + v[15]);
+    float e = (v[16] + v[17]) + v[18];
+    return ((a + b) + (c + d)) + e;
+}
+
+// Threshold below which the colour gradient is treated as zero (no perturbation,
+// no recolouring segregation): above the rounding level (~1e-7) of the FP32
+// stencil on an O(1) colour field, so FP32 and FP64 evaluations agree on the branch.
+constexpr float kGradZero = 1e-6f;
+
+// Collision of one node from its post-stream total populations f[19], species
+// densities and colour gradient; writes the two new species populations through
+// the storage format. Order: BGK + EDM source (Eqs. 1, 2, 9) on the total
+// population, perturbation Delta_i = (A/2)|G|[w_i (c_i.G)^2/|G|^2 - B_i] with
+// A = 9 omega sigma / 2, recolouring f^r = (rho_r/rho) f + beta (rho_r rho_b/rho)
+// w_i cos(theta_i), f^b = (rho_b/rho) f - (same).
+// Evaluated in "small-number" form: with f'_i = w_i rho + s_i, the outputs are
+// f^r_i = w_i rho_r + (rho_r/rho) s_i + seg_i, so the large parts w_i rho_k are
+// rounded once and all other terms are O(|u|, |F|, |G|) corrections. Opposite
+// directions share their symmetric terms. The rest direction takes minus the sum of
+// the other perturbations, so the perturbation conserves mass exactly.
+template <class St>
+__device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
+                                              float rb, float Gx, float Gy, float Gz, float Fx,
+                                              float Fy, float Fz, typename St::T* out,
+                                              size_t node) {
+    const float rho = rr + rb;
+    const float inv_rho = 1.0f / rho;
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = pair_dir(k);
+        const float d = f[i] - f[opp(i)];
+        if (cx(i)) jx += cx(i) > 0 ? d : -d;
+        if (cy(i)) jy += cy(i) > 0 ? d : -d;
+        if (cz(i)) jz += cz(i) > 0 ? d : -d;
+    }
+    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    float omega = p.omega0;
+    if (p.var_tau) {
+        const float inv_nu = (rr * p.inv_nu_r + rb * p.inv_nu_b) * inv_rho;
+        omega = 1.0f / (3.0f / inv_nu + 0.5f);
+    }
+    const float om1 = 1.0f - omega;
+    const float dx = Fx * inv_rho, dy = Fy * inv_rho, dz = Fz * inv_rho;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float du_dot = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+    const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
+    const bool has_g = gm >= kGradZero;
+    const float inv_g = has_g ? 1.0f / gm : 0.0f;
+    const float half_A_g = has_g ? 0.5f * (4.5f * omega * p.sigma) * gm : 0.0f;
+    const float seg0 = has_g ? p.beta * rr * rb * inv_rho : 0.0f;
+    const float ar = rr * inv_rho, ab = rb * inv_rho;
+    const float ref = p.ref_half;
+    float pert_sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = pair_dir(k), o = opp(i);
+        const float w = wgt(i);
+        const float wr = w * rho;
+        const float a = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+        const float b = (float)cx(i) * dx + (float)cy(i) * dy + (float)cz(i) * dz;
+        const float es = wr * (4.5f * a * a - 1.5f * usq);
+        const float ea = wr * (3.0f * a);
+        const float ss = wr * (4.5f * b * (2.0f * a + b) - 1.5f * du_dot);
+        const float sa = wr * (3.0f * b);
+        const float ni = (f[i] - wr) - (es + ea);
+        const float no = (f[o] - wr) - (es - ea);
+        const float cg = (float)cx(i) * Gx + (float)cy(i) * Gy + (float)cz(i) * Gz;
+        const float cn = cg * inv_g;
+        const float dlt = half_A_g * (w * cn * cn - bpert(i));
+        pert_sum += 2.0f * dlt;
+        const float si = (es + ea) + om1 * ni + (ss + sa) + dlt;
+        const float so = (es - ea) + om1 * no + (ss - sa) + dlt;
+        const float sg = seg0 * w * cn * inv_clen(i);
+        const float wrr = w * rr, wrb = w * rb;
+        St::store(out, (size_t)i * p.N + node, wrr + (ar * si + sg), w * ref);
+        St::store(out, (size_t)o * p.N + node, wrr + (ar * so - sg), w * ref);
+        St::store(out, (size_t)(Q + i) * p.N + node, wrb + (ab * si - sg), w * ref);
+        St::store(out, (size_t)(Q + o) * p.N + node, wrb + (ab * so + sg), w * ref);
+    }
+    {
+        constexpr int i = 9;
+        const float w = wgt(i);
+        const float wr = w * rho;
+        const float e0 = wr * (-1.5f * usq);
+        const float s0 = wr * (-1.5f * du_dot);
+        const float n0 = (f[i] - wr) - e0;
+        const float si = e0 + om1 * n0 + s0 - pert_sum;
+        St::store(out, (size_t)i * p.N + node, w * rr + ar * si, w * ref);
+        St::store(out, (size_t)(Q + i) * p.N + node, w * rb + ab * si, w * ref);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA library (FP32 arithmetic) against the FP64 oracle.
+
+Bars (fixed by the method's accuracy target): after 100 steps max|d rho| <= 1e-5
+for each species density and max|d u| <= 1e-6 for the physical velocity; FP16
+deviation storage: rho within 1e-3. Inputs are the seeded synthetic workloads.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_12764_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RHO_TOL, U_TOL = 1e-5, 1e-6
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12764_gb300 import build_lib, lbm as L
+    build_lib.build()
+    L.load()
+    return L
+
+
+def run_pair(lbm, shape, fields, steps, storage="fp32", pins=None, **kw):
+    nz, ny, nx = shape
+    o = oracle.Lattice(oracle.make_params(nx, ny, nz, **kw))
+    o.set_fields(*fields)
+    if pins is not None:
+        o.set_pins(pins)
+    o.step(steps)
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, storage=storage, **kw))
+    g.set_fields(*fields)
+    if pins is not None:
+        g.set_pin_mask(pins)
+    g.step(steps)
+    return o.get_fields(), g.get_fields(), o, g
+
+
+def errs(fo, fg):
+    return {k: float(np.abs(fo[k] - fg[k]).max()) for k in ("rho_r", "rho_b", "u", "phi")}
+
+
+def assert_parity(fo, fg, rho_tol=RHO_TOL, u_tol=U_TOL):
+    e = errs(fo, fg)
+    assert e["rho_r"] <= rho_tol and e["rho_b"] <= rho_tol, e
+    assert e["u"] <= u_tol, e
+
+
+def test_static_droplet_100_steps(lbm):
+    w = inputs.static_droplet(L=32, R=8.0)
+    fo, fg, _, _ = run_pair(lbm, w.shape, (w.rho_r, w.rho_b), 100, **w.params)
+    assert_parity(fo, fg)
+
+
+def test_walls_forces_near_contact_ragged_tiles(lbm):
+    # x, y not multiples of the 32 x 8 tile; walls in y and z; body force; near contact
+    shape = (13, 29, 45)
+    drops = [(12.0, 10.0, 6.0, 5.0), (24.5, 18.0, 6.5, 5.5), (38.0, 9.0, 6.0, 4.5)]
+    rr, rb = inputs.paint_droplets(shape, drops, periodic=(True, False, False))
+    kw = dict(wall_y=1, wall_z=1, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0, g=(1e-5, 0, 0))
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, rb), 100, **kw)
+    assert_parity(fo, fg)
+
+
+def test_channel_workload_shape_small(lbm):
+    w = inputs.channel_droplets(nx=64, ny=40, nz=24, n_grid=(2, 2, 1), r_range=(4, 6), seed=5)
+    fo, fg, _, _ = run_pair(lbm, w.shape, (w.rho_r, w.rho_b), 100, **w.params)
+    assert_parity(fo, fg)
+
+
+def test_unequal_viscosities_and_kolmogorov(lbm):
+    shape = (24, 20, 36)
+    rr, rb, u = inputs.random_state(shape, seed=21, u_amp=0.01)
+    kw = dict(tau_r=0.8, tau_b=1.3, sigma=0.015, beta=0.7, kolmogorov_amp=1e-4)
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, rb, u), 100, **kw)
+    assert_parity(fo, fg)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 4), (3, 1, 5), (1, 6, 1), (7, 3, 5), (2, 2, 2)])
+def test_degenerate_and_tiny_boxes(lbm, shape):
+    rr, rb, u = inputs.random_state(shape, seed=sum(shape), u_amp=0.01)
+    kw = dict(sigma=0.02, beta=0.7)
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, rb, u), 20, **kw)
+    assert_parity(fo, fg)
+
+
+def test_pinning_sites(lbm):
+    # A droplet with pinning sites scattered around its interface (distances 4-10
+    # from the centre). A stable configuration: the symmetric noise quench of the
+    # gel workload is a physical instability, where FP32 and FP64 runs separate
+    # exponentially, so it is checked one step at a time instead (below).
+    shape = (24, 24, 24)
+    rr, rb = inputs.paint_droplets(shape, [(12.0, 12.0, 12.0, 6.0)])
+    rng = np.random.default_rng(17)
+    pins = np.zeros(shape, np.uint8)
+    for _ in range(12):
+        d = rng.normal(size=3)
+        pt = np.array([12.0, 12.0, 12.0]) + d / np.linalg.norm(d) * rng.uniform(4, 10)
+        x, y, z = np.round(pt).astype(int) % 24
+        pins[z, y, x] = 1
+    kw = dict(sigma=0.01, beta=0.7, A_nc=0.01, h_min=3.0)
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, rb), 60, pins=pins, **kw)
+    assert_parity(fo, fg)
+
+
+def test_gel_quench_one_step_sampled(lbm):
+    # Symmetric mixture with colour noise and 2 % pinning sites (the gel workload at
+    # 48^3): after 20 GPU steps, one more step against the oracle evaluated at
+    # sampled nodes from the same state.
+    w = inputs.bicontinuous(L=48, seed=5)
+    n = 48
+    g = lbm.Lattice(lbm.make_params(n, n, n, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    g.set_pin_mask(w.pins)
+    g.step(20)
+    fr, fb, lag = g.get_pops()
+    g.step(1)
+    gr, gb, _ = g.get_pops()
+    m = _map_to_oracle(lbm)
+    N = n ** 3
+    nodes = np.random.default_rng(4).choice(N, 3000, replace=False)
+    P = oracle.make_params(n, n, n, **w.params)
+    oa, ob, _ = oracle.step_nodes(P, fr.reshape(19, N)[m], fb.reshape(19, N)[m], lag.ravel(),
+                                  nodes, pin=w.pins.ravel())
+    ga = gr.reshape(19, N)[m][:, nodes].T
+    gbb = gb.reshape(19, N)[m][:, nodes].T
+    bad = (np.abs(oa - ga).max(1) > 1e-6) | (np.abs(ob - gbb).max(1) > 1e-6)
+    # a node whose film thickness sits on a zero crossing of phi may take the other
+    # branch in FP32; allow at most 0.5 % of the sampled nodes to differ
+    assert bad.mean() <= 0.005, (bad.sum(), np.abs(oa - ga).max())
+
+
+def test_zero_steps_returns_set_fields(lbm):
+    shape = (5, 6, 7)
+    rr, rb, u = inputs.random_state(shape, seed=3)
+    g = lbm.Lattice(lbm.make_params(7, 6, 5))
+    g.set_fields(rr, rb, u)
+    g.step(0)
+    f = g.get_fields()
+    assert np.abs(f["rho_r"] - rr).max() < 2e-7 and np.abs(f["rho_b"] - rb).max() < 2e-7
+    assert np.abs(f["u"] - u).max() < 1e-7
+
+
+def test_conservation_on_gpu(lbm):
+    w = inputs.static_droplet(L=32, R=8.0)
+    g = lbm.Lattice(lbm.make_params(32, 32, 32, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    t0 = g.observables()
+    g.step(500)
+    t = g.observables()
+    # FP32 arithmetic: per-species mass conserved to FP32 round-off accumulation
+    assert abs(t[0] - t0[0]) / t0[0] < 1e-6 and abs(t[1] - t0[1]) / t0[1] < 1e-6
+    assert np.abs(t[2:5]).max() / (t0[0] + t0[1]) < 1e-7
+    assert t[5] == 500
+
+
+def test_laplace_on_gpu_matches_oracle(lbm):
+    w = inputs.static_droplet(L=32, R=8.0)
+    fo, fg, o, g = run_pair(lbm, w.shape, (w.rho_r, w.rho_b), 200, **w.params)
+    lo = o.laplace((16, 16, 16))
+    lg = g.laplace((16, 16, 16))
+    assert abs(lg["R_eff"] - lo["R_eff"]) < 1e-4
+    assert abs(lg["dp"] - lo["dp"]) / abs(lo["dp"]) < 1e-3
+
+
+def test_checkpoint_resume_is_bitwise(lbm):
+    w = inputs.channel_droplets(nx=64, ny=40, nz=24, n_grid=(2, 2, 1), r_range=(4, 6), seed=5)
+    P = lbm.make_params(64, 40, 24, **w.params)
+    a = lbm.Lattice(P)
+    a.set_fields(w.rho_r, w.rho_b)
+    a.step(30)
+    blob = a.save_state()
+    a.step(30)
+    b = lbm.Lattice(P)
+    b.load_state(blob)
+    b.step(30)
+    pa, pb = a.get_pops(), b.get_pops()
+    assert all(np.array_equal(x, y) for x, y in zip(pa, pb))
+    assert b.steps_taken == 60
+
+
+def test_fp16_deviation_storage_accuracy(lbm):
+    w = inputs.static_droplet(L=32, R=8.0)
+    fo, fg, o, g = run_pair(lbm, w.shape, (w.rho_r, w.rho_b), 100, storage="fp16", **w.params)
+    e = errs(fo, fg)
+    assert e["rho_r"] <= 1e-3 and e["rho_b"] <= 1e-3, e
+
+
+def test_invalid_arguments_are_rejected(lbm):
+    for bad in (dict(tau_r=0.5), dict(beta=1.5), dict(storage=7)):
+        kw = dict(tau_r=1.0)
+        kw.update(bad)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Lattice(lbm.make_params(8, 8, 8, **kw))
+        assert ei.value.status == -1
+    g = lbm.Lattice(lbm.make_params(8, 8, 8))
+    with pytest.raises(lbm.LbmError) as ei:
+        g.step(1)                     # no fields yet
+    assert ei.value.status == -4
+    with pytest.raises(lbm.LbmError):
+        g.step(-1)
+
+
+def _map_to_oracle(lbm):
+    """index map: oracle direction k -> library direction."""
+    cg = lbm.velocity_set()
+    co = oracle.lattice()[0]
+    return np.array([int(np.nonzero((cg == co[k]).all(1))[0][0]) for k in range(19)])
+
+
+def test_one_step_full_size_channel_sampled(lbm):
+    # The microfluidic-crystal channel at its full size (256 x 128 x 64, 40 droplets)
+    # after 50 GPU steps: one more GPU step compared with the oracle's step evaluated
+    # at 4000 sampled nodes from the same (downloaded) state.
+    w = inputs.channel_droplets()
+    nz, ny, nx = w.shape
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    g.step(50)
+    fr, fb, lag = g.get_pops()
+    g.step(1)
+    gr, gb, _ = g.get_pops()
+    m = _map_to_oracle(lbm)
+    N = nx * ny * nz
+    frr = fr.reshape(19, N)[m]
+    fbb = fb.reshape(19, N)[m]
+    rng = np.random.default_rng(9)
+    phi = lag.ravel()
+    iface = np.nonzero(np.abs(phi) < 0.9)[0]
+    nodes = np.unique(np.concatenate([rng.choice(N, 2000, replace=False),
+                                      rng.choice(iface, 2000, replace=False)]))
+    P = oracle.make_params(nx, ny, nz, **w.params)
+    oa, ob, _ = oracle.step_nodes(P, frr, fbb, phi, nodes)
+    ga = gr.reshape(19, N)[m][:, nodes].T
+    gbb = gb.reshape(19, N)[m][:, nodes].T
+    assert np.abs(oa - ga).max() < 1e-6 and np.abs(ob - gbb).max() < 1e-6
