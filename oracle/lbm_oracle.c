@@ -334,7 +334,7 @@ double or_nc_strength_node(const or_params* p, const double* phi_ray,
     double G[3];
     gradient_node(p, phi_ray, x, y, z, G);
     double gm = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-    if (gm < 1e-3) return 0.0;
+    if (!(gm >= 1e-3) || !isfinite(gm)) return 0.0;   /* non-finite fields: no force */
     double n[3] = {-G[0] / gm, -G[1] / gm, -G[2] / gm};
     int nsamp = (int)floor(2.0 * (p->h_cut + 3.0)) + 1; /* t = -1 ... h_cut + 2 */
     /* A sample carries a sign only if |phi| > 1e-5 (samples at rounding level of

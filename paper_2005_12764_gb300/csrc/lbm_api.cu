@@ -1,6 +1,8 @@
 // lbm_api.cu -- C-ABI of liblbm.so (declared in include/lbm.h): context and device
 // memory management, field set/get conversions, FP64 reductions and the launch of
 // the fused step kernel (lbm_step.cu).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,10 +16,15 @@
 #include "lbm_device.cuh"
 
 namespace lbm {
-cudaError_t launch_step(const StepParams& p, int storage, int grid, cudaStream_t s);
+cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage, int grid,
+                        cudaStream_t s);
 cudaError_t launch_nc(const StepParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
+                              cudaStream_t s);
 int step_tile_x();
 int step_tile_y();
+int step_box_rows();
+int step_box_width(int storage);
 }  // namespace lbm
 
 using namespace lbm;
@@ -26,6 +33,9 @@ struct lbm_ctx {
     lbm_params p{};
     size_t N = 0;
     size_t elem = 4;            // bytes per stored population
+    int pitch = 0, nyp = 0;     // padded row length and rows per plane (ghosts included)
+    size_t P = 0;               // elements per padded [z][y][x] block
+    CUtensorMap tmap[2];        // TMA descriptors of the two population copies
     void* f[2] = {nullptr, nullptr};
     float* phi[2] = {nullptr, nullptr};
     float* fx_row = nullptr;
@@ -76,13 +86,25 @@ __host__ __device__ inline size_t nidx(const lbm_params& p, int x, int y, int z)
     return ((size_t)z * p.ny + y) * p.nx + x;
 }
 
+// Padded index of unpadded node n.
+__device__ __forceinline__ size_t node_pidx(const StepParams& sp, size_t n) {
+    const size_t plane = (size_t)sp.nx * sp.ny;
+    const int z = (int)(n / plane);
+    const int rem = (int)(n - (size_t)z * plane);
+    const int y = rem / sp.nx, x = rem - y * sp.nx;
+    return pidx(sp.pitch, sp.nyp, x, y, z);
+}
+
 // f_i^k = f_i^eq(rho_k, u), Eq. (2); both colour-field buffers get phi.
 template <class St>
 __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
                                    const double* rho_r, const double* rho_b, const double* u,
-                                   size_t N, float ref_half) {
+                                   StepParams sp) {
+    const size_t N = sp.N, P = sp.P;
+    const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
         const double rr = rho_r[n], rb = rho_b[n];
         double ux = 0, uy = 0, uz = 0;
         if (u) {
@@ -97,8 +119,8 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
             const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
             const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
             const float ref = wgt(i) * ref_half;
-            St::store(f, (size_t)i * N + n, (float)(rr * e), ref);
-            St::store(f, (size_t)(Q + i) * N + n, (float)(rb * e), ref);
+            St::store(f, (size_t)i * P + q, (float)(rr * e), ref);
+            St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), ref);
         }
         const float ph = (float)((rr - rb) / (rr + rb));
         phi0[n] = ph;
@@ -119,14 +141,15 @@ template <class St>
 __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int have_force,
                                      const float* phi_now, double* rho_r, double* rho_b,
                                      double* u, double* phi) {
-    const size_t N = sp.N;
+    const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
         float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float a = ldpop<St>(f, (size_t)i * N + n, i, sp.ref_half);
-            const float b = ldpop<St>(f, (size_t)(Q + i) * N + n, i, sp.ref_half);
+            const float a = ldpop<St>(f, (size_t)i * P + q, i, sp.ref_half);
+            const float b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, sp.ref_half);
             rr += a;
             rb += b;
             jx += cx(i) * (a + b);
@@ -163,28 +186,32 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
 }
 
 template <class St>
-__global__ void pops_to_f64_kernel(const typename St::T* f, size_t N, float ref_half, double* fr,
+__global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, double* fr,
                                    double* fb) {
+    const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * N + n, i, ref_half);
-            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * P + q, i, sp.ref_half);
+            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * P + q, i, sp.ref_half);
         }
     }
 }
 
 template <class St>
-__global__ void f64_to_pops_kernel(typename St::T* f, size_t N, float ref_half, const double* fr,
+__global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const double* fr,
                                    const double* fb) {
+    const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float ref = wgt(i) * ref_half;
-            St::store(f, (size_t)i * N + n, (float)fr[(size_t)i * N + n], ref);
-            St::store(f, (size_t)(Q + i) * N + n, (float)fb[(size_t)i * N + n], ref);
+            const float ref = wgt(i) * sp.ref_half;
+            St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], ref);
+            St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], ref);
         }
     }
 }
@@ -234,14 +261,17 @@ __global__ void finish_sum_kernel(const double* part, int nblocks, double* out) 
 
 // Conserved totals (FP64): sum f^r, sum f^b, P.
 template <class St>
-__global__ void totals_kernel(const typename St::T* f, size_t N, float ref_half, double* part) {
+__global__ void totals_kernel(const typename St::T* f, StepParams sp, double* part) {
     double v[5] = {0, 0, 0, 0, 0};
+    const size_t N = sp.N, P = sp.P;
+    const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double a = ldpop<St>(f, (size_t)i * N + n, i, ref_half);
-            const double b = ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+            const double a = ldpop<St>(f, (size_t)i * P + q, i, ref_half);
+            const double b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
             v[0] += a;
             v[1] += b;
             v[2] += cx(i) * (a + b);
@@ -254,15 +284,18 @@ __global__ void totals_kernel(const typename St::T* f, size_t N, float ref_half,
 
 // Laplace measurement, pass 1: V = sum (1 + phi)/2 with phi from the populations.
 template <class St>
-__global__ void volume_kernel(const typename St::T* f, size_t N, float ref_half, double* part) {
+__global__ void volume_kernel(const typename St::T* f, StepParams sp, double* part) {
     double v[1] = {0};
+    const size_t N = sp.N, P = sp.P;
+    const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
         double rr = 0, rb = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            rr += ldpop<St>(f, (size_t)i * N + n, i, ref_half);
-            rb += ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+            rr += ldpop<St>(f, (size_t)i * P + q, i, ref_half);
+            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
         }
         v[0] += 0.5 * (1.0 + (rr - rb) / (rr + rb));
     }
@@ -271,9 +304,11 @@ __global__ void volume_kernel(const typename St::T* f, size_t N, float ref_half,
 
 // Pass 2: pressure sums and node counts inside r < R-3 and outside r > R+5.
 template <class St>
-__global__ void pressure_kernel(const typename St::T* f, lbm_params p, size_t N, float ref_half,
+__global__ void pressure_kernel(const typename St::T* f, lbm_params p, StepParams sp,
                                 double c0, double c1, double c2, double R, double* part) {
     double v[4] = {0, 0, 0, 0};
+    const size_t N = sp.N, P = sp.P;
+    const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((size_t)p.nx * p.ny));
@@ -287,11 +322,12 @@ __global__ void pressure_kernel(const typename St::T* f, lbm_params p, size_t N,
             }
         const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (r < R - 3.0 || r > R + 5.0) {
+            const size_t q = node_pidx(sp, n);
             double rho = 0;
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                rho += (double)ldpop<St>(f, (size_t)i * N + n, i, ref_half) +
-                       (double)ldpop<St>(f, (size_t)(Q + i) * N + n, i, ref_half);
+                rho += (double)ldpop<St>(f, (size_t)i * P + q, i, ref_half) +
+                       (double)ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
             if (r < R - 3.0) {
                 v[0] += rho / 3.0;
                 v[1] += 1;
@@ -346,6 +382,22 @@ int grid_for(size_t n, int num_sms) {
 // ---------------------------------------------------------------- helpers
 static size_t elem_bytes(int storage) { return storage == 0 ? 4 : 2; }
 
+// Padded population layout: two ghost columns and rows on each side, row length
+// rounded up to a multiple of 16 bytes (TMA row alignment).
+struct PadLayout {
+    int pitch, nyp;
+    size_t P;
+};
+static PadLayout pad_layout(const lbm_params& p) {
+    const int per16 = (int)(16 / elem_bytes(p.storage));
+    PadLayout L;
+    L.pitch = (p.nx + 4 + per16 - 1) / per16 * per16;
+    L.pitch = std::max(L.pitch, 40);                    // at least one staged box wide
+    L.nyp = std::max(p.ny + 4, 18);                     // at least one staged box high
+    L.P = (size_t)L.pitch * L.nyp * p.nz;
+    return L;
+}
+
 static lbm_status validate(const lbm_params* p, std::string& why) {
     if (!p) { why = "params is NULL"; return LBM_EINVAL; }
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_EINVAL; }
@@ -368,7 +420,10 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
 extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     if (!p) return 0;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    return 2 * 2 * Q * N * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
+    const PadLayout L = pad_layout(*p);
+    size_t b = 2 * 2 * Q * L.P * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
+    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int));
+    return b;
 }
 
 extern "C" void lbm_velocity_set(int c[LBM_Q * 3]) {
@@ -390,6 +445,11 @@ static void fill_step_params(lbm_ctx* c) {
     s.ny = p.ny;
     s.nz = p.nz;
     s.N = c->N;
+    s.pitch = c->pitch;
+    s.nyp = c->nyp;
+    s.plane_p = (size_t)c->pitch * c->nyp;
+    s.P = c->P;
+    s.ghost_in_kernel = (p.nx >= 4 && (p.wall_y || p.ny >= 4)) ? 1 : 0;
     s.wall_y = p.wall_y ? 1 : 0;
     s.wall_z = p.wall_z ? 1 : 0;
     s.var_tau = p.tau_r != p.tau_b;
@@ -410,7 +470,6 @@ static void fill_step_params(lbm_ctx* c) {
     const int tx = step_tile_x(), ty = step_tile_y();
     s.tiles_x = (p.nx + tx - 1) / tx;
     s.tiles_y = (p.ny + ty - 1) / ty;
-    s.bulk_ok = (p.nx % 32 == 0) ? 1 : 0;
     s.err = c->err_word;
     s.ah = c->ah;
     // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
@@ -461,7 +520,11 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         delete c;
         return fail(nullptr, LBM_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
-    const size_t pop_bytes = 2 * Q * c->N * c->elem;
+    const PadLayout L = pad_layout(*p);
+    c->pitch = L.pitch;
+    c->nyp = L.nyp;
+    c->P = L.P;
+    const size_t pop_bytes = 2 * Q * c->P * c->elem;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMalloc(ptr, bytes) == cudaSuccess;
     };
@@ -497,6 +560,37 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (e != cudaSuccess) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    }
+    // TMA descriptors of the two population copies: 4-D [38][nz][nyp][pitch], boxes of
+    // BW x (TY+2) x 1 x 1 elements, zero fill outside
+    {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess) {
+            lbm_destroy(c);
+            return fail(nullptr, LBM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        }
+        auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        const cuuint64_t dims[4] = {(cuuint64_t)c->pitch, (cuuint64_t)c->nyp, (cuuint64_t)p->nz,
+                                    (cuuint64_t)(2 * Q)};
+        const cuuint64_t strides[3] = {(cuuint64_t)c->pitch * c->elem,
+                                       (cuuint64_t)c->pitch * c->nyp * c->elem,
+                                       (cuuint64_t)c->P * c->elem};
+        const cuuint32_t box[4] = {(cuuint32_t)step_box_width(p->storage), (cuuint32_t)step_box_rows(), 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUtensorMapDataType dt = p->storage == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+        for (int b = 0; b < 2; ++b) {
+            CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                lbm_destroy(c);
+                return fail(nullptr, LBM_ECUDA, "cuTensorMapEncodeTiled failed");
+            }
+        }
     }
     fill_step_params(c);
     *out = c;
@@ -566,9 +660,10 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const doub
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         init_fields_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (typename St::T*)c->f[0], c->phi[0], c->phi[1], dr, db, du, N, c->sp.ref_half);
+            (typename St::T*)c->f[0], c->phi[0], c->phi[1], dr, db, du, c->sp);
     });
     CK(c, cudaGetLastError());
+    CK(c, launch_ghost_fill(c->f[0], c->sp, c->p.storage, c->num_sms, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed
     c->steps = 0;
     c->fields_set = true;
@@ -645,7 +740,9 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
         s.cand_count = c->cand_count + c->cw;
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
-    if (e == cudaSuccess) e = launch_step(s, c->p.storage, c->grid, c->stream);
+    if (e == cudaSuccess) e = launch_step(s, c->tmap[c->cur], c->p.storage, c->grid, c->stream);
+    if (e == cudaSuccess && !s.ghost_in_kernel)
+        e = launch_ghost_fill(c->f[1 - c->cur], s, c->p.storage, c->num_sms, c->stream);
     if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
     if (e != cudaSuccess) return e;
     c->nc_scan = false;
@@ -751,7 +848,7 @@ extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double*
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         pops_to_f64_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (const typename St::T*)c->f[c->cur], N, c->sp.ref_half, dr, db);
+            (const typename St::T*)c->f[c->cur], c->sp, dr, db);
     });
     CK(c, cudaGetLastError());
     if (!on_device) {
@@ -791,9 +888,10 @@ extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* 
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         f64_to_pops_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (typename St::T*)c->f[c->cur], N, c->sp.ref_half, dr, db);
+            (typename St::T*)c->f[c->cur], c->sp, dr, db);
     });
     CK(c, cudaGetLastError());
+    CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
     if (phi_lag) {
         const double* src = phi_lag;
         if (!on_device) {
@@ -817,7 +915,7 @@ extern "C" lbm_status lbm_observables(lbm_ctx* c, double out[8]) {
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         totals_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
-                                                            c->N, c->sp.ref_half, c->red);
+                                                            c->sp, c->red);
     });
     finish_sum_kernel<5><<<1, kThreads, 0, c->stream>>>(c->red, grid, c->red + (size_t)grid * 8);
     CK(c, cudaGetLastError());
@@ -837,7 +935,7 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         volume_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
-                                                             c->N, c->sp.ref_half, c->red);
+                                                             c->sp, c->red);
     });
     finish_sum_kernel<1><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
     CK(c, cudaGetLastError());
@@ -848,8 +946,8 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         pressure_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (const typename St::T*)c->f[c->cur], c->p, c->N, c->sp.ref_half, centre[0], centre[1],
-            centre[2], R, c->red);
+            (const typename St::T*)c->f[c->cur], c->p, c->sp, centre[0], centre[1], centre[2], R,
+            c->red);
     });
     finish_sum_kernel<4><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
     CK(c, cudaGetLastError());
@@ -867,14 +965,14 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
 
 extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
     if (!c) return 0;
-    return 2 * Q * c->N * c->elem + 2 * c->N * sizeof(float) + sizeof(long long);
+    return 2 * Q * c->P * c->elem + 2 * c->N * sizeof(float) + sizeof(long long);
 }
 
 extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
     if (!c || !host_buf) return LBM_EINVAL;
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
     char* b = (char*)host_buf;
-    const size_t pb = 2 * Q * c->N * c->elem, fb = c->N * sizeof(float);
+    const size_t pb = 2 * Q * c->P * c->elem, fb = c->N * sizeof(float);
     CK(c, cudaMemcpyAsync(b, c->f[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(b + pb, c->phi[c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(b + pb + fb, c->phi[1 - c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
@@ -886,7 +984,7 @@ extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
 extern "C" lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf) {
     if (!c || !host_buf) return LBM_EINVAL;
     const char* b = (const char*)host_buf;
-    const size_t pb = 2 * Q * c->N * c->elem, fb = c->N * sizeof(float);
+    const size_t pb = 2 * Q * c->P * c->elem, fb = c->N * sizeof(float);
     c->cur = 0;
     c->pc = 0;
     CK(c, cudaMemcpyAsync(c->f[0], b, pb, cudaMemcpyHostToDevice, c->stream));

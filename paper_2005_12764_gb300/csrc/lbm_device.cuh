@@ -96,7 +96,11 @@ struct StepParams {
     const int* nc_count;
     float gy, gz;
     int nx, ny, nz;
-    size_t N;
+    size_t N;               // nodes (fields phi, ah are [N], x fastest)
+    // population arrays are padded: two ghost columns and rows on each side, row
+    // pitch rounded up to 16 bytes; one [nz][nyp][pitch] block per species/direction
+    int pitch, nyp;
+    size_t plane_p, P;      // pitch * nyp, plane_p * nz
     int wall_y, wall_z;
     int var_tau;            // 0: omega0 everywhere; 1: mixture rule per node
     float omega0;
@@ -106,8 +110,8 @@ struct StepParams {
     int nsamp;              // ray samples t = -1, -1/2, ..., h_cut + 2
     float ref_half;         // rho0/2: deviation reference per species (FP16/BF16)
     int tiles_x, tiles_y;   // xy tiles of the step kernel
-    int bulk_ok;            // rows can be staged with 16-byte bulk copies (nx % 32 == 0)
     int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
+    int ghost_in_kernel;    // the step kernel writes the ghost copies (else a fill pass)
     int* err;               // device error word: 1 = a bounded wait gave up
 };
 
@@ -123,11 +127,18 @@ __device__ __forceinline__ int wrapi(int a, int n) {
     a %= n;
     return a < 0 ? a + n : a;
 }
-// Wrap of an index that lies within a few periods of [0, n): no integer division.
+// Wrap of an index that lies within a few periods of [0, n): no integer division in
+// the common case; falls back to a modulo (bounded time) for anything further out.
 __device__ __forceinline__ int wrap_near(int a, int n) {
+    if (a < -4 * n || a >= 5 * n) return wrapi(a, n);
     while (a < 0) a += n;
     while (a >= n) a -= n;
     return a;
+}
+
+// Index of node (x, y, z) in one padded population block (x, y may be ghosts, -2..n+1).
+__host__ __device__ __forceinline__ size_t pidx(int pitch, int nyp, int x, int y, int z) {
+    return ((size_t)z * nyp + (y + 2)) * pitch + (x + 2);
 }
 
 // Trilinear sample of the lagged colour field at node (x, y, z) + offset o; false if
@@ -136,6 +147,7 @@ __device__ __forceinline__ int wrap_near(int a, int n) {
 // o, not of x + o.
 __device__ __forceinline__ bool axis_cell(int base, float o, int n, bool walled, int& i0, int& i1,
                                           float& fr) {
+    if (!(fabsf(o) < 1.0e6f)) return false;   // non-finite or absurd offset
     const float fl = floorf(o);
     int b = base + (int)fl;
     float f = o - fl;
@@ -218,7 +230,7 @@ __device__ inline float nc_strength(const StepParams& p, size_t node, int x, int
     float Gx, Gy, Gz;
     gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
     const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
-    if (!(gm >= 1e-3f)) return 0.0f;
+    if (!(gm >= 1e-3f) || !isfinite(gm)) return 0.0f;   // non-finite fields: no force
     const float inv = 1.0f / gm;
     const float nx_ = -Gx * inv, ny_ = -Gy * inv, nz_ = -Gz * inv;
     float t_a = 0.0f, v_a = 0.0f, t_d = 0.0f, t_u = 0.0f;
@@ -271,10 +283,6 @@ __device__ inline float nc_strength(const StepParams& p, size_t node, int x, int
 }
 
 // ---------------------------------------------------------------- collision
-// Index of the direction opposite to one of the 9 "positive" directions used in
-// the pair loop (directions 10..18 are opposite to 8..0).
-__host__ __device__ constexpr int pair_dir(int k) { return k < 9 ? k : k + 1; }
-
 // Pairwise (fixed-tree) sum of 19 values; every caller sums the same node's
 // populations in the same order, so a node's density is bitwise the same whichever
 // thread computes it.
@@ -303,17 +311,30 @@ constexpr float kGradZero = 1e-6f;
 // rounded once and all other terms are O(|u|, |F|, |G|) corrections. Opposite
 // directions share their symmetric terms. The rest direction takes minus the sum of
 // the other perturbations, so the perturbation conserves mass exactly.
-template <class St>
+// Output of one value to its node and, on edge nodes of periodic axes, to the ghost
+// copies (ng extra offsets relative to the node, in elements).
+template <class St, bool Ghost>
+__device__ __forceinline__ void put(typename St::T* out, size_t off, float v, float ref, int ng,
+                                    const long long (&goff)[3]) {
+    St::store(out, off, v, ref);
+    if (Ghost) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+            if (g < ng) St::store(out + goff[g], off, v, ref);
+    }
+}
+
+template <class St, bool UnitOmega, bool Ghost>
 __device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
                                               float rb, float Gx, float Gy, float Gz, float Fx,
-                                              float Fy, float Fz, typename St::T* out,
-                                              size_t node) {
+                                              float Fy, float Fz, typename St::T* out, int ng,
+                                              const long long (&goff)[3]) {
+    const size_t N = p.P;
     const float rho = rr + rb;
     const float inv_rho = 1.0f / rho;
     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int i = pair_dir(k);
+    for (int i = 0; i < 9; ++i) {
         const float d = f[i] - f[opp(i)];
         if (cx(i)) jx += cx(i) > 0 ? d : -d;
         if (cy(i)) jy += cy(i) > 0 ? d : -d;
@@ -321,14 +342,14 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
     }
     const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
     float omega = p.omega0;
-    if (p.var_tau) {
+    if (!UnitOmega && p.var_tau) {
         const float inv_nu = (rr * p.inv_nu_r + rb * p.inv_nu_b) * inv_rho;
         omega = 1.0f / (3.0f / inv_nu + 0.5f);
     }
-    const float om1 = 1.0f - omega;
+    const float om1 = UnitOmega ? 0.0f : 1.0f - omega;
     const float dx = Fx * inv_rho, dy = Fy * inv_rho, dz = Fz * inv_rho;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    const float du_dot = dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz);
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float dd15 = 1.5f * (dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz));
     const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
     const bool has_g = gm >= kGradZero;
     const float inv_g = has_g ? 1.0f / gm : 0.0f;
@@ -336,43 +357,52 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
     const float seg0 = has_g ? p.beta * rr * rb * inv_rho : 0.0f;
     const float ar = rr * inv_rho, ab = rb * inv_rho;
     const float ref = p.ref_half;
+    // per weight class (face / edge): products that do not depend on the direction
+    const float wr_f = wgt(2) * rho, wr_e = wgt(0) * rho;
+    const float wrr_f = wgt(2) * rr, wrr_e = wgt(0) * rr;
+    const float wrb_f = wgt(2) * rb, wrb_e = wgt(0) * rb;
+    const float hw_f = half_A_g * wgt(2), hw_e = half_A_g * wgt(0);
+    const float hb_f = half_A_g * bpert(2), hb_e = half_A_g * bpert(0);
+    const float sg_f = seg0 * wgt(2) * inv_clen(2), sg_e = seg0 * wgt(0) * inv_clen(0);
     float pert_sum = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int i = pair_dir(k), o = opp(i);
-        const float w = wgt(i);
-        const float wr = w * rho;
+    for (int i = 0; i < 9; ++i) {
+        const int o = opp(i);
+        const bool face = csq(i) == 1;
+        const float wr = face ? wr_f : wr_e;
         const float a = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
         const float b = (float)cx(i) * dx + (float)cy(i) * dy + (float)cz(i) * dz;
-        const float es = wr * (4.5f * a * a - 1.5f * usq);
+        const float es = wr * (4.5f * a * a - usq15);
         const float ea = wr * (3.0f * a);
-        const float ss = wr * (4.5f * b * (2.0f * a + b) - 1.5f * du_dot);
+        const float ss = wr * (4.5f * b * (2.0f * a + b) - dd15);
         const float sa = wr * (3.0f * b);
-        const float ni = (f[i] - wr) - (es + ea);
-        const float no = (f[o] - wr) - (es - ea);
         const float cg = (float)cx(i) * Gx + (float)cy(i) * Gy + (float)cz(i) * Gz;
         const float cn = cg * inv_g;
-        const float dlt = half_A_g * (w * cn * cn - bpert(i));
-        pert_sum += 2.0f * dlt;
-        const float si = (es + ea) + om1 * ni + (ss + sa) + dlt;
-        const float so = (es - ea) + om1 * no + (ss - sa) + dlt;
-        const float sg = seg0 * w * cn * inv_clen(i);
-        const float wrr = w * rr, wrb = w * rb;
-        St::store(out, (size_t)i * p.N + node, wrr + (ar * si + sg), w * ref);
-        St::store(out, (size_t)o * p.N + node, wrr + (ar * so - sg), w * ref);
-        St::store(out, (size_t)(Q + i) * p.N + node, wrb + (ab * si - sg), w * ref);
-        St::store(out, (size_t)(Q + o) * p.N + node, wrb + (ab * so + sg), w * ref);
+        const float dlt = (face ? hw_f : hw_e) * (cn * cn) - (face ? hb_f : hb_e);
+        pert_sum += dlt;
+        float si = (es + ea) + (ss + sa) + dlt;
+        float so = (es - ea) + (ss - sa) + dlt;
+        if (!UnitOmega) {
+            si += om1 * ((f[i] - wr) - (es + ea));
+            so += om1 * ((f[o] - wr) - (es - ea));
+        }
+        const float sg = (face ? sg_f : sg_e) * cn;
+        const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
+        const float w = wgt(i);
+        put<St, Ghost>(out, (size_t)i * N, wrr + (ar * si + sg), w * ref, ng, goff);
+        put<St, Ghost>(out, (size_t)o * N, wrr + (ar * so - sg), w * ref, ng, goff);
+        put<St, Ghost>(out, (size_t)(Q + i) * N, wrb + (ab * si - sg), w * ref, ng, goff);
+        put<St, Ghost>(out, (size_t)(Q + o) * N, wrb + (ab * so + sg), w * ref, ng, goff);
     }
     {
         constexpr int i = 9;
         const float w = wgt(i);
         const float wr = w * rho;
-        const float e0 = wr * (-1.5f * usq);
-        const float s0 = wr * (-1.5f * du_dot);
-        const float n0 = (f[i] - wr) - e0;
-        const float si = e0 + om1 * n0 + s0 - pert_sum;
-        St::store(out, (size_t)i * p.N + node, w * rr + ar * si, w * ref);
-        St::store(out, (size_t)(Q + i) * p.N + node, w * rb + ab * si, w * ref);
+        const float e0 = -wr * usq15;
+        float si = e0 - wr * dd15 - 2.0f * pert_sum;
+        if (!UnitOmega) si += om1 * ((f[i] - wr) - e0);
+        put<St, Ghost>(out, (size_t)i * N, w * rr + ar * si, w * ref, ng, goff);
+        put<St, Ghost>(out, (size_t)(Q + i) * N, w * rb + ab * si, w * ref, ng, goff);
     }
 }
 

@@ -1,43 +1,47 @@
-// lbm_step.cu -- the fused time-step kernel (one launch = one full lattice update).
+// lbm_step.cu -- the fused time-step kernel (one launch = one full lattice update)
+// and the near-contact pass.
 //
 // Data layout: populations in [2 species][19 directions][z][y][x] (x fastest), two
-// copies (read one, write the other).
+// copies (read one, write the other). Each [z][y][x] block is padded with two ghost
+// columns and two ghost rows on each side; on periodic axes the ghosts hold copies
+// of the wrapped-around nodes, written by the step kernel together with the nodes.
 //
-// A CTA owns a 32 x 16 tile of (x, y) columns and marches along z. For every plane p
-// it stages in shared memory, per species and direction i, the rows of the source
-// plane p - c_iz that the pull of the tile and of a one-node ring around it reads
-// (rows y0-1-c_iy .. y0+16-c_iy, columns x0-PAD .. x0+32+PAD). Rows are moved with
-// cp.async.bulk (16-byte aligned bulk copies, wrapped rows split in two) that
-// complete on an mbarrier, two planes in flight. From a staged plane every thread
-// pulls its node with constant-offset shared-memory loads, the colour field of the
-// plane (tile + ring) goes to a 4-slot ring buffer, and one plane behind, the owned
-// nodes are collided using the isotropic gradient read from that ring. The colour
-// field of the same step is thus available at all 18 neighbours without a second
-// pass over the populations. Links whose source lies beyond a bounce-back wall read
-// the node's own opposite population directly from global memory.
+// A CTA owns a 32 x 16 tile of (x, y) columns and marches along z over one part of
+// the lattice height. For every plane p it stages in shared memory, per species and
+// direction i, the 36 x 18 box of the source plane p - c_iz that the pull of the
+// tile and of a one-node ring around it reads (columns x0-2 .. x0+33, rows
+// y0-1-c_iy .. y0+16-c_iy): 38 TMA tensor copies issued by one thread, completing on
+// an mbarrier, two planes in flight. From a staged plane every thread pulls its
+// node with constant-offset shared-memory loads, the colour field of the plane
+// (tile + ring) goes to a 4-slot ring buffer, and one plane behind, the owned nodes
+// are collided using the isotropic gradient read from that ring. The colour field of
+// the same step is thus available at all 18 neighbours without a second pass over
+// the populations. Links whose source lies beyond a bounce-back wall read the
+// node's own opposite population directly from global memory.
 //
 // Work split: z is cut into `zparts` equal parts and every CTA marches one part of
 // one tile. CTAs are numbered part-major, so the CTAs resident at the same time work
 // on neighbouring tiles at the same heights: the halo rows one tile stages are the
 // rows its neighbours are reading, and come from L2 rather than HBM.
-// Lattices whose x extent is not a multiple of 32 (or that need element-wise
-// wrapping) stage rows with ordinary loads instead of bulk copies; the compute is
-// identical, so results do not depend on the staging path.
+#include <cuda.h>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
 
 constexpr int TX = 32, TY = 16, NT = TX * TY;
-constexpr int SH = TY + 2, SWP = TX + 2;   // colour-field ring: rows, columns
+constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
 
 template <class St>
 struct Geo {
     using T = typename St::T;
-    static constexpr int PAD = 16 / (int)sizeof(T);       // 16-byte alignment of rows
-    static constexpr int W = TX + 2 * PAD;                  // staged row length (elements)
-    static constexpr int ROWS = 2 * Q * SH;                 // staged rows per plane
-    static constexpr size_t STAGE_BYTES = (size_t)ROWS * W * sizeof(T);
+    // box width: columns x0-2 .. x0+33 (36), widened so a row is a multiple of 16 bytes
+    static constexpr int BW = ((TX + 4) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    static constexpr int BOX_BYTES = BW * SH * (int)sizeof(T);
+    static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
+    static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
+    static constexpr size_t STAGE_BYTES = (size_t)2 * Q * IK_BYTES;
     static constexpr size_t PHI_BYTES = 4 * SH * SWP * sizeof(float);
     static constexpr size_t SMEM = 2 * STAGE_BYTES + PHI_BYTES + 2 * sizeof(unsigned long long);
 };
@@ -49,13 +53,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
     uint32_t ok;
@@ -68,13 +69,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         unsigned long long* bar) {
-    mbar_expect_tx(bar, bytes);
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, unsigned long long* bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
@@ -94,11 +95,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 }
 
 // ---------------------------------------------------------------- the kernel
-template <class St>
-__global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
+template <class St, bool UnitOmega>
+__global__ void __launch_bounds__(NT, 1)
+step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
     using T = typename St::T;
     using G = Geo<St>;
-    constexpr int W = G::W, PAD = G::PAD;
+    constexpr int BW = G::BW, IKS = G::IKS;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
     float* sphi = reinterpret_cast<float*>(smem + 2 * G::STAGE_BYTES);   // [4][SH][SWP]
@@ -112,12 +114,13 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
     const size_t plane = (size_t)p.nx * p.ny;
 
     if (tid == 0) {
-        mbar_init(&bars[0], NT);
-        mbar_init(&bars[1], NT);
+        mbar_init(&bars[0], 2 * Q);   // one arrival per (species, direction) box
+        mbar_init(&bars[1], 2 * Q);
         fence_mbar_init();
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fin_map)) : "memory");
     }
     __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
+    uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
     bool failed = false;
 
     // one (z part, tile) work item per CTA, part-major
@@ -128,7 +131,6 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
         const int ze = (int)((long long)p.nz * (part + 1) / p.zparts);
         const int x0 = (tile % p.tiles_x) * TX, y0 = (tile / p.tiles_x) * TY;
         const int xw = min(TX, p.nx - x0), yh = min(TY, p.ny - y0);   // owned extent
-        const bool fast = p.bulk_ok;   // aligned bulk-copy staging possible
 
         // ---- this thread's owned node and (optionally) one ring node
         const int otx = lane, oty = warp;
@@ -146,54 +148,38 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
             if (p.wall_y && (gy < 0 || gy >= p.ny)) ring = false;  // beyond a wall: unused
         }
 
-        // ---- staging of plane pl into buffer b (rows of every species/direction)
+        // ---- staging of plane pl into buffer b: one 36 x 18 box per species and
+        // direction, taken from source plane pl - c_iz; thread 0 issues all of them
+        // threads 0..37 each issue the box of one (species, direction) and arrive on
+        // the barrier (with 0 bytes if the box is not needed)
+        const int my_ik = tid < 2 * Q ? tid : -1;
+        const int my_i = my_ik < Q ? my_ik : my_ik - Q;
+        const int my_cy = my_ik >= 0 ? cy(my_i) : 0, my_cz = my_ik >= 0 ? cz(my_i) : 0;
         auto issue = [&](int b, int pl) {
-            T* st = stage0 + (size_t)b * (G::ROWS * W);
-            const bool pvalid = !failed && (!p.wall_z || (pl >= 0 && pl < p.nz));
-            if (pvalid) {
-                for (int row = tid; row < G::ROWS; row += NT) {
-                    const int ik = row / SH, r = row - ik * SH;
-                    const int i = ik < Q ? ik : ik - Q;
-                    const int zs0 = pl - cz(i);
-                    const int ys0 = y0 - 1 - cy(i) + r;
-                    if ((p.wall_z && (zs0 < 0 || zs0 >= p.nz)) || (p.wall_y && (ys0 < 0 || ys0 >= p.ny)))
-                        continue;
-                    const int zs = wrapi(zs0, p.nz), ys = wrapi(ys0, p.ny);
-                    const T* src = fin + (size_t)ik * p.N + (size_t)zs * plane + (size_t)ys * p.nx;
-                    T* dst = st + (size_t)row * W;
-                    if (fast) {
-                        // columns x0-PAD .. x0+TX+PAD-1, wrapped at 0 and nx in whole pieces
-                        int xa = x0 - PAD, c = 0;
-                        if (xa < 0) {
-                            bulk_g2s(dst, src + (p.nx + xa), (uint32_t)(-xa * sizeof(T)), &bars[b]);
-                            c = -xa;
-                            xa = 0;
-                        }
-                        int len = min(W - c, p.nx - xa);
-                        bulk_g2s(dst + c, src + xa, (uint32_t)(len * sizeof(T)), &bars[b]);
-                        c += len;
-                        if (c < W) {
-                            bulk_g2s(dst + c, src, (uint32_t)((W - c) * sizeof(T)), &bars[b]);
-                        }
-                    } else {
-                        // element-wise: only the columns the pulls read (PAD-2 .. TX+PAD+1)
-                        for (int c = PAD - 2; c < TX + PAD + 2; ++c)
-                            dst[c] = src[wrapi(x0 - PAD + c, p.nx)];
-                    }
-                }
+            if (my_ik < 0) return;
+            T* st = stage0 + (size_t)b * (2 * Q * IKS);
+            const int zs0 = pl - my_cz;
+            const bool need = !failed && (!p.wall_z || (pl >= 0 && pl < p.nz)) &&
+                              !(p.wall_z && (zs0 < 0 || zs0 >= p.nz));
+            if (need) {
+                // box origin: x = x0 - 2 and y = y0 - 1 - c_iy, in padded coordinates
+                mbar_arrive_tx(&bars[b], (uint32_t)G::BOX_BYTES);
+                tma_load_4d(st + (size_t)my_ik * IKS, &fin_map, x0, y0 + 1 - my_cy,
+                            wrap_near(zs0, p.nz), my_ik, &bars[b]);
+            } else {
+                mbar_arrive_tx(&bars[b], 0u);
             }
-            mbar_arrive(&bars[b]);
         };
         auto wait = [&](int b) {
-            if (!failed && !mbar_wait(&bars[b], parity[b], p.err)) failed = true;
-            parity[b] ^= 1u;
+            if (!failed && !mbar_wait(&bars[b], (parity >> b) & 1u, p.err)) failed = true;
+            parity ^= 1u << b;
         };
 
         // ---- pull of node (tx, ty) of plane pl from staged buffer b
         // returns densities; for keep == true also the total populations
         auto pull = [&](int b, int pl, int tx, int ty, float (&ft)[Q], float& rr, float& rb,
                         bool keep) {
-            const T* st = stage0 + (size_t)b * (G::ROWS * W) + (size_t)(ty + 1) * W + (tx + PAD);
+            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + 2);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
@@ -203,19 +189,19 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float ref = wgt(i) * refh;
-                vr[i] = St::cvt(st[(size_t)i * SH * W - cx(i)], ref);
-                vb[i] = St::cvt(st[(size_t)(Q + i) * SH * W - cx(i)], ref);
+                vr[i] = St::cvt(st[(size_t)i * IKS - cx(i)], ref);
+                vb[i] = St::cvt(st[(size_t)(Q + i) * IKS - cx(i)], ref);
             }
             if (any_wall) {
-                const size_t self = (size_t)pl * plane + (size_t)wrapi(gy, p.ny) * p.nx + wrapi(x0 + tx, p.nx);
+                const size_t self = pidx(p.pitch, p.nyp, wrap_near(x0 + tx, p.nx), gy, pl);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
                                      (cz(i) > 0 && zlo) || (cz(i) < 0 && zhi);
                     if (out) {
                         const float ref = wgt(i) * refh;
-                        vr[i] = St::load(fin, (size_t)opp(i) * p.N + self, ref);
-                        vb[i] = St::load(fin, (size_t)(Q + opp(i)) * p.N + self, ref);
+                        vr[i] = St::load(fin, (size_t)opp(i) * p.P + self, ref);
+                        vb[i] = St::load(fin, (size_t)(Q + opp(i)) * p.P + self, ref);
                     }
                 }
             }
@@ -234,7 +220,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
         auto densities = [&](int b, int pl, float (&ft)[Q], float& rr, float& rb, bool keep) {
             const bool pvalid = !p.wall_z || (pl >= 0 && pl < p.nz);
             if (!pvalid) return;
-            const int plw = wrapi(pl, p.nz);
+            const int plw = wrap_near(pl, p.nz);
             if (owned) {
                 pull(b, plw, otx, oty, ft, rr, rb, keep);
                 phi_at(slot(pl), otx, oty) = (rr - rb) / (rr + rb);
@@ -246,8 +232,33 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
             }
         };
 
+        // ---- ghost copies this thread's node writes (periodic axes, edge nodes)
+        const int gxn = x0 + otx, gyn = y0 + oty;
+        int ng = 0;
+        long long goff[3] = {0, 0, 0};
+        if (owned && p.ghost_in_kernel) {
+            int dxg = 0, dyg = 0;
+            if (gxn < 2) dxg = p.nx;
+            else if (gxn >= p.nx - 2) dxg = -p.nx;
+            if (!p.wall_y) {
+                if (gyn < 2) dyg = p.ny;
+                else if (gyn >= p.ny - 2) dyg = -p.ny;
+            }
+            const long long oy = (long long)dyg * p.pitch;
+            ng = (dxg != 0) + (dyg != 0) + (dxg != 0 && dyg != 0);
+            goff[0] = dxg ? (long long)dxg : oy;
+            goff[1] = oy;
+            goff[2] = dxg + oy;
+        }
+        const bool warp_ghost = __any_sync(0xffffffffu, ng > 0);
+
         float cur[Q], nxt[Q];
         float c_rr = 0.f, c_rb = 0.f, n_rr = 0.f, n_rb = 0.f;
+        const bool use_nc = p.A_nc > 0.0f;
+        const size_t col = (size_t)gyn * p.nx + gxn;   // owned column (unpadded fields)
+        const float fx_y = owned ? __ldg(p.fx_row + gyn) : 0.0f;
+        // A_h of the plane being collided, loaded one iteration ahead
+        float ah_cur = (owned && use_nc) ? p.ah[(size_t)zb * plane + col] : 0.0f;
 
         // ---- prologue: planes zb-1 and zb
         fence_proxy_async();
@@ -266,14 +277,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
             const int bn = (z + 1 - zb + 1) & 1;   // buffer of plane z+1
             fence_proxy_async();
             if (z + 2 <= ze) issue(bn ^ 1, z + 2);
+            const float ah_nxt =
+                (owned && use_nc && z + 1 < ze) ? p.ah[(size_t)(z + 1) * plane + col] : 0.0f;
             wait(bn);
             densities(bn, z + 1, nxt, n_rr, n_rb, true);
             __syncthreads();
             if (owned && !failed) {
-                const int x = x0 + otx, y = y0 + oty;
-                const bool ylo = p.wall_y && y == 0, yhi = p.wall_y && y == p.ny - 1;
+                const bool ylo = p.wall_y && gyn == 0, yhi = p.wall_y && gyn == p.ny - 1;
                 const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
-                const float phic = phi_at(slot(z), otx, oty);
+                const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
+                const float phic = phi_at(s1, otx, oty);
                 // isotropic colour gradient, 3 w_i = 1/6 (faces), 1/12 (edges); a
                 // neighbour beyond a wall takes the centre value
                 float Gx = 0.f, Gy = 0.f, Gz = 0.f;
@@ -282,23 +295,23 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
                     if (i == 9) continue;
                     const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
                                       (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
-                    const float v = wall ? phic : phi_at(slot(z + cz(i)), otx + cx(i), oty + cy(i));
+                    const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
+                    const float v = wall ? phic : phi_at(sl, otx + cx(i), oty + cy(i));
                     const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
                     if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
                     if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
                     if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
                 }
-                const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
-                float Fx = __ldg(p.fx_row + y), Fy = p.gy, Fz = p.gz;
-                if (p.A_nc > 0.0f) {
+                const size_t node = (size_t)z * plane + col;
+                float Fx = fx_y, Fy = p.gy, Fz = p.gz;
+                if (use_nc) {
                     // near-contact force A_h G, A_h measured by the near-contact pass;
                     // the entry is consumed (reset to 0) so that only the next pass's
                     // candidates are nonzero when the next step reads it
-                    const float ah = p.ah[node];
-                    if (ah != 0.0f) {
-                        Fx += ah * Gx;
-                        Fy += ah * Gy;
-                        Fz += ah * Gz;
+                    if (ah_cur != 0.0f) {
+                        Fx += ah_cur * Gx;
+                        Fy += ah_cur * Gy;
+                        Fz += ah_cur * Gz;
                         p.ah[node] = 0.0f;
                     }
                     // this node's gradient is the next pass's lagged gradient: list it
@@ -313,9 +326,16 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
                         p.cand[base + __popc(m & ((1u << lane) - 1u))] = (int)node;
                     }
                 }
-                collide_store<St>(p, cur, c_rr, c_rb, Gx, Gy, Gz, Fx, Fy, Fz, fout, node);
+                T* out = fout + pidx(p.pitch, p.nyp, gxn, gyn, z);
+                if (warp_ghost)
+                    collide_store<St, UnitOmega, true>(p, cur, c_rr, c_rb, Gx, Gy, Gz, Fx, Fy, Fz,
+                                                       out, ng, goff);
+                else
+                    collide_store<St, UnitOmega, false>(p, cur, c_rr, c_rb, Gx, Gy, Gz, Fx, Fy,
+                                                        Fz, out, 0, goff);
                 p.phi_out[node] = phic;
             }
+            ah_cur = ah_nxt;
 #pragma unroll
             for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
             c_rr = n_rr;
@@ -327,7 +347,29 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(const StepParams p) {
         // to land before the CTA exits
         for (int b = 0; b < 2; ++b)
             for (uint32_t it = 0; it < (1u << 20); ++it)
-                if (mbar_try_wait(&bars[b], parity[b])) break;
+                if (mbar_try_wait(&bars[b], (parity >> b) & 1u)) break;
+    }
+}
+
+// ---------------------------------------------------------------- ghost fill
+// Copies the wrapped-around nodes into the ghost columns/rows of periodic axes, for
+// every species and direction (after the state was set, and after each step on
+// lattices too small for the step kernel to write its ghosts itself).
+template <class St>
+__global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
+    const size_t per = p.plane_p * p.nz;   // padded positions per block
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < per;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int xp = (int)(k % p.pitch);
+        const int yp = (int)((k / p.pitch) % p.nyp);
+        const int z = (int)(k / p.plane_p);
+        const int x = xp - 2, y = yp - 2;
+        const bool xin = x >= 0 && x < p.nx, yin = y >= 0 && y < p.ny;
+        if (xin && yin) continue;
+        if (x < -2 || x > p.nx + 1) continue;              // row padding, unused
+        if (!yin && (p.wall_y || y < -2 || y > p.ny + 1)) continue;
+        const size_t src = pidx(p.pitch, p.nyp, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
+        for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + k] = f[(size_t)ik * p.P + src];
     }
 }
 
@@ -395,29 +437,59 @@ cudaError_t launch_nc(const StepParams& p, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class St>
-static cudaError_t launch_tpl(const StepParams& p, int grid, cudaStream_t s) {
+template <class St, bool U>
+static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map, int grid,
+                               cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<St, U>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Geo<St>::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    step_kernel<St><<<grid, NT, Geo<St>::SMEM, s>>>(p);
+    step_kernel<St, U><<<grid, NT, Geo<St>::SMEM, s>>>(p, map);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepParams& p, int storage, int grid, cudaStream_t s) {
+// omega == 1 everywhere (equal relaxation times tau = 1) drops the non-equilibrium
+// terms of the collision
+template <class St>
+static cudaError_t launch_tpl(const StepParams& p, const CUtensorMap& map, int grid,
+                              cudaStream_t s) {
+    if (!p.var_tau && p.omega0 == 1.0f) return launch_tpl2<St, true>(p, map, grid, s);
+    return launch_tpl2<St, false>(p, map, grid, s);
+}
+
+cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage, int grid,
+                        cudaStream_t s) {
     switch (storage) {
-        case 0: return launch_tpl<StoreF32>(p, grid, s);
-        case 1: return launch_tpl<StoreF16>(p, grid, s);
-        case 2: return launch_tpl<StoreBF16>(p, grid, s);
+        case 0: return launch_tpl<StoreF32>(p, map, grid, s);
+        case 1: return launch_tpl<StoreF16>(p, map, grid, s);
+        case 2: return launch_tpl<StoreBF16>(p, map, grid, s);
     }
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
+                              cudaStream_t s) {
+    const int threads = 256;
+    size_t blocks = (p.plane_p * p.nz + threads - 1) / threads;
+    const size_t cap = (size_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    switch (storage) {
+        case 0: ghost_fill_kernel<StoreF32><<<(unsigned)blocks, threads, 0, s>>>((float*)f, p); break;
+        case 1: ghost_fill_kernel<StoreF16><<<(unsigned)blocks, threads, 0, s>>>((__half*)f, p); break;
+        case 2: ghost_fill_kernel<StoreBF16><<<(unsigned)blocks, threads, 0, s>>>((__nv_bfloat16*)f, p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Geometry the host needs for the tensor maps.
 int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
+int step_box_rows() { return SH; }
+int step_box_width(int storage) { return storage == 0 ? Geo<StoreF32>::BW : Geo<StoreF16>::BW; }
 
 }  // namespace lbm
