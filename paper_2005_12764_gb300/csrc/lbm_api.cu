@@ -25,6 +25,8 @@ int step_tile_x();
 int step_tile_y();
 int step_box_rows();
 int step_box_width(int storage);
+int step_ctas_per_sm();
+int step_pad_x(int storage);
 }  // namespace lbm
 
 using namespace lbm;
@@ -34,8 +36,9 @@ struct lbm_ctx {
     size_t N = 0;
     size_t elem = 4;            // bytes per stored population
     int pitch = 0, nyp = 0;     // padded row length and rows per plane (ghosts included)
+    int padx = 0;               // interior offset within a padded row
     size_t P = 0;               // elements per padded [z][y][x] block
-    CUtensorMap tmap[2];        // TMA descriptors of the two population copies
+    CUtensorMap tmap[2];        // TMA load descriptors of the two population copies
     void* f[2] = {nullptr, nullptr};
     float* phi[2] = {nullptr, nullptr};
     float* fx_row = nullptr;
@@ -92,7 +95,7 @@ __device__ __forceinline__ size_t node_pidx(const StepParams& sp, size_t n) {
     const int z = (int)(n / plane);
     const int rem = (int)(n - (size_t)z * plane);
     const int y = rem / sp.nx, x = rem - y * sp.nx;
-    return pidx(sp.pitch, sp.nyp, x, y, z);
+    return pidx(sp.pitch, sp.nyp, sp.padx, x, y, z);
 }
 
 // f_i^k = f_i^eq(rho_k, u), Eq. (2); both colour-field buffers get phi.
@@ -382,17 +385,18 @@ int grid_for(size_t n, int num_sms) {
 // ---------------------------------------------------------------- helpers
 static size_t elem_bytes(int storage) { return storage == 0 ? 4 : 2; }
 
-// Padded population layout: two ghost columns and rows on each side, row length
-// rounded up to a multiple of 16 bytes (TMA row alignment).
+// Padded population layout: two ghost columns left and right of each row, the row
+// length a multiple of 16 bytes (TMA alignment); two ghost rows above and below.
 struct PadLayout {
-    int pitch, nyp;
+    int pitch, nyp, padx;
     size_t P;
 };
 static PadLayout pad_layout(const lbm_params& p) {
     const int per16 = (int)(16 / elem_bytes(p.storage));
     PadLayout L;
-    L.pitch = (p.nx + 4 + per16 - 1) / per16 * per16;
-    L.pitch = std::max(L.pitch, 40);                    // at least one staged box wide
+    L.padx = step_pad_x(p.storage);
+    L.pitch = (p.nx + 2 * L.padx + per16 - 1) / per16 * per16;
+    L.pitch = std::max(L.pitch, 72);                    // at least one staged box wide
     L.nyp = std::max(p.ny + 4, 18);                     // at least one staged box high
     L.P = (size_t)L.pitch * L.nyp * p.nz;
     return L;
@@ -447,6 +451,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.N = c->N;
     s.pitch = c->pitch;
     s.nyp = c->nyp;
+    s.padx = c->padx;
     s.plane_p = (size_t)c->pitch * c->nyp;
     s.P = c->P;
     s.ghost_in_kernel = (p.nx >= 4 && (p.wall_y || p.ny >= 4)) ? 1 : 0;
@@ -476,7 +481,7 @@ static void fill_step_params(lbm_ctx* c) {
     // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
     // pipeline fill), the cost of a part-major launch.
     const long long tiles = (long long)s.tiles_x * s.tiles_y;
-    const int S = c->num_sms > 0 ? c->num_sms : 1;
+    const int S = (c->num_sms > 0 ? c->num_sms : 1) * step_ctas_per_sm();
     int best_k = 1;
     double best = 1e300;
     for (int k = 1; k <= p.nz && k <= 4096; ++k) {
@@ -523,6 +528,7 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const PadLayout L = pad_layout(*p);
     c->pitch = L.pitch;
     c->nyp = L.nyp;
+    c->padx = L.padx;
     c->P = L.P;
     const size_t pop_bytes = 2 * Q * c->P * c->elem;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {

@@ -57,6 +57,7 @@ struct StoreF32 {
     __device__ __forceinline__ static float load(const T* p, size_t i, float) { return __ldg(p + i); }
     __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
     __device__ __forceinline__ static float cvt(T v, float) { return v; }
+    __device__ __forceinline__ static T enc(float v, float) { return v; }
 };
 struct StoreF16 {
     using T = __half;
@@ -68,6 +69,7 @@ struct StoreF16 {
         p[i] = __float2half_rn(v - ref);
     }
     __device__ __forceinline__ static float cvt(T v, float ref) { return __half2float(v) + ref; }
+    __device__ __forceinline__ static T enc(float v, float ref) { return __float2half_rn(v - ref); }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
@@ -79,6 +81,7 @@ struct StoreBF16 {
         p[i] = __float2bfloat16_rn(v - ref);
     }
     __device__ __forceinline__ static float cvt(T v, float ref) { return __bfloat162float(v) + ref; }
+    __device__ __forceinline__ static T enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
 };
 
 // ---------------------------------------------------------------- parameters
@@ -97,9 +100,10 @@ struct StepParams {
     float gy, gz;
     int nx, ny, nz;
     size_t N;               // nodes (fields phi, ah are [N], x fastest)
-    // population arrays are padded: two ghost columns and rows on each side, row
-    // pitch rounded up to 16 bytes; one [nz][nyp][pitch] block per species/direction
-    int pitch, nyp;
+    // population arrays are padded: ghost columns and rows around the lattice (the
+    // interior starts padx columns in, 16 bytes), row pitch a multiple of 16 bytes;
+    // one [nz][nyp][pitch] block per species/direction
+    int pitch, nyp, padx;
     size_t plane_p, P;      // pitch * nyp, plane_p * nz
     int wall_y, wall_z;
     int var_tau;            // 0: omega0 everywhere; 1: mixture rule per node
@@ -137,8 +141,8 @@ __device__ __forceinline__ int wrap_near(int a, int n) {
 }
 
 // Index of node (x, y, z) in one padded population block (x, y may be ghosts, -2..n+1).
-__host__ __device__ __forceinline__ size_t pidx(int pitch, int nyp, int x, int y, int z) {
-    return ((size_t)z * nyp + (y + 2)) * pitch + (x + 2);
+__host__ __device__ __forceinline__ size_t pidx(int pitch, int nyp, int padx, int x, int y, int z) {
+    return ((size_t)z * nyp + (y + 2)) * pitch + (x + padx);
 }
 
 // Trilinear sample of the lagged colour field at node (x, y, z) + offset o; false if
@@ -295,6 +299,12 @@ __device__ __forceinline__ float sum19(const float (&v)[Q]) {
     return ((a + b) + (c + d)) + e;
 }
 
+// Colour field (rho_r - rho_b)/(rho_r + rho_b); every thread that evaluates a node's
+// colour uses this same expression, so it is bitwise the same wherever computed.
+__device__ __forceinline__ float colour(float rr, float rb) {
+    return (rr - rb) * __frcp_rn(rr + rb);
+}
+
 // Threshold below which the colour gradient is treated as zero (no perturbation,
 // no recolouring segregation): above the rounding level (~1e-7) of the FP32
 // stencil on an O(1) colour field, so FP32 and FP64 evaluations agree on the branch.
@@ -311,27 +321,34 @@ constexpr float kGradZero = 1e-6f;
 // rounded once and all other terms are O(|u|, |F|, |G|) corrections. Opposite
 // directions share their symmetric terms. The rest direction takes minus the sum of
 // the other perturbations, so the perturbation conserves mass exactly.
-// Output of one value to its node and, on edge nodes of periodic axes, to the ghost
-// copies (ng extra offsets relative to the node, in elements).
+// Output of the collision: one value per direction block k (species * 19 + direction)
+// handed to an emitter functor, emit(k, value, ref), with k a compile-time constant
+// after unrolling. Two emitters are used: one writes a shared-memory output tile
+// (stored to global memory by TMA), the other writes global memory directly.
 template <class St, bool Ghost>
-__device__ __forceinline__ void put(typename St::T* out, size_t off, float v, float ref, int ng,
-                                    const long long (&goff)[3]) {
-    St::store(out, off, v, ref);
-    if (Ghost) {
+struct GlobalEmit {
+    typename St::T* plane_out;   // start of this plane in block 0
+    size_t P;
+    uint32_t off;                // node offset within the padded plane
+    int ng;
+    int goff[3];                 // ghost offsets within the plane
+    __device__ __forceinline__ void operator()(int k, float v, float ref) const {
+        typename St::T* base = plane_out + (size_t)k * P;
+        St::store(base, off, v, ref);
+        if (Ghost) {
 #pragma unroll
-        for (int g = 0; g < 3; ++g)
-            if (g < ng) St::store(out + goff[g], off, v, ref);
+            for (int g = 0; g < 3; ++g)
+                if (g < ng) St::store(base, (uint32_t)((int)off + goff[g]), v, ref);
+        }
     }
-}
+};
 
-template <class St, bool UnitOmega, bool Ghost>
+template <class St, bool UnitOmega, class Emit>
 __device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
                                               float rb, float Gx, float Gy, float Gz, float Fx,
-                                              float Fy, float Fz, typename St::T* out, int ng,
-                                              const long long (&goff)[3]) {
-    const size_t N = p.P;
+                                              float Fy, float Fz, const Emit& emit) {
     const float rho = rr + rb;
-    const float inv_rho = 1.0f / rho;
+    const float inv_rho = __frcp_rn(rho);
     float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -347,12 +364,16 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         omega = 1.0f / (3.0f / inv_nu + 0.5f);
     }
     const float om1 = UnitOmega ? 0.0f : 1.0f - omega;
-    const float dx = Fx * inv_rho, dy = Fy * inv_rho, dz = Fz * inv_rho;
+    // BGK + EDM source: f' = f^eq(rho, U) + (1 - omega)(f - f^eq(rho, u)) with the
+    // shifted velocity U = u + F/rho, since the source f^eq(U) - f^eq(u) and the
+    // relaxed part omega f^eq(u) + (1 - omega) f combine to that (Eqs. 1, 9)
+    const float Ux = ux + Fx * inv_rho, Uy = uy + Fy * inv_rho, Uz = uz + Fz * inv_rho;
+    const float U15 = 1.5f * (Ux * Ux + Uy * Uy + Uz * Uz);
     const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float dd15 = 1.5f * (dx * (2.0f * ux + dx) + dy * (2.0f * uy + dy) + dz * (2.0f * uz + dz));
-    const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
-    const bool has_g = gm >= kGradZero;
-    const float inv_g = has_g ? 1.0f / gm : 0.0f;
+    const float g2 = Gx * Gx + Gy * Gy + Gz * Gz;
+    const bool has_g = g2 >= kGradZero * kGradZero;
+    const float inv_g = has_g ? rsqrtf(g2) : 0.0f;
+    const float gm = g2 * inv_g;
     const float half_A_g = has_g ? 0.5f * (4.5f * omega * p.sigma) * gm : 0.0f;
     const float seg0 = has_g ? p.beta * rr * rb * inv_rho : 0.0f;
     const float ar = rr * inv_rho, ab = rb * inv_rho;
@@ -370,39 +391,38 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         const int o = opp(i);
         const bool face = csq(i) == 1;
         const float wr = face ? wr_f : wr_e;
-        const float a = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
-        const float b = (float)cx(i) * dx + (float)cy(i) * dy + (float)cz(i) * dz;
-        const float es = wr * (4.5f * a * a - usq15);
-        const float ea = wr * (3.0f * a);
-        const float ss = wr * (4.5f * b * (2.0f * a + b) - dd15);
-        const float sa = wr * (3.0f * b);
+        // f^eq(U) - w rho = e_sym +- e_asym for the pair (i, opposite)
+        const float v = (float)cx(i) * Ux + (float)cy(i) * Uy + (float)cz(i) * Uz;
+        const float es = wr * (4.5f * v * v - U15);
+        const float ea = wr * (3.0f * v);
         const float cg = (float)cx(i) * Gx + (float)cy(i) * Gy + (float)cz(i) * Gz;
         const float cn = cg * inv_g;
         const float dlt = (face ? hw_f : hw_e) * (cn * cn) - (face ? hb_f : hb_e);
         pert_sum += dlt;
-        float si = (es + ea) + (ss + sa) + dlt;
-        float so = (es - ea) + (ss - sa) + dlt;
+        float si = (es + ea) + dlt;
+        float so = (es - ea) + dlt;
         if (!UnitOmega) {
-            si += om1 * ((f[i] - wr) - (es + ea));
-            so += om1 * ((f[o] - wr) - (es - ea));
+            const float a = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+            const float qs = wr * (4.5f * a * a - usq15), qa = wr * (3.0f * a);
+            si += om1 * ((f[i] - wr) - (qs + qa));
+            so += om1 * ((f[o] - wr) - (qs - qa));
         }
         const float sg = (face ? sg_f : sg_e) * cn;
         const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
         const float w = wgt(i);
-        put<St, Ghost>(out, (size_t)i * N, wrr + (ar * si + sg), w * ref, ng, goff);
-        put<St, Ghost>(out, (size_t)o * N, wrr + (ar * so - sg), w * ref, ng, goff);
-        put<St, Ghost>(out, (size_t)(Q + i) * N, wrb + (ab * si - sg), w * ref, ng, goff);
-        put<St, Ghost>(out, (size_t)(Q + o) * N, wrb + (ab * so + sg), w * ref, ng, goff);
+        emit(i, wrr + (ar * si + sg), w * ref);
+        emit(o, wrr + (ar * so - sg), w * ref);
+        emit(Q + i, wrb + (ab * si - sg), w * ref);
+        emit(Q + o, wrb + (ab * so + sg), w * ref);
     }
     {
         constexpr int i = 9;
         const float w = wgt(i);
         const float wr = w * rho;
-        const float e0 = -wr * usq15;
-        float si = e0 - wr * dd15 - 2.0f * pert_sum;
-        if (!UnitOmega) si += om1 * ((f[i] - wr) - e0);
-        put<St, Ghost>(out, (size_t)i * N, w * rr + ar * si, w * ref, ng, goff);
-        put<St, Ghost>(out, (size_t)(Q + i) * N, w * rb + ab * si, w * ref, ng, goff);
+        float si = -wr * U15 - 2.0f * pert_sum;
+        if (!UnitOmega) si += om1 * ((f[i] - wr) + wr * usq15);
+        emit(i, w * rr + ar * si, w * ref);
+        emit(Q + i, w * rb + ab * si, w * ref);
     }
 }
 

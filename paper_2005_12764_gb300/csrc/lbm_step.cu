@@ -2,16 +2,19 @@
 // and the near-contact pass.
 //
 // Data layout: populations in [2 species][19 directions][z][y][x] (x fastest), two
-// copies (read one, write the other). Each [z][y][x] block is padded with two ghost
-// columns and two ghost rows on each side; on periodic axes the ghosts hold copies
-// of the wrapped-around nodes, written by the step kernel together with the nodes.
+// copies (read one, write the other). Each [z][y][x] block is padded with ghost
+// columns (the interior starts 16 bytes into a row) and two ghost rows on each side;
+// on periodic axes the ghosts next to the lattice hold copies of the wrapped-around
+// nodes, written by the step kernel together with the nodes.
 //
-// A CTA owns a 32 x 16 tile of (x, y) columns and marches along z over one part of
+// A CTA owns a TX x TY tile of (x, y) columns and marches along z over one part of
 // the lattice height. For every plane p it stages in shared memory, per species and
-// direction i, the 36 x 18 box of the source plane p - c_iz that the pull of the
-// tile and of a one-node ring around it reads (columns x0-2 .. x0+33, rows
-// y0-1-c_iy .. y0+16-c_iy): 38 TMA tensor copies issued by one thread, completing on
-// an mbarrier, two planes in flight. From a staged plane every thread pulls its
+// direction i, the (TX+4) x (TY+2) box of the source plane p - c_iz that the pull of
+// the tile and of a one-node ring around it reads (columns x0-2 .. x0+TX+1, rows
+// y0-1-c_iy .. y0+TY-c_iy): 38 TMA tensor copies, one per issuing thread, completing
+// on an mbarrier. The copy of plane p+2 is issued as soon as every thread has pulled
+// plane p+1, so it overlaps the collision of plane p; two CTAs share an SM, so one
+// CTA's pulls overlap the other's collisions. From a staged plane every thread pulls its
 // node with constant-offset shared-memory loads, the colour field of the plane
 // (tile + ring) goes to a 4-slot ring buffer, and one plane behind, the owned nodes
 // are collided using the isotropic gradient read from that ring. The colour field of
@@ -29,21 +32,24 @@
 
 namespace lbm {
 
-constexpr int TX = 32, TY = 16, NT = TX * TY;
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int STAGES = 1;      // staged planes per CTA
+constexpr int CTAS_PER_SM = 2;
 constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
 
 template <class St>
 struct Geo {
     using T = typename St::T;
-    // box width: columns x0-2 .. x0+33 (36), widened so a row is a multiple of 16 bytes
+    static constexpr int PADX = 2;                        // interior offset in a padded row
+    // load box: columns x0-2 .. x0+TX+1, widened so a row is a multiple of 16 bytes
     static constexpr int BW = ((TX + 4) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
     static constexpr int BOX_BYTES = BW * SH * (int)sizeof(T);
     static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
     static constexpr size_t STAGE_BYTES = (size_t)2 * Q * IK_BYTES;
     static constexpr size_t PHI_BYTES = 4 * SH * SWP * sizeof(float);
-    static constexpr size_t SMEM = 2 * STAGE_BYTES + PHI_BYTES + 2 * sizeof(unsigned long long);
+    static constexpr size_t SMEM = STAGES * STAGE_BYTES + PHI_BYTES + 2 * sizeof(unsigned long long);
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -96,21 +102,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 
 // ---------------------------------------------------------------- the kernel
 template <class St, bool UnitOmega>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, CTAS_PER_SM)
 step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
     using T = typename St::T;
     using G = Geo<St>;
-    constexpr int BW = G::BW, IKS = G::IKS;
+    constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
-    float* sphi = reinterpret_cast<float*>(smem + 2 * G::STAGE_BYTES);   // [4][SH][SWP]
+    float* sphi = reinterpret_cast<float*>(smem + STAGES * G::STAGE_BYTES);   // [4][SH][SWP]
     unsigned long long* bars =
-        reinterpret_cast<unsigned long long*>(smem + 2 * G::STAGE_BYTES + G::PHI_BYTES);
+        reinterpret_cast<unsigned long long*>(smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES);
 
     const T* __restrict__ fin = static_cast<const T*>(p.fin);
     T* __restrict__ fout = static_cast<T*>(p.fout);
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31;
     const size_t plane = (size_t)p.nx * p.ny;
 
     if (tid == 0) {
@@ -133,7 +139,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
         const int xw = min(TX, p.nx - x0), yh = min(TY, p.ny - y0);   // owned extent
 
         // ---- this thread's owned node and (optionally) one ring node
-        const int otx = lane, oty = warp;
+        const int otx = tid % TX, oty = tid / TX;
         const bool owned = otx < xw && oty < yh;
         int rtx = 0, rty = 0;
         bool ring = false;
@@ -148,8 +154,8 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             if (p.wall_y && (gy < 0 || gy >= p.ny)) ring = false;  // beyond a wall: unused
         }
 
-        // ---- staging of plane pl into buffer b: one 36 x 18 box per species and
-        // direction, taken from source plane pl - c_iz; thread 0 issues all of them
+        // ---- staging of plane pl into buffer b: one box per species and direction,
+        // taken from source plane pl - c_iz
         // threads 0..37 each issue the box of one (species, direction) and arrive on
         // the barrier (with 0 bytes if the box is not needed)
         const int my_ik = tid < 2 * Q ? tid : -1;
@@ -179,7 +185,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
         // returns densities; for keep == true also the total populations
         auto pull = [&](int b, int pl, int tx, int ty, float (&ft)[Q], float& rr, float& rb,
                         bool keep) {
-            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + 2);
+            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + PADX);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
@@ -193,7 +199,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                 vb[i] = St::cvt(st[(size_t)(Q + i) * IKS - cx(i)], ref);
             }
             if (any_wall) {
-                const size_t self = pidx(p.pitch, p.nyp, wrap_near(x0 + tx, p.nx), gy, pl);
+                const size_t self = pidx(p.pitch, p.nyp, PADX, wrap_near(x0 + tx, p.nx), gy, pl);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
@@ -223,84 +229,99 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             const int plw = wrap_near(pl, p.nz);
             if (owned) {
                 pull(b, plw, otx, oty, ft, rr, rb, keep);
-                phi_at(slot(pl), otx, oty) = (rr - rb) / (rr + rb);
+                phi_at(slot(pl), otx, oty) = colour(rr, rb);
             }
             if (ring) {
                 float dummy[Q], a, c;
                 pull(b, plw, rtx, rty, dummy, a, c, false);
-                phi_at(slot(pl), rtx, rty) = (a - c) / (a + c);
+                phi_at(slot(pl), rtx, rty) = colour(a, c);
             }
         };
 
-        // ---- ghost copies this thread's node writes (periodic axes, edge nodes)
+        // ---- ghost copies this thread's node writes (periodic axes, edge nodes), as
+        // offsets within a padded plane
         const int gxn = x0 + otx, gyn = y0 + oty;
-        int ng = 0;
-        long long goff[3] = {0, 0, 0};
-        if (owned && p.ghost_in_kernel) {
+        // (recomputed where used, to keep them out of the registers live in the march)
+        auto ghost_offsets = [&](int (&goff)[3]) {
             int dxg = 0, dyg = 0;
-            if (gxn < 2) dxg = p.nx;
-            else if (gxn >= p.nx - 2) dxg = -p.nx;
-            if (!p.wall_y) {
-                if (gyn < 2) dyg = p.ny;
-                else if (gyn >= p.ny - 2) dyg = -p.ny;
+            if (owned && p.ghost_in_kernel) {
+                if (gxn < 2) dxg = p.nx;
+                else if (gxn >= p.nx - 2) dxg = -p.nx;
+                if (!p.wall_y) {
+                    if (gyn < 2) dyg = p.ny;
+                    else if (gyn >= p.ny - 2) dyg = -p.ny;
+                }
             }
-            const long long oy = (long long)dyg * p.pitch;
-            ng = (dxg != 0) + (dyg != 0) + (dxg != 0 && dyg != 0);
-            goff[0] = dxg ? (long long)dxg : oy;
+            const int oy = dyg * p.pitch;
+            goff[0] = dxg ? dxg : oy;
             goff[1] = oy;
             goff[2] = dxg + oy;
+            return (dxg != 0) + (dyg != 0) + (dxg != 0 && dyg != 0);
+        };
+        bool warp_ghost;
+        {
+            int g[3];
+            warp_ghost = __any_sync(0xffffffffu, ghost_offsets(g) > 0);
         }
-        const bool warp_ghost = __any_sync(0xffffffffu, ng > 0);
+        // this node's offset within a padded plane
+        const uint32_t toff = (uint32_t)((gyn + 2) * p.pitch + (gxn + PADX));
 
-        float cur[Q], nxt[Q];
-        float c_rr = 0.f, c_rb = 0.f, n_rr = 0.f, n_rb = 0.f;
         const bool use_nc = p.A_nc > 0.0f;
         const size_t col = (size_t)gyn * p.nx + gxn;   // owned column (unpadded fields)
         const float fx_y = owned ? __ldg(p.fx_row + gyn) : 0.0f;
-        // A_h of the plane being collided, loaded one iteration ahead
-        float ah_cur = (owned && use_nc) ? p.ah[(size_t)zb * plane + col] : 0.0f;
+        const bool ylo = p.wall_y && gyn == 0, yhi = p.wall_y && gyn == p.ny - 1;
 
-        // ---- prologue: planes zb-1 and zb
-        fence_proxy_async();
-        issue(0, zb - 1);
-        issue(1, zb);
-        wait(0);
-        densities(0, zb - 1, nxt, n_rr, n_rb, false);
-        __syncthreads();
-        fence_proxy_async();
-        issue(0, zb + 1);
-        wait(1);
-        densities(1, zb, cur, c_rr, c_rb, true);
-        __syncthreads();
-
-        for (int z = zb; z < ze; ++z) {
-            const int bn = (z + 1 - zb + 1) & 1;   // buffer of plane z+1
-            fence_proxy_async();
-            if (z + 2 <= ze) issue(bn ^ 1, z + 2);
+        // one plane of the march: densities of plane z+1 into (nx_f, nx_rr, nx_rb), then
+        // the collision of plane z from (cu, cu_rr, cu_rb); A_h is carried in ah_c
+        auto march = [&](int z, float (&cu)[Q], float cu_rr, float cu_rb, float (&nx_f)[Q],
+                         float& nx_rr, float& nx_rb, float& ah_c) {
+            // buffer of plane z+1; with two stages plane z+2 is issued before the wait,
+            // with one stage right after the barrier that frees the buffer
+            const int bn = STAGES == 2 ? ((z + 1 - zb + 1) & 1) : 0;
+            if (STAGES == 2) {
+                fence_proxy_async();
+                if (z + 2 <= ze) issue(bn ^ 1, z + 2);
+            }
             const float ah_nxt =
                 (owned && use_nc && z + 1 < ze) ? p.ah[(size_t)(z + 1) * plane + col] : 0.0f;
             wait(bn);
-            densities(bn, z + 1, nxt, n_rr, n_rb, true);
+            densities(bn, z + 1, nx_f, nx_rr, nx_rb, true);
             __syncthreads();
+            if (STAGES == 1) {
+                fence_proxy_async();
+                if (z + 2 <= ze) issue(0, z + 2);
+            }
             if (owned && !failed) {
-                const bool ylo = p.wall_y && gyn == 0, yhi = p.wall_y && gyn == p.ny - 1;
                 const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
                 const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
                 const float phic = phi_at(s1, otx, oty);
                 // isotropic colour gradient, 3 w_i = 1/6 (faces), 1/12 (edges); a
                 // neighbour beyond a wall takes the centre value
                 float Gx = 0.f, Gy = 0.f, Gz = 0.f;
+                if (!(ylo || yhi || zlo || zhi)) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (i == 9) continue;
-                    const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
-                                      (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
-                    const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
-                    const float v = wall ? phic : phi_at(sl, otx + cx(i), oty + cy(i));
-                    const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
-                    if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
-                    if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
-                    if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+                    for (int i = 0; i < Q; ++i) {
+                        if (i == 9) continue;
+                        const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
+                        const float v = phi_at(sl, otx + cx(i), oty + cy(i));
+                        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
+                        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
+                        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
+                        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        if (i == 9) continue;
+                        const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
+                                          (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
+                        const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
+                        const float v = wall ? phic : phi_at(sl, otx + cx(i), oty + cy(i));
+                        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
+                        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
+                        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
+                        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+                    }
                 }
                 const size_t node = (size_t)z * plane + col;
                 float Fx = fx_y, Fy = p.gy, Fz = p.gz;
@@ -308,10 +329,10 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                     // near-contact force A_h G, A_h measured by the near-contact pass;
                     // the entry is consumed (reset to 0) so that only the next pass's
                     // candidates are nonzero when the next step reads it
-                    if (ah_cur != 0.0f) {
-                        Fx += ah_cur * Gx;
-                        Fy += ah_cur * Gy;
-                        Fz += ah_cur * Gz;
+                    if (ah_c != 0.0f) {
+                        Fx += ah_c * Gx;
+                        Fy += ah_c * Gy;
+                        Fz += ah_c * Gz;
                         p.ah[node] = 0.0f;
                     }
                     // this node's gradient is the next pass's lagged gradient: list it
@@ -326,26 +347,66 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                         p.cand[base + __popc(m & ((1u << lane) - 1u))] = (int)node;
                     }
                 }
-                T* out = fout + pidx(p.pitch, p.nyp, gxn, gyn, z);
-                if (warp_ghost)
-                    collide_store<St, UnitOmega, true>(p, cur, c_rr, c_rb, Gx, Gy, Gz, Fx, Fy, Fz,
-                                                       out, ng, goff);
-                else
-                    collide_store<St, UnitOmega, false>(p, cur, c_rr, c_rb, Gx, Gy, Gz, Fx, Fy,
-                                                        Fz, out, 0, goff);
+                T* plane_out = fout + (size_t)z * p.plane_p;
+                if (warp_ghost) {
+                    GlobalEmit<St, true> em{plane_out, p.P, toff, 0, {0, 0, 0}};
+                    em.ng = ghost_offsets(em.goff);
+                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, Gx, Gy, Gz, Fx, Fy, Fz, em);
+                } else {
+                    const GlobalEmit<St, false> em{plane_out, p.P, toff, 0, {0, 0, 0}};
+                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, Gx, Gy, Gz, Fx, Fy, Fz, em);
+                }
                 p.phi_out[node] = phic;
             }
-            ah_cur = ah_nxt;
+            ah_c = ah_nxt;
+        };
+
+        float fa[Q], fb[Q];
+        float a_rr = 0.f, a_rb = 0.f, b_rr = 0.f, b_rb = 0.f;
+        // A_h of the plane being collided, loaded one iteration ahead
+        float ah_c = (owned && use_nc) ? p.ah[(size_t)zb * plane + col] : 0.0f;
+
+        // ---- prologue: planes zb-1 and zb
+        if (STAGES == 2) {
+            fence_proxy_async();
+            issue(0, zb - 1);
+            issue(1, zb);
+            wait(0);
+            densities(0, zb - 1, fb, b_rr, b_rb, false);
+            __syncthreads();
+            fence_proxy_async();
+            issue(0, zb + 1);
+            wait(1);
+            densities(1, zb, fa, a_rr, a_rb, true);
+            __syncthreads();
+        } else {
+            fence_proxy_async();
+            issue(0, zb - 1);
+            wait(0);
+            densities(0, zb - 1, fb, b_rr, b_rb, false);
+            __syncthreads();
+            fence_proxy_async();
+            issue(0, zb);
+            wait(0);
+            densities(0, zb, fa, a_rr, a_rb, true);
+            __syncthreads();
+            fence_proxy_async();
+            issue(0, zb + 1);
+        }
+
+        // ---- the march: plane z is collided from fa while plane z+1 is pulled into fb
+        for (int z = zb; z < ze; ++z) {
+            march(z, fa, a_rr, a_rb, fb, b_rr, b_rb, ah_c);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
-            c_rr = n_rr;
-            c_rb = n_rb;
+            for (int i = 0; i < Q; ++i) fa[i] = fb[i];
+            a_rr = b_rr;
+            a_rb = b_rb;
         }
     }
     if (failed) {
         // give copies still in flight into this CTA's shared memory a bounded chance
         // to land before the CTA exits
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < STAGES; ++b)
             for (uint32_t it = 0; it < (1u << 20); ++it)
                 if (mbar_try_wait(&bars[b], (parity >> b) & 1u)) break;
     }
@@ -363,12 +424,12 @@ __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
         const int xp = (int)(k % p.pitch);
         const int yp = (int)((k / p.pitch) % p.nyp);
         const int z = (int)(k / p.plane_p);
-        const int x = xp - 2, y = yp - 2;
+        const int x = xp - p.padx, y = yp - 2;
         const bool xin = x >= 0 && x < p.nx, yin = y >= 0 && y < p.ny;
         if (xin && yin) continue;
         if (x < -2 || x > p.nx + 1) continue;              // row padding, unused
         if (!yin && (p.wall_y || y < -2 || y > p.ny + 1)) continue;
-        const size_t src = pidx(p.pitch, p.nyp, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
+        const size_t src = pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
         for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + k] = f[(size_t)ik * p.P + src];
     }
 }
@@ -491,5 +552,7 @@ int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
 int step_box_rows() { return SH; }
 int step_box_width(int storage) { return storage == 0 ? Geo<StoreF32>::BW : Geo<StoreF16>::BW; }
+int step_pad_x(int storage) { return storage == 0 ? Geo<StoreF32>::PADX : Geo<StoreF16>::PADX; }
+int step_ctas_per_sm() { return CTAS_PER_SM; }
 
 }  // namespace lbm
