@@ -154,6 +154,29 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf);
 
+/* Conserved totals of a population array the caller owns, computed without
+ * allocating any memory -- for callers that cannot call cudaMalloc (code running
+ * while a CUDA graph is being captured, processes whose device memory is handed out
+ * by their own pool allocator, or latency-critical loops where an allocation's
+ * implicit synchronisation is not acceptable). The paper has no counterpart; it is
+ * a variant of the reduction behind lbm_observables.
+ *   pops    device pointer, float32 populations [2 species][19 directions][n_nodes]
+ *           in the order of lbm_velocity_set (node order is irrelevant: it is a sum)
+ *   n_nodes number of nodes, 1 <= n_nodes <= 134217728 (512^3): larger arrays are
+ *           rejected with LBM_EINVAL, because the partial sums live in a fixed
+ *           1 MiB device array of the library (16384 blocks of 8192 nodes)
+ *   out     device pointer to 5 doubles: {sum f^r, sum f^b, P_x, P_y, P_z}
+ *   cuda_stream  cudaStream_t to run on, or NULL; the call is asynchronous.
+ * No cudaMalloc, cudaFree or allocating library routine is called. The first call
+ * on a device looks up the device address of the scratch array (make that first
+ * call before any stream capture). All calls share the scratch array: calls that
+ * may overlap on the GPU (different streams) race and give wrong results. Every
+ * call overwrites the partial sums it reads, so nothing has to be cleared between
+ * calls. Errors: LBM_EINVAL (null pointer, size), LBM_ECUDA; message in
+ * lbm_last_error(NULL).                                                         */
+lbm_status lbm_totals_noalloc(const float* pops, long long n_nodes, double* out,
+                              void* cuda_stream);
+
 /* Blocks until the context's queued work is done.                               */
 lbm_status lbm_sync(lbm_ctx* ctx);
 

@@ -67,6 +67,11 @@ struct lbm_ctx {
 
 static thread_local std::string g_create_err;
 
+namespace lbm {
+// Error message of a failed call that has no context (read by lbm_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace lbm
+
 static lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
     if (c) c->err = msg; else g_create_err = msg;
     return s;

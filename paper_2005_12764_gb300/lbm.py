@@ -28,7 +28,8 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_step_timed", "lbm_launches_per_step",
            "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_observables", "lbm_laplace",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
-           "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error"]
+           "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
+           "lbm_totals_noalloc"]
 
 
 class LbmError(RuntimeError):
@@ -90,6 +91,7 @@ def load():
             "lbm_steps_taken": (C.c_longlong, [_P]),
             "lbm_destroy": (None, [_P]),
             "lbm_last_error": (C.c_char_p, [_P]),
+            "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -123,6 +125,15 @@ def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.cuda_stream = stream
     return p
+
+
+def totals_noalloc(pops_ptr: int, n_nodes: int, out_ptr: int, stream=None) -> None:
+    """Conserved totals of a float32 device population array [2][19][n] into the
+    device array out (5 doubles), without any allocation (see include/lbm.h)."""
+    lib = load()
+    rc = lib.lbm_totals_noalloc(pops_ptr, int(n_nodes), out_ptr, stream)
+    if rc != 0:
+        raise LbmError(rc, lib.lbm_last_error(None).decode())
 
 
 def footprint_bytes(params: Params) -> int:
