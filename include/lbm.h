@@ -54,7 +54,11 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the populations in device memory. Arithmetic is FP32 in all cases.
- * FP16/BF16 store the deviation f_i^k - w_i rho0/2 rounded to nearest even.    */
+ * FP16/BF16 store, rounded to nearest even, the deviation of f_i^k from
+ * w_i rho0 (1 + s_k phi)/2 (s_r = +1, s_b = -1), where phi is the colour field of
+ * the node that wrote the population, in the step that wrote it: the species'
+ * share of the reference rest population w_i rho0 of the total population:
+ * the total deviation f_i - w_i rho0 split between the species by colour.      */
 typedef enum {
     LBM_STORE_FP32 = 0,
     LBM_STORE_FP16_DEV = 1,

@@ -121,24 +121,32 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
             uz = u[2 * N + n];
         }
         const double usq = ux * ux + uy * uy + uz * uz;
+        const float ph = (float)((rr - rb) / (rr + rb));
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
             const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
             const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-            const float ref = wgt(i) * ref_half;
-            St::store(f, (size_t)i * P + q, (float)(rr * e), ref);
-            St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), ref);
+            const float hw = wgt(i) * ref_half;
+            St::store(f, (size_t)i * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
+            St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
         }
-        const float ph = (float)((rr - rb) / (rr + rb));
         phi0[n] = ph;
         phi1[n] = ph;
     }
 }
 
+// Population (species k, direction i) at padded index idx of a node whose current
+// colour field is ph: deviation storage decodes against the reference of that node.
 template <class St>
-__device__ inline float ldpop(const typename St::T* f, size_t idx, int i, float ref_half) {
-    return St::load(f, idx, wgt(i) * ref_half);
+__device__ inline float ldpop(const typename St::T* f, size_t idx, int i, int k, float ref_half,
+                              float ph) {
+    return St::load(f, idx, dev_ref(wgt(i) * ref_half, ph, k));
+}
+// Current colour field of node n as the deviation references need it (0 for FP32).
+template <class St>
+__device__ inline float ref_phi(const float* phi_cur, size_t n) {
+    return St::kind != 0 ? phi_cur[n] : 0.0f;
 }
 
 // Fields of the current state. rho_k = sum_i f_i^k of the stored (post-collision)
@@ -153,11 +161,12 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_now, n);
         float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float a = ldpop<St>(f, (size_t)i * P + q, i, sp.ref_half);
-            const float b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, sp.ref_half);
+            const float a = ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
+            const float b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
             rr += a;
             rb += b;
             jx += cx(i) * (a + b);
@@ -194,32 +203,34 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
 }
 
 template <class St>
-__global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, double* fr,
-                                   double* fb) {
+__global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, const float* phi_cur,
+                                   double* fr, double* fb) {
     const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * P + q, i, sp.ref_half);
-            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * P + q, i, sp.ref_half);
+            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
+            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
         }
     }
 }
 
 template <class St>
-__global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const double* fr,
-                                   const double* fb) {
+__global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const float* phi_cur,
+                                   const double* fr, const double* fb) {
     const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float ref = wgt(i) * sp.ref_half;
-            St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], ref);
-            St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], ref);
+            const float hw = wgt(i) * sp.ref_half;
+            St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], dev_ref(hw, ph, 0));
+            St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], dev_ref(hw, ph, 1));
         }
     }
 }
@@ -269,17 +280,19 @@ __global__ void finish_sum_kernel(const double* part, int nblocks, double* out) 
 
 // Conserved totals (FP64): sum f^r, sum f^b, P.
 template <class St>
-__global__ void totals_kernel(const typename St::T* f, StepParams sp, double* part) {
+__global__ void totals_kernel(const typename St::T* f, StepParams sp, const float* phi_cur,
+                              double* part) {
     double v[5] = {0, 0, 0, 0, 0};
     const size_t N = sp.N, P = sp.P;
     const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double a = ldpop<St>(f, (size_t)i * P + q, i, ref_half);
-            const double b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
+            const double a = ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
+            const double b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
             v[0] += a;
             v[1] += b;
             v[2] += cx(i) * (a + b);
@@ -292,18 +305,20 @@ __global__ void totals_kernel(const typename St::T* f, StepParams sp, double* pa
 
 // Laplace measurement, pass 1: V = sum (1 + phi)/2 with phi from the populations.
 template <class St>
-__global__ void volume_kernel(const typename St::T* f, StepParams sp, double* part) {
+__global__ void volume_kernel(const typename St::T* f, StepParams sp, const float* phi_cur,
+                              double* part) {
     double v[1] = {0};
     const size_t N = sp.N, P = sp.P;
     const float ref_half = sp.ref_half;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_cur, n);
         double rr = 0, rb = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            rr += ldpop<St>(f, (size_t)i * P + q, i, ref_half);
-            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
+            rr += ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
+            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
         }
         v[0] += 0.5 * (1.0 + (rr - rb) / (rr + rb));
     }
@@ -313,7 +328,8 @@ __global__ void volume_kernel(const typename St::T* f, StepParams sp, double* pa
 // Pass 2: pressure sums and node counts inside r < R-3 and outside r > R+5.
 template <class St>
 __global__ void pressure_kernel(const typename St::T* f, lbm_params p, StepParams sp,
-                                double c0, double c1, double c2, double R, double* part) {
+                                const float* phi_cur, double c0, double c1, double c2, double R,
+                                double* part) {
     double v[4] = {0, 0, 0, 0};
     const size_t N = sp.N, P = sp.P;
     const float ref_half = sp.ref_half;
@@ -331,11 +347,12 @@ __global__ void pressure_kernel(const typename St::T* f, lbm_params p, StepParam
         const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (r < R - 3.0 || r > R + 5.0) {
             const size_t q = node_pidx(sp, n);
+            const float ph = ref_phi<St>(phi_cur, n);
             double rho = 0;
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                rho += (double)ldpop<St>(f, (size_t)i * P + q, i, ref_half) +
-                       (double)ldpop<St>(f, (size_t)(Q + i) * P + q, i, ref_half);
+                rho += (double)ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph) +
+                       (double)ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
             if (r < R - 3.0) {
                 v[0] += rho / 3.0;
                 v[1] += 1;
@@ -568,6 +585,10 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     e = cudaMemcpy(c->fx_row, row, p->ny * sizeof(float), cudaMemcpyHostToDevice);
     delete[] row;
     if (e == cudaSuccess) e = cudaMemset(c->err_word, 0, sizeof(int));
+    // colour fields start at 0, so deviation storage has a finite reference even when
+    // populations are set before any field
+    if (e == cudaSuccess) e = cudaMemset(c->phi[0], 0, c->N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->phi[1], 0, c->N * sizeof(float));
     if (e != cudaSuccess) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
@@ -859,7 +880,7 @@ extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double*
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         pops_to_f64_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (const typename St::T*)c->f[c->cur], c->sp, dr, db);
+            (const typename St::T*)c->f[c->cur], c->sp, c->phi[c->pc], dr, db);
     });
     CK(c, cudaGetLastError());
     if (!on_device) {
@@ -887,32 +908,32 @@ extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* 
     if (!c) return LBM_EINVAL;
     if (!f_r || !f_b) return fail(c, LBM_EINVAL, "f_r and f_b are required");
     const size_t N = c->N;
-    const double *dr = f_r, *db = f_b;
-    if (!on_device) {
-        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
-        CK(c, cudaMemcpyAsync(c->stage, f_r, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        CK(c, cudaMemcpyAsync(c->stage + Q * N, f_b, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        dr = c->stage;
-        db = c->stage + Q * N;
-    }
     const int grid = grid_for(N, c->num_sms);
-    dispatch(c->p.storage, [&](auto st) {
-        using St = decltype(st);
-        f64_to_pops_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (typename St::T*)c->f[c->cur], c->sp, dr, db);
-    });
-    CK(c, cudaGetLastError());
-    CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
+    if (!on_device && ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+    // the colour field first: deviation storage encodes the populations against it
     if (phi_lag) {
         const double* src = phi_lag;
         if (!on_device) {
-            CK(c, cudaStreamSynchronize(c->stream));
             CK(c, cudaMemcpyAsync(c->stage, phi_lag, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
             src = c->stage;
         }
         f64_to_f32_kernel<<<grid, kThreads, 0, c->stream>>>(c->phi[c->pc], src, N);
         CK(c, cudaGetLastError());
     }
+    const double *dr = f_r, *db = f_b;
+    if (!on_device) {
+        CK(c, cudaMemcpyAsync(c->stage, f_r, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->stage + Q * N, f_b, Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        dr = c->stage;
+        db = c->stage + Q * N;
+    }
+    dispatch(c->p.storage, [&](auto st) {
+        using St = decltype(st);
+        f64_to_pops_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+            (typename St::T*)c->f[c->cur], c->sp, c->phi[c->pc], dr, db);
+    });
+    CK(c, cudaGetLastError());
+    CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
     c->fields_set = true;
     c->nc_scan = true;
@@ -926,7 +947,7 @@ extern "C" lbm_status lbm_observables(lbm_ctx* c, double out[8]) {
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         totals_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
-                                                            c->sp, c->red);
+                                                            c->sp, c->phi[c->pc], c->red);
     });
     finish_sum_kernel<5><<<1, kThreads, 0, c->stream>>>(c->red, grid, c->red + (size_t)grid * 8);
     CK(c, cudaGetLastError());
@@ -946,7 +967,7 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         volume_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur],
-                                                             c->sp, c->red);
+                                                             c->sp, c->phi[c->pc], c->red);
     });
     finish_sum_kernel<1><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
     CK(c, cudaGetLastError());
@@ -957,8 +978,8 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         pressure_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (const typename St::T*)c->f[c->cur], c->p, c->sp, centre[0], centre[1], centre[2], R,
-            c->red);
+            (const typename St::T*)c->f[c->cur], c->p, c->sp, c->phi[c->pc], centre[0], centre[1],
+            centre[2], R, c->red);
     });
     finish_sum_kernel<4><<<1, kThreads, 0, c->stream>>>(c->red, grid, fin);
     CK(c, cudaGetLastError());

@@ -49,8 +49,20 @@ __host__ __device__ constexpr float inv_clen(int i) {
 
 // ---------------------------------------------------------------- storage formats
 // Populations live in [2 species][19 directions][N nodes] arrays. FP32 stores the
-// value; FP16/BF16 store the deviation f - ref with ref = w_i rho0 / 2, rounded to
-// nearest even.
+// value; FP16/BF16 store the deviation f - ref rounded to nearest even, with the
+// reference ref = w_i rho0 (1 +- phi)/2 (+ red, - blue): the species' share of the
+// rest population at the reference density, split by the colour field phi of the
+// node that wrote the population (in the step that wrote it). In the bulk of either
+// phase the stored deviation is then O(|u|, |rho - rho0|) instead of O(w_i rho0/2),
+// so the 11-bit FP16 (8-bit BF16) mantissa is spent on the part that changes.
+// Deviation reference of species k (0 red, 1 blue) for a direction whose w_i rho0/2
+// is hw, at a node with colour field phi. Encoding and decoding both use this one
+// expression (explicit FMAs, no contraction choices), so the reference cancels
+// exactly and only the rounding of the stored deviation remains.
+__device__ __forceinline__ float dev_ref(float hw, float phi, int k) {
+    return k == 0 ? __fmaf_rn(hw, phi, hw) : __fmaf_rn(-hw, phi, hw);
+}
+
 struct StoreF32 {
     using T = float;
     static constexpr int kind = 0;
@@ -112,7 +124,7 @@ struct StepParams {
     float sigma, beta;
     float A_nc, h_min, h_cut, ah_b3, ah_inv;  // A_h tail: b3 = (h_min/h_cut)^3, inv = 1/(1-b3)
     int nsamp;              // ray samples t = -1, -1/2, ..., h_cut + 2
-    float ref_half;         // rho0/2: deviation reference per species (FP16/BF16)
+    float ref_half;         // rho0/2 for FP16/BF16 deviation storage, 0 for FP32
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
     int ghost_in_kernel;    // the step kernel writes the ghost copies (else a fill pass)
@@ -345,8 +357,8 @@ struct GlobalEmit {
 
 template <class St, bool UnitOmega, class Emit>
 __device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
-                                              float rb, float Gx, float Gy, float Gz, float Fx,
-                                              float Fy, float Fz, const Emit& emit) {
+                                              float rb, float phi, float Gx, float Gy, float Gz,
+                                              float Fx, float Fy, float Fz, const Emit& emit) {
     const float rho = rr + rb;
     const float inv_rho = __frcp_rn(rho);
     float jx = 0.f, jy = 0.f, jz = 0.f;
@@ -377,7 +389,9 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
     const float half_A_g = has_g ? 0.5f * (4.5f * omega * p.sigma) * gm : 0.0f;
     const float seg0 = has_g ? p.beta * rr * rb * inv_rho : 0.0f;
     const float ar = rr * inv_rho, ab = rb * inv_rho;
-    const float ref = p.ref_half;
+    // deviation references of this node (phi = its colour field of this step); they
+    // vanish for FP32 storage, whose store ignores them
+    const float refh = p.ref_half;
     // per weight class (face / edge): products that do not depend on the direction
     const float wr_f = wgt(2) * rho, wr_e = wgt(0) * rho;
     const float wrr_f = wgt(2) * rr, wrr_e = wgt(0) * rr;
@@ -409,11 +423,12 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         }
         const float sg = (face ? sg_f : sg_e) * cn;
         const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
-        const float w = wgt(i);
-        emit(i, wrr + (ar * si + sg), w * ref);
-        emit(o, wrr + (ar * so - sg), w * ref);
-        emit(Q + i, wrb + (ab * si - sg), w * ref);
-        emit(Q + o, wrb + (ab * so + sg), w * ref);
+        const float hw = wgt(i) * refh;
+        const float rf_r = dev_ref(hw, phi, 0), rf_b = dev_ref(hw, phi, 1);
+        emit(i, wrr + (ar * si + sg), rf_r);
+        emit(o, wrr + (ar * so - sg), rf_r);
+        emit(Q + i, wrb + (ab * si - sg), rf_b);
+        emit(Q + o, wrb + (ab * so + sg), rf_b);
     }
     {
         constexpr int i = 9;
@@ -421,8 +436,9 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         const float wr = w * rho;
         float si = -wr * U15 - 2.0f * pert_sum;
         if (!UnitOmega) si += om1 * ((f[i] - wr) + wr * usq15);
-        emit(i, w * rr + ar * si, w * ref);
-        emit(Q + i, w * rb + ab * si, w * ref);
+        const float hw = w * refh;
+        emit(i, w * rr + ar * si, dev_ref(hw, phi, 0));
+        emit(Q + i, w * rb + ab * si, dev_ref(hw, phi, 1));
     }
 }
 

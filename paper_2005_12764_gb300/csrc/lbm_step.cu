@@ -49,7 +49,13 @@ struct Geo {
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
     static constexpr size_t STAGE_BYTES = (size_t)2 * Q * IK_BYTES;
     static constexpr size_t PHI_BYTES = 4 * SH * SWP * sizeof(float);
-    static constexpr size_t SMEM = STAGES * STAGE_BYTES + PHI_BYTES + 2 * sizeof(unsigned long long);
+    // deviation storage: 4-slot ring of the lagged colour field, (TX+4) x (TY+4) per
+    // plane (the sources of the tile and its ring), which decodes the pulled values
+    static constexpr bool DEV = St::kind != 0;
+    static constexpr int LW = TX + 4, LH = TY + 4;
+    static constexpr size_t LAG_BYTES = DEV ? 4 * LH * LW * sizeof(float) : 0;
+    static constexpr size_t SMEM =
+        STAGES * STAGE_BYTES + PHI_BYTES + LAG_BYTES + 2 * sizeof(unsigned long long);
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -110,8 +116,9 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
     float* sphi = reinterpret_cast<float*>(smem + STAGES * G::STAGE_BYTES);   // [4][SH][SWP]
-    unsigned long long* bars =
-        reinterpret_cast<unsigned long long*>(smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES);
+    float* slag = reinterpret_cast<float*>(smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(
+        smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES + G::LAG_BYTES);
 
     const T* __restrict__ fin = static_cast<const T*>(p.fin);
     T* __restrict__ fout = static_cast<T*>(p.fout);
@@ -181,10 +188,17 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             parity ^= 1u << b;
         };
 
-        // ---- pull of node (tx, ty) of plane pl from staged buffer b
-        // returns densities; for keep == true also the total populations
-        auto pull = [&](int b, int pl, int tx, int ty, float (&ft)[Q], float& rr, float& rb,
-                        bool keep) {
+        // lagged colour field of column (tx, ty) (tile coordinates, -2 .. TX+1 and
+        // -2 .. TY+1) in lag-ring slot sl
+        auto lag_at = [&](int sl, int tx, int ty) -> float& {
+            return slag[(sl * G::LH + ty + 2) * G::LW + tx + 2];
+        };
+        // ---- pull of node (tx, ty) of plane pl (wrapped; sc = lag-ring slot of the
+        // unwrapped plane) from staged buffer b; returns densities, and for keep == true
+        // also the total populations. Deviation storage decodes every value against
+        // the colour field its source node had when it wrote it.
+        auto pull = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
+                        float& rb, bool keep) {
             const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + PADX);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
@@ -194,20 +208,27 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             const float refh = p.ref_half;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const float ref = wgt(i) * refh;
-                vr[i] = St::cvt(st[(size_t)i * IKS - cx(i)], ref);
-                vb[i] = St::cvt(st[(size_t)(Q + i) * IKS - cx(i)], ref);
+                const float hw = wgt(i) * refh;
+                float rf_r = hw, rf_b = hw;
+                if (G::DEV) {
+                    const float ph = lag_at((sc - cz(i)) & 3, tx - cx(i), ty - cy(i));
+                    rf_r = dev_ref(hw, ph, 0);
+                    rf_b = dev_ref(hw, ph, 1);
+                }
+                vr[i] = St::cvt(st[(size_t)i * IKS - cx(i)], rf_r);
+                vb[i] = St::cvt(st[(size_t)(Q + i) * IKS - cx(i)], rf_b);
             }
             if (any_wall) {
                 const size_t self = pidx(p.pitch, p.nyp, PADX, wrap_near(x0 + tx, p.nx), gy, pl);
+                const float ph_self = G::DEV ? lag_at(sc, tx, ty) : 0.0f;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
                                      (cz(i) > 0 && zlo) || (cz(i) < 0 && zhi);
                     if (out) {
-                        const float ref = wgt(i) * refh;
-                        vr[i] = St::load(fin, (size_t)opp(i) * p.P + self, ref);
-                        vb[i] = St::load(fin, (size_t)(Q + opp(i)) * p.P + self, ref);
+                        const float hw = wgt(i) * refh;
+                        vr[i] = St::load(fin, (size_t)opp(i) * p.P + self, dev_ref(hw, ph_self, 0));
+                        vb[i] = St::load(fin, (size_t)(Q + opp(i)) * p.P + self, dev_ref(hw, ph_self, 1));
                     }
                 }
             }
@@ -228,14 +249,38 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             if (!pvalid) return;
             const int plw = wrap_near(pl, p.nz);
             if (owned) {
-                pull(b, plw, otx, oty, ft, rr, rb, keep);
+                pull(b, plw, slot(pl), otx, oty, ft, rr, rb, keep);
                 phi_at(slot(pl), otx, oty) = colour(rr, rb);
             }
             if (ring) {
                 float dummy[Q], a, c;
-                pull(b, plw, rtx, rty, dummy, a, c, false);
+                pull(b, plw, slot(pl), rtx, rty, dummy, a, c, false);
                 phi_at(slot(pl), rtx, rty) = colour(a, c);
             }
+        };
+
+        // ---- lagged colour field of plane pl (deviation storage): element e of the
+        // (TX+4) x (TY+4) box, wrapped on periodic axes, clamped at walls (values
+        // beyond a wall are never read: those links bounce back)
+        constexpr int LN = G::LW * G::LH;
+        auto lag_load = [&](int pl, int e) -> float {
+            if (e >= LN) return 0.0f;
+            const int r = e / G::LW, c = e - r * G::LW;
+            const int gx = wrap_near(x0 - 2 + c, p.nx);
+            int gy = y0 - 2 + r, gz = pl;
+            gy = p.wall_y ? min(max(gy, 0), p.ny - 1) : wrap_near(gy, p.ny);
+            gz = p.wall_z ? min(max(gz, 0), p.nz - 1) : wrap_near(gz, p.nz);
+            return __ldg(p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
+        };
+        float lag_reg0 = 0.f, lag_reg1 = 0.f;   // plane fetched ahead of its slot store
+        auto lag_fetch = [&](int pl) {
+            lag_reg0 = lag_load(pl, tid);
+            lag_reg1 = lag_load(pl, tid + NT);
+        };
+        auto lag_commit = [&](int pl) {
+            float* d = slag + (size_t)slot(pl) * LN;
+            d[tid] = lag_reg0;
+            if (tid + NT < LN) d[tid + NT] = lag_reg1;
         };
 
         // ---- ghost copies this thread's node writes (periodic axes, edge nodes), as
@@ -284,8 +329,13 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             }
             const float ah_nxt =
                 (owned && use_nc && z + 1 < ze) ? p.ah[(size_t)(z + 1) * plane + col] : 0.0f;
+            // lag plane z+3 goes to the slot of plane z-1, last read before the barrier
+            // of the previous plane; the densities of z+1 read planes z .. z+2. It is
+            // fetched here and stored after those densities, which hide the latency.
+            if (G::DEV) lag_fetch(z + 3);
             wait(bn);
             densities(bn, z + 1, nx_f, nx_rr, nx_rb, true);
+            if (G::DEV) lag_commit(z + 3);
             __syncthreads();
             if (STAGES == 1) {
                 fence_proxy_async();
@@ -351,10 +401,12 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                 if (warp_ghost) {
                     GlobalEmit<St, true> em{plane_out, p.P, toff, 0, {0, 0, 0}};
                     em.ng = ghost_offsets(em.goff);
-                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, Gx, Gy, Gz, Fx, Fy, Fz, em);
+                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy,
+                                                 Fz, em);
                 } else {
                     const GlobalEmit<St, false> em{plane_out, p.P, toff, 0, {0, 0, 0}};
-                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, Gx, Gy, Gz, Fx, Fy, Fz, em);
+                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy,
+                                                 Fz, em);
                 }
                 p.phi_out[node] = phic;
             }
@@ -366,7 +418,16 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
         // A_h of the plane being collided, loaded one iteration ahead
         float ah_c = (owned && use_nc) ? p.ah[(size_t)zb * plane + col] : 0.0f;
 
-        // ---- prologue: planes zb-1 and zb
+        // ---- prologue: planes zb-1 and zb (their pulls read lag planes zb-2 .. zb+1;
+        // lag plane zb+2 replaces zb-2 once the pull of zb-1 is done)
+        if (G::DEV) {
+            for (int q = -2; q <= 1; ++q) {
+                lag_fetch(zb + q);
+                lag_commit(zb + q);
+            }
+            lag_fetch(zb + 2);
+            __syncthreads();
+        }
         if (STAGES == 2) {
             fence_proxy_async();
             issue(0, zb - 1);
@@ -374,6 +435,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             wait(0);
             densities(0, zb - 1, fb, b_rr, b_rb, false);
             __syncthreads();
+            if (G::DEV) lag_commit(zb + 2);
             fence_proxy_async();
             issue(0, zb + 1);
             wait(1);
@@ -385,6 +447,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             wait(0);
             densities(0, zb - 1, fb, b_rr, b_rb, false);
             __syncthreads();
+            if (G::DEV) lag_commit(zb + 2);
             fence_proxy_async();
             issue(0, zb);
             wait(0);
