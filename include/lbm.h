@@ -78,7 +78,7 @@ typedef struct {
     double beta;             /* recolouring segregation parameter in [0, 1]               */
     double A_nc;             /* near-contact amplitude A of Eq. (11); 0 = off             */
     double h_min;            /* plateau length of A_h[h] (lattice units), e.g. 3          */
-    double h_cut;            /* cutoff of A_h[h]; <= 0 means 2*h_min                      */
+    double h_cut;            /* cutoff of A_h[h]; <= 0 means 2*h_min; at most 9           */
     double g[3];             /* uniform body-force density                                */
     double kolmogorov_amp;   /* adds F_x = amp * sin(2 pi y / ny); 0 = off                */
     double rho0;             /* reference density of the FP16/BF16 deviation storage (1)  */
@@ -123,7 +123,9 @@ lbm_status lbm_step(lbm_ctx* ctx, int n);
  * For measurement; it serialises the host with the device.                      */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[2]);
 
-/* Kernel launches one lbm_step makes per time step (1, or 2 when A_nc > 0).      */
+/* Kernel launches one lbm_step makes per time step: 1 (the fused step), or 3 when
+ * A_nc > 0 (the near-contact ray-bound field and pass; the first step after a
+ * change of state adds a candidate scan).                                        */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the
@@ -131,6 +133,12 @@ int lbm_launches_per_step(const lbm_ctx* ctx);
  * step, the fields that were set. Synchronises the stream.                      */
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u,
                           double* phi, int on_device);
+
+/* Near-contact strength A_h[h] (Eq. 11) of every node ([N] float64), measured on
+ * the current colour field -- the field the next step's film measurement reads --
+ * exactly as that step will measure it; 0 where no film is within h_cut or
+ * A_nc == 0. For diagnostics and tests; synchronises the stream.                 */
+lbm_status lbm_get_nc_field(lbm_ctx* ctx, double* ah, int on_device);
 
 /* Raw populations as float64 [19][N] per species, in the order of
  * lbm_velocity_set, plus the colour field of the previous step (lag buffer, [N];

@@ -330,6 +330,7 @@ static void gradient_node(const or_params* p, const double* phi, long x, long y,
  * This routine returns the strength A_h at node (x, y, z).                       */
 double or_nc_strength_node(const or_params* p, const double* phi_ray,
                            const unsigned char* pin, long x, long y, long z) {
+    lattice_init();
     if (p->A_nc == 0.0) return 0.0;
     double G[3];
     gradient_node(p, phi_ray, x, y, z, G);

@@ -18,7 +18,8 @@
 namespace lbm {
 cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage, int grid,
                         cudaStream_t s);
-cudaError_t launch_nc(const StepParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int num_sms,
+                      cudaStream_t s);
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s);
 int step_tile_x();
@@ -45,8 +46,9 @@ struct lbm_ctx {
     uint8_t* pin_d2 = nullptr;
     uint8_t* pin_mask = nullptr;
     float* ah = nullptr;        // near-contact strength per node (A_nc > 0)
-    int* cand[2] = {nullptr, nullptr};  // candidate lists (ping-pong) and counters
+    int4* cand[2] = {nullptr, nullptr}; // candidate lists {node, G} (ping-pong) and counters
     int* cand_count = nullptr;          // [2]
+    uint32_t* nc_pos = nullptr;         // near-contact ray bound (block bit field)
     int cw = 0;                 // list the next step kernel writes
     bool nc_scan = true;        // next near-contact pass must scan every node
     double* stage = nullptr;    // device FP64 staging, 6N doubles
@@ -89,10 +91,6 @@ static lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
 namespace {
 
 constexpr int kThreads = 256;
-
-__host__ __device__ inline size_t nidx(const lbm_params& p, int x, int y, int z) {
-    return ((size_t)z * p.ny + y) * p.nx + x;
-}
 
 // Padded index of unpadded node n.
 __device__ __forceinline__ size_t node_pidx(const StepParams& sp, size_t n) {
@@ -435,7 +433,7 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->A_nc > 0.0 && !(p->h_min > 0.0)) { why = "h_min must be > 0 when A_nc > 0"; return LBM_EINVAL; }
     double hcut = p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min;
     if (p->A_nc > 0.0 && !(hcut > p->h_min)) { why = "h_cut must exceed h_min"; return LBM_EINVAL; }
-    if (p->A_nc > 0.0 && hcut > 64.0) { why = "h_cut must be <= 64"; return LBM_EINVAL; }
+    if (p->A_nc > 0.0 && hcut > 9.0) { why = "h_cut must be <= 9 (film rays of at most 25 samples)"; return LBM_EINVAL; }
     if (p->storage < 0 || p->storage > 2) { why = "unknown storage"; return LBM_EINVAL; }
     if ((p->storage != 0) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
@@ -443,12 +441,19 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     return LBM_OK;
 }
 
+// Bytes of the near-contact ray-bound bit field (one bit per 2x2x2 block, rows of
+// 32-bit words along x).
+static size_t nc_pos_bytes(const lbm_params& p) {
+    const size_t nbx = (size_t)(p.nx + 1) / 2;
+    return ((nbx + 31) / 32) * ((p.ny + 1) / 2) * ((p.nz + 1) / 2) * sizeof(uint32_t);
+}
+
 extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     if (!p) return 0;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     const PadLayout L = pad_layout(*p);
     size_t b = 2 * 2 * Q * L.P * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
-    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int));
+    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int4)) + nc_pos_bytes(*p);
     return b;
 }
 
@@ -499,6 +504,11 @@ static void fill_step_params(lbm_ctx* c) {
     s.tiles_y = (p.ny + ty - 1) / ty;
     s.err = c->err_word;
     s.ah = c->ah;
+    s.nbx = (p.nx + 1) / 2;
+    s.nby = (p.ny + 1) / 2;
+    s.nbz = (p.nz + 1) / 2;
+    s.nbw = (s.nbx + 31) / 32;
+    s.nc_pos = c->nc_pos;
     // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
     // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
     // pipeline fill), the cost of a part-major launch.
@@ -562,9 +572,10 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
               alloc((void**)&c->fx_row, p->ny * sizeof(float)) &&
               alloc((void**)&c->err_word, sizeof(int)) &&
               (p->A_nc > 0.0 ? alloc((void**)&c->ah, c->N * sizeof(float)) &&
-                                   alloc((void**)&c->cand[0], c->N * sizeof(int)) &&
-                                   alloc((void**)&c->cand[1], c->N * sizeof(int)) &&
-                                   alloc((void**)&c->cand_count, 2 * sizeof(int))
+                                   alloc((void**)&c->cand[0], c->N * sizeof(int4)) &&
+                                   alloc((void**)&c->cand[1], c->N * sizeof(int4)) &&
+                                   alloc((void**)&c->cand_count, 2 * sizeof(int)) &&
+                                   alloc((void**)&c->nc_pos, nc_pos_bytes(*p))
                                : true);
     c->red_blocks = c->num_sms * 8;
     ok = ok && alloc((void**)&c->red, (size_t)(c->red_blocks + 1) * 8 * sizeof(double));
@@ -645,6 +656,7 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->cand[0]);
     cudaFree(c->cand[1]);
     cudaFree(c->cand_count);
+    cudaFree(c->nc_pos);
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
 }
@@ -764,7 +776,10 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
                 s.nc_list = c->cand[1 - c->cw];
                 s.nc_count = c->cand_count + (1 - c->cw);
             }
-            e = launch_nc(s, c->num_sms, c->stream);
+            // scan mode compacts its candidates into the list slot this pass would
+            // otherwise read (stale after a change of state)
+            e = launch_nc(s, c->cand[1 - c->cw], c->cand_count + (1 - c->cw), c->num_sms,
+                          c->stream);
         }
         if (e == cudaSuccess)
             e = cudaMemsetAsync(c->cand_count + c->cw, 0, sizeof(int), c->stream);
@@ -845,7 +860,8 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
         s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
         s.nc_list = nullptr;
         s.nc_count = nullptr;
-        CK(c, launch_nc(s, c->num_sms, c->stream));
+        // scan-mode candidates go to the list slot the next step kernel overwrites
+        CK(c, launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->num_sms, c->stream));
     }
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
@@ -860,6 +876,35 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
         if (u) CK(c, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (phi) CK(c, cudaMemcpyAsync(phi, dp, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (!ah) return fail(c, LBM_EINVAL, "ah is required");
+    const size_t N = c->N;
+    if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+    const int grid = grid_for(N, c->num_sms);
+    float* scratch = reinterpret_cast<float*>(c->stage + 6 * N);
+    if (c->p.A_nc > 0.0) {
+        // measured in scan mode on the current colour field (the next step's lag
+        // field) into scratch; the live A_h buffer and candidate lists are untouched
+        StepParams s = c->sp;
+        s.phi_lag = c->phi[c->pc];
+        s.ah = scratch;
+        s.nc_list = nullptr;
+        s.nc_count = nullptr;
+        // scan-mode candidates go to the list slot the next step kernel overwrites
+        CK(c, launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->num_sms, c->stream));
+    } else {
+        CK(c, cudaMemsetAsync(scratch, 0, N * sizeof(float), c->stream));
+    }
+    double* dst = on_device ? ah : c->stage;
+    f32_to_f64_kernel<<<grid, kThreads, 0, c->stream>>>(dst, scratch, N);
+    CK(c, cudaGetLastError());
+    if (!on_device) CK(c, cudaMemcpyAsync(ah, dst, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -1039,5 +1084,6 @@ extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
-    return c->p.A_nc > 0.0 ? 2 : 1;
+    // near contact: the ray-bound bit field and the list pass, then the fused step
+    return c->p.A_nc > 0.0 ? 3 : 1;
 }

@@ -105,10 +105,15 @@ struct StepParams {
     const float* fx_row;    // [ny] x body force per row: g_x + Kolmogorov profile
     const uint8_t* pin_d2;  // [N] squared distance to the nearest pin, 255 = none; or null
     float* ah;              // [N] near-contact strength A_h of this step (A_nc > 0)
-    int* cand;              // candidate list written by the step kernel: nodes with |G| >= 0.9e-3
+    int4* cand;             // candidates written by the step kernel: nodes with |G| >= 0.9e-3,
+                            // {node, G_x, G_y, G_z} (float bits), G of the step's colour field
     int* cand_count;        // its length (reset before the step kernel)
-    const int* nc_list;     // list the near-contact pass works on (null: scan every node)
+    const int4* nc_list;    // list the near-contact pass works on (null: scan every node)
     const int* nc_count;
+    uint32_t* nc_pos;       // [nbz][nby][nbw] bits: block (bx, by, bz) of the 2x2x2 block grid
+                            // may hold a node with phi_lag > kPosBand among nodes 2b .. 2b+2
+                            // per axis (bit bx & 31 of word bx >> 5)
+    int nbx, nby, nbz, nbw; // block grid: ceil(n / 2) per axis; nbw = ceil(nbx / 32)
     float gy, gz;
     int nx, ny, nz;
     size_t N;               // nodes (fields phi, ah are [N], x fastest)
@@ -209,8 +214,18 @@ __device__ __forceinline__ bool sample_phi(const StepParams& p, int x, int y, in
     return true;
 }
 
-// Isotropic colour gradient of a node field at (x, y, z): 3 w_i = 1/6 (faces), 1/12
-// (edges); a neighbour beyond a wall takes the centre value.
+// One term 3 w_i c_i v of the isotropic colour gradient (3 w_i = 1/6 for faces, 1/12
+// for edges), accumulated with explicit FMAs in direction order: every kernel that
+// evaluates a node's gradient gets the same bits.
+__device__ __forceinline__ void grad_add(int i, float v, float& Gx, float& Gy, float& Gz) {
+    const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
+    if (cx(i)) Gx = __fmaf_rn(cx(i) > 0 ? w3 : -w3, v, Gx);
+    if (cy(i)) Gy = __fmaf_rn(cy(i) > 0 ? w3 : -w3, v, Gy);
+    if (cz(i)) Gz = __fmaf_rn(cz(i) > 0 ? w3 : -w3, v, Gz);
+}
+
+// Isotropic colour gradient of a node field at (x, y, z); a neighbour beyond a wall
+// takes the centre value.
 __device__ __forceinline__ void gradient_global(const StepParams& p, const float* phi, int x, int y,
                                                 int z, float& Gx, float& Gy, float& Gz) {
     const size_t self = ((size_t)z * p.ny + y) * p.nx + x;
@@ -225,10 +240,7 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
         if (!wall)
             v = __ldg(phi + ((size_t)wrap_near(zz, p.nz) * p.ny + wrap_near(yy, p.ny)) * p.nx +
                       wrap_near(x + cx(i), p.nx));
-        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
-        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
-        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
-        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+        grad_add(i, v, Gx, Gy, Gz);
     }
 }
 
@@ -238,64 +250,78 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
 // n' = -G'/|G'|, sampled every half lattice unit from t = -1 to h_cut + 2. Samples
 // within 1e-5 of zero carry no sign; h is the distance between the first downward
 // zero crossing and the next upward one, each located by linear interpolation
-// between consecutive signed samples. Pinning sites add A_h[d], d the distance to
-// the nearest pin. Samples are fetched four at a time so their loads overlap.
+// between consecutive signed samples; a ray that leaves the fluid through a wall
+// stops there. Pinning sites add A_h[d], d the distance to the nearest pin.
+//
+// Work bound (exact): an upward crossing needs a positive sample, and a trilinear
+// sample is a convex combination of its 8 corner nodes, so it cannot exceed 1e-5
+// when every corner is <= kPosBand = 1e-5/2. A bit field over 2x2x2 blocks marks
+// where such a corner may be; samples after the last marked one cannot complete a
+// crossing pair, so the march ends there with the same A_h. Most candidate rays
+// (outward from a droplet into the bulk) have no marked sample at all.
 constexpr float kSignBand = 1e-5f;
+constexpr float kPosBand = 0.5e-5f;
+constexpr int kMaxSamples = 25;   // t = -1 .. h_cut + 2 for h_cut <= 9
 
-__device__ inline float nc_strength(const StepParams& p, size_t node, int x, int y, int z) {
-    float Gx, Gy, Gz;
-    gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
+// Ray of a candidate: unit direction -G'/|G'|; false when |G'| < 1e-3 or non-finite.
+__device__ __forceinline__ bool nc_ray(float Gx, float Gy, float Gz, float& nx_, float& ny_,
+                                       float& nz_) {
     const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
-    if (!(gm >= 1e-3f) || !isfinite(gm)) return 0.0f;   // non-finite fields: no force
+    if (!(gm >= 1e-3f) || !isfinite(gm)) return false;
     const float inv = 1.0f / gm;
-    const float nx_ = -Gx * inv, ny_ = -Gy * inv, nz_ = -Gz * inv;
-    float t_a = 0.0f, v_a = 0.0f, t_d = 0.0f, t_u = 0.0f;
-    bool have_a = false, have_d = false, have_u = false, stop = false;
-    for (int s0 = 0; s0 < p.nsamp && !stop; s0 += 4) {
-        float val[4];
-        bool ok[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float t = -1.0f + 0.5f * (float)(s0 + k);
-            ok[k] = (s0 + k < p.nsamp) && sample_phi(p, x, y, z, t * nx_, t * ny_, t * nz_, val[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (stop) break;
-            if (!ok[k]) {
-                stop = true;
-                break;
-            }
-            const float t = -1.0f + 0.5f * (float)(s0 + k);
-            const float v = val[k];
-            if (fabsf(v) <= kSignBand) continue;
-            if (have_a) {
-                if (!have_d && v_a > 0.0f && v < 0.0f) {
-                    t_d = t_a + (t - t_a) * v_a / (v_a - v);
-                    have_d = true;
-                } else if (have_d && v_a < 0.0f && v > 0.0f) {
-                    t_u = t_a + (t - t_a) * v_a / (v_a - v);
-                    have_u = true;
-                    stop = true;
-                    break;
-                }
-            }
-            // any upward crossing after this sample gives h >= h_cut, where A_h vanishes
-            if (have_d && t - t_d >= p.h_cut) {
-                stop = true;
-                break;
-            }
-            t_a = t;
-            v_a = v;
-            have_a = true;
-        }
+    nx_ = -Gx * inv;
+    ny_ = -Gy * inv;
+    nz_ = -Gz * inv;
+    return true;
+}
+
+// Samples of a ray that must be evaluated: bit s set if sample s may be positive.
+// Scanning stops at the first sample outside the fluid (the march stops there).
+__device__ __forceinline__ uint32_t nc_sample_mask(const StepParams& p, int x, int y, int z,
+                                                   float nx_, float ny_, float nz_) {
+    uint32_t mask = 0u;
+    for (int s = 0; s < p.nsamp; ++s) {
+        const float t = -1.0f + 0.5f * (float)s;
+        int ix0, iy0, iz0, i1;
+        float f;
+        if (!axis_cell(x, t * nx_, p.nx, false, ix0, i1, f) ||
+            !axis_cell(y, t * ny_, p.ny, p.wall_y, iy0, i1, f) ||
+            !axis_cell(z, t * nz_, p.nz, p.wall_z, iz0, i1, f))
+            break;
+        const int bx = ix0 >> 1;
+        const uint32_t w =
+            __ldg(p.nc_pos + ((size_t)(iz0 >> 1) * p.nby + (iy0 >> 1)) * p.nbw + (bx >> 5));
+        mask |= ((w >> (bx & 31)) & 1u) << s;
     }
-    float ah = (have_d && have_u) ? A_h(p, t_u - t_d) : 0.0f;
-    if (p.pin_d2) {
-        const unsigned d2 = __ldg(p.pin_d2 + node);
-        if (d2 != 255u) ah += A_h(p, sqrtf((float)d2));
+    return mask;
+}
+
+// Crossing search over the evaluated samples v[0 .. s_last] of one ray (stride
+// `stride` between consecutive samples) -> A_h of the film, 0 if none.
+__device__ __forceinline__ float nc_march(const StepParams& p, const float* v, int stride,
+                                          int s_last) {
+    float t_a = 0.0f, v_a = 0.0f, t_d = 0.0f;
+    bool have_a = false, have_d = false;
+    for (int s = 0; s <= s_last; ++s) {
+        const float t = -1.0f + 0.5f * (float)s;
+        const float vs = v[s * stride];
+        if (fabsf(vs) <= kSignBand) continue;
+        if (have_a) {
+            if (!have_d && v_a > 0.0f && vs < 0.0f) {
+                t_d = t_a + (t - t_a) * v_a / (v_a - vs);
+                have_d = true;
+            } else if (have_d && v_a < 0.0f && vs > 0.0f) {
+                const float t_u = t_a + (t - t_a) * v_a / (v_a - vs);
+                return A_h(p, t_u - t_d);
+            }
+        }
+        // any upward crossing after this sample gives h >= h_cut, where A_h vanishes
+        if (have_d && t - t_d >= p.h_cut) return 0.0f;
+        t_a = t;
+        v_a = vs;
+        have_a = true;
     }
-    return ah;
+    return 0.0f;
 }
 
 // ---------------------------------------------------------------- collision

@@ -353,11 +353,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                     for (int i = 0; i < Q; ++i) {
                         if (i == 9) continue;
                         const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
-                        const float v = phi_at(sl, otx + cx(i), oty + cy(i));
-                        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
-                        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
-                        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
-                        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+                        grad_add(i, phi_at(sl, otx + cx(i), oty + cy(i)), Gx, Gy, Gz);
                     }
                 } else {
 #pragma unroll
@@ -366,11 +362,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                         const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
                                           (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
                         const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
-                        const float v = wall ? phic : phi_at(sl, otx + cx(i), oty + cy(i));
-                        const float w3 = csq(i) == 1 ? (1.0f / 6.0f) : (1.0f / 12.0f);
-                        if (cx(i)) Gx += (cx(i) > 0 ? w3 : -w3) * v;
-                        if (cy(i)) Gy += (cy(i) > 0 ? w3 : -w3) * v;
-                        if (cz(i)) Gz += (cz(i) > 0 ? w3 : -w3) * v;
+                        grad_add(i, wall ? phic : phi_at(sl, otx + cx(i), oty + cy(i)), Gx, Gy, Gz);
                     }
                 }
                 const size_t node = (size_t)z * plane + col;
@@ -385,8 +377,9 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                         Fz += ah_c * Gz;
                         p.ah[node] = 0.0f;
                     }
-                    // this node's gradient is the next pass's lagged gradient: list it
-                    // as a candidate if it may reach the 1e-3 threshold there
+                    // this node's gradient is the next pass's lagged gradient: list it,
+                    // with that gradient, as a candidate if it may reach the 1e-3
+                    // threshold there
                     const bool cand = Gx * Gx + Gy * Gy + Gz * Gz >= 0.81e-6f;
                     const unsigned m = __ballot_sync(__activemask(), cand);
                     if (cand) {
@@ -394,7 +387,9 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                         int base = 0;
                         if (lane == leader) base = atomicAdd(p.cand_count, __popc(m));
                         base = __shfl_sync(m, base, leader);
-                        p.cand[base + __popc(m & ((1u << lane) - 1u))] = (int)node;
+                        p.cand[base + __popc(m & ((1u << lane) - 1u))] =
+                            make_int4((int)node, __float_as_int(Gx), __float_as_int(Gy),
+                                      __float_as_int(Gz));
                     }
                 }
                 T* plane_out = fout + (size_t)z * p.plane_p;
@@ -498,66 +493,188 @@ __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
 }
 
 // ---------------------------------------------------------------- near-contact pass
-// A_h from the lagged colour field. In list mode it visits only the candidate nodes
-// the previous step kernel listed (lagged gradient >= 0.9e-3, a superset of the
-// nodes where A_h can be nonzero), one thread per node, so rays do not diverge
-// across a warp with non-interface lanes. In scan mode (first step after the state
-// was set) each block takes 1024 consecutive nodes, writes 0 everywhere, gathers
-// the candidates into a shared-memory list and marches their rays.
-constexpr int NC_THREADS = 256, NC_CHUNK = 1024;
+// A_h from the lagged colour field, for the nodes of a candidate list {node, G'}:
+// the list the previous step kernel wrote (lagged gradient >= 0.9e-3, a superset of
+// the nodes where A_h can be nonzero), or, after a change of state, the list the
+// scan kernel below compacts from every node. Every other entry of ah is 0.
+//
+// One warp takes 32 candidates at a time, in three phases:
+//  1. each lane classifies the samples of its own ray with the block bit field
+//     (independent, cheap lookups) and keeps the index of the last one that may be
+//     positive;
+//  2. the samples that must be evaluated (all samples up to that index, over the
+//     32 rays) are spread evenly over the lanes and interpolated into shared memory,
+//     so a few long rays do not hold the warp back;
+//  3. each lane runs the crossing search of its ray over those samples.
+constexpr int NC_THREADS = 256, NC_WARPS = NC_THREADS / 32;
 
-__global__ void __launch_bounds__(NC_THREADS) nc_kernel(const StepParams p) {
-    __shared__ int list[NC_CHUNK];
-    __shared__ int count;
-    const size_t N = p.N;
-    const size_t plane = (size_t)p.nx * p.ny;
-    if (p.nc_list) {
-        // list mode: the candidates written by the previous step kernel (every other
-        // entry of ah is 0, consumed by that kernel)
-        const int cnt = *p.nc_count;
-        for (int k = blockIdx.x * NC_THREADS + threadIdx.x; k < cnt; k += gridDim.x * NC_THREADS) {
-            const size_t n = (size_t)p.nc_list[k];
-            const int z = (int)(n / plane);
-            const int rem = (int)(n - (size_t)z * plane);
-            const int y = rem / p.nx, x = rem - y * p.nx;
-            const float a = nc_strength(p, n, x, y, z);
-            if (a != 0.0f) p.ah[n] = a;
+__global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p) {
+    __shared__ float vals[NC_WARPS][kMaxSamples][32];   // [sample][ray]
+    __shared__ int rx[NC_WARPS][32], ry[NC_WARPS][32], rz[NC_WARPS][32], pre[NC_WARPS][33];
+    __shared__ float rnx[NC_WARPS][32], rny[NC_WARPS][32], rnz[NC_WARPS][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int cnt = *p.nc_count;
+    const int plane = p.nx * p.ny;
+    const int nwarps = gridDim.x * NC_WARPS;
+    for (int k0 = (blockIdx.x * NC_WARPS + wib) * 32; k0 < cnt; k0 += nwarps * 32) {
+        const int k = k0 + lane;
+        int node = 0, x = 0, y = 0, z = 0, s_last = -1;
+        float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
+        bool valid = false;
+        if (k < cnt) {
+            const int4 c = p.nc_list[k];
+            node = c.x;
+            z = node / plane;
+            const int rem = node - z * plane;
+            y = rem / p.nx;
+            x = rem - y * p.nx;
+            valid = nc_ray(__int_as_float(c.y), __int_as_float(c.z), __int_as_float(c.w), nx_,
+                           ny_, nz_);
+            if (valid) {
+                const uint32_t m = nc_sample_mask(p, x, y, z, nx_, ny_, nz_);
+                s_last = 31 - __clz((int)m);   // -1 when no sample may be positive
+            }
         }
-        return;
-    }
-    // scan mode: every node
-    for (size_t base = (size_t)blockIdx.x * NC_CHUNK; base < N; base += (size_t)gridDim.x * NC_CHUNK) {
-        if (threadIdx.x == 0) count = 0;
-        __syncthreads();
-        for (int k = threadIdx.x; k < NC_CHUNK; k += NC_THREADS) {
-            const size_t n = base + k;
-            if (n >= N) break;
-            const int z = (int)(n / plane);
-            const int rem = (int)(n - (size_t)z * plane);
-            const int y = rem / p.nx, x = rem - y * p.nx;
-            float Gx, Gy, Gz;
-            gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
-            if (Gx * Gx + Gy * Gy + Gz * Gz >= 0.81e-6f) list[atomicAdd(&count, 1)] = k;
-            p.ah[n] = 0.0f;
+        // phase 2: exclusive prefix of the sample counts over the warp
+        const int my = s_last + 1;
+        int incl = my;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        __syncthreads();
-        const int cnt = count;
-        for (int k = threadIdx.x; k < cnt; k += NC_THREADS) {
-            const size_t n = base + list[k];
-            const int z = (int)(n / plane);
-            const int rem = (int)(n - (size_t)z * plane);
-            const int y = rem / p.nx, x = rem - y * p.nx;
-            p.ah[n] = nc_strength(p, n, x, y, z);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        pre[wib][lane + 1] = incl;
+        if (lane == 0) pre[wib][0] = 0;
+        rx[wib][lane] = x;
+        ry[wib][lane] = y;
+        rz[wib][lane] = z;
+        rnx[wib][lane] = nx_;
+        rny[wib][lane] = ny_;
+        rnz[wib][lane] = nz_;
+        __syncwarp();
+        for (int task = lane; task < total; task += 32) {
+            // ray r: pre[r] <= task < pre[r + 1]
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pre[wib][mid] <= task) lo = mid;
+                else hi = mid - 1;
+            }
+            const int r = lo, sidx = task - pre[wib][r];
+            const float t = -1.0f + 0.5f * (float)sidx;
+            float v = 0.0f;
+            sample_phi(p, rx[wib][r], ry[wib][r], rz[wib][r], t * rnx[wib][r], t * rny[wib][r],
+                       t * rnz[wib][r], v);   // inside the fluid: checked in phase 1
+            vals[wib][sidx][r] = v;
         }
-        __syncthreads();
+        __syncwarp();
+        // phase 3
+        if (valid) {
+            float a = nc_march(p, &vals[wib][0][lane], 32, s_last);
+            if (p.pin_d2) {
+                const unsigned d2 = __ldg(p.pin_d2 + node);
+                if (d2 != 255u) a += A_h(p, sqrtf((float)d2));
+            }
+            if (a != 0.0f) p.ah[node] = a;
+        }
+        __syncwarp();
     }
 }
 
-cudaError_t launch_nc(const StepParams& p, int num_sms, cudaStream_t s) {
-    size_t blocks = (p.N + NC_CHUNK - 1) / NC_CHUNK;
-    const size_t cap = (size_t)num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    nc_kernel<<<(unsigned)blocks, NC_THREADS, 0, s>>>(p);
+// Scan mode (after the state was set): ah = 0 everywhere, and every node whose
+// lagged gradient may reach the threshold is appended, with that gradient, to the
+// list the list kernel then works on.
+__global__ void nc_scan_kernel(const StepParams p, int4* list, int* count) {
+    const int lane = threadIdx.x & 31;
+    const int N = (int)p.N;
+    const int plane = p.nx * p.ny;
+    const int stride = gridDim.x * blockDim.x;
+    // uniform trip count over the warp, for the ballot
+    for (int base = blockIdx.x * blockDim.x; base < N; base += stride) {
+        const int n = base + (int)threadIdx.x;
+        bool cand = false;
+        float Gx = 0.f, Gy = 0.f, Gz = 0.f;
+        if (n < N) {
+            const int z = n / plane;
+            const int rem = n - z * plane;
+            const int y = rem / p.nx, x = rem - y * p.nx;
+            gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
+            cand = Gx * Gx + Gy * Gy + Gz * Gz >= 0.81e-6f;
+            p.ah[n] = 0.0f;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        int b = 0;
+        if (lane == 0 && m) b = atomicAdd(count, __popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (cand)
+            list[b + __popc(m & ((1u << lane) - 1u))] =
+                make_int4(n, __float_as_int(Gx), __float_as_int(Gy), __float_as_int(Gz));
+    }
+}
+
+// Block bit field of the ray bound: one warp per 32 consecutive x-blocks; a block
+// is marked when one of the nodes 2b .. 2b+2 per axis (wrapped on periodic axes,
+// clipped at walls) has phi_lag > kPosBand.
+__global__ void nc_pos_kernel(const StepParams p) {
+    const int lane = threadIdx.x & 31;
+    const long long words = (long long)p.nbw * p.nby * p.nbz;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < words;
+         w += wstride) {
+        const int wx = (int)(w % p.nbw);
+        const int by = (int)((w / p.nbw) % p.nby);
+        const int bz = (int)(w / ((long long)p.nbw * p.nby));
+        const int bx = wx * 32 + lane;
+        bool pos = false;
+        if (bx < p.nbx) {
+            for (int dz = 0; dz < 3 && !pos; ++dz) {
+                int z = 2 * bz + dz;
+                if (z >= p.nz) {
+                    if (p.wall_z) break;
+                    z %= p.nz;
+                }
+                for (int dy = 0; dy < 3 && !pos; ++dy) {
+                    int y = 2 * by + dy;
+                    if (y >= p.ny) {
+                        if (p.wall_y) break;
+                        y %= p.ny;
+                    }
+                    const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int x = (2 * bx + dx) % p.nx;
+                        pos |= __ldg(row + x) > kPosBand;
+                    }
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pos);
+        if (lane == 0) p.nc_pos[w] = m;
+    }
+}
+
+// The near-contact pass: bit field, then (scan mode: p.nc_list == null) the
+// candidate compaction into scan_list / scan_count, then the list kernel.
+cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, int num_sms,
+                      cudaStream_t s) {
+    StepParams p = p_in;
+    const long long words = (long long)p.nbw * p.nby * p.nbz;
+    long long g = (words + NC_WARPS - 1) / NC_WARPS;
+    if (g > (long long)num_sms * 16) g = (long long)num_sms * 16;
+    nc_pos_kernel<<<(unsigned)g, NC_THREADS, 0, s>>>(p);
+    if (!p.nc_list) {
+        cudaError_t e = cudaMemsetAsync(scan_count, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        long long gs = ((long long)p.N + NC_THREADS - 1) / NC_THREADS;
+        if (gs > (long long)num_sms * 8) gs = (long long)num_sms * 8;
+        nc_scan_kernel<<<(unsigned)gs, NC_THREADS, 0, s>>>(p, scan_list, scan_count);
+        p.nc_list = scan_list;
+        p.nc_count = scan_count;
+    }
+    long long gl = ((long long)p.N / 4 + NC_THREADS - 1) / NC_THREADS;   // ~1/4 of the nodes
+    if (gl > (long long)num_sms * 8) gl = (long long)num_sms * 8;
+    if (gl < 1) gl = 1;
+    nc_list_kernel<<<(unsigned)gl, NC_THREADS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
