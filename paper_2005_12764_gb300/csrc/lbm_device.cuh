@@ -162,58 +162,6 @@ __host__ __device__ __forceinline__ size_t pidx(int pitch, int nyp, int padx, in
     return ((size_t)z * nyp + (y + 2)) * pitch + (x + padx);
 }
 
-// Trilinear sample of the lagged colour field at node (x, y, z) + offset o; false if
-// the point lies outside the fluid along a walled axis. The cell and the weights come
-// from the offset alone (|o| is small), so the point is located to the precision of
-// o, not of x + o.
-__device__ __forceinline__ bool axis_cell(int base, float o, int n, bool walled, int& i0, int& i1,
-                                          float& fr) {
-    if (!(fabsf(o) < 1.0e6f)) return false;   // non-finite or absurd offset
-    const float fl = floorf(o);
-    int b = base + (int)fl;
-    float f = o - fl;
-    if (walled) {
-        if (b < 0 || b > n - 1 || (b == n - 1 && f > 0.0f)) return false;
-        if (n == 1) {
-            i0 = i1 = 0;
-            fr = 0.0f;
-            return true;
-        }
-        if (b == n - 1) {
-            b = n - 2;
-            f = 1.0f;
-        }
-        i0 = b;
-        i1 = b + 1;
-        fr = f;
-        return true;
-    }
-    i0 = wrap_near(b, n);
-    i1 = i0 + 1 == n ? 0 : i0 + 1;
-    fr = f;
-    return true;
-}
-
-__device__ __forceinline__ bool sample_phi(const StepParams& p, int x, int y, int z, float ox,
-                                           float oy, float oz, float& v) {
-    int ix0, ix1, iy0, iy1, iz0, iz1;
-    float fx, fy, fz;
-    if (!axis_cell(x, ox, p.nx, false, ix0, ix1, fx)) return false;
-    if (!axis_cell(y, oy, p.ny, p.wall_y, iy0, iy1, fy)) return false;
-    if (!axis_cell(z, oz, p.nz, p.wall_z, iz0, iz1, fz)) return false;
-    const float* f = p.phi_lag;
-    const size_t r00 = ((size_t)iz0 * p.ny + iy0) * p.nx, r01 = ((size_t)iz0 * p.ny + iy1) * p.nx;
-    const size_t r10 = ((size_t)iz1 * p.ny + iy0) * p.nx, r11 = ((size_t)iz1 * p.ny + iy1) * p.nx;
-    const float c00 = (1.0f - fx) * __ldg(f + r00 + ix0) + fx * __ldg(f + r00 + ix1);
-    const float c01 = (1.0f - fx) * __ldg(f + r01 + ix0) + fx * __ldg(f + r01 + ix1);
-    const float c10 = (1.0f - fx) * __ldg(f + r10 + ix0) + fx * __ldg(f + r10 + ix1);
-    const float c11 = (1.0f - fx) * __ldg(f + r11 + ix0) + fx * __ldg(f + r11 + ix1);
-    const float c0 = (1.0f - fy) * c00 + fy * c01;
-    const float c1 = (1.0f - fy) * c10 + fy * c11;
-    v = (1.0f - fz) * c0 + fz * c1;
-    return true;
-}
-
 // One term 3 w_i c_i v of the isotropic colour gradient (3 w_i = 1/6 for faces, 1/12
 // for edges), accumulated with explicit FMAs in direction order: every kernel that
 // evaluates a node's gradient gets the same bits.
@@ -275,25 +223,86 @@ __device__ __forceinline__ bool nc_ray(float Gx, float Gy, float Gz, float& nx_,
     return true;
 }
 
+// Ray sample positions: cell b = base + floor(o) and fraction o - floor(o) along one
+// axis, for |o| <= h_cut + 2 <= 11. Periodic axes of at least 12 nodes wrap with one
+// conditional add or subtract; shorter ones take the general wrap. On a walled axis
+// the point lies inside the fluid iff -base <= o <= n - 1 - base, i.e. its cell is a
+// fluid node and it does not pass the last node.
+__device__ __forceinline__ int ray_wrap(int b, int n) {
+    if (n >= 12) {
+        b = b < 0 ? b + n : b;
+        return b >= n ? b - n : b;
+    }
+    return wrap_near(b, n);
+}
+
 // Samples of a ray that must be evaluated: bit s set if sample s may be positive.
 // Scanning stops at the first sample outside the fluid (the march stops there).
+// A sample on the last node of a walled axis (fraction 0) is looked up in that
+// node's block: its value is that node's, whatever the other corner holds.
 __device__ __forceinline__ uint32_t nc_sample_mask(const StepParams& p, int x, int y, int z,
                                                    float nx_, float ny_, float nz_) {
     uint32_t mask = 0u;
+    const float ylo = (float)-y, yhi = (float)(p.ny - 1 - y);
+    const float zlo = (float)-z, zhi = (float)(p.nz - 1 - z);
     for (int s = 0; s < p.nsamp; ++s) {
         const float t = -1.0f + 0.5f * (float)s;
-        int ix0, iy0, iz0, i1;
-        float f;
-        if (!axis_cell(x, t * nx_, p.nx, false, ix0, i1, f) ||
-            !axis_cell(y, t * ny_, p.ny, p.wall_y, iy0, i1, f) ||
-            !axis_cell(z, t * nz_, p.nz, p.wall_z, iz0, i1, f))
-            break;
-        const int bx = ix0 >> 1;
-        const uint32_t w =
-            __ldg(p.nc_pos + ((size_t)(iz0 >> 1) * p.nby + (iy0 >> 1)) * p.nbw + (bx >> 5));
+        const float ox = t * nx_, oy = t * ny_, oz = t * nz_;
+        if (p.wall_y && !(oy >= ylo && oy <= yhi)) break;
+        if (p.wall_z && !(oz >= zlo && oz <= zhi)) break;
+        const int ix = ray_wrap(x + (int)floorf(ox), p.nx);
+        const int iy = ray_wrap(y + (int)floorf(oy), p.ny);   // identity on walled axes
+        const int iz = ray_wrap(z + (int)floorf(oz), p.nz);
+        const int bx = ix >> 1;
+        const uint32_t w = __ldg(p.nc_pos + ((iz >> 1) * p.nby + (iy >> 1)) * p.nbw + (bx >> 5));
         mask |= ((w >> (bx & 31)) & 1u) << s;
     }
     return mask;
+}
+
+// Trilinear sample of the lagged colour field at node (x, y, z) + offset o, for a
+// point known to lie inside the fluid (as nc_sample_mask established). The cell and
+// the weights come from the offset alone (|o| is small), so the point is located to
+// the precision of o, not of x + o; on the last node of a walled axis (fraction 0)
+// the cell below is used with fraction 1, which gives that node's value.
+__device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, int z, float ox,
+                                            float oy, float oz) {
+    const float flx = floorf(ox), fly = floorf(oy), flz = floorf(oz);
+    float fx = ox - flx, fy = oy - fly, fz = oz - flz;
+    int ix0 = x + (int)flx, iy0 = y + (int)fly, iz0 = z + (int)flz;
+    int ix1, iy1, iz1;
+    ix0 = ray_wrap(ix0, p.nx);
+    ix1 = ix0 + 1 == p.nx ? 0 : ix0 + 1;
+    if (p.wall_y) {
+        if (iy0 == p.ny - 1) {
+            iy0 = p.ny - 2;
+            fy = 1.0f;
+        }
+        iy1 = iy0 + 1;
+    } else {
+        iy0 = ray_wrap(iy0, p.ny);
+        iy1 = iy0 + 1 == p.ny ? 0 : iy0 + 1;
+    }
+    if (p.wall_z) {
+        if (iz0 == p.nz - 1) {
+            iz0 = p.nz - 2;
+            fz = 1.0f;
+        }
+        iz1 = iz0 + 1;
+    } else {
+        iz0 = ray_wrap(iz0, p.nz);
+        iz1 = iz0 + 1 == p.nz ? 0 : iz0 + 1;
+    }
+    const float* f = p.phi_lag;
+    const int r00 = (iz0 * p.ny + iy0) * p.nx, r01 = (iz0 * p.ny + iy1) * p.nx;
+    const int r10 = (iz1 * p.ny + iy0) * p.nx, r11 = (iz1 * p.ny + iy1) * p.nx;
+    const float c00 = (1.0f - fx) * __ldg(f + r00 + ix0) + fx * __ldg(f + r00 + ix1);
+    const float c01 = (1.0f - fx) * __ldg(f + r01 + ix0) + fx * __ldg(f + r01 + ix1);
+    const float c10 = (1.0f - fx) * __ldg(f + r10 + ix0) + fx * __ldg(f + r10 + ix1);
+    const float c11 = (1.0f - fx) * __ldg(f + r11 + ix0) + fx * __ldg(f + r11 + ix1);
+    const float c0 = (1.0f - fy) * c00 + fy * c01;
+    const float c1 = (1.0f - fy) * c10 + fy * c11;
+    return (1.0f - fz) * c0 + fz * c1;
 }
 
 // Crossing search over the evaluated samples v[0 .. s_last] of one ray (stride

@@ -563,10 +563,9 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
             }
             const int r = lo, sidx = task - pre[wib][r];
             const float t = -1.0f + 0.5f * (float)sidx;
-            float v = 0.0f;
-            sample_phi(p, rx[wib][r], ry[wib][r], rz[wib][r], t * rnx[wib][r], t * rny[wib][r],
-                       t * rnz[wib][r], v);   // inside the fluid: checked in phase 1
-            vals[wib][sidx][r] = v;
+            // inside the fluid: established in phase 1
+            vals[wib][sidx][r] = ray_sample(p, rx[wib][r], ry[wib][r], rz[wib][r], t * rnx[wib][r],
+                                            t * rny[wib][r], t * rnz[wib][r]);
         }
         __syncwarp();
         // phase 3
@@ -613,43 +612,45 @@ __global__ void nc_scan_kernel(const StepParams p, int4* list, int* count) {
     }
 }
 
-// Block bit field of the ray bound: one warp per 32 consecutive x-blocks; a block
-// is marked when one of the nodes 2b .. 2b+2 per axis (wrapped on periodic axes,
-// clipped at walls) has phi_lag > kPosBand.
+// Block bit field of the ray bound: one warp per 32 consecutive x-blocks (one
+// word); a block is marked when one of the nodes 2b .. 2b+2 per axis (wrapped on
+// periodic axes, clipped at walls) has phi_lag > kPosBand. For each of the 3 x 3
+// rows a lane loads the two nodes 2b, 2b+1 of its block (coalesced over the warp)
+// and takes node 2b+2 from the next lane.
 __global__ void nc_pos_kernel(const StepParams p) {
     const int lane = threadIdx.x & 31;
-    const long long words = (long long)p.nbw * p.nby * p.nbz;
-    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long w = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); w < words;
-         w += wstride) {
-        const int wx = (int)(w % p.nbw);
-        const int by = (int)((w / p.nbw) % p.nby);
-        const int bz = (int)(w / ((long long)p.nbw * p.nby));
+    const int words = p.nbw * p.nby * p.nbz;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < words; w += wstride) {
+        const int wx = w % p.nbw;
+        const int by = (w / p.nbw) % p.nby;
+        const int bz = w / (p.nbw * p.nby);
         const int bx = wx * 32 + lane;
-        bool pos = false;
-        if (bx < p.nbx) {
-            for (int dz = 0; dz < 3 && !pos; ++dz) {
-                int z = 2 * bz + dz;
-                if (z >= p.nz) {
-                    if (p.wall_z) break;
-                    z %= p.nz;
+        const int xa = (2 * bx) % p.nx, xb = (2 * bx + 1) % p.nx, xe = (64 * wx + 64) % p.nx;
+        float m = -1.0f;   // max over the block's nodes
+        for (int dz = 0; dz < 3; ++dz) {
+            int z = 2 * bz + dz;
+            if (z >= p.nz) {
+                if (p.wall_z) break;
+                z -= p.nz;
+                if (z >= p.nz) z %= p.nz;
+            }
+            for (int dy = 0; dy < 3; ++dy) {
+                int y = 2 * by + dy;
+                if (y >= p.ny) {
+                    if (p.wall_y) break;
+                    y -= p.ny;
+                    if (y >= p.ny) y %= p.ny;
                 }
-                for (int dy = 0; dy < 3 && !pos; ++dy) {
-                    int y = 2 * by + dy;
-                    if (y >= p.ny) {
-                        if (p.wall_y) break;
-                        y %= p.ny;
-                    }
-                    const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const int x = (2 * bx + dx) % p.nx;
-                        pos |= __ldg(row + x) > kPosBand;
-                    }
-                }
+                const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
+                const float v0 = __ldg(row + xa), v1 = __ldg(row + xb);
+                float v2 = __shfl_down_sync(0xffffffffu, v0, 1);
+                if (lane == 31) v2 = __ldg(row + xe);
+                m = fmaxf(m, fmaxf(v0, fmaxf(v1, v2)));
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, pos);
-        if (lane == 0) p.nc_pos[w] = m;
+        const unsigned bits = __ballot_sync(0xffffffffu, bx < p.nbx && m > kPosBand);
+        if (lane == 0) p.nc_pos[w] = bits;
     }
 }
 
