@@ -481,7 +481,10 @@ static void fill_step_params(lbm_ctx* c) {
     s.padx = c->padx;
     s.plane_p = (size_t)c->pitch * c->nyp;
     s.P = c->P;
-    s.ghost_in_kernel = (p.nx >= 4 && (p.wall_y || p.ny >= 4)) ? 1 : 0;
+    // the step kernel writes ghost copies itself (FP32; lattices of >= 4 nodes along
+    // the periodic axes). FP16/BF16 leave them to the ghost-fill pass: the extra
+    // emitter state costs more registers than that pass costs time.
+    s.ghost_in_kernel = (p.storage == 0 && p.nx >= 4 && (p.wall_y || p.ny >= 4)) ? 1 : 0;
     s.wall_y = p.wall_y ? 1 : 0;
     s.wall_z = p.wall_z ? 1 : 0;
     s.var_tau = p.tau_r != p.tau_b;

@@ -375,7 +375,7 @@ constexpr float kGradZero = 1e-6f;
 template <class St, bool Ghost>
 struct GlobalEmit {
     typename St::T* plane_out;   // start of this plane in block 0
-    size_t P;
+    size_t P;                    // elements between blocks
     uint32_t off;                // node offset within the padded plane
     int ng;
     int goff[3];                 // ghost offsets within the plane

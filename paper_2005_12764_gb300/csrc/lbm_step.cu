@@ -393,7 +393,8 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                     }
                 }
                 T* plane_out = fout + (size_t)z * p.plane_p;
-                if (warp_ghost) {
+                // (deviation storage never writes ghosts here: see ghost_in_kernel)
+                if (!G::DEV && warp_ghost) {
                     GlobalEmit<St, true> em{plane_out, p.P, toff, 0, {0, 0, 0}};
                     em.ng = ghost_offsets(em.goff);
                     collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy,
@@ -476,19 +477,30 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
 // lattices too small for the step kernel to write its ghosts itself).
 template <class St>
 __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
-    const size_t per = p.plane_p * p.nz;   // padded positions per block
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < per;
-         k += (size_t)gridDim.x * blockDim.x) {
-        const int xp = (int)(k % p.pitch);
-        const int yp = (int)((k / p.pitch) % p.nyp);
-        const int z = (int)(k / p.plane_p);
-        const int x = xp - p.padx, y = yp - 2;
-        const bool xin = x >= 0 && x < p.nx, yin = y >= 0 && y < p.ny;
-        if (xin && yin) continue;
-        if (x < -2 || x > p.nx + 1) continue;              // row padding, unused
-        if (!yin && (p.wall_y || y < -2 || y > p.ny + 1)) continue;
+    // ghost cells of one plane: x ghosts (2 + 2) of every row, then, on a periodic
+    // y axis, the 2 + 2 ghost rows including their corners
+    const int ncol = 4 * p.ny;
+    const int G = ncol + (p.wall_y ? 0 : 4 * (p.nx + 4));
+    const int total = G * p.nz;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int z = e / G, g = e - z * G;
+        int x, y;
+        if (g < ncol) {
+            y = g >> 2;
+            const int c = g & 3;
+            x = c < 2 ? c - 2 : p.nx + c - 2;
+        } else {
+            const int h = g - ncol, r = h / (p.nx + 4);
+            x = h - r * (p.nx + 4) - 2;
+            y = r < 2 ? r - 2 : p.ny + r - 2;
+        }
+        const size_t dst = pidx(p.pitch, p.nyp, p.padx, x, y, z);
         const size_t src = pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
-        for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + k] = f[(size_t)ik * p.P + src];
+        typename St::T v[2 * Q];
+#pragma unroll
+        for (int ik = 0; ik < 2 * Q; ++ik) v[ik] = f[(size_t)ik * p.P + src];
+#pragma unroll
+        for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + dst] = v[ik];
     }
 }
 
@@ -627,27 +639,25 @@ __global__ void nc_pos_kernel(const StepParams p) {
         const int bz = w / (p.nbw * p.nby);
         const int bx = wx * 32 + lane;
         const int xa = (2 * bx) % p.nx, xb = (2 * bx + 1) % p.nx, xe = (64 * wx + 64) % p.nx;
+        // all 3 x 3 rows are loaded before any is reduced, so the loads overlap
+        float a[9], b[9], e[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            int z = 2 * bz + r / 3, y = 2 * by + r % 3;
+            const bool zin = z < p.nz || !p.wall_z, yin = y < p.ny || !p.wall_y;
+            z = z < p.nz ? z : (z - p.nz) % p.nz;
+            y = y < p.ny ? y : (y - p.ny) % p.ny;
+            const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
+            a[r] = zin && yin ? __ldg(row + xa) : -1.0f;
+            b[r] = zin && yin ? __ldg(row + xb) : -1.0f;
+            e[r] = zin && yin && lane == 31 ? __ldg(row + xe) : -1.0f;
+        }
         float m = -1.0f;   // max over the block's nodes
-        for (int dz = 0; dz < 3; ++dz) {
-            int z = 2 * bz + dz;
-            if (z >= p.nz) {
-                if (p.wall_z) break;
-                z -= p.nz;
-                if (z >= p.nz) z %= p.nz;
-            }
-            for (int dy = 0; dy < 3; ++dy) {
-                int y = 2 * by + dy;
-                if (y >= p.ny) {
-                    if (p.wall_y) break;
-                    y -= p.ny;
-                    if (y >= p.ny) y %= p.ny;
-                }
-                const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
-                const float v0 = __ldg(row + xa), v1 = __ldg(row + xb);
-                float v2 = __shfl_down_sync(0xffffffffu, v0, 1);
-                if (lane == 31) v2 = __ldg(row + xe);
-                m = fmaxf(m, fmaxf(v0, fmaxf(v1, v2)));
-            }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            float c = __shfl_down_sync(0xffffffffu, a[r], 1);
+            if (lane == 31) c = e[r];
+            m = fmaxf(m, fmaxf(a[r], fmaxf(b[r], c)));
         }
         const unsigned bits = __ballot_sync(0xffffffffu, bx < p.nbx && m > kPosBand);
         if (lane == 0) p.nc_pos[w] = bits;
@@ -716,7 +726,8 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s) {
     const int threads = 256;
-    size_t blocks = (p.plane_p * p.nz + threads - 1) / threads;
+    const size_t cells = (size_t)(4 * p.ny + (p.wall_y ? 0 : 4 * (p.nx + 4))) * p.nz;
+    size_t blocks = (cells + threads - 1) / threads;
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     switch (storage) {
