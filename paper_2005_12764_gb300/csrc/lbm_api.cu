@@ -16,7 +16,8 @@
 #include "lbm_device.cuh"
 
 namespace lbm {
-cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage, int grid,
+cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
+                        int storage, int grid,
                         cudaStream_t s);
 cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int num_sms,
                       cudaStream_t s);
@@ -40,6 +41,7 @@ struct lbm_ctx {
     int padx = 0;               // interior offset within a padded row
     size_t P = 0;               // elements per padded [z][y][x] block
     CUtensorMap tmap[2];        // TMA load descriptors of the two population copies
+    CUtensorMap smap[2];        // TMA store descriptors (interior only: x < nx, y < ny)
     void* f[2] = {nullptr, nullptr};
     float* phi[2] = {nullptr, nullptr};
     float* fx_row = nullptr;
@@ -481,10 +483,6 @@ static void fill_step_params(lbm_ctx* c) {
     s.padx = c->padx;
     s.plane_p = (size_t)c->pitch * c->nyp;
     s.P = c->P;
-    // the step kernel writes ghost copies itself (FP32; lattices of >= 4 nodes along
-    // the periodic axes). FP16/BF16 leave them to the ghost-fill pass: the extra
-    // emitter state costs more registers than that pass costs time.
-    s.ghost_in_kernel = (p.storage == 0 && p.nx >= 4 && (p.wall_y || p.ny >= 4)) ? 1 : 0;
     s.wall_y = p.wall_y ? 1 : 0;
     s.wall_z = p.wall_z ? 1 : 0;
     s.var_tau = p.tau_r != p.tau_b;
@@ -627,11 +625,20 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         const CUtensorMapDataType dt = p->storage == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                        : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+        // store maps end at the interior (x < nx, y < ny), so the tile stores of edge
+        // tiles are clipped there and never touch ghost or padding cells
+        const cuuint64_t sdims[4] = {(cuuint64_t)(c->padx + p->nx), (cuuint64_t)(2 + p->ny),
+                                     (cuuint64_t)p->nz, (cuuint64_t)(2 * Q)};
+        const cuuint32_t sbox[4] = {(cuuint32_t)step_tile_x(), (cuuint32_t)step_tile_y(), 1, 1};
         for (int b = 0; b < 2; ++b) {
             CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r == CUDA_SUCCESS)
+                r = encode(&c->smap[b], dt, 4, c->f[b], sdims, strides, sbox, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) {
                 lbm_destroy(c);
                 return fail(nullptr, LBM_ECUDA, "cuTensorMapEncodeTiled failed");
@@ -765,7 +772,6 @@ extern "C" lbm_status lbm_set_pin_mask(lbm_ctx* c, const uint8_t* mask, int on_d
 static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
     StepParams s = c->sp;
     s.fin = c->f[c->cur];
-    s.fout = c->f[1 - c->cur];
     s.phi_lag = c->phi[c->pc];
     s.phi_out = c->phi[1 - c->pc];
     cudaError_t e = cudaSuccess;
@@ -790,8 +796,10 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
         s.cand_count = c->cand_count + c->cw;
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
-    if (e == cudaSuccess) e = launch_step(s, c->tmap[c->cur], c->p.storage, c->grid, c->stream);
-    if (e == cudaSuccess && !s.ghost_in_kernel)
+    if (e == cudaSuccess)
+        e = launch_step(s, c->tmap[c->cur], c->smap[1 - c->cur], c->p.storage, c->grid, c->stream);
+    // ghost copies of the periodic axes for the next step's halo loads
+    if (e == cudaSuccess)
         e = launch_ghost_fill(c->f[1 - c->cur], s, c->p.storage, c->num_sms, c->stream);
     if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
     if (e != cudaSuccess) return e;

@@ -99,7 +99,6 @@ struct StoreBF16 {
 // ---------------------------------------------------------------- parameters
 struct StepParams {
     const void* fin;        // populations at the start of the step (post-collision)
-    void* fout;             // populations after the step
     const float* phi_lag;   // colour field of the previous step (near-contact rays)
     float* phi_out;         // colour field of this step
     const float* fx_row;    // [ny] x body force per row: g_x + Kolmogorov profile
@@ -132,7 +131,6 @@ struct StepParams {
     float ref_half;         // rho0/2 for FP16/BF16 deviation storage, 0 for FP32
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
-    int ghost_in_kernel;    // the step kernel writes the ghost copies (else a fill pass)
     int* err;               // device error word: 1 = a bounded wait gave up
 };
 
@@ -370,23 +368,13 @@ constexpr float kGradZero = 1e-6f;
 // the other perturbations, so the perturbation conserves mass exactly.
 // Output of the collision: one value per direction block k (species * 19 + direction)
 // handed to an emitter functor, emit(k, value, ref), with k a compile-time constant
-// after unrolling. Two emitters are used: one writes a shared-memory output tile
-// (stored to global memory by TMA), the other writes global memory directly.
-template <class St, bool Ghost>
-struct GlobalEmit {
-    typename St::T* plane_out;   // start of this plane in block 0
-    size_t P;                    // elements between blocks
-    uint32_t off;                // node offset within the padded plane
-    int ng;
-    int goff[3];                 // ghost offsets within the plane
+// after unrolling. The emitter writes the plane's shared-memory output tile, which
+// the step kernel stores to global memory with tensor copies.
+template <class St, int NT>
+struct SmemEmit {
+    typename St::T* tile;        // this node in block 0 of the shared output tile
     __device__ __forceinline__ void operator()(int k, float v, float ref) const {
-        typename St::T* base = plane_out + (size_t)k * P;
-        St::store(base, off, v, ref);
-        if (Ghost) {
-#pragma unroll
-            for (int g = 0; g < 3; ++g)
-                if (g < ng) St::store(base, (uint32_t)((int)off + goff[g]), v, ref);
-        }
+        tile[k * NT] = St::enc(v, ref);   // NT nodes per block of the tile
     }
 };
 

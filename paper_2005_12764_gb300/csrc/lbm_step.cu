@@ -33,7 +33,6 @@
 namespace lbm {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int STAGES = 1;      // staged planes per CTA
 constexpr int CTAS_PER_SM = 2;
 constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
@@ -41,9 +40,11 @@ constexpr int NRING = 2 * (TX + 2) + 2 * TY;
 template <class St>
 struct Geo {
     using T = typename St::T;
-    static constexpr int PADX = 2;                        // interior offset in a padded row
-    // load box: columns x0-2 .. x0+TX+1, widened so a row is a multiple of 16 bytes
-    static constexpr int BW = ((TX + 4) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    // interior offset in a padded row: 16 bytes, so that tensor stores of a tile start
+    // on a 16-byte boundary
+    static constexpr int PADX = 16 / (int)sizeof(T);
+    // load box: columns x0-PADX .. x0+TX+PADX-1 (covers the pulls x0-2 .. x0+TX+1)
+    static constexpr int BW = TX + 2 * PADX;
     static constexpr int BOX_BYTES = BW * SH * (int)sizeof(T);
     static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
@@ -54,8 +55,13 @@ struct Geo {
     static constexpr bool DEV = St::kind != 0;
     static constexpr int LW = TX + 4, LH = TY + 4;
     static constexpr size_t LAG_BYTES = DEV ? 4 * LH * LW * sizeof(float) : 0;
-    static constexpr size_t SMEM =
-        STAGES * STAGE_BYTES + PHI_BYTES + LAG_BYTES + 2 * sizeof(unsigned long long);
+    // output tile of a plane, [2Q][TY][TX], stored by tensor copies
+    static constexpr size_t OUT_BYTES = (size_t)2 * Q * TX * TY * sizeof(T);
+    // staged planes per CTA: two where they fit beside the output tile at two CTAs
+    // per SM (2-byte storage), so a plane's copy is issued a full plane ahead
+    static constexpr int STAGES = sizeof(T) == 2 ? 2 : 1;
+    static constexpr size_t SMEM = STAGES * STAGE_BYTES + OUT_BYTES + PHI_BYTES + LAG_BYTES +
+                                   2 * sizeof(unsigned long long);
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -90,6 +96,20 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         "r"(smem_u32(bar))
         : "memory");
 }
+// Tensor store of one box from shared memory (bulk group), and the group waits.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                             const void* src) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -109,19 +129,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 // ---------------------------------------------------------------- the kernel
 template <class St, bool UnitOmega>
 __global__ void __launch_bounds__(NT, CTAS_PER_SM)
-step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
+step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
+            const __grid_constant__ CUtensorMap fout_map) {
     using T = typename St::T;
     using G = Geo<St>;
-    constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX;
+    constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, STAGES = G::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
-    float* sphi = reinterpret_cast<float*>(smem + STAGES * G::STAGE_BYTES);   // [4][SH][SWP]
-    float* slag = reinterpret_cast<float*>(smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES);
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(
-        smem + STAGES * G::STAGE_BYTES + G::PHI_BYTES + G::LAG_BYTES);
+    T* sout = reinterpret_cast<T*>(smem + STAGES * G::STAGE_BYTES);           // [2Q][TY][TX]
+    unsigned char* rest = smem + STAGES * G::STAGE_BYTES + G::OUT_BYTES;
+    float* sphi = reinterpret_cast<float*>(rest);                              // [4][SH][SWP]
+    float* slag = reinterpret_cast<float*>(rest + G::PHI_BYTES);
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(rest + G::PHI_BYTES + G::LAG_BYTES);
 
     const T* __restrict__ fin = static_cast<const T*>(p.fin);
-    T* __restrict__ fout = static_cast<T*>(p.fout);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const size_t plane = (size_t)p.nx * p.ny;
@@ -131,6 +153,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
         mbar_init(&bars[1], 2 * Q);
         fence_mbar_init();
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fin_map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fout_map)) : "memory");
     }
     __syncthreads();
     uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
@@ -283,34 +306,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             if (tid + NT < LN) d[tid + NT] = lag_reg1;
         };
 
-        // ---- ghost copies this thread's node writes (periodic axes, edge nodes), as
-        // offsets within a padded plane
         const int gxn = x0 + otx, gyn = y0 + oty;
-        // (recomputed where used, to keep them out of the registers live in the march)
-        auto ghost_offsets = [&](int (&goff)[3]) {
-            int dxg = 0, dyg = 0;
-            if (owned && p.ghost_in_kernel) {
-                if (gxn < 2) dxg = p.nx;
-                else if (gxn >= p.nx - 2) dxg = -p.nx;
-                if (!p.wall_y) {
-                    if (gyn < 2) dyg = p.ny;
-                    else if (gyn >= p.ny - 2) dyg = -p.ny;
-                }
-            }
-            const int oy = dyg * p.pitch;
-            goff[0] = dxg ? dxg : oy;
-            goff[1] = oy;
-            goff[2] = dxg + oy;
-            return (dxg != 0) + (dyg != 0) + (dxg != 0 && dyg != 0);
-        };
-        bool warp_ghost;
-        {
-            int g[3];
-            warp_ghost = __any_sync(0xffffffffu, ghost_offsets(g) > 0);
-        }
-        // this node's offset within a padded plane
-        const uint32_t toff = (uint32_t)((gyn + 2) * p.pitch + (gxn + PADX));
-
         const bool use_nc = p.A_nc > 0.0f;
         const size_t col = (size_t)gyn * p.nx + gxn;   // owned column (unpadded fields)
         const float fx_y = owned ? __ldg(p.fx_row + gyn) : 0.0f;
@@ -336,6 +332,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             wait(bn);
             densities(bn, z + 1, nx_f, nx_rr, nx_rb, true);
             if (G::DEV) lag_commit(z + 3);
+            if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
             __syncthreads();
             if (STAGES == 1) {
                 fence_proxy_async();
@@ -392,19 +389,20 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
                                       __float_as_int(Gz));
                     }
                 }
-                T* plane_out = fout + (size_t)z * p.plane_p;
-                // (deviation storage never writes ghosts here: see ghost_in_kernel)
-                if (!G::DEV && warp_ghost) {
-                    GlobalEmit<St, true> em{plane_out, p.P, toff, 0, {0, 0, 0}};
-                    em.ng = ghost_offsets(em.goff);
-                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy,
-                                                 Fz, em);
-                } else {
-                    const GlobalEmit<St, false> em{plane_out, p.P, toff, 0, {0, 0, 0}};
-                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy,
-                                                 Fz, em);
-                }
+                // outputs go to the shared output tile; the tile is stored below
+                const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
+                collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
                 p.phi_out[node] = phic;
+            }
+            // store the output tile of plane z: 2Q tensor copies of TX x TY, clipped by
+            // the store map at the lattice edge (ghost copies are written by the fill
+            // pass); the tile is rewritten only after these copies have read it
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                for (int k = 0; k < 2 * Q; ++k)
+                    tma_store_4d(&fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
+                bulk_commit();
             }
             ah_c = ah_nxt;
         };
@@ -462,6 +460,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map) {
             a_rb = b_rb;
         }
     }
+    if (tid == 0) bulk_wait_all();   // output tiles written before the CTA exits
     if (failed) {
         // give copies still in flight into this CTA's shared memory a bounded chance
         // to land before the CTA exits
@@ -690,8 +689,8 @@ cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, 
 }
 
 template <class St, bool U>
-static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map, int grid,
-                               cudaStream_t s) {
+static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map,
+                               const CUtensorMap& omap, int grid, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel<St, U>,
@@ -700,25 +699,25 @@ static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    step_kernel<St, U><<<grid, NT, Geo<St>::SMEM, s>>>(p, map);
+    step_kernel<St, U><<<grid, NT, Geo<St>::SMEM, s>>>(p, map, omap);
     return cudaGetLastError();
 }
 
 // omega == 1 everywhere (equal relaxation times tau = 1) drops the non-equilibrium
 // terms of the collision
 template <class St>
-static cudaError_t launch_tpl(const StepParams& p, const CUtensorMap& map, int grid,
-                              cudaStream_t s) {
-    if (!p.var_tau && p.omega0 == 1.0f) return launch_tpl2<St, true>(p, map, grid, s);
-    return launch_tpl2<St, false>(p, map, grid, s);
+static cudaError_t launch_tpl(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
+                              int grid, cudaStream_t s) {
+    if (!p.var_tau && p.omega0 == 1.0f) return launch_tpl2<St, true>(p, map, omap, grid, s);
+    return launch_tpl2<St, false>(p, map, omap, grid, s);
 }
 
-cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, int storage, int grid,
-                        cudaStream_t s) {
+cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
+                        int storage, int grid, cudaStream_t s) {
     switch (storage) {
-        case 0: return launch_tpl<StoreF32>(p, map, grid, s);
-        case 1: return launch_tpl<StoreF16>(p, map, grid, s);
-        case 2: return launch_tpl<StoreBF16>(p, map, grid, s);
+        case 0: return launch_tpl<StoreF32>(p, map, omap, grid, s);
+        case 1: return launch_tpl<StoreF16>(p, map, omap, grid, s);
+        case 2: return launch_tpl<StoreBF16>(p, map, omap, grid, s);
     }
     return cudaErrorInvalidValue;
 }
