@@ -148,6 +148,15 @@ lbm_status lbm_get_pops(lbm_ctx* ctx, double* f_r, double* f_b, double* phi_lag,
 lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f_r, const double* f_b,
                         const double* phi_lag, int on_device);
 
+/* The same data for the sub-box of wx x wy x wz nodes starting at node (x0, y0, z0):
+ * f_r, f_b float64 [19][wz][wy][wx], phi_lag [wz][wy][wx] (may be NULL), wrapped
+ * around periodic axes. 1 <= w <= n per axis; along a walled axis the box must lie
+ * inside the lattice. Lets a caller inspect (or check against a reference) part of
+ * a lattice too large to copy out whole. Allocates a temporary device buffer of
+ * 39 wx wy wz doubles; synchronises the stream.                                  */
+lbm_status lbm_get_window(lbm_ctx* ctx, int x0, int y0, int z0, int wx, int wy, int wz,
+                          double* f_r, double* f_b, double* phi_lag, int on_device);
+
 /* FP64 conserved totals of the current state, summed on the device in a fixed
  * order: out = {sum f^r, sum f^b, P_x, P_y, P_z, steps, 0, 0}, P = sum_i c_i f_i.
  * Synchronises the stream.                                                      */

@@ -53,7 +53,8 @@ struct lbm_ctx {
     uint32_t* nc_pos = nullptr;         // near-contact ray bound (block bit field)
     int cw = 0;                 // list the next step kernel writes
     bool nc_scan = true;        // next near-contact pass must scan every node
-    double* stage = nullptr;    // device FP64 staging, 6N doubles
+    double* stage = nullptr;    // device FP64 staging, grown on demand
+    size_t stage_cap = 0;       // its size in doubles
     double* red = nullptr;      // reduction partials
     double* red_host = nullptr; // pinned host copy of reduction results
     int red_blocks = 0;
@@ -215,6 +216,29 @@ __global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, const
             fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
             fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
         }
+    }
+}
+
+// Populations and current colour field of the sub-box (x0, y0, z0) + [0, wx) x
+// [0, wy) x [0, wz), wrapped on periodic axes, into out = {f_r [19][M], f_b [19][M],
+// phi [M]}, M = wx wy wz (box index x fastest).
+template <class St>
+__global__ void window_kernel(const typename St::T* f, StepParams sp, const float* phi_cur, int x0,
+                              int y0, int z0, int wx, int wy, int wz, double* out) {
+    const size_t M = (size_t)wx * wy * wz, P = sp.P;
+    for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M;
+         m += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(m % wx), j = (int)((m / wx) % wy), k = (int)(m / ((size_t)wx * wy));
+        const int x = wrap_near(x0 + i, sp.nx), y = wrap_near(y0 + j, sp.ny), z = wrap_near(z0 + k, sp.nz);
+        const size_t n = ((size_t)z * sp.ny + y) * sp.nx + x;
+        const size_t q = pidx(sp.pitch, sp.nyp, sp.padx, x, y, z);
+        const float ph = ref_phi<St>(phi_cur, n);
+#pragma unroll
+        for (int d = 0; d < Q; ++d) {
+            out[(size_t)d * M + m] = ldpop<St>(f, (size_t)d * P + q, d, 0, sp.ref_half, ph);
+            out[(size_t)(Q + d) * M + m] = ldpop<St>(f, (size_t)(Q + d) * P + q, d, 1, sp.ref_half, ph);
+        }
+        out[(size_t)2 * Q * M + m] = phi_cur[n];
     }
 }
 
@@ -675,12 +699,21 @@ extern "C" const char* lbm_last_error(const lbm_ctx* c) {
     return c ? c->err.c_str() : g_create_err.c_str();
 }
 
-static lbm_status ensure_stage(lbm_ctx* c) {
-    if (c->stage) return LBM_OK;
-    if (cudaMalloc((void**)&c->stage, 2 * Q * c->N * sizeof(double)) != cudaSuccess) {
+// FP64 staging of at least `doubles` values (grown on demand; the old contents are
+// not kept). Calls that only exchange fields need 7N, population calls 2QN.
+static lbm_status ensure_stage(lbm_ctx* c, size_t doubles) {
+    if (c->stage && c->stage_cap >= doubles) return LBM_OK;
+    if (c->stage) {
+        cudaStreamSynchronize(c->stream);   // queued work may still read the old buffer
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_cap = 0;
+    }
+    if (cudaMalloc((void**)&c->stage, doubles * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, LBM_ENOMEM, "staging allocation failed");
     }
+    c->stage_cap = doubles;
     return LBM_OK;
 }
 
@@ -698,7 +731,7 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const doub
     const size_t N = c->N;
     const double *dr = rho_r, *db = rho_b, *du = u;
     if (!on_device) {
-        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        if (ensure_stage(c, 5 * c->N) != LBM_OK) return LBM_ENOMEM;
         CK(c, cudaMemcpyAsync(c->stage, rho_r, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemcpyAsync(c->stage + N, rho_b, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         dr = c->stage;
@@ -855,7 +888,7 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
     const size_t N = c->N;
     double *dr = rho_r, *db = rho_b, *du = u, *dp = phi;
     if (!on_device) {
-        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
         dr = rho_r ? c->stage : nullptr;
         db = rho_b ? c->stage + N : nullptr;
         du = u ? c->stage + 2 * N : nullptr;
@@ -867,7 +900,7 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
     if (c->steps > 0 && c->p.A_nc > 0.0) {
         // A_h of the last step, re-measured on its lag field in scan mode into scratch
         // space after the staged fields (the live A_h buffer is left untouched)
-        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
         s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
         s.nc_list = nullptr;
         s.nc_count = nullptr;
@@ -896,7 +929,7 @@ extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
     if (!ah) return fail(c, LBM_EINVAL, "ah is required");
     const size_t N = c->N;
-    if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+    if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
     const int grid = grid_for(N, c->num_sms);
     float* scratch = reinterpret_cast<float*>(c->stage + 6 * N);
     if (c->p.A_nc > 0.0) {
@@ -928,7 +961,7 @@ extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double*
     const size_t N = c->N;
     double *dr = f_r, *db = f_b;
     if (!on_device) {
-        if (ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+        if (ensure_stage(c, 2 * Q * N) != LBM_OK) return LBM_ENOMEM;
         dr = c->stage;
         db = c->stage + Q * N;
     }
@@ -959,13 +992,47 @@ extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double*
     return LBM_OK;
 }
 
+extern "C" lbm_status lbm_get_window(lbm_ctx* c, int x0, int y0, int z0, int wx, int wy, int wz,
+                                     double* f_r, double* f_b, double* phi_lag, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (!f_r || !f_b) return fail(c, LBM_EINVAL, "f_r and f_b are required");
+    const lbm_params& p = c->p;
+    if (wx < 1 || wy < 1 || wz < 1 || wx > p.nx || wy > p.ny || wz > p.nz)
+        return fail(c, LBM_EINVAL, "window extents must be in [1, n] per axis");
+    if ((p.wall_y && (y0 < 0 || y0 + wy > p.ny)) || (p.wall_z && (z0 < 0 || z0 + wz > p.nz)))
+        return fail(c, LBM_EINVAL, "window must lie inside the lattice along walled axes");
+    const size_t M = (size_t)wx * wy * wz, total = (2 * Q + 1) * M;
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, total * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LBM_ENOMEM, "window staging allocation failed");
+    }
+    const int grid = grid_for(M, c->num_sms);
+    dispatch(p.storage, [&](auto st) {
+        using St = decltype(st);
+        window_kernel<St><<<grid, kThreads, 0, c->stream>>>((const typename St::T*)c->f[c->cur], c->sp,
+                                                            c->phi[c->pc], x0, y0, z0, wx, wy, wz, buf);
+    });
+    cudaError_t e = cudaGetLastError();
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_r, buf, Q * M * sizeof(double), kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_b, buf + Q * M, Q * M * sizeof(double), kind, c->stream);
+    if (e == cudaSuccess && phi_lag)
+        e = cudaMemcpyAsync(phi_lag, buf + 2 * Q * M, M * sizeof(double), kind, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_window");
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* f_b,
                                    const double* phi_lag, int on_device) {
     if (!c) return LBM_EINVAL;
     if (!f_r || !f_b) return fail(c, LBM_EINVAL, "f_r and f_b are required");
     const size_t N = c->N;
     const int grid = grid_for(N, c->num_sms);
-    if (!on_device && ensure_stage(c) != LBM_OK) return LBM_ENOMEM;
+    if (!on_device && ensure_stage(c, 2 * Q * N) != LBM_OK) return LBM_ENOMEM;
     // the colour field first: deviation storage encodes the populations against it
     if (phi_lag) {
         const double* src = phi_lag;

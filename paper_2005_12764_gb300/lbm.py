@@ -29,7 +29,7 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_observables", "lbm_laplace",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
-           "lbm_totals_noalloc", "lbm_get_nc_field"]
+           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_get_window"]
 
 
 class LbmError(RuntimeError):
@@ -93,6 +93,7 @@ def load():
             "lbm_last_error": (C.c_char_p, [_P]),
             "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
+            "lbm_get_window": (C.c_int, [_P] + [C.c_int] * 6 + [_D, _D, _D, C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -265,6 +266,17 @@ class Lattice:
     def set_pops(self, fr, fb, phi_lag=None):
         (pr, pb, pl), dev, keep = self._ptrs([fr, fb, phi_lag], [Q * self.N, Q * self.N, self.N])
         self._check(self._lib.lbm_set_pops(self._h, pr, pb, pl, dev))
+
+    def get_window(self, x0, y0, z0, wx, wy, wz):
+        """(f_r [19, wz, wy, wx], f_b, phi_lag [wz, wy, wx]) of a sub-box, wrapped on
+        periodic axes (host copies)."""
+        fr = np.empty((Q, wz, wy, wx))
+        fb = np.empty((Q, wz, wy, wx))
+        lag = np.empty((wz, wy, wx))
+        self._check(self._lib.lbm_get_window(self._h, int(x0), int(y0), int(z0), int(wx), int(wy),
+                                             int(wz), fr.ctypes.data, fb.ctypes.data,
+                                             lag.ctypes.data, 0))
+        return fr, fb, lag
 
     def get_nc_field(self):
         """A_h [z, y, x] on the current colour field (what the next step will use)."""

@@ -1,0 +1,137 @@
+"""Full-size workloads on the GPU, in the launch configuration of the benchmark.
+
+- Dense emulsion: 512^3 periodic, random non-overlapping droplets (volume fraction
+  0.35, radii uniform in [6, 12]), Kolmogorov forcing 1e-5 sin(2 pi y / 512),
+  near-contact force on.
+- Bicontinuous gel quench: 640^3 periodic, symmetric mixture with colour noise of
+  amplitude 0.01 and 2 % pinning sites, tau = 0.8, sigma = 0.015, A_nc = 0.02.
+
+The oracle cannot hold these lattices, so each is checked in two ways:
+1. at sampled nodes, one step at a time: a cube of 2R+1 nodes around each sample
+   (R = 12 covers the pull, the gradient of the pulled densities and the
+   near-contact rays of the lagged field, at most h_cut + 3 = 9 nodes) is copied
+   out of the GPU state, the oracle steps that cube as a periodic lattice of its
+   own, and the GPU's next-step populations at the sample must match the oracle's
+   at the cube's centre (nodes further out are wrong in the oracle's cube, but the
+   centre depends on none of them);
+2. by invariants that hold at any size: each species' mass is conserved and every
+   value stays finite.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_12764_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+R = 12
+W = 2 * R + 1
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12764_gb300 import build_lib, lbm as L
+    build_lib.build()
+    L.load()
+    return L
+
+
+def _map_to_oracle(lbm):
+    """index map: oracle direction k -> library direction."""
+    cg = lbm.velocity_set()
+    co = oracle.lattice()[0]
+    return np.array([int(np.nonzero((cg == co[k]).all(1))[0][0]) for k in range(19)])
+
+
+def _window_params(params, shape, y_centre):
+    """Oracle parameters of a window cube: Kolmogorov forcing depends on the
+    absolute row, so it enters as the uniform force the centre row feels."""
+    kw = dict(params)
+    ny = shape[1]
+    amp = kw.pop("kolmogorov_amp", 0.0)
+    g = list(kw.pop("g", (0.0, 0.0, 0.0)))
+    g[0] += amp * math.sin(2.0 * math.pi * y_centre / ny)
+    return oracle.make_params(W, W, W, g=tuple(g), **kw)
+
+
+def _check_sampled_step(lbm, g, w, samples, pins=None):
+    m = _map_to_oracle(lbm)
+    nz, ny, nx = w.shape
+    before = [g.get_window(x - R, y - R, z - R, W, W, W) for (x, y, z) in samples]
+    g.step(1)
+    worst, bad = 0.0, 0
+    for (x, y, z), (fr, fb, lag) in zip(samples, before):
+        P = _window_params(w.params, w.shape, y)
+        pw = None
+        if pins is not None:
+            zz = (np.arange(z - R, z + R + 1) % nz)[:, None, None]
+            yy = (np.arange(y - R, y + R + 1) % ny)[None, :, None]
+            xx = (np.arange(x - R, x + R + 1) % nx)[None, None, :]
+            pw = pins[zz, yy, xx].ravel()
+        centre = (R * W + R) * W + R
+        oa, ob, _ = oracle.step_nodes(P, fr.reshape(19, -1)[m], fb.reshape(19, -1)[m],
+                                      lag.ravel(), np.array([centre]), pin=pw)
+        gr, gb, _ = g.get_window(x, y, z, 1, 1, 1)
+        d = max(np.abs(oa[0] - gr.reshape(19)[m]).max(), np.abs(ob[0] - gb.reshape(19)[m]).max())
+        worst = max(worst, d)
+        bad += d > 1e-6
+    return worst, bad
+
+
+def _samples(rng, shape, droplets, n_any, n_iface):
+    """n_any uniformly random nodes, plus n_iface nodes on droplet surfaces (the
+    nearest node to a random point of a random droplet's sphere)."""
+    nz, ny, nx = shape
+    out = [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz)))
+           for _ in range(n_any)]
+    for _ in range(n_iface if droplets else 0):
+        cx, cy, cz, r = droplets[int(rng.integers(len(droplets)))]
+        d = rng.normal(size=3)
+        p = np.array([cx, cy, cz]) + r * d / np.linalg.norm(d)
+        out.append((int(round(p[0])) % nx, int(round(p[1])) % ny, int(round(p[2])) % nz))
+    return out
+
+
+def test_dense_emulsion_512_full_size(lbm):
+    w = inputs.dense_emulsion()        # 512^3, volume fraction 0.35, radii 6-12
+    assert w.params_extra["achieved_fraction"] > 0.34
+    n = w.shape[0]
+    g = lbm.Lattice(lbm.make_params(n, n, n, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    m0 = g.observables()
+    g.step(20)
+    samples = _samples(np.random.default_rng(31), w.shape, w.droplets, 6, 10)
+    worst, bad = _check_sampled_step(lbm, g, w, samples)
+    print("emulsion 512^3: worst |d f| at samples", worst)
+    assert bad == 0, worst
+    m1 = g.observables()
+    assert np.isfinite(m1[:5]).all()
+    # per-species mass: FP32 arithmetic on 1.3e8 nodes, relative drift well below 1e-6
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6
+    g.close()
+
+
+def test_bicontinuous_gel_640_full_size(lbm):
+    w = inputs.bicontinuous()          # 640^3, noise 0.01, 2 % pins
+    n = w.shape[0]
+    g = lbm.Lattice(lbm.make_params(n, n, n, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    g.set_pin_mask(w.pins)
+    m0 = g.observables()
+    g.step(10)
+    # every node of the noise field lies on an interface
+    samples = _samples(np.random.default_rng(32), w.shape, [], 16, 0)
+    worst, bad = _check_sampled_step(lbm, g, w, samples, pins=w.pins)
+    print("gel 640^3: worst |d f| at samples", worst)
+    # a film thickness that sits on a zero crossing may take the other branch in FP32
+    assert bad <= 1, worst
+    m1 = g.observables()
+    assert np.isfinite(m1[:5]).all()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6
+    g.close()

@@ -276,6 +276,26 @@ def test_deviation_storage_pops_round_trip(lbm, storage):
     assert np.abs(fr2 - fr).max() <= 1e-6 and np.abs(fb2 - fb).max() <= 1e-6
 
 
+def test_window_matches_full_download_with_wrap(lbm):
+    # a box that wraps around all three periodic axes, against the full download
+    shape = (12, 10, 16)
+    rr, rb, u = inputs.random_state(shape, seed=8, u_amp=0.01)
+    for storage in ("fp32", "fp16"):
+        g = lbm.Lattice(lbm.make_params(16, 10, 12, sigma=0.01, storage=storage))
+        g.set_fields(rr, rb, u)
+        g.step(3)
+        fr, fb, lag = g.get_pops()
+        x0, y0, z0, wx, wy, wz = 13, -2, 9, 7, 5, 6
+        wr, wb, wl = g.get_window(x0, y0, z0, wx, wy, wz)
+        zz = (np.arange(z0, z0 + wz) % 12)[:, None, None]
+        yy = (np.arange(y0, y0 + wy) % 10)[None, :, None]
+        xx = (np.arange(x0, x0 + wx) % 16)[None, None, :]
+        assert np.array_equal(wr, fr[:, zz, yy, xx]) and np.array_equal(wb, fb[:, zz, yy, xx])
+        assert np.array_equal(wl, lag[zz, yy, xx])
+    with pytest.raises(lbm.LbmError):
+        g.get_window(0, 0, 0, 17, 1, 1)
+
+
 def test_invalid_arguments_are_rejected(lbm):
     for bad in (dict(tau_r=0.5), dict(beta=1.5), dict(storage=7)):
         kw = dict(tau_r=1.0)
