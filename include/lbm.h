@@ -214,6 +214,80 @@ void lbm_destroy(lbm_ctx* ctx);
  * NULL). Valid until the next call on the same context.                          */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
+/* ------------------------------------------------------------------------------
+ * Serving engine: independent lattices ("requests": droplet or emulsion design runs
+ * of any box size) kept resident on the device and advanced together. The paper
+ * has no counterpart; it is the batching and serving layer around the step above.
+ *
+ * - Requests are queued (FIFO) by lbm_engine_submit and admitted by
+ *   lbm_engine_tick while the device memory of the resident lattices (their
+ *   lbm_footprint_bytes plus 56 bytes of host-exchange staging per node) stays
+ *   within hbm_budget_bytes and at most max_slots are resident. A request that can
+ *   never fit is refused at submission (LBM_ENOMEM).
+ * - Every tick advances all resident lattices by the same number of steps k (at most
+ *   chunk_steps, and not past any lattice's last step): the lattices of one storage
+ *   format and relaxation class advance in one batched launch of the step kernel
+ *   (CTAs of all lattices in one grid) followed by one batched ghost fill, captured
+ *   in a CUDA graph of two steps that is replayed k/2 times and re-captured when the
+ *   resident set changes. Lattices that reach their last step retire at the end of
+ *   the tick: their fields are copied to host memory and their device memory is
+ *   released, so queued requests are admitted at the next tick (continuous
+ *   batching).
+ * - Block schedule: each lattice's z range is cut into parts of at most T planes
+ *   (one CTA per part and 32 x 8 tile); T is chosen per batch composition by timing
+ *   the candidates T = 8, 16, 32, 64, 128 on the first tick of a new composition
+ *   (the timed steps are real steps of the requests) and remembered.
+ * - A request's result does not depend on the other requests or on the schedule:
+ *   every node is computed by the same arithmetic in any batch.
+ * - Requests with A_nc > 0 are refused (LBM_EINVAL): the near-contact pass is not
+ *   batched.
+ * An engine is not thread-safe; its calls run on its stream and synchronise it.  */
+typedef struct lbm_engine lbm_engine;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory the resident lattices may hold          */
+    int max_slots;            /* resident lattices at most (>= 1)                      */
+    int chunk_steps;          /* steps per tick at most (>= 2)                         */
+    int autotune;             /* 1: time the block-schedule candidates; 0: T = 32      */
+    void* cuda_stream;        /* cudaStream_t of all engine work, or NULL              */
+} lbm_engine_params;
+
+lbm_status lbm_engine_create(const lbm_engine_params* p, lbm_engine** out);
+
+/* Queues a request: a lattice with parameters p (p->cuda_stream is ignored) and
+ * initial fields as for lbm_set_fields (host arrays, copied; u may be NULL), to be
+ * advanced `steps` >= 1 steps. *ticket identifies it (> 0).                     */
+lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, const double* rho_r,
+                             const double* rho_b, const double* u, long long steps,
+                             long long* ticket);
+
+/* One round: admit, advance, retire (see above). Writes (any pointer may be NULL)
+ * the number of resident lattices after admission, of queued requests left, of
+ * requests retired by this tick, and of steps k advanced. Synchronises.          */
+lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued, int* retired,
+                           int* steps_advanced);
+
+/* State of a request: 0 queued, 1 resident, 2 finished (result ready), 3 result
+ * taken, -1 unknown ticket.                                                      */
+int lbm_engine_state(const lbm_engine* e, long long ticket);
+
+/* Fields of a finished request (host arrays, any may be NULL; layouts as for
+ * lbm_get_fields) and info = {steps done, tick of submission, tick of admission,
+ * tick of retirement}. The result is released afterwards (state 3). LBM_ESTATE if
+ * the request has not finished.                                                 */
+lbm_status lbm_engine_result(lbm_engine* e, long long ticket, double* rho_r, double* rho_b,
+                             double* u, double* phi, long long info[4]);
+
+/* Engine counters: {ticks, resident, queued, device bytes held, peak device bytes,
+ * block-schedule T in use, batched launches per step}.                          */
+void lbm_engine_stats(const lbm_engine* e, long long out[7]);
+
+/* Releases the engine, its resident lattices and unreturned results. NULL: no-op. */
+void lbm_engine_destroy(lbm_engine* e);
+
+/* Message of the last failed engine call.                                        */
+const char* lbm_engine_last_error(const lbm_engine* e);
+
 #ifdef __cplusplus
 }
 #endif

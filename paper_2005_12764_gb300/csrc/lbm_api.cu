@@ -13,62 +13,9 @@
 #include <string>
 
 #include "../../include/lbm.h"
-#include "lbm_device.cuh"
-
-namespace lbm {
-cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
-                        int storage, int grid,
-                        cudaStream_t s);
-cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int num_sms,
-                      cudaStream_t s);
-cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
-                              cudaStream_t s);
-int step_tile_x();
-int step_tile_y();
-int step_box_rows();
-int step_box_width(int storage);
-int step_ctas_per_sm();
-int step_pad_x(int storage);
-}  // namespace lbm
+#include "lbm_ctx.cuh"
 
 using namespace lbm;
-
-struct lbm_ctx {
-    lbm_params p{};
-    size_t N = 0;
-    size_t elem = 4;            // bytes per stored population
-    int pitch = 0, nyp = 0;     // padded row length and rows per plane (ghosts included)
-    int padx = 0;               // interior offset within a padded row
-    size_t P = 0;               // elements per padded [z][y][x] block
-    CUtensorMap tmap[2];        // TMA load descriptors of the two population copies
-    CUtensorMap smap[2];        // TMA store descriptors (interior only: x < nx, y < ny)
-    void* f[2] = {nullptr, nullptr};
-    float* phi[2] = {nullptr, nullptr};
-    float* fx_row = nullptr;
-    uint8_t* pin_d2 = nullptr;
-    uint8_t* pin_mask = nullptr;
-    float* ah = nullptr;        // near-contact strength per node (A_nc > 0)
-    int4* cand[2] = {nullptr, nullptr}; // candidate lists {node, G} (ping-pong) and counters
-    int* cand_count = nullptr;          // [2]
-    uint32_t* nc_pos = nullptr;         // near-contact ray bound (block bit field)
-    int cw = 0;                 // list the next step kernel writes
-    bool nc_scan = true;        // next near-contact pass must scan every node
-    double* stage = nullptr;    // device FP64 staging, grown on demand
-    size_t stage_cap = 0;       // its size in doubles
-    double* red = nullptr;      // reduction partials
-    double* red_host = nullptr; // pinned host copy of reduction results
-    int red_blocks = 0;
-    int cur = 0;                // population copy holding the current state
-    int pc = 0;                 // phi buffer of the last step (the other one = its lag)
-    long long steps = 0;
-    bool fields_set = false;
-    cudaStream_t stream = nullptr;
-    int num_sms = 0;
-    int grid = 1;               // CTAs of the step kernel (one per SM at most)
-    int* err_word = nullptr;    // device error word (bounded waits)
-    StepParams sp{};
-    std::string err;
-};
 
 static thread_local std::string g_create_err;
 
@@ -562,6 +509,33 @@ static lbm_status check_err_word(lbm_ctx* c) {
     if (h) return fail(c, LBM_ETIMEOUT, "a bounded wait in the step kernel gave up");
     return LBM_OK;
 }
+
+namespace lbm {
+void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* out) {
+    const int cur = c->cur ^ (ahead & 1), pc = c->pc ^ (ahead & 1);
+    StepParams s = c->sp;
+    s.fin = c->f[cur];
+    s.phi_lag = c->phi[pc];
+    s.phi_out = c->phi[1 - pc];
+    if (zparts > 0) s.zparts = zparts;
+    out->in_map = c->tmap[cur];
+    out->out_map = c->smap[1 - cur];
+    out->p = s;
+    out->fout = c->f[1 - cur];
+}
+void advance_state(lbm_ctx* c, long long k) {
+    if (k & 1) {
+        c->cur ^= 1;
+        c->pc ^= 1;
+        c->cw ^= 1;
+    }
+    c->steps += k;
+    if (k > 0) c->nc_scan = false;
+}
+lbm_status check_errors(lbm_ctx* c) { return check_err_word(c); }
+int ctx_num_sms(const lbm_ctx* c) { return c->num_sms; }
+cudaStream_t ctx_stream(const lbm_ctx* c) { return c->stream; }
+}  // namespace lbm
 
 // ---------------------------------------------------------------- API
 extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -132,6 +133,20 @@ struct StepParams {
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
     int* err;               // device error word: 1 = a bounded wait gave up
+};
+
+static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
+
+// One lattice of a batched launch: its tensor maps (load: populations of this step,
+// store: populations after it), step parameters, the array the step writes (for
+// the ghost fill) and its first CTA / first ghost cell in the batched grids.
+struct alignas(64) BatchLattice {
+    CUtensorMap in_map;
+    CUtensorMap out_map;
+    StepParams p;
+    void* fout;
+    int cta_begin;
+    long long ghost_begin;
 };
 
 // ---------------------------------------------------------------- near-contact force

@@ -127,10 +127,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 }
 
 // ---------------------------------------------------------------- the kernel
+// Body of the step kernel for CTA `cta` of one lattice's grid: the single-lattice
+// kernel passes its parameters and tensor maps (kernel parameter space), the
+// batched kernel those of the lattice the CTA belongs to.
 template <class St, bool UnitOmega>
-__global__ void __launch_bounds__(NT, CTAS_PER_SM)
-step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
-            const __grid_constant__ CUtensorMap fout_map) {
+__device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap* fin_map,
+                                          const CUtensorMap* fout_map, const int cta) {
     using T = typename St::T;
     using G = Geo<St>;
     constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, STAGES = G::STAGES;
@@ -152,8 +154,8 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
         mbar_init(&bars[0], 2 * Q);   // one arrival per (species, direction) box
         mbar_init(&bars[1], 2 * Q);
         fence_mbar_init();
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fin_map)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fout_map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(fin_map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(fout_map)) : "memory");
     }
     __syncthreads();
     uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
@@ -161,7 +163,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
 
     // one (z part, tile) work item per CTA, part-major
     const int ntiles = p.tiles_x * p.tiles_y;
-    const int part = blockIdx.x / ntiles, tile = blockIdx.x - part * ntiles;
+    const int part = cta / ntiles, tile = cta - part * ntiles;
     {
         const int zb = (int)((long long)p.nz * part / p.zparts);
         const int ze = (int)((long long)p.nz * (part + 1) / p.zparts);
@@ -200,7 +202,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
             if (need) {
                 // box origin: x = x0 - 2 and y = y0 - 1 - c_iy, in padded coordinates
                 mbar_arrive_tx(&bars[b], (uint32_t)G::BOX_BYTES);
-                tma_load_4d(st + (size_t)my_ik * IKS, &fin_map, x0, y0 + 1 - my_cy,
+                tma_load_4d(st + (size_t)my_ik * IKS, fin_map, x0, y0 + 1 - my_cy,
                             wrap_near(zs0, p.nz), my_ik, &bars[b]);
             } else {
                 mbar_arrive_tx(&bars[b], 0u);
@@ -401,7 +403,7 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
             __syncthreads();
             if (tid == 0) {
                 for (int k = 0; k < 2 * Q; ++k)
-                    tma_store_4d(&fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
+                    tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
                 bulk_commit();
             }
             ah_c = ah_nxt;
@@ -470,36 +472,100 @@ step_kernel(const StepParams p, const __grid_constant__ CUtensorMap fin_map,
     }
 }
 
+template <class St, bool UnitOmega>
+__global__ void __launch_bounds__(NT, CTAS_PER_SM)
+step_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap fin_map,
+            const __grid_constant__ CUtensorMap fout_map) {
+    step_body<St, UnitOmega>(p, &fin_map, &fout_map, (int)blockIdx.x);
+}
+
+// Several lattices in one launch: CTA b belongs to the last lattice whose first CTA
+// is <= b. Its parameters are copied to shared memory once; its tensor maps are read
+// from the table (global memory).
+template <class St, bool UnitOmega>
+__global__ void __launch_bounds__(NT, CTAS_PER_SM)
+step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
+    __shared__ StepParams sp;
+    __shared__ int lat;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].cta_begin <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        lat = lo;
+    }
+    __syncthreads();
+    const BatchLattice& L = tab[lat];
+    {
+        const int* src = reinterpret_cast<const int*>(&L.p);
+        int* dst = reinterpret_cast<int*>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / sizeof(int)); i += blockDim.x)
+            dst[i] = src[i];
+    }
+    __syncthreads();
+    step_body<St, UnitOmega>(sp, &L.in_map, &L.out_map, (int)blockIdx.x - L.cta_begin);
+}
+
 // ---------------------------------------------------------------- ghost fill
 // Copies the wrapped-around nodes into the ghost columns/rows of periodic axes, for
 // every species and direction (after the state was set, and after each step on
 // lattices too small for the step kernel to write its ghosts itself).
+// Ghost cells of one plane: x ghosts (2 + 2) of every row, then, on a periodic y
+// axis, the 2 + 2 ghost rows including their corners.
+__host__ __device__ inline long long ghost_cells_per_plane(const StepParams& p) {
+    return 4LL * p.ny + (p.wall_y ? 0 : 4LL * (p.nx + 4));
+}
+
+// Copies ghost cell e (of ghost_cells_per_plane * nz) from its wrapped-around node,
+// for every species and direction.
+template <class St>
+__device__ __forceinline__ void ghost_copy(typename St::T* f, const StepParams& p, int e) {
+    const int ncol = 4 * p.ny;
+    const int G = (int)ghost_cells_per_plane(p);
+    const int z = e / G, g = e - z * G;
+    int x, y;
+    if (g < ncol) {
+        y = g >> 2;
+        const int c = g & 3;
+        x = c < 2 ? c - 2 : p.nx + c - 2;
+    } else {
+        const int h = g - ncol, r = h / (p.nx + 4);
+        x = h - r * (p.nx + 4) - 2;
+        y = r < 2 ? r - 2 : p.ny + r - 2;
+    }
+    const size_t dst = pidx(p.pitch, p.nyp, p.padx, x, y, z);
+    const size_t src = pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
+    typename St::T v[2 * Q];
+#pragma unroll
+    for (int ik = 0; ik < 2 * Q; ++ik) v[ik] = f[(size_t)ik * p.P + src];
+#pragma unroll
+    for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + dst] = v[ik];
+}
+
 template <class St>
 __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
-    // ghost cells of one plane: x ghosts (2 + 2) of every row, then, on a periodic
-    // y axis, the 2 + 2 ghost rows including their corners
-    const int ncol = 4 * p.ny;
-    const int G = ncol + (p.wall_y ? 0 : 4 * (p.nx + 4));
-    const int total = G * p.nz;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        const int z = e / G, g = e - z * G;
-        int x, y;
-        if (g < ncol) {
-            y = g >> 2;
-            const int c = g & 3;
-            x = c < 2 ? c - 2 : p.nx + c - 2;
-        } else {
-            const int h = g - ncol, r = h / (p.nx + 4);
-            x = h - r * (p.nx + 4) - 2;
-            y = r < 2 ? r - 2 : p.ny + r - 2;
+    const int total = (int)(ghost_cells_per_plane(p) * p.nz);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
+        ghost_copy<St>(f, p, e);
+}
+
+// Ghost cells of every lattice of a batch: cell e belongs to the last lattice whose
+// first ghost cell is <= e.
+template <class St>
+__global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nlat,
+                                   long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].ghost_begin <= e) lo = mid;
+            else hi = mid - 1;
         }
-        const size_t dst = pidx(p.pitch, p.nyp, p.padx, x, y, z);
-        const size_t src = pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
-        typename St::T v[2 * Q];
-#pragma unroll
-        for (int ik = 0; ik < 2 * Q; ++ik) v[ik] = f[(size_t)ik * p.P + src];
-#pragma unroll
-        for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + dst] = v[ik];
+        const BatchLattice& L = tab[lo];
+        ghost_copy<St>(static_cast<typename St::T*>(L.fout), L.p, (int)(e - L.ghost_begin));
     }
 }
 
@@ -722,10 +788,67 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
     return cudaErrorInvalidValue;
 }
 
+template <class St, bool U>
+static cudaError_t launch_batched_tpl(const BatchLattice* tab, int nlat, int ctas, cudaStream_t s) {
+    step_kernel_batched<St, U><<<ctas, NT, Geo<St>::SMEM, s>>>(tab, nlat);
+    return cudaGetLastError();
+}
+
+template <class St, bool U>
+static cudaError_t prepare_batched_tpl() {
+    return cudaFuncSetAttribute(step_kernel_batched<St, U>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<St>::SMEM);
+}
+
+// Shared-memory attribute of a batched step kernel: set before any launch (and
+// outside stream capture).
+cudaError_t prepare_step_batched(int storage, bool unit_omega) {
+    switch (storage * 2 + (unit_omega ? 1 : 0)) {
+        case 0: return prepare_batched_tpl<StoreF32, false>();
+        case 1: return prepare_batched_tpl<StoreF32, true>();
+        case 2: return prepare_batched_tpl<StoreF16, false>();
+        case 3: return prepare_batched_tpl<StoreF16, true>();
+        case 4: return prepare_batched_tpl<StoreBF16, false>();
+        case 5: return prepare_batched_tpl<StoreBF16, true>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// One launch advancing every lattice of a device table by one step (all lattices of
+// one storage format and relaxation class).
+cudaError_t launch_step_batched(const BatchLattice* tab, int nlat, int ctas, int storage,
+                                bool unit_omega, cudaStream_t s) {
+    switch (storage * 2 + (unit_omega ? 1 : 0)) {
+        case 0: return launch_batched_tpl<StoreF32, false>(tab, nlat, ctas, s);
+        case 1: return launch_batched_tpl<StoreF32, true>(tab, nlat, ctas, s);
+        case 2: return launch_batched_tpl<StoreF16, false>(tab, nlat, ctas, s);
+        case 3: return launch_batched_tpl<StoreF16, true>(tab, nlat, ctas, s);
+        case 4: return launch_batched_tpl<StoreBF16, false>(tab, nlat, ctas, s);
+        case 5: return launch_batched_tpl<StoreBF16, true>(tab, nlat, ctas, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long cells, int storage,
+                                 int num_sms, cudaStream_t s) {
+    long long blocks = (cells + 255) / 256;
+    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+    if (blocks < 1) blocks = 1;
+    switch (storage) {
+        case 0: ghost_fill_batched<StoreF32><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
+        case 1: ghost_fill_batched<StoreF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
+        case 2: ghost_fill_batched<StoreBF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+long long ghost_cells(const StepParams& p) { return ghost_cells_per_plane(p) * p.nz; }
+
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s) {
     const int threads = 256;
-    const size_t cells = (size_t)(4 * p.ny + (p.wall_y ? 0 : 4 * (p.nx + 4))) * p.nz;
+    const size_t cells = (size_t)(ghost_cells_per_plane(p) * p.nz);
     size_t blocks = (cells + threads - 1) / threads;
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;

@@ -29,7 +29,15 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_observables", "lbm_laplace",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
-           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_get_window"]
+           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_get_window",
+           "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
+           "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy",
+           "lbm_engine_last_error"]
+
+
+class EngineParams(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int),
+                ("chunk_steps", C.c_int), ("autotune", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
 class LbmError(RuntimeError):
@@ -94,6 +102,16 @@ def load():
             "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
             "lbm_get_window": (C.c_int, [_P] + [C.c_int] * 6 + [_D, _D, _D, C.c_int]),
+            "lbm_engine_create": (C.c_int, [C.POINTER(EngineParams), C.POINTER(C.c_void_p)]),
+            "lbm_engine_submit": (C.c_int, [_P, PP, _D, _D, _D, C.c_longlong,
+                                            C.POINTER(C.c_longlong)]),
+            "lbm_engine_tick": (C.c_int, [_P] + [C.POINTER(C.c_int)] * 4),
+            "lbm_engine_state": (C.c_int, [_P, C.c_longlong]),
+            "lbm_engine_result": (C.c_int, [_P, C.c_longlong, _D, _D, _D, _D,
+                                            C.POINTER(C.c_longlong)]),
+            "lbm_engine_stats": (None, [_P, C.POINTER(C.c_longlong)]),
+            "lbm_engine_destroy": (None, [_P]),
+            "lbm_engine_last_error": (C.c_char_p, [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -305,3 +323,81 @@ class Lattice:
     def load_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(self._lib.lbm_load_state(self._h, buf))
+
+
+class Engine:
+    """Serving engine of liblbm.so (lbm_engine_* in include/lbm.h): requests are
+    queued, admitted by device memory, advanced together in batched launches and
+    retired with their fields copied to host memory."""
+
+    STATES = {0: "queued", 1: "resident", 2: "finished", 3: "taken", 4: "failed", -1: "unknown"}
+
+    def __init__(self, budget_bytes, max_slots=64, chunk_steps=50, autotune=True, stream=None):
+        self._lib = load()
+        ep = EngineParams()
+        ep.hbm_budget_bytes = int(budget_bytes)
+        ep.max_slots, ep.chunk_steps, ep.autotune = int(max_slots), int(chunk_steps), int(autotune)
+        ep.cuda_stream = stream
+        h = C.c_void_p()
+        rc = self._lib.lbm_engine_create(C.byref(ep), C.byref(h))
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_last_error(None).decode())
+        self._h = h
+        self.shapes = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_engine_last_error(self._h).decode())
+
+    def submit(self, params: Params, rho_r, rho_b, steps, u=None) -> int:
+        n = params.nx * params.ny * params.nz
+        rr = np.ascontiguousarray(rho_r, dtype=np.float64).reshape(-1)
+        rb = np.ascontiguousarray(rho_b, dtype=np.float64).reshape(-1)
+        assert rr.size == n and rb.size == n
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        t = C.c_longlong()
+        self._check(self._lib.lbm_engine_submit(self._h, C.byref(params), rr.ctypes.data,
+                                                rb.ctypes.data,
+                                                None if uu is None else uu.ctypes.data,
+                                                int(steps), C.byref(t)))
+        self.shapes[t.value] = (params.nz, params.ny, params.nx)
+        return t.value
+
+    def tick(self):
+        """One round; returns (resident, queued, retired, steps advanced)."""
+        v = [C.c_int() for _ in range(4)]
+        self._check(self._lib.lbm_engine_tick(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def state(self, ticket) -> str:
+        return self.STATES[self._lib.lbm_engine_state(self._h, int(ticket))]
+
+    def result(self, ticket):
+        """Fields of a finished request (dict as Lattice.get_fields) plus 'info' =
+        (steps, tick submitted, tick admitted, tick retired); releases the result."""
+        shape = self.shapes[ticket]
+        out = {"rho_r": np.empty(shape), "rho_b": np.empty(shape), "u": np.empty((3,) + shape),
+               "phi": np.empty(shape)}
+        info = (C.c_longlong * 4)()
+        self._check(self._lib.lbm_engine_result(self._h, int(ticket), out["rho_r"].ctypes.data,
+                                                out["rho_b"].ctypes.data, out["u"].ctypes.data,
+                                                out["phi"].ctypes.data, info))
+        out["info"] = tuple(info)
+        return out
+
+    def stats(self):
+        v = (C.c_longlong * 7)()
+        self._lib.lbm_engine_stats(self._h, v)
+        keys = ("ticks", "resident", "queued", "bytes", "peak_bytes", "planes_per_cta", "groups")
+        return dict(zip(keys, list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_engine_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

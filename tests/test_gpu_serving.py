@@ -1,0 +1,123 @@
+"""Serving engine on the GPU (lbm_engine_*): batched, graph-captured stepping of
+many resident lattices, admission by device memory, continuous batching.
+
+The bar: a request's result is the same alone and in any mix -- here bitwise,
+since every node is computed by the same arithmetic whatever the batch -- and the
+same as a plain context stepped by lbm_step.
+"""
+import numpy as np
+import pytest
+
+from paper_2005_12764_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12764_gb300 import build_lib, lbm as L
+    build_lib.build()
+    L.load()
+    return L
+
+
+REQS = [dict(id=0, L=32, R=8.0, sigma=0.02, steps=37, sheared=False),
+        dict(id=1, L=48, R=12.0, sigma=0.01, steps=64, sheared=True),
+        dict(id=2, L=32, R=8.0, sigma=0.005, steps=90, sheared=True),
+        dict(id=3, L=40, R=10.0, sigma=0.03, steps=51, sheared=False)]
+
+
+def _run_alone(lbm, serving, req, storage):
+    e = lbm.Engine(budget_bytes=8 << 30, max_slots=1, chunk_steps=16, autotune=False)
+    p, rr, rb = serving.request_lattice(req, storage)
+    t = e.submit(p, rr, rb, req["steps"])
+    while e.state(t) != "finished":
+        e.tick()
+    out = e.result(t)
+    e.close()
+    return out
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp32"])
+def test_result_is_the_same_alone_in_the_mix_and_by_lbm_step(lbm, storage):
+    from paper_2005_12764_gb300 import serving
+    alone = {r["id"]: _run_alone(lbm, serving, r, storage) for r in REQS}
+    # the mix: two requests first, the others arrive while those are resident
+    e = lbm.Engine(budget_bytes=8 << 30, max_slots=8, chunk_steps=12, autotune=True)
+    tickets = {}
+    for r in REQS[:2]:
+        p, rr, rb = serving.request_lattice(r, storage)
+        tickets[e.submit(p, rr, rb, r["steps"])] = r["id"]
+    e.tick()
+    e.tick()
+    for r in REQS[2:]:
+        p, rr, rb = serving.request_lattice(r, storage)
+        tickets[e.submit(p, rr, rb, r["steps"])] = r["id"]
+    mixed = {}
+    for _ in range(200):
+        e.tick()
+        for t, k in tickets.items():
+            if k not in mixed and e.state(t) == "finished":
+                mixed[k] = e.result(t)
+        if len(mixed) == len(REQS):
+            break
+    e.close()
+    assert len(mixed) == len(REQS)
+    for r in REQS:
+        a, m = alone[r["id"]], mixed[r["id"]]
+        assert a["info"][0] == m["info"][0] == r["steps"]
+        for key in ("rho_r", "rho_b", "u", "phi"):
+            assert np.array_equal(a[key], m[key]), (r["id"], key)
+        # and the same as a plain context stepped by lbm_step
+        p, rr, rb = serving.request_lattice(r, storage)
+        g = lbm.Lattice(p)
+        g.set_fields(rr, rb)
+        g.step(r["steps"])
+        f = g.get_fields()
+        g.close()
+        for key in ("rho_r", "rho_b", "u", "phi"):
+            assert np.array_equal(f[key], m[key]), (r["id"], key, "lbm_step")
+
+
+def test_admission_by_device_memory(lbm):
+    from paper_2005_12764_gb300 import serving
+    reqs = [dict(id=k, L=48, R=12.0, sigma=0.01, steps=20, sheared=bool(k % 2)) for k in range(6)]
+    p, _, _ = serving.request_lattice(reqs[0])
+    one = lbm.footprint_bytes(p) + 7 * 48 ** 3 * 8        # a request's device memory
+    budget = int(2.5 * one)                                  # room for two at a time
+    e = lbm.Engine(budget_bytes=budget, max_slots=16, chunk_steps=8, autotune=False)
+    tickets = []
+    for r in reqs:
+        p, rr, rb = serving.request_lattice(r)
+        tickets.append(e.submit(p, rr, rb, r["steps"]))
+    seen_queue = 0
+    for _ in range(100):
+        res, q, _, _ = e.tick()
+        assert res <= 2
+        seen_queue = max(seen_queue, q)
+        if all(e.state(t) == "finished" for t in tickets):
+            break
+    st = e.stats()
+    assert all(e.state(t) == "finished" for t in tickets)
+    assert seen_queue >= 3 and st["peak_bytes"] <= budget
+    # a request larger than the whole budget is refused at submission
+    big = lbm.make_params(256, 256, 256, storage="fp16")
+    with pytest.raises(lbm.LbmError):
+        e.submit(big, np.ones(256 ** 3), np.zeros(256 ** 3), 10)
+    e.close()
+
+
+def test_serving_loop_reports_latency_and_throughput(lbm):
+    from paper_2005_12764_gb300 import serving
+    reqs = inputs.serving_requests(n=24, seed=7, rate_hz=400.0, edges=(32, 48, 64),
+                                   steps_range=(40, 160))
+    e = lbm.Engine(budget_bytes=16 << 30, max_slots=32, chunk_steps=20)
+    rep = serving.serve(e, reqs, storage="fp16")
+    e.close()
+    assert rep["requests"] == 24 and len(rep["latency_s"]) == 24
+    assert 0 < rep["p50_ms"] <= rep["p99_ms"]
+    assert rep["glups"] > 0
+    print("serving report:", {k: v for k, v in rep.items() if k != "latency_s"})
