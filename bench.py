@@ -6,16 +6,21 @@ bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigm
 One step = one lattice update of every node (one launch of the fused kernel).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--no-serving] [--no-cpu-baseline]
 
 Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second)
 over all ranks; ``e2e`` times the same job through the public C-ABI with host
 buffers (set fields from pinned host memory, K steps, fields back to the host);
 ``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations
 per node, read once and written once) to the measured HBM bandwidth;
-``cpu_baseline`` times the FP64 oracle on the host cores. ``--impl reference``
-times the oracle itself on the same workload (the method has no other reference
-implementation). Multi-GPU runs are independent replicas (one lattice per rank).
+``fp16_store`` repeats the device-resident measurement with FP16 deviation
+storage; ``serving`` runs the served request stream (256 droplet / sheared-droplet
+runs of edge 32-128, Poisson arrivals at 50/s, FP16 storage) through the serving
+engine and reports p50/p99 latency beside aggregate GLUPS; ``cpu_baseline`` times
+the FP64 oracle on the host cores. ``--impl reference`` times the oracle itself on
+the same workload (the method has no other reference implementation). Multi-GPU
+runs are independent replicas: one channel lattice per rank, the request stream
+sharded over the ranks.
 """
 from __future__ import annotations
 
@@ -173,12 +178,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def device_resident_glups(lbm, w, storage, steps, warmup, stream, local):
+    """GLUPS of `steps` steps queued back to back (CUDA events on the library's
+    stream) and the mean step-kernel time (ms) from the library's own events."""
+    import torch
+    nz, ny, nx = w.shape
+    lat = lbm.Lattice(lbm.make_params(nx, ny, nz, storage=storage, stream=stream.cuda_stream,
+                                      **w.params))
+    lat.set_fields(torch.from_numpy(w.rho_r).to(f"cuda:{local}"),
+                   torch.from_numpy(w.rho_b).to(f"cuda:{local}"))
+    lat.step(warmup)
+    lat.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    lat.step(steps)
+    b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b)
+    kt = max(5, min(steps, 50))
+    _, step_ms, _ = lat.step_timed(kt)
+    lat.close()
+    return nx * ny * nz * steps / (ms * 1e-3) / 1e9, ms / steps, step_ms / kt
+
+
+def serving_run(lbm, rank, world, dist, local):
+    """The served request stream (sharded over replicas) through the serving engine."""
+    from paper_2005_12764_gb300 import inputs, replicas, serving
+    reqs = replicas.shard(inputs.serving_requests(), rank, world)
+    eng = lbm.Engine(budget_bytes=64 << 30, max_slots=64, chunk_steps=50)
+    rep = serving.serve(eng, reqs, storage="fp16")
+    eng.close()
+    lat = replicas.gather_lists(rep["latency_s"], dist)
+    wall = replicas.max_over_ranks(rep["wall_s"], dist, f"cuda:{local}")
+    lups = replicas.sum_over_ranks(rep["lattice_updates"], dist, f"cuda:{local}")
+    first = min(r["arrival_s"] for r in inputs.serving_requests())
+    return {"requests": len(lat), "storage": "fp16",
+            "p50_ms": serving.percentile(lat, 50) * 1e3,
+            "p99_ms": serving.percentile(lat, 99) * 1e3,
+            "glups": lups / (wall - first) / 1e9, "wall_s": wall,
+            "stream": "256 requests, edge {32,48,64,96,128}, R = L/4, sigma U[0.005,0.03], "
+                      "steps U[200,2000], half sheared (Kolmogorov 1e-5), Poisson 50/s",
+            "engine": {k: rep["engine"][k] for k in ("ticks", "peak_bytes", "planes_per_cta")}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2005_12764_gb300 import build_lib, inputs, lbm
+    from paper_2005_12764_gb300 import build_lib, inputs, lbm, replicas
 
     rank, world, local = dist_env()
     if world > 1:
@@ -214,18 +262,16 @@ def run_ours(args):
         t_end.record(stream)
         stream.synchronize()
     barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist if world > 1 else None,
+                                       f"cuda:{local}")
     ms_per_step = total_ms / args.steps
     glups = world * N * args.steps / (total_ms * 1e-3) / 1e9
     # per-kernel durations (events around each launch, inside the library)
     kt = max(5, min(args.steps, 50))
-    nc_ms, step_ms = lat.step_timed(kt)
+    nc_ms, step_ms, ghost_ms = lat.step_timed(kt)
     kern_ms = [step_ms / kt]
     nc_avg_ms = nc_ms / kt
+    ghost_avg_ms = ghost_ms / kt
     # ---- end to end through the public API with pinned host buffers
     host_rr = torch.from_numpy(w.rho_r).pin_memory()
     host_rb = torch.from_numpy(w.rho_b).pin_memory()
@@ -238,11 +284,8 @@ def run_ours(args):
     lat.set_fields(host_rr, host_rb)
     lat.step(args.steps)
     lat.get_fields(outs)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None,
+                                    f"cuda:{local}")
     e2e = world * N * args.steps / e2e_s / 1e9
     h2d = 2 * N * 8
     d2h = 6 * N * 8
@@ -257,6 +300,20 @@ def run_ours(args):
 
     obs = lat.observables()
     finite = bool(np.isfinite(obs[:5]).all())
+    launches = args.steps * lat.launches_per_step
+    lat.close()
+    # the same workload with FP16 deviation storage (device-resident, as `value`)
+    fp16 = None
+    if args.storage == "fp32":
+        g16, ms16, k16 = device_resident_glups(lbm, w, "fp16", args.steps, args.warmup, stream, local)
+        g16 = replicas.sum_over_ranks(g16, dist if world > 1 else None, f"cuda:{local}")
+        alg16 = 2 * Q * C * 2 * N
+        fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
+                "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
+                "algorithmic_bytes_per_launch": alg16}
+    serving_rep = None
+    if not args.no_serving:
+        serving_rep = serving_run(lbm, rank, world, dist if world > 1 else None, local)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -283,15 +340,19 @@ def run_ours(args):
                          "kernel": "step_kernel (fused stream/collide/perturb/recolour)",
                          "kernel_ms": statistics.mean(kern_ms),
                          "near_contact_pass_ms": nc_avg_ms,
+                         "ghost_fill_ms": ghost_avg_ms,
                          "algorithmic_bytes_per_launch": alg_bytes},
-            "gpu_launches": args.steps * lat.launches_per_step,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
             "finite": finite,
         }
+        if fp16:
+            line["fp16_store"] = fp16
+        if serving_rep:
+            line["serving"] = serving_rep
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    lat.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -305,6 +366,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

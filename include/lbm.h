@@ -118,14 +118,15 @@ lbm_status lbm_set_pin_mask(lbm_ctx* ctx, const uint8_t* mask, int on_device);
 lbm_status lbm_step(lbm_ctx* ctx, int n);
 
 /* As lbm_step, but synchronising after every step and timing its kernels with CUDA
- * events on the context stream: out_ms[0] += time of the near-contact pass (0 when
- * A_nc == 0), out_ms[1] += time of the fused step kernel, summed over the n steps.
- * For measurement; it serialises the host with the device.                      */
-lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[2]);
+ * events on the context stream, summed over the n steps: out_ms[0] the near-contact
+ * pass (0 when A_nc == 0), out_ms[1] the fused step kernel, out_ms[2] the ghost-copy
+ * fill of the periodic axes. For measurement; it serialises the host with the
+ * device.                                                                       */
+lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[3]);
 
-/* Kernel launches one lbm_step makes per time step: 1 (the fused step), or 3 when
- * A_nc > 0 (the near-contact ray-bound field and pass; the first step after a
- * change of state adds a candidate scan).                                        */
+/* Kernel launches one lbm_step makes per time step: 2 (the fused step and the
+ * ghost-copy fill), or 4 when A_nc > 0 (plus the near-contact ray-bound field and
+ * pass; the first step after a change of state adds a candidate scan).          */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the

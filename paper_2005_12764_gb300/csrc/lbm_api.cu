@@ -776,7 +776,8 @@ extern "C" lbm_status lbm_set_pin_mask(lbm_ctx* c, const uint8_t* mask, int on_d
 // and consumes (zeroes) the A_h entries it reads; the pass of step t+1 reads that
 // list and writes A_h only at those nodes. After any change of state the pass scans
 // every node once instead. Events (optional) bracket the two launches.
-static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2,
+                                   cudaEvent_t e3 = nullptr) {
     StepParams s = c->sp;
     s.fin = c->f[c->cur];
     s.phi_lag = c->phi[c->pc];
@@ -805,10 +806,11 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess)
         e = launch_step(s, c->tmap[c->cur], c->smap[1 - c->cur], c->p.storage, c->grid, c->stream);
+    if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
     // ghost copies of the periodic axes for the next step's halo loads
     if (e == cudaSuccess)
         e = launch_ghost_fill(c->f[1 - c->cur], s, c->p.storage, c->num_sms, c->stream);
-    if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
+    if (e == cudaSuccess && e3) e = cudaEventRecord(e3, c->stream);
     if (e != cudaSuccess) return e;
     c->nc_scan = false;
     c->cw ^= 1;
@@ -829,28 +831,30 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
     return LBM_OK;
 }
 
-extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[2]) {
+extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[3]) {
     if (!c || !out_ms) return LBM_EINVAL;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
-    out_ms[0] = out_ms[1] = 0.0;
-    cudaEvent_t ev[3];
-    for (int k = 0; k < 3; ++k) CK(c, cudaEventCreate(&ev[k]));
+    out_ms[0] = out_ms[1] = out_ms[2] = 0.0;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) CK(c, cudaEventCreate(&ev[k]));
     lbm_status st = LBM_OK;
     for (int t = 0; t < n && st == LBM_OK; ++t) {
-        cudaError_t e = launch_one_step(c, ev[0], ev[1], ev[2]);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-        float a = 0.f, b = 0.f;
+        cudaError_t e = launch_one_step(c, ev[0], ev[1], ev[2], ev[3]);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        float a = 0.f, b = 0.f, g = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&g, ev[2], ev[3]);
         if (e != cudaSuccess) {
             st = cuda_fail(c, e, "timed step");
             break;
         }
         out_ms[0] += a;
         out_ms[1] += b;
+        out_ms[2] += g;
     }
-    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
     if (st != LBM_OK) return st;
     return check_err_word(c);
 }
@@ -1136,6 +1140,7 @@ extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
-    // near contact: the ray-bound bit field and the list pass, then the fused step
-    return c->p.A_nc > 0.0 ? 3 : 1;
+    // the fused step and the ghost fill; near contact adds the ray-bound bit field
+    // and the list pass
+    return c->p.A_nc > 0.0 ? 4 : 2;
 }

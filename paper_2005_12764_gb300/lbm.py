@@ -239,10 +239,11 @@ class Lattice:
 
     def step_timed(self, n=1):
         """Advance n steps, returning (ms in the near-contact pass, ms in the step
-        kernel) summed over the steps, from CUDA events inside the library."""
-        out = (C.c_double * 2)()
+        kernel, ms in the ghost fill) summed over the steps, from CUDA events inside
+        the library."""
+        out = (C.c_double * 3)()
         self._check(self._lib.lbm_step_timed(self._h, int(n), out))
-        return float(out[0]), float(out[1])
+        return float(out[0]), float(out[1]), float(out[2])
 
     @property
     def launches_per_step(self):
