@@ -124,9 +124,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int n);
  * device.                                                                       */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[3]);
 
-/* Kernel launches one lbm_step makes per time step: 2 (the fused step and the
- * ghost-copy fill), or 4 when A_nc > 0 (plus the near-contact ray-bound field and
- * pass; the first step after a change of state adds a candidate scan).          */
+/* Kernel launches one lbm_step makes per time step: the fused step; the ghost-copy
+ * fill where ghost copies are kept in memory (a periodic y axis, or a lattice of a
+ * single 32-node tile along x); and, when A_nc > 0, the near-contact ray-bound
+ * field and pass (the first step after a change of state adds a candidate scan). */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the

@@ -385,11 +385,11 @@ struct PadLayout {
     size_t P;
 };
 static PadLayout pad_layout(const lbm_params& p) {
-    const int per16 = (int)(16 / elem_bytes(p.storage));
+    const int per32 = (int)(32 / elem_bytes(p.storage));
     PadLayout L;
-    L.padx = step_pad_x(p.storage);
-    L.pitch = (p.nx + 2 * L.padx + per16 - 1) / per16 * per16;
-    L.pitch = std::max(L.pitch, 72);                    // at least one staged box wide
+    L.padx = step_pad_x(p.storage);                     // 32 bytes of ghosts + padding
+    L.pitch = (p.nx + 2 * L.padx + per32 - 1) / per32 * per32;   // 32-byte rows
+    L.pitch = std::max(L.pitch, 80);                    // at least one staged box wide
     L.nyp = std::max(p.ny + 4, 18);                     // at least one staged box high
     L.P = (size_t)L.pitch * L.nyp * p.nz;
     return L;
@@ -498,6 +498,7 @@ static void fill_step_params(lbm_ctx* c) {
         }
     }
     s.zparts = best_k;
+
     c->grid = (int)(tiles * best_k);
 }
 
@@ -515,6 +516,7 @@ void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* ou
     const int cur = c->cur ^ (ahead & 1), pc = c->pc ^ (ahead & 1);
     StepParams s = c->sp;
     s.fin = c->f[cur];
+    s.fout = c->f[1 - cur];
     s.phi_lag = c->phi[pc];
     s.phi_out = c->phi[1 - pc];
     if (zparts > 0) s.zparts = zparts;
@@ -780,6 +782,7 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
                                    cudaEvent_t e3 = nullptr) {
     StepParams s = c->sp;
     s.fin = c->f[c->cur];
+    s.fout = c->f[1 - c->cur];
     s.phi_lag = c->phi[c->pc];
     s.phi_out = c->phi[1 - c->pc];
     cudaError_t e = cudaSuccess;
@@ -1140,7 +1143,7 @@ extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
-    // the fused step and the ghost fill; near contact adds the ray-bound bit field
-    // and the list pass
-    return c->p.A_nc > 0.0 ? 4 : 2;
+    // the fused step, the ghost fill where a periodic axis needs ghost copies in
+    // memory, and near contact's ray-bound field and list pass
+    return 1 + (ghost_cells(c->sp) > 0 ? 1 : 0) + (c->p.A_nc > 0.0 ? 2 : 0);
 }

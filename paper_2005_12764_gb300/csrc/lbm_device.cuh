@@ -118,7 +118,7 @@ struct StepParams {
     int nx, ny, nz;
     size_t N;               // nodes (fields phi, ah are [N], x fastest)
     // population arrays are padded: ghost columns and rows around the lattice (the
-    // interior starts padx columns in, 16 bytes), row pitch a multiple of 16 bytes;
+    // interior starts padx columns in, 32 bytes), row pitch a multiple of 32 bytes;
     // one [nz][nyp][pitch] block per species/direction
     int pitch, nyp, padx;
     size_t plane_p, P;      // pitch * nyp, plane_p * nz
@@ -132,6 +132,7 @@ struct StepParams {
     float ref_half;         // rho0/2 for FP16/BF16 deviation storage, 0 for FP32
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
+    void* fout;             // populations after the step
     int* err;               // device error word: 1 = a bounded wait gave up
 };
 

@@ -171,7 +171,7 @@ cudaError_t build_batch(lbm_engine* e, int T) {
             if (err == cudaSuccess)
                 err = launch_step_batched(g.d_tab[j], (int)g.members.size(), g.ctas, g.storage, g.unit,
                                           e->stream);
-            if (err == cudaSuccess)
+            if (err == cudaSuccess && g.ghost > 0)
                 err = launch_ghost_batched(g.d_tab[j], (int)g.members.size(), g.ghost, g.storage,
                                            e->num_sms, e->stream);
         }
@@ -192,7 +192,7 @@ cudaError_t single_step(lbm_engine* e) {
         if (err == cudaSuccess)
             err = launch_step_batched(g.d_tab[0], (int)g.members.size(), g.ctas, g.storage, g.unit,
                                       e->stream);
-        if (err == cudaSuccess)
+        if (err == cudaSuccess && g.ghost > 0)
             err = launch_ghost_batched(g.d_tab[0], (int)g.members.size(), g.ghost, g.storage,
                                        e->num_sms, e->stream);
     }

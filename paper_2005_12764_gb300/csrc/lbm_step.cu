@@ -1,26 +1,29 @@
-// lbm_step.cu -- the fused time-step kernel (one launch = one full lattice update)
-// and the near-contact pass.
+// lbm_step.cu -- the fused time-step kernel (one launch = one full lattice update),
+// the ghost-copy fill and the near-contact pass.
 //
 // Data layout: populations in [2 species][19 directions][z][y][x] (x fastest), two
-// copies (read one, write the other). Each [z][y][x] block is padded with ghost
-// columns (the interior starts 16 bytes into a row) and two ghost rows on each side;
-// on periodic axes the ghosts next to the lattice hold copies of the wrapped-around
-// nodes, written by the step kernel together with the nodes.
+// copies (read one, write the other). Each [z][y][x] block is padded: the interior
+// of a row starts 32 bytes in (the sector holding the two x ghosts before it) and is
+// followed by another such sector, and there are two ghost rows on each side; on
+// periodic axes the ghosts hold copies of the wrapped-around nodes, written by the
+// ghost-copy fill after every step.
 //
 // A CTA owns a TX x TY tile of (x, y) columns and marches along z over one part of
 // the lattice height. For every plane p it stages in shared memory, per species and
-// direction i, the (TX+4) x (TY+2) box of the source plane p - c_iz that the pull of
-// the tile and of a one-node ring around it reads (columns x0-2 .. x0+TX+1, rows
-// y0-1-c_iy .. y0+TY-c_iy): 38 TMA tensor copies, one per issuing thread, completing
-// on an mbarrier. The copy of plane p+2 is issued as soon as every thread has pulled
-// plane p+1, so it overlaps the collision of plane p; two CTAs share an SM, so one
-// CTA's pulls overlap the other's collisions. From a staged plane every thread pulls its
-// node with constant-offset shared-memory loads, the colour field of the plane
-// (tile + ring) goes to a 4-slot ring buffer, and one plane behind, the owned nodes
-// are collided using the isotropic gradient read from that ring. The colour field of
-// the same step is thus available at all 18 neighbours without a second pass over
-// the populations. Links whose source lies beyond a bounce-back wall read the
-// node's own opposite population directly from global memory.
+// direction i, the (TX + 16 bytes of halo on each side) x (TY+2) box of the source
+// plane p - c_iz that the pull of the tile and of a one-node ring around it reads
+// (columns x0-2 .. x0+TX+1, rows y0-1-c_iy .. y0+TY-c_iy): 38 TMA tensor copies, one
+// per issuing thread, completing on an mbarrier. The copy of plane p+2 is issued as
+// soon as every thread has pulled plane p+1, so it overlaps the collision of plane
+// p; two CTAs share an SM, so one CTA's pulls overlap the other's collisions. From a
+// staged plane every thread pulls its node with constant-offset shared-memory loads,
+// the colour field of the plane (tile + ring) goes to a 4-slot ring buffer, and one
+// plane behind, the owned nodes are collided using the isotropic gradient read from
+// that ring. The colour field of the same step is thus available at all 18
+// neighbours without a second pass over the populations. Links whose source lies
+// beyond a bounce-back wall read the node's own opposite population directly from
+// global memory. The collision writes the plane's outputs to a shared output tile
+// that one thread stores with 38 TMA tensor copies.
 //
 // Work split: z is cut into `zparts` equal parts and every CTA marches one part of
 // one tile. CTAs are numbered part-major, so the CTAs resident at the same time work
@@ -42,9 +45,13 @@ struct Geo {
     using T = typename St::T;
     // interior offset in a padded row: 16 bytes, so that tensor stores of a tile start
     // on a 16-byte boundary
-    static constexpr int PADX = 16 / (int)sizeof(T);
-    // load box: columns x0-PADX .. x0+TX+PADX-1 (covers the pulls x0-2 .. x0+TX+1)
-    static constexpr int BW = TX + 2 * PADX;
+    // interior offset in a padded row: 32 bytes, so that each row's two x ghosts
+    // (just before the interior, and just after it) sit in 32-byte sectors of their
+    // own, written whole by the ghost fill; tile stores start on a 16-byte boundary
+    static constexpr int PADX = 32 / (int)sizeof(T);
+    // load box: columns x0-HALO .. x0+TX+HALO-1 (covers the pulls x0-2 .. x0+TX+1)
+    static constexpr int HALO = 16 / (int)sizeof(T);
+    static constexpr int BW = TX + 2 * HALO;
     static constexpr int BOX_BYTES = BW * SH * (int)sizeof(T);
     static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
@@ -57,9 +64,7 @@ struct Geo {
     static constexpr size_t LAG_BYTES = DEV ? 4 * LH * LW * sizeof(float) : 0;
     // output tile of a plane, [2Q][TY][TX], stored by tensor copies
     static constexpr size_t OUT_BYTES = (size_t)2 * Q * TX * TY * sizeof(T);
-    // staged planes per CTA: two where they fit beside the output tile at two CTAs
-    // per SM (2-byte storage), so a plane's copy is issued a full plane ahead
-    static constexpr int STAGES = sizeof(T) == 2 ? 2 : 1;
+    static constexpr int STAGES = 1;   // staged planes per CTA
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + OUT_BYTES + PHI_BYTES + LAG_BYTES +
                                    2 * sizeof(unsigned long long);
 };
@@ -135,7 +140,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                                           const CUtensorMap* fout_map, const int cta) {
     using T = typename St::T;
     using G = Geo<St>;
-    constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, STAGES = G::STAGES;
+    constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, HALO = G::HALO, STAGES = G::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
     T* sout = reinterpret_cast<T*>(smem + STAGES * G::STAGE_BYTES);           // [2Q][TY][TX]
@@ -200,9 +205,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             const bool need = !failed && (!p.wall_z || (pl >= 0 && pl < p.nz)) &&
                               !(p.wall_z && (zs0 < 0 || zs0 >= p.nz));
             if (need) {
-                // box origin: x = x0 - 2 and y = y0 - 1 - c_iy, in padded coordinates
+                // box origin: interior x0 - HALO and y0 - 1 - c_iy, in padded coordinates
                 mbar_arrive_tx(&bars[b], (uint32_t)G::BOX_BYTES);
-                tma_load_4d(st + (size_t)my_ik * IKS, fin_map, x0, y0 + 1 - my_cy,
+                tma_load_4d(st + (size_t)my_ik * IKS, fin_map, x0 + PADX - HALO, y0 + 1 - my_cy,
                             wrap_near(zs0, p.nz), my_ik, &bars[b]);
             } else {
                 mbar_arrive_tx(&bars[b], 0u);
@@ -224,7 +229,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // the colour field its source node had when it wrote it.
         auto pull = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
                         float& rb, bool keep) {
-            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + PADX);
+            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + HALO);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
@@ -318,13 +323,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // the collision of plane z from (cu, cu_rr, cu_rb); A_h is carried in ah_c
         auto march = [&](int z, float (&cu)[Q], float cu_rr, float cu_rb, float (&nx_f)[Q],
                          float& nx_rr, float& nx_rb, float& ah_c) {
-            // buffer of plane z+1; with two stages plane z+2 is issued before the wait,
-            // with one stage right after the barrier that frees the buffer
-            const int bn = STAGES == 2 ? ((z + 1 - zb + 1) & 1) : 0;
-            if (STAGES == 2) {
-                fence_proxy_async();
-                if (z + 2 <= ze) issue(bn ^ 1, z + 2);
-            }
+            // plane z+1 is in the staging buffer (issued after the previous barrier);
+            // plane z+2 is issued right after this plane's barrier frees the buffer
+            const int bn = 0;
             const float ah_nxt =
                 (owned && use_nc && z + 1 < ze) ? p.ah[(size_t)(z + 1) * plane + col] : 0.0f;
             // lag plane z+3 goes to the slot of plane z-1, last read before the barrier
@@ -336,10 +337,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             if (G::DEV) lag_commit(z + 3);
             if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
             __syncthreads();
-            if (STAGES == 1) {
-                fence_proxy_async();
-                if (z + 2 <= ze) issue(0, z + 2);
-            }
+            fence_proxy_async();
+            if (z + 2 <= ze) issue(0, z + 2);
             if (owned && !failed) {
                 const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
                 const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
@@ -397,8 +396,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 p.phi_out[node] = phic;
             }
             // store the output tile of plane z: 2Q tensor copies of TX x TY, clipped by
-            // the store map at the lattice edge (ghost copies are written by the fill
-            // pass); the tile is rewritten only after these copies have read it
+            // the store map at the lattice edge (to 16 bytes: ghost copies are written
+            // afterwards by the fill pass); the tile is rewritten only after these
+            // copies have read it
             fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
@@ -424,20 +424,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             lag_fetch(zb + 2);
             __syncthreads();
         }
-        if (STAGES == 2) {
-            fence_proxy_async();
-            issue(0, zb - 1);
-            issue(1, zb);
-            wait(0);
-            densities(0, zb - 1, fb, b_rr, b_rb, false);
-            __syncthreads();
-            if (G::DEV) lag_commit(zb + 2);
-            fence_proxy_async();
-            issue(0, zb + 1);
-            wait(1);
-            densities(1, zb, fa, a_rr, a_rb, true);
-            __syncthreads();
-        } else {
+        {
             fence_proxy_async();
             issue(0, zb - 1);
             wait(0);
@@ -512,60 +499,88 @@ step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
 // Copies the wrapped-around nodes into the ghost columns/rows of periodic axes, for
 // every species and direction (after the state was set, and after each step on
 // lattices too small for the step kernel to write its ghosts itself).
-// Ghost cells of one plane: x ghosts (2 + 2) of every row, then, on a periodic y
-// axis, the 2 + 2 ghost rows including their corners.
-__host__ __device__ inline long long ghost_cells_per_plane(const StepParams& p) {
-    return 4LL * p.ny + (p.wall_y ? 0 : 4LL * (p.nx + 4));
+// ---------------------------------------------------------------- ghost fill
+// Ghost copies of the periodic axes, per block k and plane z:
+//  part 1, one thread per interior row y: x ghosts -2, -1 <- nodes nx-2, nx-1 and
+//          nx, nx+1 <- nodes 0, 1, each side as one aligned pair of elements when
+//          nx is even (two elements otherwise);
+//  part 2 (periodic y only), one thread per element of the ghost rows -2, -1, ny,
+//          ny+1 over x = -2 .. nx+1, from the wrapped node (corners included).
+// Part 1 covers 2Q nz ny rows, part 2 2Q nz 4 (nx + 4) elements. (Writing the whole
+// 32-byte ghost sectors instead of the pairs measured slower.)
+__host__ __device__ inline long long ghost_part1(const StepParams& p) {
+    return (long long)2 * Q * p.nz * p.ny;
+}
+__host__ __device__ inline long long ghost_work(const StepParams& p) {
+    return ghost_part1(p) + (p.wall_y ? 0 : (long long)2 * Q * p.nz * 4 * (p.nx + 4));
 }
 
-// Copies ghost cell e (of ghost_cells_per_plane * nz) from its wrapped-around node,
-// for every species and direction.
+template <int B> struct PairOf;
+template <> struct PairOf<2> { using type = unsigned int; };
+template <> struct PairOf<4> { using type = unsigned long long; };
+
 template <class St>
-__device__ __forceinline__ void ghost_copy(typename St::T* f, const StepParams& p, int e) {
-    const int ncol = 4 * p.ny;
-    const int G = (int)ghost_cells_per_plane(p);
-    const int z = e / G, g = e - z * G;
-    int x, y;
-    if (g < ncol) {
-        y = g >> 2;
-        const int c = g & 3;
-        x = c < 2 ? c - 2 : p.nx + c - 2;
-    } else {
-        const int h = g - ncol, r = h / (p.nx + 4);
-        x = h - r * (p.nx + 4) - 2;
-        y = r < 2 ? r - 2 : p.ny + r - 2;
+__device__ __forceinline__ void ghost_item(typename St::T* f, const StepParams& p, long long i) {
+    using T = typename St::T;
+    using Pair = typename PairOf<sizeof(T)>::type;
+    const long long n1 = ghost_part1(p);
+    if (i < n1) {
+        const int y = (int)(i % p.ny);
+        const long long kz = i / p.ny;
+        const int z = (int)(kz % p.nz), k = (int)(kz / p.nz);
+        T* row = f + (size_t)k * p.P + pidx(p.pitch, p.nyp, p.padx, 0, y, z);   // node x = 0
+        if ((p.nx & 1) == 0 && p.nx >= 2) {
+            // row[-2], row[-1] <- row[nx-2], row[nx-1]; row[nx], row[nx+1] <- row[0], row[1]
+            const Pair a = *reinterpret_cast<const Pair*>(row + p.nx - 2);
+            const Pair b = *reinterpret_cast<const Pair*>(row);
+            *reinterpret_cast<Pair*>(row - 2) = a;
+            *reinterpret_cast<Pair*>(row + p.nx) = b;
+        } else {
+            const T a0 = row[wrap_near(-2, p.nx)], a1 = row[wrap_near(-1, p.nx)];
+            const T b0 = row[wrap_near(p.nx, p.nx)], b1 = row[wrap_near(p.nx + 1, p.nx)];
+            row[-2] = a0;
+            row[-1] = a1;
+            row[p.nx] = b0;
+            row[p.nx + 1] = b1;
+        }
+        return;
     }
-    const size_t dst = pidx(p.pitch, p.nyp, p.padx, x, y, z);
-    const size_t src = pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z);
-    typename St::T v[2 * Q];
-#pragma unroll
-    for (int ik = 0; ik < 2 * Q; ++ik) v[ik] = f[(size_t)ik * p.P + src];
-#pragma unroll
-    for (int ik = 0; ik < 2 * Q; ++ik) f[(size_t)ik * p.P + dst] = v[ik];
+    const long long j = i - n1;
+    const int w = p.nx + 4;
+    const int x = (int)(j % w) - 2;
+    const long long r1 = j / w;
+    const int r = (int)(r1 % 4);
+    const long long kz = r1 / 4;
+    const int z = (int)(kz % p.nz), k = (int)(kz / p.nz);
+    const int y = r < 2 ? r - 2 : p.ny + r - 2;
+    T* blk = f + (size_t)k * p.P;
+    blk[pidx(p.pitch, p.nyp, p.padx, x, y, z)] =
+        blk[pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z)];
 }
 
 template <class St>
 __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
-    const int total = (int)(ghost_cells_per_plane(p) * p.nz);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
-        ghost_copy<St>(f, p, e);
+    const long long total = ghost_work(p);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        ghost_item<St>(f, p, i);
 }
 
-// Ghost cells of every lattice of a batch: cell e belongs to the last lattice whose
-// first ghost cell is <= e.
+// Ghost copies of every lattice of a batch: item i belongs to the last lattice whose
+// first item is <= i.
 template <class St>
 __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nlat,
                                    long long total) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
         int lo = 0, hi = nlat - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].ghost_begin <= e) lo = mid;
+            if (tab[mid].ghost_begin <= i) lo = mid;
             else hi = mid - 1;
         }
         const BatchLattice& L = tab[lo];
-        ghost_copy<St>(static_cast<typename St::T*>(L.fout), L.p, (int)(e - L.ghost_begin));
+        ghost_item<St>(static_cast<typename St::T*>(L.fout), L.p, i - L.ghost_begin);
     }
 }
 
@@ -843,12 +858,14 @@ cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long ce
     return cudaGetLastError();
 }
 
-long long ghost_cells(const StepParams& p) { return ghost_cells_per_plane(p) * p.nz; }
+// Work items of one lattice's ghost fill.
+long long ghost_cells(const StepParams& p) { return ghost_work(p); }
 
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s) {
     const int threads = 256;
-    const size_t cells = (size_t)(ghost_cells_per_plane(p) * p.nz);
+    const size_t cells = (size_t)ghost_work(p);
+    if (cells == 0) return cudaSuccess;   // nothing to copy (no launch)
     size_t blocks = (cells + threads - 1) / threads;
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
