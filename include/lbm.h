@@ -221,11 +221,12 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * of any box size) kept resident on the device and advanced together. The paper
  * has no counterpart; it is the batching and serving layer around the step above.
  *
- * - Requests are queued (FIFO) by lbm_engine_submit and admitted by
- *   lbm_engine_tick while the device memory of the resident lattices (their
- *   lbm_footprint_bytes plus 56 bytes of host-exchange staging per node) stays
- *   within hbm_budget_bytes and at most max_slots are resident. A request that can
- *   never fit is refused at submission (LBM_ENOMEM).
+ * - Requests are queued by lbm_engine_submit and admitted by lbm_engine_tick, in
+ *   the order of the admission policy, while the device memory of the resident
+ *   lattices (their lbm_footprint_bytes plus 56 bytes of host-exchange staging per
+ *   node) stays within hbm_budget_bytes and at most max_slots are resident.
+ *   Admission stops at the first request in that order that does not fit. A
+ *   request that can never fit is refused at submission (LBM_ENOMEM).
  * - Every tick advances all resident lattices by the same number of steps k (at most
  *   chunk_steps, and not past any lattice's last step): the lattices of one storage
  *   format and relaxation class advance in one batched launch of the step kernel
@@ -251,6 +252,10 @@ typedef struct {
     int max_slots;            /* resident lattices at most (>= 1)                      */
     int chunk_steps;          /* steps per tick at most (>= 2)                         */
     int autotune;             /* 1: time the block-schedule candidates; 0: T = 32      */
+    int policy;               /* admission order: 0 first come first served; 1 shortest
+                                 job first (fewest node-steps; ties by arrival), which
+                                 lowers the mean and median latency of a saturated
+                                 stream                                                */
     void* cuda_stream;        /* cudaStream_t of all engine work, or NULL              */
 } lbm_engine_params;
 

@@ -227,9 +227,13 @@ cudaError_t replay(lbm_engine* e, long long pairs, float* ms) {
 }
 
 lbm_status admit(lbm_engine* e) {
+    if (e->ep.policy == 1)   // shortest job first: fewest node-steps, then arrival
+        std::stable_sort(e->queue.begin(), e->queue.end(), [](const Request* a, const Request* b) {
+            return (double)a->N * a->steps_total < (double)b->N * b->steps_total;
+        });
     while (!e->queue.empty() && (int)e->resident.size() < e->ep.max_slots) {
         Request* r = e->queue.front();
-        if (e->used + r->bytes > e->ep.hbm_budget_bytes) break;   // first in, first admitted
+        if (e->used + r->bytes > e->ep.hbm_budget_bytes) break;   // in policy order
         e->queue.pop_front();
         lbm_params p = r->p;
         p.cuda_stream = e->stream;
@@ -289,8 +293,10 @@ lbm_status retire(lbm_engine* e, int* retired) {
 extern "C" lbm_status lbm_engine_create(const lbm_engine_params* p, lbm_engine** out) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;
-    if (!p || p->max_slots < 1 || p->chunk_steps < 2 || p->hbm_budget_bytes == 0) {
-        set_global_error("lbm_engine_create: need max_slots >= 1, chunk_steps >= 2, a budget");
+    if (!p || p->max_slots < 1 || p->chunk_steps < 2 || p->hbm_budget_bytes == 0 ||
+        p->policy < 0 || p->policy > 1) {
+        set_global_error("lbm_engine_create: need max_slots >= 1, chunk_steps >= 2, a budget, "
+                         "policy 0 or 1");
         return LBM_EINVAL;
     }
     lbm_engine* e = new (std::nothrow) lbm_engine();

@@ -37,7 +37,8 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
 
 class EngineParams(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int),
-                ("chunk_steps", C.c_int), ("autotune", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("chunk_steps", C.c_int), ("autotune", C.c_int), ("policy", C.c_int),
+                ("cuda_stream", C.c_void_p)]
 
 
 class LbmError(RuntimeError):
@@ -333,11 +334,15 @@ class Engine:
 
     STATES = {0: "queued", 1: "resident", 2: "finished", 3: "taken", 4: "failed", -1: "unknown"}
 
-    def __init__(self, budget_bytes, max_slots=64, chunk_steps=50, autotune=True, stream=None):
+    POLICIES = {"fcfs": 0, "sjf": 1}
+
+    def __init__(self, budget_bytes, max_slots=64, chunk_steps=50, autotune=True, policy="fcfs",
+                 stream=None):
         self._lib = load()
         ep = EngineParams()
         ep.hbm_budget_bytes = int(budget_bytes)
         ep.max_slots, ep.chunk_steps, ep.autotune = int(max_slots), int(chunk_steps), int(autotune)
+        ep.policy = self.POLICIES[policy]
         ep.cuda_stream = stream
         h = C.c_void_p()
         rc = self._lib.lbm_engine_create(C.byref(ep), C.byref(h))

@@ -121,3 +121,28 @@ def test_serving_loop_reports_latency_and_throughput(lbm):
     assert 0 < rep["p50_ms"] <= rep["p99_ms"]
     assert rep["glups"] > 0
     print("serving report:", {k: v for k, v in rep.items() if k != "latency_s"})
+
+
+def test_shortest_job_first_admission(lbm):
+    from paper_2005_12764_gb300 import serving
+    big = dict(id=0, L=48, R=12.0, sigma=0.01, steps=60, sheared=False)
+    small = [dict(id=k, L=32, R=8.0, sigma=0.01, steps=10 + k, sheared=False) for k in (1, 2, 3)]
+    order = []
+    for policy in ("fcfs", "sjf"):
+        e = lbm.Engine(budget_bytes=8 << 30, max_slots=1, chunk_steps=8, autotune=False, policy=policy)
+        tickets = {}
+        for r in [big] + small:          # the big request arrives first
+            p, rr, rb = serving.request_lattice(r)
+            tickets[e.submit(p, rr, rb, r["steps"])] = r["id"]
+        done = []
+        for _ in range(100):
+            e.tick()
+            for t, k in tickets.items():
+                if k not in done and e.state(t) == "finished":
+                    done.append(k)
+            if len(done) == 4:
+                break
+        e.close()
+        order.append(done)
+    assert order[0] == [0, 1, 2, 3]          # first come, first served
+    assert order[1] == [1, 2, 3, 0]          # shortest (fewest node-steps) first
