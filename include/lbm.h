@@ -119,15 +119,15 @@ lbm_status lbm_step(lbm_ctx* ctx, int n);
 
 /* As lbm_step, but synchronising after every step and timing its kernels with CUDA
  * events on the context stream, summed over the n steps: out_ms[0] the near-contact
- * pass (0 when A_nc == 0), out_ms[1] the fused step kernel, out_ms[2] the ghost-copy
- * fill of the periodic axes. For measurement; it serialises the host with the
- * device.                                                                       */
+ * pass (0 when A_nc == 0; it includes the ghost-copy fill of the step's input),
+ * out_ms[1] the fused step kernel, out_ms[2] the ghost-copy fill of the periodic
+ * axes (0 when A_nc > 0). For measurement; it serialises the host with the device. */
 lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[3]);
 
-/* Kernel launches one lbm_step makes per time step: the fused step; the ghost-copy
- * fill where ghost copies are kept in memory (a periodic y axis, or a lattice of a
- * single 32-node tile along x); and, when A_nc > 0, the near-contact ray-bound
- * field and pass (the first step after a change of state adds a candidate scan). */
+/* Kernel launches one lbm_step makes per time step: the fused step, and either the
+ * ghost-copy fill of the periodic axes (A_nc == 0) or the near-contact pass, which
+ * writes those ghost copies too (A_nc > 0; the first step after a change of state
+ * adds the ray-bound field and a candidate scan).                              */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the
@@ -141,6 +141,16 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u,
  * exactly as that step will measure it; 0 where no film is within h_cut or
  * A_nc == 0. For diagnostics and tests; synchronises the stream.                 */
 lbm_status lbm_get_nc_field(lbm_ctx* ctx, double* ah, int on_device);
+
+/* Self-check of the near-contact work bound (an implementation device with no
+ * counterpart in the paper: the paper does not say how the film is searched).
+ * The step kernel marks, for the next step's film measurement, every 2x2x2 block
+ * of the block grid (block b = nodes 2b .. 2b+2 per axis) that holds a node with
+ * colour field > 0.5e-5. This recomputes that bit field from the current colour
+ * field with a separate kernel and compares: out[0] = 32-bit words that differ,
+ * out[1] = words compared. LBM_ESTATE unless A_nc > 0 and a step has run since the
+ * last change of state. Synchronises the stream.                                 */
+lbm_status lbm_nc_bound_check(lbm_ctx* ctx, long long out[2]);
 
 /* Raw populations as float64 [19][N] per species, in the order of
  * lbm_velocity_set, plus the colour field of the previous step (lag buffer, [N];

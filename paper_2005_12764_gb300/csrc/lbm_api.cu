@@ -426,7 +426,7 @@ extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     const PadLayout L = pad_layout(*p);
     size_t b = 2 * 2 * Q * L.P * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
-    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int4)) + nc_pos_bytes(*p);
+    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int4)) + 3 * nc_pos_bytes(*p);
     return b;
 }
 
@@ -480,7 +480,6 @@ static void fill_step_params(lbm_ctx* c) {
     s.nby = (p.ny + 1) / 2;
     s.nbz = (p.nz + 1) / 2;
     s.nbw = (s.nbx + 31) / 32;
-    s.nc_pos = c->nc_pos;
     // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
     // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
     // pipeline fill), the cost of a part-major launch.
@@ -498,8 +497,17 @@ static void fill_step_params(lbm_ctx* c) {
         }
     }
     s.zparts = best_k;
-
+    s.chain = 0;
     c->grid = (int)(tiles * best_k);
+    // chain mode when one wave of whole parts would leave SMs unevenly loaded: a
+    // multiple of the tile columns, at most the CTAs resident at once, and at least
+    // 8 planes per CTA
+    const long long units = tiles * p.nz;
+    const long long g = (long long)(S / s.tiles_x) * s.tiles_x;
+    if (tiles < S && g > 0 && units >= 8 * g && tiles * best_k != g) {
+        s.chain = (int)g;
+        c->grid = (int)g;
+    }
 }
 
 // The step kernel's bounded waits record a give-up in a device word; report it.
@@ -519,7 +527,10 @@ void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* ou
     s.fout = c->f[1 - cur];
     s.phi_lag = c->phi[pc];
     s.phi_out = c->phi[1 - pc];
-    if (zparts > 0) s.zparts = zparts;
+    if (zparts > 0) {
+        s.zparts = zparts;
+        s.chain = 0;
+    }
     out->in_map = c->tmap[cur];
     out->out_map = c->smap[1 - cur];
     out->p = s;
@@ -576,8 +587,16 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
                                    alloc((void**)&c->cand[0], c->N * sizeof(int4)) &&
                                    alloc((void**)&c->cand[1], c->N * sizeof(int4)) &&
                                    alloc((void**)&c->cand_count, 2 * sizeof(int)) &&
-                                   alloc((void**)&c->nc_pos, nc_pos_bytes(*p))
+                                   alloc((void**)&c->nc_pos[0], 3 * nc_pos_bytes(*p)) &&
+                                   alloc((void**)&c->nc_next, 3 * sizeof(int))
                                : true);
+    if (ok && p->A_nc > 0.0) {
+        const size_t words = nc_pos_bytes(*p) / sizeof(uint32_t);
+        c->nc_pos[1] = c->nc_pos[0] + words;
+        c->nc_pos[2] = c->nc_pos[0] + 2 * words;
+        ok = cudaMemset(c->nc_next, 0, 3 * sizeof(int)) == cudaSuccess &&
+             cudaMemset(c->cand_count, 0, 2 * sizeof(int)) == cudaSuccess;
+    }
     c->red_blocks = c->num_sms * 8;
     ok = ok && alloc((void**)&c->red, (size_t)(c->red_blocks + 1) * 8 * sizeof(double));
     ok = ok && cudaMallocHost((void**)&c->red_host, 8 * sizeof(double)) == cudaSuccess;
@@ -666,7 +685,8 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->cand[0]);
     cudaFree(c->cand[1]);
     cudaFree(c->cand_count);
-    cudaFree(c->nc_pos);
+    cudaFree(c->nc_pos[0]);
+    cudaFree(c->nc_next);
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
 }
@@ -773,11 +793,15 @@ extern "C" lbm_status lbm_set_pin_mask(lbm_ctx* c, const uint8_t* mask, int on_d
     return LBM_OK;
 }
 
-// Launches of one time step: the near-contact pass (A_nc > 0) and the step kernel.
+// Launches of one time step: the near-contact pass (A_nc > 0), the step kernel and,
+// without near-contact force, the ghost-copy fill of the step's output (with it, the
+// next pass writes those ghost copies).
 // Near-contact bookkeeping: the step kernel of step t lists candidates in cand[cw]
 // and consumes (zeroes) the A_h entries it reads; the pass of step t+1 reads that
-// list and writes A_h only at those nodes. After any change of state the pass scans
-// every node once instead. Events (optional) bracket the two launches.
+// list and writes A_h only at those nodes. The step kernel also sets the ray-bound
+// bits of its colour field, nc_pos[k] for phi[k], which that pass reads. After any
+// change of state the pass scans every node once instead. Events (optional) bracket
+// the launches: e0 .. e1 pass, e1 .. e2 step kernel, e2 .. e3 ghost fill.
 static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2,
                                    cudaEvent_t e3 = nullptr) {
     StepParams s = c->sp;
@@ -785,33 +809,37 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
     s.fout = c->f[1 - c->cur];
     s.phi_lag = c->phi[c->pc];
     s.phi_out = c->phi[1 - c->pc];
+    const bool nc = c->p.A_nc > 0.0;
     cudaError_t e = cudaSuccess;
     if (e0) e = cudaEventRecord(e0, c->stream);
-    if (c->p.A_nc > 0.0) {
-        if (e == cudaSuccess) {
-            if (c->nc_scan) {
-                s.nc_list = nullptr;
-                s.nc_count = nullptr;
-            } else {
-                s.nc_list = c->cand[1 - c->cw];
-                s.nc_count = c->cand_count + (1 - c->cw);
-            }
-            // scan mode compacts its candidates into the list slot this pass would
-            // otherwise read (stale after a change of state)
-            e = launch_nc(s, c->cand[1 - c->cw], c->cand_count + (1 - c->cw), c->num_sms,
-                          c->stream);
-        }
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(c->cand_count + c->cw, 0, sizeof(int), c->stream);
+    if (nc) {
+        s.nc_pos = c->nc_pos[c->pc];
+        s.nc_pos_out = c->nc_pos[1 - c->pc];
         s.cand = c->cand[c->cw];
         s.cand_count = c->cand_count + c->cw;
+        s.cand_clear = s.cand_count;
+        s.nc_next = c->nc_next + (1 - c->cw);
+        s.nc_next_clear = c->nc_next + c->cw;
+        s.ghost_f = ghost_cells(s) > 0 ? c->f[c->cur] : nullptr;
+        if (c->nc_scan) {
+            s.nc_list = nullptr;
+            s.nc_count = nullptr;
+        } else {
+            s.nc_list = c->cand[1 - c->cw];
+            s.nc_count = c->cand_count + (1 - c->cw);
+        }
+        // scan mode compacts its candidates into the list slot this pass would
+        // otherwise read (stale after a change of state)
+        if (e == cudaSuccess)
+            e = launch_nc(s, c->cand[1 - c->cw], c->cand_count + (1 - c->cw), c->p.storage,
+                          c->num_sms, c->stream);
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess)
         e = launch_step(s, c->tmap[c->cur], c->smap[1 - c->cur], c->p.storage, c->grid, c->stream);
     if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
     // ghost copies of the periodic axes for the next step's halo loads
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !nc)
         e = launch_ghost_fill(c->f[1 - c->cur], s, c->p.storage, c->num_sms, c->stream);
     if (e == cudaSuccess && e3) e = cudaEventRecord(e3, c->stream);
     if (e != cudaSuccess) return e;
@@ -862,6 +890,22 @@ extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[3]) {
     return check_err_word(c);
 }
 
+// A near-contact pass outside the time step (diagnostics): scan mode on s.phi_lag
+// into s.ah, with the scratch bit field and work counter, touching none of the
+// live step state; its candidates go to the list slot the next step kernel
+// overwrites.
+static cudaError_t diag_pass(lbm_ctx* c, StepParams s) {
+    s.nc_list = nullptr;
+    s.nc_count = nullptr;
+    s.nc_pos = c->nc_pos[2];
+    s.nc_pos_out = nullptr;
+    s.nc_next = c->nc_next + 2;
+    s.nc_next_clear = nullptr;
+    s.cand_clear = nullptr;
+    s.ghost_f = nullptr;
+    return launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->p.storage, c->num_sms, c->stream);
+}
+
 extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, double* u,
                                      double* phi, int on_device) {
     if (!c) return LBM_EINVAL;
@@ -883,10 +927,7 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
         // space after the staged fields (the live A_h buffer is left untouched)
         if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
         s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
-        s.nc_list = nullptr;
-        s.nc_count = nullptr;
-        // scan-mode candidates go to the list slot the next step kernel overwrites
-        CK(c, launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->num_sms, c->stream));
+        CK(c, diag_pass(c, s));
     }
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
@@ -919,10 +960,7 @@ extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
         StepParams s = c->sp;
         s.phi_lag = c->phi[c->pc];
         s.ah = scratch;
-        s.nc_list = nullptr;
-        s.nc_count = nullptr;
-        // scan-mode candidates go to the list slot the next step kernel overwrites
-        CK(c, launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->num_sms, c->stream));
+        CK(c, diag_pass(c, s));
     } else {
         CK(c, cudaMemsetAsync(scratch, 0, N * sizeof(float), c->stream));
     }
@@ -931,6 +969,39 @@ extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
     CK(c, cudaGetLastError());
     if (!on_device) CK(c, cudaMemcpyAsync(ah, dst, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+__global__ void count_diff_kernel(const uint32_t* a, const uint32_t* b, long long n,
+                                  unsigned long long* out) {
+    unsigned long long k = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        k += a[i] != b[i];
+    if (k) atomicAdd(out, k);
+}
+
+extern "C" lbm_status lbm_nc_bound_check(lbm_ctx* c, long long out[2]) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!(c->p.A_nc > 0.0)) return fail(c, LBM_ESTATE, "no near-contact force on this lattice");
+    if (c->steps == 0 || c->nc_scan)
+        return fail(c, LBM_ESTATE, "no step has run since the last change of state");
+    const long long words = (long long)(nc_pos_bytes(c->p) / sizeof(uint32_t));
+    if (ensure_stage(c, 1) != LBM_OK) return LBM_ENOMEM;
+    StepParams s = c->sp;
+    s.phi_lag = c->phi[c->pc];
+    s.nc_pos = c->nc_pos[2];
+    CK(c, launch_nc_pos(s, c->num_sms, c->stream));
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(c->stage);
+    CK(c, cudaMemsetAsync(d, 0, sizeof(*d), c->stream));
+    count_diff_kernel<<<grid_for((size_t)words, c->num_sms), kThreads, 0, c->stream>>>(
+        c->nc_pos[2], c->nc_pos[c->pc], words, d);
+    CK(c, cudaGetLastError());
+    unsigned long long h = 0;
+    CK(c, cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    out[0] = (long long)h;
+    out[1] = words;
     return LBM_OK;
 }
 
@@ -1143,7 +1214,8 @@ extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
-    // the fused step, the ghost fill where a periodic axis needs ghost copies in
-    // memory, and near contact's ray-bound field and list pass
-    return 1 + (ghost_cells(c->sp) > 0 ? 1 : 0) + (c->p.A_nc > 0.0 ? 2 : 0);
+    // the fused step, and the near-contact pass (which writes the ghost copies) or
+    // the ghost fill
+    if (c->p.A_nc > 0.0) return 2;
+    return 1 + (ghost_cells(c->sp) > 0 ? 1 : 0);
 }

@@ -113,6 +113,12 @@ struct StepParams {
     uint32_t* nc_pos;       // [nbz][nby][nbw] bits: block (bx, by, bz) of the 2x2x2 block grid
                             // may hold a node with phi_lag > kPosBand among nodes 2b .. 2b+2
                             // per axis (bit bx & 31 of word bx >> 5)
+    uint32_t* nc_pos_out;   // the same bits for phi_out: cleared by the near-contact pass and
+                            // set by the step kernel (null: not kept)
+    int* nc_next;           // work counter of the near-contact list kernel (0 on entry)
+    int* nc_next_clear;     // counter the list kernel zeroes for the next pass (or null)
+    int* cand_clear;        // candidate counter the list kernel zeroes for the step kernel
+    void* ghost_f;          // populations whose ghost copies the list kernel fills (or null)
     int nbx, nby, nbz, nbw; // block grid: ceil(n / 2) per axis; nbw = ceil(nbx / 32)
     float gy, gz;
     int nx, ny, nz;
@@ -131,7 +137,10 @@ struct StepParams {
     int nsamp;              // ray samples t = -1, -1/2, ..., h_cut + 2
     float ref_half;         // rho0/2 for FP16/BF16 deviation storage, 0 for FP32
     int tiles_x, tiles_y;   // xy tiles of the step kernel
-    int zparts;             // z is cut into this many equal parts, one CTA per (part, tile)
+    int zparts;             // part mode: z is cut into this many equal parts, one CTA per
+                            // (part, tile)
+    int chain;              // chain mode (> 0): this many CTAs share the (tile, plane) units
+                            // equally, each a contiguous run of them in column-major tile order
     void* fout;             // populations after the step
     int* err;               // device error word: 1 = a bounded wait gave up
 };
@@ -224,6 +233,48 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
 constexpr float kSignBand = 1e-5f;
 constexpr float kPosBand = 0.5e-5f;
 constexpr int kMaxSamples = 25;   // t = -1 .. h_cut + 2 for h_cut <= 9
+
+// Blocks of the bit field that hold node n of an axis of N nodes (nb = ceil(N/2)
+// blocks, block b = nodes 2b, 2b+1, 2b+2): `second` = 0 gives n/2, `second` = 1 the
+// other block holding it, or -1. Even n >= 2 also lie in block n/2 - 1; on a
+// periodic axis the last block wraps over node 0 (and over node 1 when N is odd).
+__device__ __forceinline__ int pos_block(int n, int second, int N, bool periodic, int nb) {
+    if (!second) return n >> 1;
+    if ((n & 1) == 0 && n >= 2) return (n >> 1) - 1;
+    if (periodic && (n == 0 || (n == 1 && (N & 1)))) return nb - 1;
+    return -1;
+}
+
+// Bits 0, 2, .., 30 of v moved to bits 0 .. 15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    return (v | (v >> 8)) & 0x0000FFFFu;
+}
+
+// Marks, in the bit field `bits`, the blocks holding the positive nodes of one row
+// segment: m = bit j set if node (x0 + j, y, z) has phi > kPosBand, x0 even, the
+// segment at most 32 nodes. Lane `which` (0 .. 3) of the calling warp handles the
+// (y, z) block pair (which & 1, which >> 1). The blocks x0/2 .. x0/2 + 15 take their
+// nodes 2b, 2b+1, 2b+2 from the segment (node x0 + 32 belongs to the next segment,
+// which marks it as its own first node); the block before the segment (wrapping
+// at x = 0) holds node x0, and for odd nx node 1 as well.
+__device__ __forceinline__ void mark_pos_row(uint32_t* bits, const StepParams& p, int x0, int y,
+                                             int z, uint32_t m, int which) {
+    const int by = pos_block(y, which & 1, p.ny, !p.wall_y, p.nby);
+    const int bz = pos_block(z, which >> 1, p.nz, !p.wall_z, p.nbz);
+    if (by < 0 || bz < 0) return;
+    uint32_t* row = bits + ((size_t)bz * p.nby + by) * p.nbw;
+    const uint32_t c = even_bits(m | (m >> 1) | (m >> 2));
+    const int b0 = x0 >> 1;
+    if (c) atomicOr(row + (b0 >> 5), c << (b0 & 31));
+    if ((m & 1u) || (x0 == 0 && (p.nx & 1) && (m & 2u))) {
+        const int pb = x0 == 0 ? p.nbx - 1 : b0 - 1;
+        atomicOr(row + (pb >> 5), 1u << (pb & 31));
+    }
+}
 
 // Ray of a candidate: unit direction -G'/|G'|; false when |G'| < 1e-3 or non-finite.
 __device__ __forceinline__ bool nc_ray(float Gx, float Gy, float Gz, float& nx_, float& ny_,

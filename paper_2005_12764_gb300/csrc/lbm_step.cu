@@ -25,10 +25,19 @@
 // global memory. The collision writes the plane's outputs to a shared output tile
 // that one thread stores with 38 TMA tensor copies.
 //
-// Work split: z is cut into `zparts` equal parts and every CTA marches one part of
-// one tile. CTAs are numbered part-major, so the CTAs resident at the same time work
-// on neighbouring tiles at the same heights: the halo rows one tile stages are the
-// rows its neighbours are reading, and come from L2 rather than HBM.
+// Work split, two modes.
+// Part mode (lattices of more tiles than the GPU holds CTAs at once): z is cut into
+// `zparts` equal parts and every CTA marches one part of one tile. CTAs are numbered
+// part-major, so the CTAs resident at the same time work on neighbouring tiles at
+// the same heights: the halo rows one tile stages are the rows its neighbours are
+// reading, and come from L2 rather than HBM.
+// Chain mode (smaller lattices): exactly as many CTAs as fit on the GPU at once
+// share the (tile, plane) units equally, each taking a contiguous run of them in
+// column-major tile order (all planes of tile (0,0), then of (0,1), ...), so a CTA
+// may finish one tile and continue on the next. Every SM then carries the same
+// work, where whole parts per tile would leave some SMs with one CTA and others
+// with two; the CTA count is a multiple of the tile columns, so tiles side by side
+// in x have the same split and are marched at the same heights at the same time.
 #include <cuda.h>
 
 #include "lbm_device.cuh"
@@ -36,6 +45,7 @@
 namespace lbm {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
+static_assert(TX == 32, "a warp is one row of a tile (near-contact bits, row stores)");
 constexpr int CTAS_PER_SM = 2;
 constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
@@ -43,8 +53,6 @@ constexpr int NRING = 2 * (TX + 2) + 2 * TY;
 template <class St>
 struct Geo {
     using T = typename St::T;
-    // interior offset in a padded row: 16 bytes, so that tensor stores of a tile start
-    // on a 16-byte boundary
     // interior offset in a padded row: 32 bytes, so that each row's two x ghosts
     // (just before the interior, and just after it) sit in 32-byte sectors of their
     // own, written whole by the ghost fill; tile stores start on a 16-byte boundary
@@ -166,13 +174,42 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
     uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
     bool failed = false;
 
-    // one (z part, tile) work item per CTA, part-major
+    // work of this CTA: one or more segments, each a tile and a range of planes
     const int ntiles = p.tiles_x * p.tiles_y;
-    const int part = cta / ntiles, tile = cta - part * ntiles;
-    {
-        const int zb = (int)((long long)p.nz * part / p.zparts);
-        const int ze = (int)((long long)p.nz * (part + 1) / p.zparts);
-        const int x0 = (tile % p.tiles_x) * TX, y0 = (tile / p.tiles_x) * TY;
+    long long u_next = 0, u_end = 0;   // chain mode: this CTA's units (tile, plane)
+    if (p.chain > 0) {
+        const long long U = (long long)ntiles * p.nz;
+        u_next = U * cta / p.chain;
+        u_end = U * (cta + 1) / p.chain;
+    }
+    bool part_done = false;
+    auto next_segment = [&](int& sx0, int& sy0, int& szb, int& sze) -> bool {
+        if (p.chain > 0) {
+            // units in column-major tile order: tile t is column t / tiles_y, row
+            // t % tiles_y; planes ascending within a tile
+            if (u_next >= u_end) return false;
+            const int t = (int)(u_next / p.nz);
+            szb = (int)(u_next - (long long)t * p.nz);
+            sze = (int)min((long long)p.nz, (long long)szb + (u_end - u_next));
+            u_next += sze - szb;
+            const int tx = t / p.tiles_y;
+            sx0 = tx * TX;
+            sy0 = (t - tx * p.tiles_y) * TY;
+            return true;
+        }
+        // part mode: one (z part, tile) item per CTA, part-major
+        if (part_done) return false;
+        part_done = true;
+        const int part = cta / ntiles, tile = cta - part * ntiles;
+        szb = (int)((long long)p.nz * part / p.zparts);
+        sze = (int)((long long)p.nz * (part + 1) / p.zparts);
+        sx0 = (tile % p.tiles_x) * TX;
+        sy0 = (tile / p.tiles_x) * TY;
+        return true;
+    };
+    int seg_x0 = 0, seg_y0 = 0, seg_zb = 0, seg_ze = 0;
+    while (!failed && next_segment(seg_x0, seg_y0, seg_zb, seg_ze)) {
+        const int zb = seg_zb, ze = seg_ze, x0 = seg_x0, y0 = seg_y0;
         const int xw = min(TX, p.nx - x0), yh = min(TY, p.ny - y0);   // owned extent
 
         // ---- this thread's owned node and (optionally) one ring node
@@ -395,6 +432,13 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
                 p.phi_out[node] = phic;
             }
+            if (p.nc_pos_out) {
+                // ray-bound bits of this step's colour field for the next near-contact
+                // pass: one warp is one row of the tile
+                const bool pos = owned && !failed && phi_at(slot(z), otx, oty) > kPosBand;
+                const uint32_t m = __ballot_sync(0xffffffffu, pos);
+                if (m != 0u && lane < 4) mark_pos_row(p.nc_pos_out, p, x0, y0 + oty, z, m, lane);
+            }
             // store the output tile of plane z: 2Q tensor copies of TX x TY, clipped by
             // the store map at the lattice edge (to 16 bytes: ghost copies are written
             // afterwards by the fill pass); the tile is rewritten only after these
@@ -590,7 +634,8 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 // the nodes where A_h can be nonzero), or, after a change of state, the list the
 // scan kernel below compacts from every node. Every other entry of ah is 0.
 //
-// One warp takes 32 candidates at a time, in three phases:
+// Warps take 32 candidates at a time from a shared counter (ray lengths vary
+// widely, so the work is handed out as it is done), in three phases:
 //  1. each lane classifies the samples of its own ray with the block bit field
 //     (independent, cheap lookups) and keeps the index of the last one that may be
 //     positive;
@@ -598,17 +643,40 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 //     32 rays) are spread evenly over the lanes and interpolated into shared memory,
 //     so a few long rays do not hold the warp back;
 //  3. each lane runs the crossing search of its ray over those samples.
+// Before that, the kernel does the bookkeeping of the step kernel that follows it:
+// it zeroes that kernel's candidate counter and ray-bound bits and the next pass's
+// work counter, and writes the ghost copies of the step's input populations (work
+// that overlaps the rays instead of taking a launch of its own).
 constexpr int NC_THREADS = 256, NC_WARPS = NC_THREADS / 32;
 
+template <class St>
 __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p) {
     __shared__ float vals[NC_WARPS][kMaxSamples][32];   // [sample][ray]
     __shared__ int rx[NC_WARPS][32], ry[NC_WARPS][32], rz[NC_WARPS][32], pre[NC_WARPS][33];
     __shared__ float rnx[NC_WARPS][32], rny[NC_WARPS][32], rnz[NC_WARPS][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    if (gtid == 0) {
+        if (p.cand_clear) *p.cand_clear = 0;
+        if (p.nc_next_clear) *p.nc_next_clear = 0;
+    }
+    if (p.nc_pos_out) {
+        const long long words = (long long)p.nbw * p.nby * p.nbz;
+        for (long long i = gtid; i < words; i += gthreads) p.nc_pos_out[i] = 0u;
+    }
+    if (p.ghost_f) {
+        const long long total = ghost_work(p);
+        for (long long i = gtid; i < total; i += gthreads)
+            ghost_item<St>(static_cast<typename St::T*>(p.ghost_f), p, i);
+    }
     const int cnt = *p.nc_count;
     const int plane = p.nx * p.ny;
-    const int nwarps = gridDim.x * NC_WARPS;
-    for (int k0 = (blockIdx.x * NC_WARPS + wib) * 32; k0 < cnt; k0 += nwarps * 32) {
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(p.nc_next, 1);
+        const int k0 = __shfl_sync(0xffffffffu, chunk, 0) * 32;
+        if (k0 >= cnt) break;
         const int k = k0 + lane;
         int node = 0, x = 0, y = 0, z = 0, s_last = -1;
         float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
@@ -744,17 +812,39 @@ __global__ void nc_pos_kernel(const StepParams p) {
     }
 }
 
-// The near-contact pass: bit field, then (scan mode: p.nc_list == null) the
-// candidate compaction into scan_list / scan_count, then the list kernel.
-cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, int num_sms,
-                      cudaStream_t s) {
-    StepParams p = p_in;
+// The bit field of p.phi_lag into p.nc_pos, on its own (scan mode, self-checks).
+cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s) {
     const long long words = (long long)p.nbw * p.nby * p.nbz;
     long long g = (words + NC_WARPS - 1) / NC_WARPS;
     if (g > (long long)num_sms * 16) g = (long long)num_sms * 16;
     nc_pos_kernel<<<(unsigned)g, NC_THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// The near-contact pass. Scan mode (p.nc_list == null, after a change of state):
+// the bit field of the lag field, then the candidate compaction into scan_list /
+// scan_count. Then the list kernel, on as many CTAs as are resident at once (the
+// warps fetch their work from the counter p.nc_next).
+template <class St>
+static cudaError_t launch_list(const StepParams& p, int num_sms, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_list_kernel<St>,
+                                                                      NC_THREADS, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    nc_list_kernel<St><<<(unsigned)(num_sms * per_sm), NC_THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, int storage,
+                      int num_sms, cudaStream_t s) {
+    StepParams p = p_in;
     if (!p.nc_list) {
-        cudaError_t e = cudaMemsetAsync(scan_count, 0, sizeof(int), s);
+        cudaError_t e = launch_nc_pos(p, num_sms, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scan_count, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.nc_next, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
         long long gs = ((long long)p.N + NC_THREADS - 1) / NC_THREADS;
         if (gs > (long long)num_sms * 8) gs = (long long)num_sms * 8;
@@ -762,11 +852,12 @@ cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, 
         p.nc_list = scan_list;
         p.nc_count = scan_count;
     }
-    long long gl = ((long long)p.N / 4 + NC_THREADS - 1) / NC_THREADS;   // ~1/4 of the nodes
-    if (gl > (long long)num_sms * 8) gl = (long long)num_sms * 8;
-    if (gl < 1) gl = 1;
-    nc_list_kernel<<<(unsigned)gl, NC_THREADS, 0, s>>>(p);
-    return cudaGetLastError();
+    switch (storage) {
+        case 0: return launch_list<StoreF32>(p, num_sms, s);
+        case 1: return launch_list<StoreF16>(p, num_sms, s);
+        case 2: return launch_list<StoreBF16>(p, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <class St, bool U>

@@ -29,7 +29,7 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_observables", "lbm_laplace",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
-           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_get_window",
+           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
            "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy",
            "lbm_engine_last_error"]
@@ -102,6 +102,7 @@ def load():
             "lbm_last_error": (C.c_char_p, [_P]),
             "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
+            "lbm_nc_bound_check": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
             "lbm_get_window": (C.c_int, [_P] + [C.c_int] * 6 + [_D, _D, _D, C.c_int]),
             "lbm_engine_create": (C.c_int, [C.POINTER(EngineParams), C.POINTER(C.c_void_p)]),
             "lbm_engine_submit": (C.c_int, [_P, PP, _D, _D, _D, C.c_longlong,
@@ -303,6 +304,13 @@ class Lattice:
         ah = np.empty(self.shape)
         self._check(self._lib.lbm_get_nc_field(self._h, ah.ctypes.data, 0))
         return ah
+
+    def nc_bound_check(self):
+        """(differing words, words) between the step kernel's near-contact ray-bound
+        bit field and one recomputed from the current colour field."""
+        out = (C.c_longlong * 2)()
+        self._check(self._lib.lbm_nc_bound_check(self._h, out))
+        return int(out[0]), int(out[1])
 
     def observables(self):
         out = (C.c_double * 8)()

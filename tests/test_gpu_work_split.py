@@ -1,0 +1,140 @@
+"""GPU checks of how the step's work is split and bounded.
+
+- Chain mode of the step kernel (lattices of fewer tiles than the GPU holds CTAs: a
+  CTA's run of (tile, plane) units may end inside one tile and continue on the
+  next) against the FP64 oracle, and bitwise against part mode (the serving
+  engine's split) on the same lattice.
+- The near-contact ray-bound bit field the step kernel sets for the next step
+  (atomic ORs per row of a tile) equals the one a separate kernel computes from the
+  same colour field, on odd, even, ragged, walled and periodic lattices.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_12764_gb300 import inputs, serving
+
+pytestmark = pytest.mark.gpu
+
+RHO_TOL, U_TOL = 1e-5, 1e-6
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12764_gb300 import build_lib, lbm as L
+    build_lib.build()
+    L.load()
+    return L
+
+
+def test_chain_mode_walls_ragged_near_contact_matches_oracle(lbm):
+    # 72 x 44 x 140: 3 x 6 tiles (ragged in x and y), 2520 (tile, plane) units, so
+    # the step kernel runs in chain mode with ~8 planes per CTA and most CTAs cross
+    # from one tile to the next, including across the z walls.
+    shape = (140, 44, 72)
+    drops = [(20.0, 12.0, 30.0, 6.0), (33.5, 24.0, 31.0, 6.5), (50.0, 30.0, 70.0, 7.0),
+             (60.0, 14.0, 110.0, 8.0), (12.0, 30.0, 95.0, 5.0)]
+    rr, rb = inputs.paint_droplets(shape, drops, periodic=(True, False, False))
+    kw = dict(wall_y=1, wall_z=1, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0, g=(1e-5, 0, 0))
+    nz, ny, nx = shape
+    o = oracle.Lattice(oracle.make_params(nx, ny, nz, **kw))
+    o.set_fields(rr, rb)
+    o.step(30)
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **kw))
+    g.set_fields(rr, rb)
+    g.step(30)
+    fo, fg = o.get_fields(), g.get_fields()
+    e = {k: float(np.abs(fo[k] - fg[k]).max()) for k in ("rho_r", "rho_b", "u")}
+    assert e["rho_r"] <= RHO_TOL and e["rho_b"] <= RHO_TOL and e["u"] <= U_TOL, e
+    g.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_chain_mode_is_bitwise_part_mode(lbm, storage):
+    # A sheared 96^3 droplet: lbm_step runs chain mode (36 tiles), the serving engine
+    # part mode; every node's update is computed the same way in both.
+    req = dict(id=0, L=96, R=24.0, sigma=0.02, steps=24, sheared=True)
+    p, rr, rb = serving.request_lattice(req, storage)
+    g = lbm.Lattice(p)
+    g.set_fields(rr, rb)
+    g.step(req["steps"])
+    f = g.get_fields()
+    g.close()
+    e = lbm.Engine(budget_bytes=8 << 30, max_slots=4, chunk_steps=10, autotune=False)
+    t = e.submit(p, rr, rb, req["steps"])
+    for _ in range(100):
+        if e.state(t) in ("finished", "failed"):
+            break
+        e.tick()
+    assert e.state(t) == "finished"
+    res = e.result(t)
+    e.close()
+    for k in ("rho_r", "rho_b", "u", "phi"):
+        assert np.array_equal(res[k], f[k]), k
+
+
+BOUND_CASES = {
+    "odd_walls_ragged": dict(shape=(13, 29, 45), walls=True,
+                             drops=[(12.0, 10.0, 6.0, 5.0), (24.5, 18.0, 6.5, 5.5),
+                                    (38.0, 9.0, 6.0, 4.5)]),
+    "odd_periodic": dict(shape=(19, 21, 37), walls=False,
+                         drops=[(10.0, 10.0, 9.0, 6.0), (25.0, 11.0, 10.0, 6.5),
+                                (36.0, 3.0, 1.0, 4.0)]),
+    "even_periodic": dict(shape=(24, 32, 48), walls=False,
+                          drops=[(10.0, 16.0, 12.0, 7.0), (26.0, 15.0, 11.0, 7.5),
+                                 (47.0, 31.0, 23.0, 5.0)]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BOUND_CASES))
+def test_ray_bound_bits_of_the_step_kernel(lbm, case):
+    c = BOUND_CASES[case]
+    shape = c["shape"]
+    nz, ny, nx = shape
+    per = (True, not c["walls"], not c["walls"])
+    rr, rb = inputs.paint_droplets(shape, c["drops"], periodic=per)
+    kw = dict(sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0)
+    if c["walls"]:
+        kw.update(wall_y=1, wall_z=1)
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **kw))
+    g.set_fields(rr, rb)
+    for steps in (1, 1, 3, 10):
+        g.step(steps)
+        diff, words = g.nc_bound_check()
+        assert words > 0 and diff == 0, (steps, diff, words)
+    g.close()
+
+
+def test_ray_bound_bits_full_size_channel_and_emulsion(lbm):
+    w = inputs.channel_droplets()
+    nz, ny, nx = w.shape
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    for steps in (1, 4):
+        g.step(steps)
+        assert g.nc_bound_check()[0] == 0
+    g.close()
+    n = 40
+    w = inputs.dense_emulsion(L=n, volume_fraction=0.3, r_range=(4.0, 7.0), seed=11)
+    g = lbm.Lattice(lbm.make_params(n, n, n, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    g.step(5)
+    assert g.nc_bound_check()[0] == 0
+    g.close()
+
+
+def test_ray_bound_check_needs_a_step(lbm):
+    g = lbm.Lattice(lbm.make_params(16, 16, 16, A_nc=0.01, sigma=0.01))
+    rr, rb = inputs.paint_droplets((16, 16, 16), [(8.0, 8.0, 8.0, 4.0)])
+    g.set_fields(rr, rb)
+    with pytest.raises(lbm.LbmError):
+        g.nc_bound_check()
+    g.step(1)
+    assert g.nc_bound_check()[0] == 0
+    g.set_fields(rr, rb)
+    with pytest.raises(lbm.LbmError):
+        g.nc_bound_check()
+    g.close()
