@@ -40,6 +40,8 @@
 // in x have the same split and are marched at the same heights at the same time.
 #include <cuda.h>
 
+#include <utility>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -139,6 +141,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
     return false;
 }
 
+// Programmatic dependent launch: kernels of the time step are launched so that the
+// next one may be scheduled while the previous one drains; each waits for the
+// previous kernel's completion (and its memory) at grid_dep_wait() before it reads
+// or writes any global data, and lets the next one be scheduled at
+// grid_dep_launch(). Both are no-ops in a plain launch.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- the kernel
 // Body of the step kernel for CTA `cta` of one lattice's grid: the single-lattice
 // kernel passes its parameters and tensor maps (kernel parameter space), the
@@ -171,6 +183,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(fout_map)) : "memory");
     }
     __syncthreads();
+    grid_dep_wait();
     uint32_t parity = 0u;   // bit b: phase parity of buffer b's barrier
     bool failed = false;
 
@@ -493,6 +506,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             a_rb = b_rb;
         }
     }
+    grid_dep_launch();
     if (tid == 0) bulk_wait_all();   // output tiles written before the CTA exits
     if (failed) {
         // give copies still in flight into this CTA's shared memory a bounded chance
@@ -604,10 +618,12 @@ __device__ __forceinline__ void ghost_item(typename St::T* f, const StepParams& 
 
 template <class St>
 __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
+    grid_dep_wait();
     const long long total = ghost_work(p);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x)
         ghost_item<St>(f, p, i);
+    grid_dep_launch();
 }
 
 // Ghost copies of every lattice of a batch: item i belongs to the last lattice whose
@@ -657,6 +673,7 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
+    grid_dep_wait();
     if (gtid == 0) {
         if (p.cand_clear) *p.cand_clear = 0;
         if (p.nc_next_clear) *p.nc_next_clear = 0;
@@ -739,6 +756,7 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
         }
         __syncwarp();
     }
+    grid_dep_launch();
 }
 
 // Scan mode (after the state was set): ah = 0 everywhere, and every node whose
@@ -812,6 +830,25 @@ __global__ void nc_pos_kernel(const StepParams p) {
     }
 }
 
+// Launch with programmatic stream serialisation (see grid_dep_wait). (The list and
+// ghost kernels keep the default shared-memory carveout: forcing the largest one
+// leaves them less L1 and measured slower.)
+template <class... KArgs, class... Args>
+static cudaError_t pdl_launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // The bit field of p.phi_lag into p.nc_pos, on its own (scan mode, self-checks).
 cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s) {
     const long long words = (long long)p.nbw * p.nby * p.nbz;
@@ -834,8 +871,7 @@ static cudaError_t launch_list(const StepParams& p, int num_sms, cudaStream_t s)
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    nc_list_kernel<St><<<(unsigned)(num_sms * per_sm), NC_THREADS, 0, s>>>(p);
-    return cudaGetLastError();
+    return pdl_launch(nc_list_kernel<St>, (unsigned)(num_sms * per_sm), NC_THREADS, 0, s, p);
 }
 
 cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, int storage,
@@ -871,8 +907,7 @@ static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map,
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    step_kernel<St, U><<<grid, NT, Geo<St>::SMEM, s>>>(p, map, omap);
-    return cudaGetLastError();
+    return pdl_launch(step_kernel<St, U>, (unsigned)grid, NT, Geo<St>::SMEM, s, p, map, omap);
 }
 
 // omega == 1 everywhere (equal relaxation times tau = 1) drops the non-equilibrium
@@ -952,6 +987,13 @@ cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long ce
 // Work items of one lattice's ghost fill.
 long long ghost_cells(const StepParams& p) { return ghost_work(p); }
 
+template <class St>
+static cudaError_t launch_ghost_tpl(void* f, const StepParams& p, unsigned blocks, unsigned threads,
+                                   cudaStream_t s) {
+    return pdl_launch(ghost_fill_kernel<St>, blocks, threads, 0, s,
+                      static_cast<typename St::T*>(f), p);
+}
+
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s) {
     const int threads = 256;
@@ -961,12 +1003,11 @@ cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     switch (storage) {
-        case 0: ghost_fill_kernel<StoreF32><<<(unsigned)blocks, threads, 0, s>>>((float*)f, p); break;
-        case 1: ghost_fill_kernel<StoreF16><<<(unsigned)blocks, threads, 0, s>>>((__half*)f, p); break;
-        case 2: ghost_fill_kernel<StoreBF16><<<(unsigned)blocks, threads, 0, s>>>((__nv_bfloat16*)f, p); break;
-        default: return cudaErrorInvalidValue;
+        case 0: return launch_ghost_tpl<StoreF32>(f, p, (unsigned)blocks, threads, s);
+        case 1: return launch_ghost_tpl<StoreF16>(f, p, (unsigned)blocks, threads, s);
+        case 2: return launch_ghost_tpl<StoreBF16>(f, p, (unsigned)blocks, threads, s);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 // Geometry the host needs for the tensor maps.
