@@ -14,7 +14,8 @@
  * (montessori2019mesoscale) in the reading stated beside the routine. Each phase
  * of a step is its own loop over all nodes, in the order of the method:
  *
- *   1. pull streaming with halfway bounce-back walls        Eq. (1), streaming text
+ *   1. pull streaming with halfway bounce-back walls        Eq. (1), streaming text;
+ *      optionally sliding y-walls                           sheared-bijel section
  *   2. moments rho_r, rho_b, j, phi                          Eq. (3)
  *   3. isotropic colour gradient                             stencil form of Eq. (10)
  *   4. forces: body + Kolmogorov + near-contact              Eq. (11); the film
@@ -97,6 +98,8 @@ typedef struct {
     double g[3];           /* uniform body-force density                              */
     double kolmogorov_amp; /* F_x(y) = amp * sin(2 pi y / ny)                         */
     int nc_lag;            /* 1: near-contact ray reads phi of the previous step      */
+    double wall_u;         /* sliding y-walls: the wall at y = ny - 1/2 moves with
+                              (+wall_u, 0, 0), the one at y = -1/2 with (-wall_u, 0, 0) */
 } or_params;
 
 typedef struct {
@@ -520,6 +523,34 @@ static void pull_node(const or_params* p, long N, const double* fr, const double
     }
 }
 
+/* Sliding walls (Sec. "High-performance LB code for bijel materials": a bijel
+ * confined between walls moving in opposite directions, +-U along the periodic
+ * axis). Reading: halfway bounce-back from a wall moving with velocity u_w adds
+ * 2 w_i rho (c_i . u_w)/c_s^2 = 6 w_i rho (c_i . u_w) to the reflected population
+ * (the moving-wall bounce-back of Ladd), per species with that species' density
+ * at the node. The terms of the links arriving from one wall sum to zero
+ * (sum of w_i c_ix over them vanishes), so the densities are those of the plain
+ * bounce-back, which is what they are computed from. Applied to the post-stream
+ * populations of a node at y = 0 or ny - 1 (walled y axis).                      */
+static void moving_wall(const or_params* p, long y, double gr[Q], double gb[Q]) {
+    if (!p->wall_y || p->wall_u == 0.0) return;
+    double rr = 0.0, rb = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        rr += gr[i];
+        rb += gb[i];
+    }
+    for (int i = 0; i < Q; ++i) {
+        long ys = y - CY[i];
+        double uw;
+        if (ys >= p->ny) uw = p->wall_u;        /* from the wall at y = ny - 1/2 */
+        else if (ys < 0) uw = -p->wall_u;       /* from the wall at y = -1/2     */
+        else continue;
+        double cu = CX[i] * uw;
+        gr[i] += 2.0 * W[i] * rr * cu / CS2;
+        gb[i] += 2.0 * W[i] * rb * cu / CS2;
+    }
+}
+
 /* Streaming alone (no collision), for the exact-permutation check. */
 void or_stream_only(or_state* s, int nsteps) {
     const or_params* p = &s->p;
@@ -576,6 +607,7 @@ void or_step(or_state* s, int nsteps) {
                     double a[Q], b[Q];
                     long id = nidx(p, x, y, z);
                     pull_node(p, N, s->fr, s->fb, x, y, z, a, b);
+                    moving_wall(p, y, a, b);
                     for (int i = 0; i < Q; ++i) {
                         s->gr[(long)i * N + id] = a[i];
                         s->gb[(long)i * N + id] = b[i];
@@ -711,6 +743,7 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
         long x = id % p->nx, y = (id / p->nx) % p->ny, z = id / ((long)p->nx * p->ny);
         double gr[Q], gb[Q];
         pull_node(p, N, fr, fb, x, y, z, gr, gb);
+        moving_wall(p, y, gr, gb);
         double rr = 0, rb = 0;
         for (int i = 0; i < Q; ++i) {
             rr += gr[i];

@@ -51,7 +51,8 @@ def equilibrium(rho, u):
 
 class MiniLattice:
     def __init__(self, nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=0.0,
-                 beta=0.7, A_nc=0.0, h_min=3.0, h_cut=None, g=(0, 0, 0), kolmogorov_amp=0.0):
+                 beta=0.7, A_nc=0.0, h_min=3.0, h_cut=None, g=(0, 0, 0), kolmogorov_amp=0.0,
+                 wall_u=0.0):
         self.n = (nz, ny, nx)
         self.wall_y, self.wall_z = bool(wall_y), bool(wall_z)
         self.tau_r = tau_r
@@ -61,6 +62,7 @@ class MiniLattice:
         self.h_cut = 2 * h_min if h_cut is None else h_cut
         self.g = np.asarray(g, dtype=float)
         self.kamp = kolmogorov_amp
+        self.wall_u = float(wall_u)
         z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         self.X, self.Y, self.Z = x, y, z
 
@@ -92,6 +94,16 @@ class MiniLattice:
             out = self._outside(-c[1], -c[2])
             gr[i] = np.where(out, self.fr[OPP_[i]], self._shift_from(self.fr[i], c))
             gb[i] = np.where(out, self.fb[OPP_[i]], self._shift_from(self.fb[i], c))
+        if self.wall_y and self.wall_u != 0.0:
+            # sliding y-walls (+U at the top, -U at the bottom, along x): a link that
+            # came back from a wall moving with u_w gains 6 w_i rho_k c_i.u_w
+            ny = self.n[1]
+            rr, rb = gr.sum(0), gb.sum(0)
+            for i, c in enumerate(C_):
+                uw = np.where(self.Y - c[1] >= ny, self.wall_u,
+                              np.where(self.Y - c[1] < 0, -self.wall_u, 0.0))
+                gr[i] = gr[i] + 6.0 * W_[i] * rr * c[0] * uw
+                gb[i] = gb[i] + 6.0 * W_[i] * rb * c[0] * uw
         return gr, gb
 
     def grad(self, phi):

@@ -109,6 +109,56 @@ def test_poiseuille_profile_within_one_percent():
     assert np.abs(u - exact).max() / exact.max() < 0.01
 
 
+# ------------------------------------------------------------------ sliding walls
+@pytest.mark.parametrize("tau", [1.0, 0.8, 1.7])
+def test_couette_between_sliding_walls_is_exact(tau):
+    # walls at y = -1/2 (moving -U) and ny - 1/2 (+U) along x: the steady profile of
+    # plain Couette flow, u_x = U (2 (y + 1/2)/ny - 1), is reached to round-off
+    # (halfway bounce-back places a moving wall exactly for linear flow, any tau)
+    ny, U = 12, 0.01
+    shape = (3, ny, 4)
+    lat = _lattice(shape, (np.ones(shape), np.zeros(shape)), wall_y=1, tau_r=tau, wall_u=U)
+    lat.step(6000)
+    f = lat.get_fields()
+    want = U * (2 * (np.arange(ny) + 0.5) / ny - 1)
+    assert np.abs(f["u"][0] - want[None, :, None]).max() < 1e-13
+    assert np.abs(f["u"][1]).max() < 1e-13 and np.abs(f["u"][2]).max() < 1e-13
+
+
+def test_sliding_walls_two_layers_conserve_mass_and_stay_linear():
+    # red below y = ny/2, blue above, sheared by the walls: each species' mass is
+    # conserved to round-off, the net x momentum stays zero (the set-up is invariant
+    # under (x, y) -> (-x, ny-1-y)), and with equal viscosities the profile is the
+    # single-fluid Couette profile
+    nx, ny, nz, U = 6, 16, 4, 0.02
+    shape = (nz, ny, nx)
+    yy = np.arange(ny)[None, :, None] * np.ones(shape)
+    rr = np.where(yy < ny / 2, 1.0, 0.0)
+    lat = _lattice(shape, (rr, 1.0 - rr), wall_y=1, tau_r=1.0, sigma=0.01, beta=0.7, wall_u=U)
+    m0 = lat.totals()
+    lat.step(4000)
+    m1 = lat.totals()
+    f = lat.get_fields()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12 and abs(m1[1] - m0[1]) / m0[1] < 1e-12
+    assert abs(((f["rho_r"] + f["rho_b"]) * f["u"][0]).sum()) < 1e-12
+    want = U * (2 * (np.arange(ny) + 0.5) / ny - 1)
+    assert np.abs(f["u"][0] - want[None, :, None]).max() < 1e-12
+
+
+def test_sliding_walls_at_rest_are_plain_bounce_back():
+    shape = (6, 7, 5)
+    rr, rb, u = inputs.random_state(shape, seed=3)
+    kw = dict(wall_y=1, wall_z=1, sigma=0.02, beta=0.7, g=(1e-4, 0, 0))
+    a = _lattice(shape, (rr, rb, u), **kw)
+    b = _lattice(shape, (rr, rb, u), wall_u=0.0, **kw)
+    c = _lattice(shape, (rr, rb, u), wall_u=0.01, **kw)
+    for lat in (a, b, c):
+        lat.step(5)
+    pa, pb, pc = a.get_pops(), b.get_pops(), c.get_pops()
+    assert all(np.array_equal(x, y) for x, y in zip(pa, pb))
+    assert not np.array_equal(pa[0], pc[0])
+
+
 # ------------------------------------------------------------------ Laplace law
 def _laplace_ratio(L, R, steps):
     w = inputs.static_droplet(L=L, R=R)
@@ -230,6 +280,7 @@ def test_mirror_symmetry_x():
     dict(shape=(5, 6, 7), wall_y=1, g=(1e-4, 2e-5, 0), tau_b=1.3),
     dict(shape=(8, 6, 7), wall_z=1, wall_y=1, A_nc=0.02, kolmogorov_amp=1e-3, tau_r=0.8),
     dict(shape=(8, 8, 8), A_nc=0.05, h_min=2.0),
+    dict(shape=(6, 7, 5), wall_y=1, wall_z=1, wall_u=0.03, A_nc=0.02, tau_b=0.9),
 ])
 def test_numpy_mini_oracle_agrees(case):
     case = dict(case)
