@@ -81,6 +81,13 @@ typedef struct {
     double h_cut;            /* cutoff of A_h[h]; <= 0 means 2*h_min; at most 9           */
     double g[3];             /* uniform body-force density                                */
     double kolmogorov_amp;   /* adds F_x = amp * sin(2 pi y / ny); 0 = off                */
+    double wall_u;           /* sliding y-walls (needs wall_y): the wall at y = ny-1/2
+                                moves with velocity (+wall_u, 0, 0), the one at y = -1/2
+                                with (-wall_u, 0, 0): shear 2 wall_u / ny, as for the
+                                confined bijel of Sec. "High-performance LB code for
+                                bijel materials". A link that comes back from a moving
+                                wall gains 6 w_i rho c_i.u_w (moving-wall halfway
+                                bounce-back, rho the node's density). |wall_u| < 0.3.  */
     double rho0;             /* reference density of the FP16/BF16 deviation storage (1)  */
     int storage;             /* lbm_storage                                               */
     void* cuda_stream;       /* cudaStream_t to run on, or NULL                           */

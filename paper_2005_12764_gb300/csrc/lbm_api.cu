@@ -408,6 +408,8 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->A_nc > 0.0 && !(hcut > p->h_min)) { why = "h_cut must exceed h_min"; return LBM_EINVAL; }
     if (p->A_nc > 0.0 && hcut > 9.0) { why = "h_cut must be <= 9 (film rays of at most 25 samples)"; return LBM_EINVAL; }
     if (p->storage < 0 || p->storage > 2) { why = "unknown storage"; return LBM_EINVAL; }
+    if (!(std::fabs(p->wall_u) < 0.3)) { why = "|wall_u| must be < 0.3"; return LBM_EINVAL; }
+    if (p->wall_u != 0.0 && !p->wall_y) { why = "wall_u needs walls at the y extremes (wall_y)"; return LBM_EINVAL; }
     if ((p->storage != 0) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
@@ -445,6 +447,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.pin_d2 = c->pin_d2;
     s.gy = (float)p.g[1];
     s.gz = (float)p.g[2];
+    s.wall_u6 = p.wall_y ? (float)(6.0 * p.wall_u) : 0.0f;
     s.nx = p.nx;
     s.ny = p.ny;
     s.nz = p.nz;

@@ -121,6 +121,7 @@ struct StepParams {
     void* ghost_f;          // populations whose ghost copies the list kernel fills (or null)
     int nbx, nby, nbz, nbw; // block grid: ceil(n / 2) per axis; nbw = ceil(nbx / 32)
     float gy, gz;
+    float wall_u6;          // 6 U of sliding y-walls (+U at y = ny-1/2, -U at y = -1/2), or 0
     int nx, ny, nz;
     size_t N;               // nodes (fields phi, ah are [N], x fastest)
     // population arrays are padded: ghost columns and rows around the lattice (the
@@ -232,7 +233,6 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
 // (outward from a droplet into the bulk) have no marked sample at all.
 constexpr float kSignBand = 1e-5f;
 constexpr float kPosBand = 0.5e-5f;
-constexpr int kMaxSamples = 25;   // t = -1 .. h_cut + 2 for h_cut <= 9
 
 // Blocks of the bit field that hold node n of an axis of N nodes (nb = ceil(N/2)
 // blocks, block b = nodes 2b, 2b+1, 2b+2): `second` = 0 gives n/2, `second` = 1 the
@@ -301,32 +301,53 @@ __device__ __forceinline__ int ray_wrap(int b, int n) {
     return wrap_near(b, n);
 }
 
-// Samples of a ray that must be evaluated: bit s set if sample s may be positive.
-// Scanning stops at the first sample outside the fluid (the march stops there).
-// A sample on the last node of a walled axis (fraction 0) is looked up in that
-// node's block: its value is that node's, whatever the other corner holds.
-__device__ __forceinline__ uint32_t nc_sample_mask(const StepParams& p, int x, int y, int z,
-                                                   float nx_, float ny_, float nz_) {
-    uint32_t mask = 0u;
-    const float ylo = (float)-y, yhi = (float)(p.ny - 1 - y);
-    const float zlo = (float)-z, zhi = (float)(p.nz - 1 - z);
-    for (int s = 0; s < p.nsamp; ++s) {
+// Index of the last sample of a ray that may be positive, or -1: the samples
+// inside the fluid are s < s_end (the first sample outside stops the march), and
+// the bit field is scanned from s_end - 1 downwards. A sample on the last node of
+// a walled axis (fraction 0) is looked up in that node's block: its value is that
+// node's, whatever the other corner holds.
+__device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y, int z, float nx_,
+                                              float ny_, float nz_) {
+    int s_end = p.nsamp;
+    if (p.wall_y || p.wall_z) {
+        const float ylo = (float)-y, yhi = (float)(p.ny - 1 - y);
+        const float zlo = (float)-z, zhi = (float)(p.nz - 1 - z);
+        auto inside = [&](int s) {
+            const float t = -1.0f + 0.5f * (float)s;
+            const float oy = t * ny_, oz = t * nz_;
+            return !((p.wall_y && !(oy >= ylo && oy <= yhi)) || (p.wall_z && !(oz >= zlo && oz <= zhi)));
+        };
+        // the samples inside the fluid along a walled axis are one interval of s (t n
+        // is monotone in s); if it holds s = 0, it ends near the sample where the ray
+        // reaches the wall, estimated and then settled with the exact test
+        if (!inside(0)) {
+            s_end = 0;
+        } else {
+            float smax = (float)(p.nsamp - 1);
+            if (p.wall_y && ny_ != 0.0f)
+                smax = fminf(smax, floorf(2.0f * ((ny_ > 0.0f ? yhi : ylo) / ny_ + 1.0f)));
+            if (p.wall_z && nz_ != 0.0f)
+                smax = fminf(smax, floorf(2.0f * ((nz_ > 0.0f ? zhi : zlo) / nz_ + 1.0f)));
+            int s = max(0, (int)smax);
+            while (s + 1 < p.nsamp && inside(s + 1)) ++s;
+            while (s > 0 && !inside(s)) --s;
+            s_end = s + 1;
+        }
+    }
+    for (int s = s_end - 1; s >= 0; --s) {
         const float t = -1.0f + 0.5f * (float)s;
-        const float ox = t * nx_, oy = t * ny_, oz = t * nz_;
-        if (p.wall_y && !(oy >= ylo && oy <= yhi)) break;
-        if (p.wall_z && !(oz >= zlo && oz <= zhi)) break;
-        const int ix = ray_wrap(x + (int)floorf(ox), p.nx);
-        const int iy = ray_wrap(y + (int)floorf(oy), p.ny);   // identity on walled axes
-        const int iz = ray_wrap(z + (int)floorf(oz), p.nz);
+        const int ix = ray_wrap(x + (int)floorf(t * nx_), p.nx);
+        const int iy = ray_wrap(y + (int)floorf(t * ny_), p.ny);   // identity on walled axes
+        const int iz = ray_wrap(z + (int)floorf(t * nz_), p.nz);
         const int bx = ix >> 1;
         const uint32_t w = __ldg(p.nc_pos + ((iz >> 1) * p.nby + (iy >> 1)) * p.nbw + (bx >> 5));
-        mask |= ((w >> (bx & 31)) & 1u) << s;
+        if ((w >> (bx & 31)) & 1u) return s;
     }
-    return mask;
+    return -1;
 }
 
 // Trilinear sample of the lagged colour field at node (x, y, z) + offset o, for a
-// point known to lie inside the fluid (as nc_sample_mask established). The cell and
+// point known to lie inside the fluid (as nc_last_sample established). The cell and
 // the weights come from the offset alone (|o| is small), so the point is located to
 // the precision of o, not of x + o; on the last node of a walled axis (fraction 0)
 // the cell below is used with fraction 1, which gives that node's value.
@@ -370,33 +391,35 @@ __device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, i
     return (1.0f - fz) * c0 + fz * c1;
 }
 
-// Crossing search over the evaluated samples v[0 .. s_last] of one ray (stride
-// `stride` between consecutive samples) -> A_h of the film, 0 if none.
-__device__ __forceinline__ float nc_march(const StepParams& p, const float* v, int stride,
-                                          int s_last) {
+// Crossing search along one ray, fed its samples in order (t = -1, -1/2, ...):
+// feed() returns true once A_h is decided (in `a`); a ray whose samples run out
+// first has A_h = 0.
+struct NcMarch {
     float t_a = 0.0f, v_a = 0.0f, t_d = 0.0f;
     bool have_a = false, have_d = false;
-    for (int s = 0; s <= s_last; ++s) {
-        const float t = -1.0f + 0.5f * (float)s;
-        const float vs = v[s * stride];
-        if (fabsf(vs) <= kSignBand) continue;
+    __device__ __forceinline__ bool feed(const StepParams& p, float t, float vs, float& a) {
+        if (fabsf(vs) <= kSignBand) return false;
         if (have_a) {
             if (!have_d && v_a > 0.0f && vs < 0.0f) {
                 t_d = t_a + (t - t_a) * v_a / (v_a - vs);
                 have_d = true;
             } else if (have_d && v_a < 0.0f && vs > 0.0f) {
                 const float t_u = t_a + (t - t_a) * v_a / (v_a - vs);
-                return A_h(p, t_u - t_d);
+                a = A_h(p, t_u - t_d);
+                return true;
             }
         }
         // any upward crossing after this sample gives h >= h_cut, where A_h vanishes
-        if (have_d && t - t_d >= p.h_cut) return 0.0f;
+        if (have_d && t - t_d >= p.h_cut) {
+            a = 0.0f;
+            return true;
+        }
         t_a = t;
         v_a = vs;
         have_a = true;
+        return false;
     }
-    return 0.0f;
-}
+};
 
 // ---------------------------------------------------------------- collision
 // Pairwise (fixed-tree) sum of 19 values; every caller sums the same node's

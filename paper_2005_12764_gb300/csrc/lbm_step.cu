@@ -317,6 +317,19 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             if (keep) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) ft[i] = vr[i] + vb[i];
+                if (p.wall_u6 != 0.0f && (ylo || yhi)) {
+                    // sliding y-walls: a link back from a wall moving with (+-U, 0, 0)
+                    // gains 6 w_i rho c_ix (+-U) (the sum of the two species' shares
+                    // rho_k; these terms cancel in the densities)
+                    const float rho = rr + rb;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        if (cx(i) == 0) continue;
+                        const float m = wgt(i) * rho * (float)cx(i) * p.wall_u6;
+                        if (cy(i) > 0 && ylo) ft[i] -= m;   // from the wall at y = -1/2
+                        if (cy(i) < 0 && yhi) ft[i] += m;   // from the wall at y = ny - 1/2
+                    }
+                }
             }
         };
         auto slot = [](int z) { return (z + 4) & 3; };
@@ -651,24 +664,26 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 // scan kernel below compacts from every node. Every other entry of ah is 0.
 //
 // Warps take 32 candidates at a time from a shared counter (ray lengths vary
-// widely, so the work is handed out as it is done), in three phases:
-//  1. each lane classifies the samples of its own ray with the block bit field
-//     (independent, cheap lookups) and keeps the index of the last one that may be
-//     positive;
-//  2. the samples that must be evaluated (all samples up to that index, over the
-//     32 rays) are spread evenly over the lanes and interpolated into shared memory,
-//     so a few long rays do not hold the warp back;
-//  3. each lane runs the crossing search of its ray over those samples.
+// widely, so the work is handed out as it is done):
+//  1. each lane finds the last sample of its ray that may be positive (the bit
+//     field, scanned from the far end: in a bicontinuous mixture the first lookup
+//     usually settles it);
+//  2. in rounds of NC_CHUNK samples per ray, the samples the unfinished rays need
+//     next are spread evenly over the lanes and interpolated into shared memory, so
+//     a few long rays do not hold the warp back, and each lane feeds its ray's
+//     crossing search, which stops as soon as A_h is decided (in a fine mixture,
+//     after a few samples; along a droplet, at the last possibly positive one).
 // Before that, the kernel does the bookkeeping of the step kernel that follows it:
 // it zeroes that kernel's candidate counter and ray-bound bits and the next pass's
 // work counter, and writes the ghost copies of the step's input populations (work
 // that overlaps the rays instead of taking a launch of its own).
-constexpr int NC_THREADS = 256, NC_WARPS = NC_THREADS / 32;
+constexpr int NC_THREADS = 256, NC_WARPS = NC_THREADS / 32, NC_CHUNK = 8;
 
 template <class St>
 __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p) {
-    __shared__ float vals[NC_WARPS][kMaxSamples][32];   // [sample][ray]
-    __shared__ int rx[NC_WARPS][32], ry[NC_WARPS][32], rz[NC_WARPS][32], pre[NC_WARPS][33];
+    __shared__ float vals[NC_WARPS][NC_CHUNK][32];   // [sample of the round][ray]
+    __shared__ int rx[NC_WARPS][32], ry[NC_WARPS][32], rz[NC_WARPS][32], rs[NC_WARPS][32];
+    __shared__ int pre[NC_WARPS][33];
     __shared__ float rnx[NC_WARPS][32], rny[NC_WARPS][32], rnz[NC_WARPS][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -707,47 +722,60 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
             x = rem - y * p.nx;
             valid = nc_ray(__int_as_float(c.y), __int_as_float(c.z), __int_as_float(c.w), nx_,
                            ny_, nz_);
-            if (valid) {
-                const uint32_t m = nc_sample_mask(p, x, y, z, nx_, ny_, nz_);
-                s_last = 31 - __clz((int)m);   // -1 when no sample may be positive
-            }
+            if (valid) s_last = nc_last_sample(p, x, y, z, nx_, ny_, nz_);
         }
-        // phase 2: exclusive prefix of the sample counts over the warp
-        const int my = s_last + 1;
-        int incl = my;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        pre[wib][lane + 1] = incl;
-        if (lane == 0) pre[wib][0] = 0;
         rx[wib][lane] = x;
         ry[wib][lane] = y;
         rz[wib][lane] = z;
         rnx[wib][lane] = nx_;
         rny[wib][lane] = ny_;
         rnz[wib][lane] = nz_;
-        __syncwarp();
-        for (int task = lane; task < total; task += 32) {
-            // ray r: pre[r] <= task < pre[r + 1]
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (pre[wib][mid] <= task) lo = mid;
-                else hi = mid - 1;
+        NcMarch mr;
+        float a = 0.0f;
+        int s0 = 0;                      // next sample of this lane's ray
+        bool active = s_last >= 0;
+        while (__any_sync(0xffffffffu, active)) {
+            const int my = active ? min(NC_CHUNK, s_last + 1 - s0) : 0;
+            // exclusive prefix of the sample counts over the warp
+            int incl = my;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
             }
-            const int r = lo, sidx = task - pre[wib][r];
-            const float t = -1.0f + 0.5f * (float)sidx;
-            // inside the fluid: established in phase 1
-            vals[wib][sidx][r] = ray_sample(p, rx[wib][r], ry[wib][r], rz[wib][r], t * rnx[wib][r],
-                                            t * rny[wib][r], t * rnz[wib][r]);
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            pre[wib][lane + 1] = incl;
+            if (lane == 0) pre[wib][0] = 0;
+            rs[wib][lane] = s0;
+            __syncwarp();
+            for (int task = lane; task < total; task += 32) {
+                // ray r: pre[r] <= task < pre[r + 1]
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pre[wib][mid] <= task) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int r = lo, j = task - pre[wib][r];
+                const float t = -1.0f + 0.5f * (float)(rs[wib][r] + j);
+                // inside the fluid: established in phase 1
+                vals[wib][j][r] = ray_sample(p, rx[wib][r], ry[wib][r], rz[wib][r],
+                                             t * rnx[wib][r], t * rny[wib][r], t * rnz[wib][r]);
+            }
+            __syncwarp();
+            if (active) {
+                for (int j = 0; j < my; ++j) {
+                    if (mr.feed(p, -1.0f + 0.5f * (float)(s0 + j), vals[wib][j][lane], a)) {
+                        active = false;
+                        break;
+                    }
+                }
+                s0 += my;
+                if (s0 > s_last) active = false;
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        // phase 3
         if (valid) {
-            float a = nc_march(p, &vals[wib][0][lane], 32, s_last);
             if (p.pin_d2) {
                 const unsigned d2 = __ldg(p.pin_d2 + node);
                 if (d2 != 255u) a += A_h(p, sqrtf((float)d2));

@@ -207,6 +207,27 @@ def bicontinuous(L=640, amplitude=0.01, pin_fraction=0.02, seed=1005, sigma=0.01
                     steps=steps)
 
 
+def sheared_bijel(nx=1024, ny=128, nz=128, amplitude=0.01, wall_u=0.01, seed=1006,
+                  sigma=0.015, tau=0.8, beta=0.7, A_nc=0.02, h_min=3.0, steps=500_000):
+    """Confined bicontinuous mixture under shear (the sheared-bijel channel of the
+    paper's bijel section, 128 x 128 x 1024 with a periodic mainstream axis).
+
+    Layout here: x is the periodic mainstream axis (nx = 1024); the walls at the y
+    extremes slide with +-wall_u along x (shear 2 wall_u / ny); the walls at the z
+    extremes are at rest. Symmetric mixture with uniform colour noise,
+    phi0 ~ U(-amplitude, amplitude). The paper's colloids are not modelled; the
+    near-contact force stands in for what arrests the coarsening.
+    """
+    rng = np.random.default_rng(seed)
+    shape = (nz, ny, nx)
+    phi0 = rng.uniform(-amplitude, amplitude, size=shape)
+    rr = 0.5 * (1.0 + phi0)
+    rb = 0.5 * (1.0 - phi0)
+    params = dict(wall_y=1, wall_z=1, wall_u=wall_u, tau_r=tau, sigma=sigma, beta=beta,
+                  A_nc=A_nc, h_min=h_min)
+    return Workload(f"sheared-bijel-{nx}x{ny}x{nz}", shape, rr, rb, params, [], steps=steps)
+
+
 def random_state(shape, seed, amp=0.05, u_amp=0.02):
     """Smooth-ish random two-phase fields for unit tests: rho_k in (0.2, 1.2)-ish."""
     rng = np.random.default_rng(seed)

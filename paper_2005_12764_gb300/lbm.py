@@ -53,7 +53,8 @@ class Params(C.Structure):
                 ("tau_r", C.c_double), ("tau_b", C.c_double),
                 ("sigma", C.c_double), ("beta", C.c_double),
                 ("A_nc", C.c_double), ("h_min", C.c_double), ("h_cut", C.c_double),
-                ("g", C.c_double * 3), ("kolmogorov_amp", C.c_double), ("rho0", C.c_double),
+                ("g", C.c_double * 3), ("kolmogorov_amp", C.c_double), ("wall_u", C.c_double),
+                ("rho0", C.c_double),
                 ("storage", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
@@ -131,7 +132,7 @@ def velocity_set() -> np.ndarray:
 
 def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=0.0, beta=0.7,
                 A_nc=0.0, h_min=3.0, h_cut=None, g=(0.0, 0.0, 0.0), kolmogorov_amp=0.0, rho0=1.0,
-                storage="fp32", stream=None) -> Params:
+                storage="fp32", stream=None, wall_u=0.0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.wall_y, p.wall_z = int(wall_y), int(wall_z)
@@ -143,6 +144,7 @@ def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=
     for a in range(3):
         p.g[a] = float(g[a])
     p.kolmogorov_amp = float(kolmogorov_amp)
+    p.wall_u = float(wall_u)
     p.rho0 = float(rho0)
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.cuda_stream = stream

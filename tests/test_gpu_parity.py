@@ -111,6 +111,37 @@ def test_pinning_sites(lbm):
     assert_parity(fo, fg)
 
 
+def test_sliding_walls_sheared_droplets(lbm):
+    # two droplets between walls sliding with +-U along x (z walls at rest), near
+    # contact on, ragged tiles
+    shape = (14, 30, 50)
+    drops = [(14.0, 12.0, 7.0, 5.5), (27.0, 17.0, 6.5, 5.0)]
+    rr, rb = inputs.paint_droplets(shape, drops, periodic=(True, False, False))
+    kw = dict(wall_y=1, wall_z=1, wall_u=0.02, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0)
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, rb), 100, **kw)
+    assert_parity(fo, fg)
+
+
+def test_sliding_walls_couette_and_fp16(lbm):
+    # single-fluid Couette flow reaches the linear profile; FP16 deviation storage of
+    # a sheared two-layer state stays within 1e-3 of the oracle in rho
+    ny, U = 16, 0.01
+    shape = (4, ny, 8)
+    g = lbm.Lattice(lbm.make_params(8, ny, 4, wall_y=1, wall_u=U))
+    g.set_fields(np.ones(shape), np.zeros(shape))
+    g.step(4000)
+    want = U * (2 * (np.arange(ny) + 0.5) / ny - 1)
+    # FP32 arithmetic over 4000 steps: within 3e-5 of U (the FP64 oracle is exact)
+    assert np.abs(g.get_fields()["u"][0] - want[None, :, None]).max() < 3e-5 * U
+    g.close()
+    yy = np.arange(ny)[None, :, None] * np.ones(shape)
+    rr = np.where(yy < ny / 2, 1.0, 0.0)
+    kw = dict(wall_y=1, wall_u=U, sigma=0.01, beta=0.7)
+    fo, fg, _, _ = run_pair(lbm, shape, (rr, 1.0 - rr), 200, storage="fp16", **kw)
+    e = errs(fo, fg)
+    assert e["rho_r"] <= 1e-3 and e["rho_b"] <= 1e-3, e
+
+
 def test_near_contact_field_matches_oracle_on_dense_emulsion(lbm):
     # A dense emulsion has many films thinner than h_cut. The GPU measures A_h with a
     # bounded ray march (it stops after the last sample that may be positive); the
