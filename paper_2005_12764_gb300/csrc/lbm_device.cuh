@@ -305,7 +305,20 @@ __device__ __forceinline__ int ray_wrap(int b, int n) {
 // inside the fluid are s < s_end (the first sample outside stops the march), and
 // the bit field is scanned from s_end - 1 downwards. A sample on the last node of
 // a walled axis (fraction 0) is looked up in that node's block: its value is that
-// node's, whatever the other corner holds.
+// node's, whatever the other corner holds. (Starting the march at the first
+// possibly positive sample instead of t = -1 gives the same A_h, but finding that
+// sample by a forward scan costs more than the samples it saves.)
+__device__ __forceinline__ bool nc_sample_marked(const StepParams& p, int x, int y, int z,
+                                                 float nx_, float ny_, float nz_, int s) {
+    const float t = -1.0f + 0.5f * (float)s;
+    const int ix = ray_wrap(x + (int)floorf(t * nx_), p.nx);
+    const int iy = ray_wrap(y + (int)floorf(t * ny_), p.ny);   // identity on walled axes
+    const int iz = ray_wrap(z + (int)floorf(t * nz_), p.nz);
+    const int bx = ix >> 1;
+    const uint32_t w = __ldg(p.nc_pos + ((iz >> 1) * p.nby + (iy >> 1)) * p.nbw + (bx >> 5));
+    return (w >> (bx & 31)) & 1u;
+}
+
 __device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y, int z, float nx_,
                                               float ny_, float nz_) {
     int s_end = p.nsamp;
@@ -334,15 +347,8 @@ __device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y,
             s_end = s + 1;
         }
     }
-    for (int s = s_end - 1; s >= 0; --s) {
-        const float t = -1.0f + 0.5f * (float)s;
-        const int ix = ray_wrap(x + (int)floorf(t * nx_), p.nx);
-        const int iy = ray_wrap(y + (int)floorf(t * ny_), p.ny);   // identity on walled axes
-        const int iz = ray_wrap(z + (int)floorf(t * nz_), p.nz);
-        const int bx = ix >> 1;
-        const uint32_t w = __ldg(p.nc_pos + ((iz >> 1) * p.nby + (iy >> 1)) * p.nbw + (bx >> 5));
-        if ((w >> (bx & 31)) & 1u) return s;
-    }
+    for (int s = s_end - 1; s >= 0; --s)
+        if (nc_sample_marked(p, x, y, z, nx_, ny_, nz_, s)) return s;
     return -1;
 }
 
@@ -351,18 +357,30 @@ __device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y,
 // the weights come from the offset alone (|o| is small), so the point is located to
 // the precision of o, not of x + o; on the last node of a walled axis (fraction 0)
 // the cell below is used with fraction 1, which gives that node's value.
-__device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, int z, float ox,
-                                            float oy, float oz) {
+// Split into the cell (corner indices and fractions), its 8 corner values, and the
+// interpolation, so that a ray can keep the corners while it stays in one cell; the
+// interpolation fixes every rounding (no contraction left to the compiler), so a
+// sample has the same value however it is evaluated.
+struct RayCell {
+    int r00, r01, r10, r11;   // row offsets of the corners (z0 y0, z0 y1, z1 y0, z1 y1)
+    int ix0, ix1;
+    float fx, fy, fz;
+};
+__device__ __forceinline__ void ray_cell(const StepParams& p, int x, int y, int z, float ox,
+                                         float oy, float oz, RayCell& c) {
     const float flx = floorf(ox), fly = floorf(oy), flz = floorf(oz);
-    float fx = ox - flx, fy = oy - fly, fz = oz - flz;
+    c.fx = ox - flx;
+    c.fy = oy - fly;
+    c.fz = oz - flz;
     int ix0 = x + (int)flx, iy0 = y + (int)fly, iz0 = z + (int)flz;
-    int ix1, iy1, iz1;
+    int iy1, iz1;
     ix0 = ray_wrap(ix0, p.nx);
-    ix1 = ix0 + 1 == p.nx ? 0 : ix0 + 1;
+    c.ix0 = ix0;
+    c.ix1 = ix0 + 1 == p.nx ? 0 : ix0 + 1;
     if (p.wall_y) {
         if (iy0 == p.ny - 1) {
             iy0 = p.ny - 2;
-            fy = 1.0f;
+            c.fy = 1.0f;
         }
         iy1 = iy0 + 1;
     } else {
@@ -372,23 +390,44 @@ __device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, i
     if (p.wall_z) {
         if (iz0 == p.nz - 1) {
             iz0 = p.nz - 2;
-            fz = 1.0f;
+            c.fz = 1.0f;
         }
         iz1 = iz0 + 1;
     } else {
         iz0 = ray_wrap(iz0, p.nz);
         iz1 = iz0 + 1 == p.nz ? 0 : iz0 + 1;
     }
+    c.r00 = (iz0 * p.ny + iy0) * p.nx;
+    c.r01 = (iz0 * p.ny + iy1) * p.nx;
+    c.r10 = (iz1 * p.ny + iy0) * p.nx;
+    c.r11 = (iz1 * p.ny + iy1) * p.nx;
+}
+__device__ __forceinline__ void ray_corners(const StepParams& p, const RayCell& c, float (&v)[8]) {
     const float* f = p.phi_lag;
-    const int r00 = (iz0 * p.ny + iy0) * p.nx, r01 = (iz0 * p.ny + iy1) * p.nx;
-    const int r10 = (iz1 * p.ny + iy0) * p.nx, r11 = (iz1 * p.ny + iy1) * p.nx;
-    const float c00 = (1.0f - fx) * __ldg(f + r00 + ix0) + fx * __ldg(f + r00 + ix1);
-    const float c01 = (1.0f - fx) * __ldg(f + r01 + ix0) + fx * __ldg(f + r01 + ix1);
-    const float c10 = (1.0f - fx) * __ldg(f + r10 + ix0) + fx * __ldg(f + r10 + ix1);
-    const float c11 = (1.0f - fx) * __ldg(f + r11 + ix0) + fx * __ldg(f + r11 + ix1);
-    const float c0 = (1.0f - fy) * c00 + fy * c01;
-    const float c1 = (1.0f - fy) * c10 + fy * c11;
-    return (1.0f - fz) * c0 + fz * c1;
+    v[0] = __ldg(f + c.r00 + c.ix0);
+    v[1] = __ldg(f + c.r00 + c.ix1);
+    v[2] = __ldg(f + c.r01 + c.ix0);
+    v[3] = __ldg(f + c.r01 + c.ix1);
+    v[4] = __ldg(f + c.r10 + c.ix0);
+    v[5] = __ldg(f + c.r10 + c.ix1);
+    v[6] = __ldg(f + c.r11 + c.ix0);
+    v[7] = __ldg(f + c.r11 + c.ix1);
+}
+__device__ __forceinline__ float ray_lerp(float a, float b, float w) {
+    return __fmaf_rn(w, b, __fmul_rn(1.0f - w, a));   // (1 - w) a + w b
+}
+__device__ __forceinline__ float ray_interp(const RayCell& c, const float (&v)[8]) {
+    const float c0 = ray_lerp(ray_lerp(v[0], v[1], c.fx), ray_lerp(v[2], v[3], c.fx), c.fy);
+    const float c1 = ray_lerp(ray_lerp(v[4], v[5], c.fx), ray_lerp(v[6], v[7], c.fx), c.fy);
+    return ray_lerp(c0, c1, c.fz);
+}
+__device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, int z, float ox,
+                                            float oy, float oz) {
+    RayCell c;
+    ray_cell(p, x, y, z, ox, oy, oz, c);
+    float v[8];
+    ray_corners(p, c, v);
+    return ray_interp(c, v);
 }
 
 // Crossing search along one ray, fed its samples in order (t = -1, -1/2, ...):

@@ -668,11 +668,13 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 //  1. each lane finds the last sample of its ray that may be positive (the bit
 //     field, scanned from the far end: in a bicontinuous mixture the first lookup
 //     usually settles it);
-//  2. in rounds of NC_CHUNK samples per ray, the samples the unfinished rays need
-//     next are spread evenly over the lanes and interpolated into shared memory, so
-//     a few long rays do not hold the warp back, and each lane feeds its ray's
-//     crossing search, which stops as soon as A_h is decided (in a fine mixture,
-//     after a few samples; along a droplet, at the last possibly positive one).
+//  2. where at least half the rays of the warp need samples (a fine mixture), each
+//     lane marches its own ray and stops as soon as A_h is decided; otherwise, in
+//     rounds of NC_CHUNK samples per ray, the samples the unfinished rays need next
+//     are spread evenly over the lanes and interpolated into shared memory, so a
+//     few long rays do not hold the warp back, and each lane feeds its ray's
+//     crossing search (along a droplet, the march ends at the last possibly
+//     positive sample). Both evaluate every sample with the same arithmetic.
 // Before that, the kernel does the bookkeeping of the step kernel that follows it:
 // it zeroes that kernel's candidate counter and ray-bound bits and the next pass's
 // work counter, and writes the ghost copies of the step's input populations (work
@@ -734,6 +736,26 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
         float a = 0.0f;
         int s0 = 0;                      // next sample of this lane's ray
         bool active = s_last >= 0;
+        if (__popc(__ballot_sync(0xffffffffu, active)) >= 16) {
+            // most rays of the warp need samples (a fine mixture): each lane marches
+            // its own ray, keeping the cell corners while the ray stays in one cell
+            if (active) {
+                RayCell cell;
+                float v[8];
+                int key = -1;
+                for (int s = 0; s <= s_last; ++s) {
+                    const float t = -1.0f + 0.5f * (float)s;
+                    ray_cell(p, x, y, z, t * nx_, t * ny_, t * nz_, cell);
+                    const int kk = cell.r00 + cell.ix0;   // corner (ix0, iy0, iz0)
+                    if (kk != key) {
+                        ray_corners(p, cell, v);
+                        key = kk;
+                    }
+                    if (mr.feed(p, t, ray_interp(cell, v), a)) break;
+                }
+            }
+            active = false;
+        }
         while (__any_sync(0xffffffffu, active)) {
             const int my = active ? min(NC_CHUNK, s_last + 1 - s0) : 0;
             // exclusive prefix of the sample counts over the warp
