@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("sigma", C.c_double), ("beta", C.c_double),
                 ("A_nc", C.c_double), ("h_min", C.c_double), ("h_cut", C.c_double),
                 ("g", C.c_double * 3), ("kolmogorov_amp", C.c_double),
-                ("nc_lag", C.c_int), ("wall_u", C.c_double)]
+                ("nc_lag", C.c_int), ("wall_u", C.c_double),
+                ("model", C.c_int), ("G_sc", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -111,7 +112,7 @@ def _f64(a, shape=None):
 
 def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=0.0,
                 beta=0.7, A_nc=0.0, h_min=3.0, h_cut=None, g=(0.0, 0.0, 0.0),
-                kolmogorov_amp=0.0, nc_lag=1, wall_u=0.0) -> Params:
+                kolmogorov_amp=0.0, nc_lag=1, wall_u=0.0, model="colour", G_sc=0.0) -> Params:
     """Parameter block with the defaults of the method (h_cut = 2 h_min)."""
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -126,6 +127,8 @@ def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=
     p.kolmogorov_amp = float(kolmogorov_amp)
     p.nc_lag = int(nc_lag)
     p.wall_u = float(wall_u)
+    p.model = {"colour": 0, "shan_chen": 1}[model] if isinstance(model, str) else int(model)
+    p.G_sc = float(G_sc)
     return p
 
 

@@ -27,6 +27,10 @@
  *   7. recolouring of the two species                        reading: Latva-Kokko &
  *                                                            Rothman segregation
  *
+ * or, with model = 1, the Shan-Chen binary mixture of the same section: phases 3-7
+ * replaced by the cohesive force of Eq. (12) and a per-species BGK + EDM collision
+ * (Eqs. (5)-(9)); the near-contact force is not part of that model.
+ *
  * The only parallelism is an OpenMP "parallel for" over z-planes inside each phase;
  * each node is computed independently, so results do not depend on thread count.
  * Compile without fast-math and with -ffp-contract=off so x86 and Arm agree.
@@ -100,6 +104,8 @@ typedef struct {
     int nc_lag;            /* 1: near-contact ray reads phi of the previous step      */
     double wall_u;         /* sliding y-walls: the wall at y = ny - 1/2 moves with
                               (+wall_u, 0, 0), the one at y = -1/2 with (-wall_u, 0, 0) */
+    int model;             /* 0: colour gradient; 1: Shan-Chen (Eqs. (5)-(9), (12))   */
+    double G_sc;           /* Shan-Chen coupling G_C (> 0 repulsive)                 */
 } or_params;
 
 typedef struct {
@@ -225,6 +231,72 @@ void or_recolour(const double f[Q], double rho_r, double rho_b, double beta,
         }
         out_r[i] = (rho_r / rho) * f[i] + seg;
         out_b[i] = (rho_b / rho) * f[i] - seg;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Shan-Chen binary mixture (Sec. "Multi-component flows", Eqs. (5)-(9), (12)):
+ * each species relaxes by BGK at the mixture rate omega_eff towards f^eq(rho_k, u)
+ * with the common velocity u = j / rho, plus its own EDM source
+ * S^k = f^eq(rho_k, u + F^k/rho_k) - f^eq(rho_k, u), where F^k is the cohesive
+ * force of Eq. (12) plus the species' share (rho_k/rho) F_body of the body force.
+ * Reading of Eq. (12): the text makes G_C > 0 repulsive, which needs the sign of
+ * the usual Shan-Chen form, F^r(x) = -G_C rho_r(x) sum_i w_i rho_b(x + c_i) c_i
+ * (and F^b with the species swapped); the printed formula has no minus sign. A
+ * neighbour beyond a wall takes the node's own density (neutral wall, as for the
+ * colour gradient). The velocity shift F^k/rho_k is formed without dividing by
+ * rho_k, so a vanishing species stays exactly zero.                             */
+static void sc_shift_node(const or_params* p, const double* rho_r, const double* rho_b, long x,
+                          long y, long z, double sr[3], double sb[3]) {
+    double ar[3] = {0, 0, 0}, ab[3] = {0, 0, 0};   /* sum_i w_i rho_k(x + c_i) c_i */
+    long id = nidx(p, x, y, z);
+    for (int i = 0; i < Q; ++i) {
+        if (i == 0) continue;
+        long xs = x + CX[i], ys = y + CY[i], zs = z + CZ[i];
+        long nb = id;
+        if (!((p->wall_y && (ys < 0 || ys >= p->ny)) || (p->wall_z && (zs < 0 || zs >= p->nz))))
+            nb = nidx(p, wrap(xs, p->nx), wrap(ys, p->ny), wrap(zs, p->nz));
+        ar[0] += W[i] * rho_r[nb] * CX[i];
+        ar[1] += W[i] * rho_r[nb] * CY[i];
+        ar[2] += W[i] * rho_r[nb] * CZ[i];
+        ab[0] += W[i] * rho_b[nb] * CX[i];
+        ab[1] += W[i] * rho_b[nb] * CY[i];
+        ab[2] += W[i] * rho_b[nb] * CZ[i];
+    }
+    for (int a = 0; a < 3; ++a) {
+        sr[a] = -p->G_sc * ab[a];   /* F^r / rho_r */
+        sb[a] = -p->G_sc * ar[a];   /* F^b / rho_b */
+    }
+}
+
+/* Collision of one node in the Shan-Chen model: species densities rho_r, rho_b,
+ * their post-stream populations, the cohesive velocity shifts sr, sb (F^k/rho_k)
+ * and the body force Fb. Returns the total force in F.                         */
+static void sc_collide_node(const or_params* p, const double gr[Q], const double gb[Q],
+                            double rr, double rb, const double sr[3], const double sb[3],
+                            const double Fb[3], double out_r[Q], double out_b[Q], double F[3]) {
+    double rho = rr + rb, j[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i) {
+        j[0] += (gr[i] + gb[i]) * CX[i];
+        j[1] += (gr[i] + gb[i]) * CY[i];
+        j[2] += (gr[i] + gb[i]) * CZ[i];
+    }
+    double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+    double omega = or_omega_eff(rr, rb, p->tau_r, p->tau_b);
+    double ur[3], ub[3];
+    for (int a = 0; a < 3; ++a) {
+        ur[a] = u[a] + sr[a] + Fb[a] / rho;
+        ub[a] = u[a] + sb[a] + Fb[a] / rho;
+        F[a] = rr * sr[a] + rb * sb[a] + Fb[a];
+    }
+    double er0[Q], er1[Q], eb0[Q], eb1[Q];
+    or_feq(rr, u, er0);
+    or_feq(rr, ur, er1);
+    or_feq(rb, u, eb0);
+    or_feq(rb, ub, eb1);
+    for (int i = 0; i < Q; ++i) {
+        out_r[i] = (1.0 - omega) * gr[i] + omega * er0[i] + (er1[i] - er0[i]);
+        out_b[i] = (1.0 - omega) * gb[i] + omega * eb0[i] + (eb1[i] - eb0[i]);
     }
 }
 
@@ -632,6 +704,34 @@ void or_step(or_state* s, int nsteps) {
             s->jz[n] = j[2];
             s->phi[n] = (rr - rb) / (rr + rb);
         }
+        if (p->model == 1) {
+            /* Shan-Chen: 3'. cohesive forces from the densities of this step, and
+             * 5'. per-species BGK + EDM (no perturbation, no recolouring) */
+#pragma omp parallel for schedule(static)
+            for (long z = 0; z < p->nz; ++z)
+                for (long y = 0; y < p->ny; ++y)
+                    for (long x = 0; x < p->nx; ++x) {
+                        long id = nidx(p, x, y, z);
+                        double a[Q], b[Q], oa[Q], ob[Q], sr[3], sb[3], Fb[3], F[3];
+                        for (int i = 0; i < Q; ++i) {
+                            a[i] = s->gr[(long)i * N + id];
+                            b[i] = s->gb[(long)i * N + id];
+                        }
+                        sc_shift_node(p, s->rho_r, s->rho_b, x, y, z, sr, sb);
+                        body_force(p, y, Fb);
+                        sc_collide_node(p, a, b, s->rho_r[id], s->rho_b[id], sr, sb, Fb, oa, ob, F);
+                        s->Fx[id] = F[0];
+                        s->Fy[id] = F[1];
+                        s->Fz[id] = F[2];
+                        for (int i = 0; i < Q; ++i) {
+                            s->fr[(long)i * N + id] = oa[i];
+                            s->fb[(long)i * N + id] = ob[i];
+                        }
+                    }
+            memcpy(s->phi_lag, s->phi, sizeof(double) * N);
+            s->steps++;
+            continue;
+        }
         /* 3. colour gradient */
         or_gradient(p, s->phi, s->Gx, s->Gy, s->Gz);
         /* 4. forces */
@@ -751,9 +851,10 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
         }
         double phi0 = (rr - rb) / (rr + rb);
         double g[3] = {0, 0, 0};
+        double ar[3] = {0, 0, 0}, ab[3] = {0, 0, 0};   /* Shan-Chen density sums */
         for (int i = 1; i < Q; ++i) {
             long xs = x + CX[i], ys = y + CY[i], zs = z + CZ[i];
-            double v;
+            double v, nr = rr, nb = rb;
             if ((p->wall_y && (ys < 0 || ys >= p->ny)) || (p->wall_z && (zs < 0 || zs >= p->nz))) {
                 v = phi0;
             } else {
@@ -765,10 +866,30 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
                     sb += hb[m];
                 }
                 v = (sr - sb) / (sr + sb);
+                nr = sr;
+                nb = sb;
             }
             g[0] += W[i] * CX[i] * v;
             g[1] += W[i] * CY[i] * v;
             g[2] += W[i] * CZ[i] * v;
+            ar[0] += W[i] * nr * CX[i];
+            ar[1] += W[i] * nr * CY[i];
+            ar[2] += W[i] * nr * CZ[i];
+            ab[0] += W[i] * nb * CX[i];
+            ab[1] += W[i] * nb * CY[i];
+            ab[2] += W[i] * nb * CZ[i];
+        }
+        if (p->model == 1) {
+            double sr3[3], sb3[3], Fb[3], F[3];
+            for (int a = 0; a < 3; ++a) {
+                sr3[a] = -p->G_sc * ab[a];
+                sb3[a] = -p->G_sc * ar[a];
+            }
+            body_force(p, y, Fb);
+            sc_collide_node(p, gr, gb, rr, rb, sr3, sb3, Fb, out_r + k * Q, out_b + k * Q, F);
+            if (Fout)
+                for (int a = 0; a < 3; ++a) Fout[3 * k + a] = F[a];
+            continue;
         }
         double G[3] = {3.0 * g[0], 3.0 * g[1], 3.0 * g[2]};
         double Fb[3], Fn[3], F[3];
