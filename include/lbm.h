@@ -65,6 +65,16 @@ typedef enum {
     LBM_STORE_BF16_DEV = 2
 } lbm_storage;
 
+/* Binary-mixture model (Sec. "Multi-component flows"). LBM_MODEL_COLOUR: the
+ * colour-gradient model (BGK of the total population + EDM source, perturbation,
+ * recolouring, optional near-contact force). LBM_MODEL_SHAN_CHEN: each species
+ * relaxes at the mixture rate towards f^eq(rho_k, u), u = j/rho, with the EDM
+ * source of its own force F^k = -G_sc rho_k sum_i w_i rho_kbar(x + c_i) c_i
+ * (Eq. (12), with the sign that makes G_sc > 0 repulsive, as the text states) plus
+ * its share rho_k/rho of the body force; sigma, beta are unused and A_nc must be 0.
+ * A neighbour beyond a wall takes the node's own densities in either model.      */
+typedef enum { LBM_MODEL_COLOUR = 0, LBM_MODEL_SHAN_CHEN = 1 } lbm_model;
+
 typedef struct {
     int nx, ny, nz;          /* lattice size, each >= 1                                  */
     int wall_y, wall_z;      /* 1 = halfway bounce-back walls at y (z) = -1/2 and n-1/2;
@@ -89,6 +99,8 @@ typedef struct {
                                 wall gains 6 w_i rho c_i.u_w (moving-wall halfway
                                 bounce-back, rho the node's density). |wall_u| < 0.3.  */
     double rho0;             /* reference density of the FP16/BF16 deviation storage (1)  */
+    int model;               /* lbm_model: LBM_MODEL_COLOUR (default) or LBM_MODEL_SHAN_CHEN */
+    double G_sc;             /* Shan-Chen coupling G_C, > 0 repulsive (Shan-Chen model)    */
     int storage;             /* lbm_storage                                               */
     void* cuda_stream;       /* cudaStream_t to run on, or NULL                           */
 } lbm_params;
@@ -280,7 +292,8 @@ lbm_status lbm_engine_create(const lbm_engine_params* p, lbm_engine** out);
 
 /* Queues a request: a lattice with parameters p (p->cuda_stream is ignored) and
  * initial fields as for lbm_set_fields (host arrays, copied; u may be NULL), to be
- * advanced `steps` >= 1 steps. *ticket identifies it (> 0).                     */
+ * advanced `steps` >= 1 steps. *ticket identifies it (> 0). Requests use the
+ * colour-gradient model without near-contact force (LBM_EINVAL otherwise).      */
 lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, const double* rho_r,
                              const double* rho_b, const double* u, long long steps,
                              long long* ticket);

@@ -103,8 +103,8 @@ __device__ inline float ref_phi(const float* phi_cur, size_t n) {
 // two colour-field buffers exactly as the step did (have_force = 0 before a step).
 template <class St>
 __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int have_force,
-                                     const float* phi_now, double* rho_r, double* rho_b,
-                                     double* u, double* phi) {
+                                     const float* phi_now, const float* sc_rho, double* rho_r,
+                                     double* rho_b, double* u, double* phi) {
     const size_t N = sp.N, P = sp.P;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
@@ -137,6 +137,18 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
                 Fy += ah * Gy;
                 Fz += ah * Gz;
             }
+            if (sc_rho) {
+                // Shan-Chen cohesive forces of the last step, from its densities
+                // ([2][N]: red, blue): F^r + F^b = -(G/3)(rho_r S_b + rho_b S_r), S_k the
+                // stencil 3 sum_i w_i rho_k(x + c_i) c_i
+                float Sr[3], Sb[3];
+                gradient_global(sp, sc_rho, x, y, z, Sr[0], Sr[1], Sr[2]);
+                gradient_global(sp, sc_rho + N, x, y, z, Sb[0], Sb[1], Sb[2]);
+                const float g3 = -sp.G_sc * (1.0f / 3.0f);
+                Fx += rr * (g3 * Sb[0]) + rb * (g3 * Sr[0]);
+                Fy += rr * (g3 * Sb[1]) + rb * (g3 * Sr[1]);
+                Fz += rr * (g3 * Sb[2]) + rb * (g3 * Sr[2]);
+            }
         }
         const double rho = (double)rr + (double)rb;
         if (rho_r) rho_r[n] = rr;
@@ -147,6 +159,26 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
             u[2 * N + n] = ((double)jz - 0.5 * Fz) / rho;
         }
         if (phi) phi[n] = phi_now[n];
+    }
+}
+
+// Species densities of the stored state ([2][N] floats), summed as the export does.
+template <class St>
+__global__ void densities_kernel(const typename St::T* f, StepParams sp, const float* phi_now,
+                                 float* rho) {
+    const size_t N = sp.N, P = sp.P;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = node_pidx(sp, n);
+        const float ph = ref_phi<St>(phi_now, n);
+        float rr = 0.f, rb = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            rr += ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
+            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
+        }
+        rho[n] = rr;
+        rho[N + n] = rb;
     }
 }
 
@@ -410,6 +442,9 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->storage < 0 || p->storage > 2) { why = "unknown storage"; return LBM_EINVAL; }
     if (!(std::fabs(p->wall_u) < 0.3)) { why = "|wall_u| must be < 0.3"; return LBM_EINVAL; }
     if (p->wall_u != 0.0 && !p->wall_y) { why = "wall_u needs walls at the y extremes (wall_y)"; return LBM_EINVAL; }
+    if (p->model != 0 && p->model != 1) { why = "unknown model"; return LBM_EINVAL; }
+    if (p->model == 1 && p->A_nc != 0.0) { why = "the near-contact force belongs to the colour-gradient model"; return LBM_EINVAL; }
+    if (!std::isfinite(p->G_sc)) { why = "G_sc must be finite"; return LBM_EINVAL; }
     if ((p->storage != 0) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
@@ -448,6 +483,8 @@ static void fill_step_params(lbm_ctx* c) {
     s.gy = (float)p.g[1];
     s.gz = (float)p.g[2];
     s.wall_u6 = p.wall_y ? (float)(6.0 * p.wall_u) : 0.0f;
+    s.model = p.model;
+    s.G_sc = (float)p.G_sc;
     s.nx = p.nx;
     s.ny = p.ny;
     s.nz = p.nz;
@@ -932,11 +969,23 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
         s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
         CK(c, diag_pass(c, s));
     }
+    float* sc_rho = nullptr;
+    if (c->steps > 0 && c->p.model == 1 && u) {
+        // densities of the last step for its cohesive forces, in the scratch space
+        // after the staged fields (2N floats)
+        if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
+        sc_rho = reinterpret_cast<float*>(c->stage + 6 * N);
+        dispatch(c->p.storage, [&](auto st) {
+            using St = decltype(st);
+            densities_kernel<St><<<grid, kThreads, 0, c->stream>>>(
+                (const typename St::T*)c->f[c->cur], s, c->phi[c->pc], sc_rho);
+        });
+    }
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         export_fields_kernel<St><<<grid, kThreads, 0, c->stream>>>(
-            (const typename St::T*)c->f[c->cur], s, c->steps > 0 ? 1 : 0, c->phi[c->pc], dr, db,
-            du, dp);
+            (const typename St::T*)c->f[c->cur], s, c->steps > 0 ? 1 : 0, c->phi[c->pc], sc_rho,
+            dr, db, du, dp);
     });
     CK(c, cudaGetLastError());
     if (!on_device) {

@@ -122,6 +122,8 @@ struct StepParams {
     int nbx, nby, nbz, nbw; // block grid: ceil(n / 2) per axis; nbw = ceil(nbx / 32)
     float gy, gz;
     float wall_u6;          // 6 U of sliding y-walls (+U at y = ny-1/2, -U at y = -1/2), or 0
+    int model;              // 0: colour gradient; 1: Shan-Chen
+    float G_sc;             // Shan-Chen coupling G_C (> 0 repulsive)
     int nx, ny, nz;
     size_t N;               // nodes (fields phi, ah are [N], x fastest)
     // population arrays are padded: ghost columns and rows around the lattice (the
@@ -591,6 +593,84 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         const float hw = w * refh;
         emit(i, w * rr + ar * si, dev_ref(hw, phi, 0));
         emit(Q + i, w * rb + ab * si, dev_ref(hw, phi, 1));
+    }
+}
+
+// Shan-Chen collision of one node (the binary mixture of Eqs. (5)-(9), (12)) from
+// its post-stream species populations fr, fb, densities rr, rb, colour field phi
+// (for deviation storage), cohesive velocity shifts s_k = F^k/rho_k and body force
+// F: each species relaxes at the mixture rate towards f^eq(rho_k, u), u = j / rho,
+// and takes the EDM source of its own force F^k + (rho_k/rho) F:
+//   f^k'_i = f^eq_i(rho_k, U_k) + (1 - omega)(f^k_i - f^eq_i(rho_k, u)),
+//   U_k = u + s_k + F / rho.
+// Small-number form as in collide_store: f^eq_i(rho_k, U) = w_i rho_k +
+// w_i rho_k (3 c.U + 4.5 (c.U)^2 - 1.5 U^2), opposite directions sharing terms.
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void sc_collide_store(const StepParams& p, const float (&fr)[Q],
+                                                 const float (&fb)[Q], float rr, float rb,
+                                                 float phi, const float (&sr)[3],
+                                                 const float (&sb)[3], float Fx, float Fy,
+                                                 float Fz, const Emit& emit) {
+    const float rho = rr + rb;
+    const float inv_rho = __frcp_rn(rho);
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float d = (fr[i] + fb[i]) - (fr[opp(i)] + fb[opp(i)]);
+        if (cx(i)) jx += cx(i) > 0 ? d : -d;
+        if (cy(i)) jy += cy(i) > 0 ? d : -d;
+        if (cz(i)) jz += cz(i) > 0 ? d : -d;
+    }
+    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    float omega = p.omega0;
+    if (!UnitOmega && p.var_tau) {
+        const float inv_nu = (rr * p.inv_nu_r + rb * p.inv_nu_b) * inv_rho;
+        omega = 1.0f / (3.0f / inv_nu + 0.5f);
+    }
+    const float om1 = UnitOmega ? 0.0f : 1.0f - omega;
+    const float bx = Fx * inv_rho, by = Fy * inv_rho, bz = Fz * inv_rho;
+    const float Urx = ux + sr[0] + bx, Ury = uy + sr[1] + by, Urz = uz + sr[2] + bz;
+    const float Ubx = ux + sb[0] + bx, Uby = uy + sb[1] + by, Ubz = uz + sb[2] + bz;
+    const float Ur15 = 1.5f * (Urx * Urx + Ury * Ury + Urz * Urz);
+    const float Ub15 = 1.5f * (Ubx * Ubx + Uby * Uby + Ubz * Ubz);
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float refh = p.ref_half;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int o = opp(i);
+        const float wrr = wgt(i) * rr, wrb = wgt(i) * rb;
+        const float vr = (float)cx(i) * Urx + (float)cy(i) * Ury + (float)cz(i) * Urz;
+        const float vb = (float)cx(i) * Ubx + (float)cy(i) * Uby + (float)cz(i) * Ubz;
+        const float esr = wrr * (4.5f * vr * vr - Ur15), ear = wrr * (3.0f * vr);
+        const float esb = wrb * (4.5f * vb * vb - Ub15), eab = wrb * (3.0f * vb);
+        float ri = esr + ear, ro = esr - ear, bi = esb + eab, bo = esb - eab;
+        if (!UnitOmega) {
+            const float a = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+            const float q = 4.5f * a * a - usq15;
+            ri += om1 * ((fr[i] - wrr) - wrr * (q + 3.0f * a));
+            ro += om1 * ((fr[o] - wrr) - wrr * (q - 3.0f * a));
+            bi += om1 * ((fb[i] - wrb) - wrb * (q + 3.0f * a));
+            bo += om1 * ((fb[o] - wrb) - wrb * (q - 3.0f * a));
+        }
+        const float hw = wgt(i) * refh;
+        const float rf_r = dev_ref(hw, phi, 0), rf_b = dev_ref(hw, phi, 1);
+        emit(i, wrr + ri, rf_r);
+        emit(o, wrr + ro, rf_r);
+        emit(Q + i, wrb + bi, rf_b);
+        emit(Q + o, wrb + bo, rf_b);
+    }
+    {
+        constexpr int i = 9;
+        const float w = wgt(i);
+        const float wrr = w * rr, wrb = w * rb;
+        float ri = -wrr * Ur15, bi = -wrb * Ub15;
+        if (!UnitOmega) {
+            ri += om1 * ((fr[i] - wrr) + wrr * usq15);
+            bi += om1 * ((fb[i] - wrb) + wrb * usq15);
+        }
+        const float hw = w * refh;
+        emit(i, wrr + ri, dev_ref(hw, phi, 0));
+        emit(Q + i, wrb + bi, dev_ref(hw, phi, 1));
     }
 }
 

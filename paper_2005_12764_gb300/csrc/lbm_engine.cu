@@ -327,6 +327,7 @@ extern "C" lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, cons
     if (!p || !rho_r || !rho_b || !ticket) return efail(e, LBM_EINVAL, "p, rho_r, rho_b and ticket are required");
     if (steps < 1) return efail(e, LBM_EINVAL, "steps must be >= 1");
     if (p->A_nc > 0.0) return efail(e, LBM_EINVAL, "engine requests must have A_nc == 0");
+    if (p->model != 0) return efail(e, LBM_EINVAL, "engine requests use the colour-gradient model");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return efail(e, LBM_EINVAL, "nx, ny, nz must be >= 1");
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return efail(e, LBM_ENOMEM, "host allocation failed");

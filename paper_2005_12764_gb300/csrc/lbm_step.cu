@@ -52,7 +52,7 @@ constexpr int CTAS_PER_SM = 2;
 constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
 
-template <class St>
+template <class St, bool SC = false>
 struct Geo {
     using T = typename St::T;
     // interior offset in a padded row: 32 bytes, so that each row's two x ghosts
@@ -66,7 +66,9 @@ struct Geo {
     static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
     static constexpr size_t STAGE_BYTES = (size_t)2 * Q * IK_BYTES;
-    static constexpr size_t PHI_BYTES = 4 * SH * SWP * sizeof(float);
+    // 4-slot ring per plane (tile + ring nodes): the colour field, or for the
+    // Shan-Chen model the two species densities
+    static constexpr size_t PHI_BYTES = (SC ? 2 : 1) * 4 * SH * SWP * sizeof(float);
     // deviation storage: 4-slot ring of the lagged colour field, (TX+4) x (TY+4) per
     // plane (the sources of the tile and its ring), which decodes the pulled values
     static constexpr bool DEV = St::kind != 0;
@@ -155,11 +157,11 @@ __device__ __forceinline__ void grid_dep_launch() {
 // Body of the step kernel for CTA `cta` of one lattice's grid: the single-lattice
 // kernel passes its parameters and tensor maps (kernel parameter space), the
 // batched kernel those of the lattice the CTA belongs to.
-template <class St, bool UnitOmega>
+template <class St, bool UnitOmega, bool SC = false>
 __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap* fin_map,
                                           const CUtensorMap* fout_map, const int cta) {
     using T = typename St::T;
-    using G = Geo<St>;
+    using G = Geo<St, SC>;
     constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, HALO = G::HALO, STAGES = G::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
@@ -273,18 +275,16 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         auto lag_at = [&](int sl, int tx, int ty) -> float& {
             return slag[(sl * G::LH + ty + 2) * G::LW + tx + 2];
         };
-        // ---- pull of node (tx, ty) of plane pl (wrapped; sc = lag-ring slot of the
-        // unwrapped plane) from staged buffer b; returns densities, and for keep == true
-        // also the total populations. Deviation storage decodes every value against
-        // the colour field its source node had when it wrote it.
-        auto pull = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
-                        float& rb, bool keep) {
+        // ---- pull of the two species' populations of node (tx, ty) of plane pl
+        // (wrapped; sc = lag-ring slot of the unwrapped plane) from staged buffer b, and
+        // their densities; wall_terms adds the sliding-wall terms per species.
+        auto pull_species = [&](int b, int pl, int sc, int tx, int ty, float (&vr)[Q],
+                                float (&vb)[Q], float& rr, float& rb, bool wall_terms) {
             const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + HALO);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
             const bool any_wall = ylo || yhi || zlo || zhi;
-            float vr[Q], vb[Q];
             const float refh = p.ref_half;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -314,7 +314,35 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             }
             rr = sum19(vr);
             rb = sum19(vb);
+            if (wall_terms && p.wall_u6 != 0.0f && (ylo || yhi)) {
+                // sliding y-walls, per species: a link back from a wall moving with
+                // (+-U, 0, 0) gains 6 w_i rho_k c_ix (+-U) (these cancel in rho_k)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if (cx(i) == 0) continue;
+                    const float m = wgt(i) * (float)cx(i) * p.wall_u6;
+                    if (cy(i) > 0 && ylo) {
+                        vr[i] -= m * rr;
+                        vb[i] -= m * rb;
+                    }
+                    if (cy(i) < 0 && yhi) {
+                        vr[i] += m * rr;
+                        vb[i] += m * rb;
+                    }
+                }
+            }
+        };
+        // pull of node (tx, ty) of plane pl (wrapped; sc = lag-ring slot of the
+        // unwrapped plane) from staged buffer b; returns densities, and for keep ==
+        // true also the total populations. Deviation storage decodes every value
+        // against the colour field its source node had when it wrote it.
+        auto pull = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
+                        float& rb, bool keep) {
+            float vr[Q], vb[Q];
+            pull_species(b, pl, sc, tx, ty, vr, vb, rr, rb, false);
             if (keep) {
+                const int gy = y0 + ty;
+                const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) ft[i] = vr[i] + vb[i];
                 if (p.wall_u6 != 0.0f && (ylo || yhi)) {
@@ -381,6 +409,103 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         const size_t col = (size_t)gyn * p.nx + gxn;   // owned column (unpadded fields)
         const float fx_y = owned ? __ldg(p.fx_row + gyn) : 0.0f;
         const bool ylo = p.wall_y && gyn == 0, yhi = p.wall_y && gyn == p.ny - 1;
+
+        if constexpr (SC) {
+            // ---- Shan-Chen model. The ring holds the species densities of planes
+            // z-1, z (and z+1 once pulled); the cohesive force of plane z needs those
+            // of its 18 neighbours. Each species' populations are kept only for the
+            // plane being collided: at the start of plane z the staged buffer holds
+            // plane z; its owned populations are pulled, the buffer is refilled with
+            // plane z+1, whose densities (tile + ring) complete the ring, and plane z
+            // is collided. (Plane z+1 is pulled once more, whole, in its own turn.)
+            auto rho_at = [&](int k, int sl, int tx, int ty) -> float& {
+                return sphi[((k * 4 + sl) * SH + ty + 1) * SWP + tx + 1];
+            };
+            auto sc_densities = [&](int b, int pl) {
+                const bool pvalid = !p.wall_z || (pl >= 0 && pl < p.nz);
+                if (!pvalid) return;
+                const int plw = wrap_near(pl, p.nz);
+                float vr[Q], vb[Q], a, c;
+                if (owned) {
+                    pull_species(b, plw, slot(pl), otx, oty, vr, vb, a, c, false);
+                    rho_at(0, slot(pl), otx, oty) = a;
+                    rho_at(1, slot(pl), otx, oty) = c;
+                }
+                if (ring) {
+                    pull_species(b, plw, slot(pl), rtx, rty, vr, vb, a, c, false);
+                    rho_at(0, slot(pl), rtx, rty) = a;
+                    rho_at(1, slot(pl), rtx, rty) = c;
+                }
+            };
+            // prologue: densities of planes zb-1 and zb; lag planes zb-2 .. zb+1
+            if (G::DEV) {
+                for (int q = -2; q <= 1; ++q) {
+                    lag_fetch(zb + q);
+                    lag_commit(zb + q);
+                }
+                lag_fetch(zb + 2);
+                __syncthreads();
+            }
+            fence_proxy_async();
+            issue(0, zb - 1);
+            wait(0);
+            sc_densities(0, zb - 1);
+            __syncthreads();
+            fence_proxy_async();
+            issue(0, zb);
+            wait(0);
+            sc_densities(0, zb);
+            __syncthreads();
+            const float g3 = -p.G_sc * (1.0f / 3.0f);
+            for (int z = zb; z < ze; ++z) {
+                // lag plane z+2 goes to the slot of z-2, last read in the previous plane
+                if (G::DEV) lag_commit(z + 2);
+                float vr[Q], vb[Q], rr = 0.f, rb = 0.f;
+                if (owned && !failed) pull_species(0, z, slot(z), otx, oty, vr, vb, rr, rb, true);
+                if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
+                __syncthreads();                  // staged plane z consumed
+                fence_proxy_async();
+                issue(0, z + 1);
+                if (G::DEV) lag_fetch(z + 3);
+                wait(0);
+                sc_densities(0, z + 1);
+                __syncthreads();                  // densities of plane z+1 in the ring
+                if (owned && !failed) {
+                    const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
+                    const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
+                    // 3 sum_i w_i rho_k(x + c_i) c_i, a neighbour beyond a wall taking
+                    // the node's own density
+                    float ar[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        if (i == 9) continue;
+                        const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
+                                          (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
+                        const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
+                        const float nr = wall ? rr : rho_at(0, sl, otx + cx(i), oty + cy(i));
+                        const float nb = wall ? rb : rho_at(1, sl, otx + cx(i), oty + cy(i));
+                        grad_add(i, nr, ar[0], ar[1], ar[2]);
+                        grad_add(i, nb, ab[0], ab[1], ab[2]);
+                    }
+                    // cohesive velocity shifts F^k / rho_k = -G sum_i w_i rho_kbar c_i
+                    const float sr[3] = {g3 * ab[0], g3 * ab[1], g3 * ab[2]};
+                    const float sb[3] = {g3 * ar[0], g3 * ar[1], g3 * ar[2]};
+                    const float phic = colour(rr, rb);
+                    const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
+                    sc_collide_store<St, UnitOmega>(p, vr, vb, rr, rb, phic, sr, sb, fx_y, p.gy,
+                                                    p.gz, em);
+                    p.phi_out[(size_t)z * plane + col] = phic;
+                }
+                fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    for (int k = 0; k < 2 * Q; ++k)
+                        tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
+                    bulk_commit();
+                }
+            }
+            continue;
+        }
 
         // one plane of the march: densities of plane z+1 into (nx_f, nx_rr, nx_rb), then
         // the collision of plane z from (cu, cu_rr, cu_rb); A_h is carried in ah_c
@@ -530,11 +655,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
     }
 }
 
-template <class St, bool UnitOmega>
+template <class St, bool UnitOmega, bool SC>
 __global__ void __launch_bounds__(NT, CTAS_PER_SM)
 step_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap fin_map,
             const __grid_constant__ CUtensorMap fout_map) {
-    step_body<St, UnitOmega>(p, &fin_map, &fout_map, (int)blockIdx.x);
+    step_body<St, UnitOmega, SC>(p, &fin_map, &fout_map, (int)blockIdx.x);
 }
 
 // Several lattices in one launch: CTA b belongs to the last lattice whose first CTA
@@ -946,18 +1071,19 @@ cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, 
     return cudaErrorInvalidValue;
 }
 
-template <class St, bool U>
-static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map,
+template <class St, bool U, bool SC>
+static cudaError_t launch_tpl3(const StepParams& p, const CUtensorMap& map,
                                const CUtensorMap& omap, int grid, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<St, U>,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<St, U, SC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Geo<St>::SMEM);
+                                             (int)Geo<St, SC>::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    return pdl_launch(step_kernel<St, U>, (unsigned)grid, NT, Geo<St>::SMEM, s, p, map, omap);
+    return pdl_launch(step_kernel<St, U, SC>, (unsigned)grid, NT, Geo<St, SC>::SMEM, s, p, map,
+                      omap);
 }
 
 // omega == 1 everywhere (equal relaxation times tau = 1) drops the non-equilibrium
@@ -965,8 +1091,12 @@ static cudaError_t launch_tpl2(const StepParams& p, const CUtensorMap& map,
 template <class St>
 static cudaError_t launch_tpl(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
                               int grid, cudaStream_t s) {
-    if (!p.var_tau && p.omega0 == 1.0f) return launch_tpl2<St, true>(p, map, omap, grid, s);
-    return launch_tpl2<St, false>(p, map, omap, grid, s);
+    const bool unit = !p.var_tau && p.omega0 == 1.0f;
+    if (p.model == 1)
+        return unit ? launch_tpl3<St, true, true>(p, map, omap, grid, s)
+                    : launch_tpl3<St, false, true>(p, map, omap, grid, s);
+    return unit ? launch_tpl3<St, true, false>(p, map, omap, grid, s)
+                : launch_tpl3<St, false, false>(p, map, omap, grid, s);
 }
 
 cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,

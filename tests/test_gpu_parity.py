@@ -142,6 +142,41 @@ def test_sliding_walls_couette_and_fp16(lbm):
     assert e["rho_r"] <= 1e-3 and e["rho_b"] <= 1e-3, e
 
 
+def _sc_pair(lbm, shape, drops, steps, storage="fp32", periodic=(True, True, True), **kw):
+    rr, rb = inputs.paint_droplets(shape, drops, periodic=periodic)
+    # a little of each species everywhere, as in a separated Shan-Chen mixture
+    rr, rb = 0.96 * rr + 0.02, 0.96 * rb + 0.02
+    return run_pair(lbm, shape, (rr, rb), steps, storage=storage, model="shan_chen", **kw)
+
+
+def test_shan_chen_droplet_periodic(lbm):
+    fo, fg, _, _ = _sc_pair(lbm, (32, 32, 32), [(16.0, 16.0, 16.0, 8.0)], 100, G_sc=1.6)
+    assert_parity(fo, fg)
+
+
+def test_shan_chen_walls_sliding_forces_unequal_tau(lbm):
+    # ragged tiles, walls in y (sliding) and z, body force, unequal relaxation times
+    shape = (14, 30, 50)
+    drops = [(14.0, 12.0, 7.0, 5.5), (31.0, 17.0, 6.5, 5.0)]
+    fo, fg, _, _ = _sc_pair(lbm, shape, drops, 100, periodic=(True, False, False), G_sc=1.4,
+                            wall_y=1, wall_z=1, wall_u=0.01, tau_r=0.9, tau_b=1.2,
+                            g=(2e-5, 0, 1e-5))
+    assert_parity(fo, fg)
+
+
+def test_shan_chen_chain_mode_and_fp16(lbm):
+    # 72 x 44 x 140 runs the step kernel in chain mode (CTAs crossing tiles)
+    shape = (140, 44, 72)
+    drops = [(20.0, 12.0, 30.0, 6.0), (50.0, 30.0, 70.0, 7.0), (60.0, 14.0, 110.0, 8.0)]
+    fo, fg, _, _ = _sc_pair(lbm, shape, drops, 20, periodic=(True, False, False), G_sc=1.5,
+                            wall_y=1, wall_z=1)
+    assert_parity(fo, fg)
+    fo, fg, _, _ = _sc_pair(lbm, (24, 24, 24), [(12.0, 12.0, 12.0, 6.0)], 100, storage="fp16",
+                            G_sc=1.6)
+    e = errs(fo, fg)
+    assert e["rho_r"] <= 1e-3 and e["rho_b"] <= 1e-3, e
+
+
 def test_near_contact_field_matches_oracle_on_dense_emulsion(lbm):
     # A dense emulsion has many films thinner than h_cut. The GPU measures A_h with a
     # bounded ray march (it stops after the last sample that may be positive); the
@@ -328,7 +363,8 @@ def test_window_matches_full_download_with_wrap(lbm):
 
 
 def test_invalid_arguments_are_rejected(lbm):
-    for bad in (dict(tau_r=0.5), dict(beta=1.5), dict(storage=7)):
+    for bad in (dict(tau_r=0.5), dict(beta=1.5), dict(storage=7), dict(wall_u=0.01),
+                dict(model=5), dict(model="shan_chen", A_nc=0.01), dict(wall_y=1, wall_u=0.5)):
         kw = dict(tau_r=1.0)
         kw.update(bad)
         with pytest.raises(lbm.LbmError) as ei:

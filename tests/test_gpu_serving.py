@@ -146,3 +146,12 @@ def test_shortest_job_first_admission(lbm):
         order.append(done)
     assert order[0] == [0, 1, 2, 3]          # first come, first served
     assert order[1] == [1, 2, 3, 0]          # shortest (fewest node-steps) first
+
+
+def test_engine_refuses_other_models(lbm):
+    e = lbm.Engine(budget_bytes=1 << 30, max_slots=2)
+    p = lbm.make_params(16, 16, 16, model="shan_chen", G_sc=1.5)
+    rr = np.ones((16, 16, 16))
+    with pytest.raises(lbm.LbmError):
+        e.submit(p, rr, 0 * rr, 5)
+    e.close()
