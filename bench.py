@@ -6,7 +6,7 @@ bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigm
 One step = one lattice update of every node (one launch of the fused kernel).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16]
-                  [--impl ours|reference] [--no-serving] [--no-cpu-baseline]
+                  [--impl ours|reference] [--no-serving] [--no-models] [--no-cpu-baseline]
 
 Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second)
 over all ranks; ``e2e`` times the same job through the public C-ABI with host
@@ -16,7 +16,9 @@ per node, read once and written once) to the measured HBM bandwidth;
 ``fp16_store`` repeats the device-resident measurement with FP16 deviation
 storage; ``serving`` runs the served request stream (256 droplet / sheared-droplet
 runs of edge 32-128, Poisson arrivals at 50/s, FP16 storage) through the serving
-engine and reports p50/p99 latency beside aggregate GLUPS; ``cpu_baseline`` times
+engine and reports p50/p99 latency beside aggregate GLUPS; ``shan_chen`` and
+``sheared_bijel`` give the device-resident GLUPS of the Shan-Chen model on the same
+channel and of the sheared-bijel channel with sliding walls; ``cpu_baseline`` times
 the FP64 oracle on the host cores. ``--impl reference`` times the oracle itself on
 the same workload (the method has no other reference implementation). Multi-GPU
 runs are independent replicas: one channel lattice per rank, the request stream
@@ -224,6 +226,51 @@ def serving_run(lbm, rank, world, dist, local):
             "engine": {k: rep["engine"][k] for k in ("ticks", "peak_bytes", "planes_per_cta")}}
 
 
+def other_workloads(lbm, stream, local, steps=200):
+    """Device-resident GLUPS of two more workloads of the same step: the Shan-Chen
+    model on the channel geometry, and the sheared-bijel channel (1024 x 128 x 128,
+    sliding walls, near contact on) after 300 steps of coarsening from the quench."""
+    import torch
+    from paper_2005_12764_gb300 import inputs
+    out = {}
+
+    def timed(lat, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(k)
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / k
+
+    w = inputs.channel_droplets()
+    nz, ny, nx = w.shape
+    lat = lbm.Lattice(lbm.make_params(nx, ny, nz, wall_y=1, wall_z=1, tau_r=1.0, g=(1e-6, 0, 0),
+                                      model="shan_chen", G_sc=1.6, stream=stream.cuda_stream))
+    lat.set_fields(0.96 * w.rho_r + 0.02, 0.96 * w.rho_b + 0.02)
+    lat.step(10)
+    ms = timed(lat, steps)
+    _, k_ms, _ = lat.step_timed(20)
+    lat.close()
+    out["shan_chen"] = {"workload": "channel 256x128x64, 40 droplets, walls y/z, G_sc = 1.6, FP32",
+                        "value": nx * ny * nz / (ms * 1e-3) / 1e9, "unit": "GLUPS",
+                        "ms_per_step": ms, "kernel_ms": k_ms / 20}
+    w = inputs.sheared_bijel()
+    nz, ny, nx = w.shape
+    lat = lbm.Lattice(lbm.make_params(nx, ny, nz, stream=stream.cuda_stream, **w.params))
+    lat.set_fields(torch.from_numpy(w.rho_r).to(f"cuda:{local}"),
+                   torch.from_numpy(w.rho_b).to(f"cuda:{local}"))
+    lat.step(300)
+    ms = timed(lat, 50)
+    nc_ms, k_ms, _ = lat.step_timed(10)
+    lat.close()
+    out["sheared_bijel"] = {"workload": "1024x128x128, walls y (sliding +-0.01) and z, "
+                                        "quench noise 0.01, NC on, FP32, after 300 steps",
+                            "value": nx * ny * nz / (ms * 1e-3) / 1e9, "unit": "GLUPS",
+                            "ms_per_step": ms, "kernel_ms": k_ms / 10,
+                            "near_contact_pass_ms": nc_ms / 10}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -271,10 +318,9 @@ def run_ours(args):
     glups = world * N * args.steps / (total_ms * 1e-3) / 1e9
     # per-kernel durations (events around each launch, inside the library)
     kt = max(5, min(args.steps, 50))
-    nc_ms, step_ms, ghost_ms = lat.step_timed(kt)
+    nc_ms, step_ms, _ = lat.step_timed(kt)
     kern_ms = [step_ms / kt]
     nc_avg_ms = nc_ms / kt
-    ghost_avg_ms = ghost_ms / kt
     # ---- end to end through the public API with pinned host buffers
     host_rr = torch.from_numpy(w.rho_r).pin_memory()
     host_rb = torch.from_numpy(w.rho_b).pin_memory()
@@ -314,6 +360,9 @@ def run_ours(args):
         fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
                 "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
                 "algorithmic_bytes_per_launch": alg16}
+    others = None
+    if not args.no_models:
+        others = other_workloads(lbm, stream, local)
     serving_rep = None
     if not args.no_serving:
         serving_rep = serving_run(lbm, rank, world, dist if world > 1 else None, local)
@@ -343,7 +392,7 @@ def run_ours(args):
                          "kernel": "step_kernel (fused stream/collide/perturb/recolour)",
                          "kernel_ms": statistics.mean(kern_ms),
                          "near_contact_pass_ms": nc_avg_ms,
-                         "ghost_fill_ms": ghost_avg_ms,
+                         "ghost_fill": "written by the near-contact pass (no launch of its own)",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "gpu_launches": launches,
             "clocks": clk.summary(),
@@ -351,6 +400,8 @@ def run_ours(args):
         }
         if fp16:
             line["fp16_store"] = fp16
+        if others:
+            line.update(others)
         if serving_rep:
             line["serving"] = serving_rep
         if cpu:
@@ -370,6 +421,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-models", action="store_true",
+                    help="skip the Shan-Chen and sheared-bijel lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
