@@ -6,7 +6,8 @@ bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigm
 One step = one lattice update of every node (one launch of the fused kernel).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16]
-                  [--impl ours|reference] [--no-serving] [--no-models] [--no-cpu-baseline]
+                  [--impl ours|reference] [--model colour|shan_chen] [--no-serving]
+                  [--no-models] [--no-cpu-baseline]
 
 Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second)
 over all ranks; ``e2e`` times the same job through the public C-ABI with host
@@ -136,6 +137,21 @@ def dist_env():
     return rank, world, local
 
 
+def bench_workload(args):
+    """The timed workload: the channel, with the colour-gradient model (default) or the
+    Shan-Chen model (--model shan_chen)."""
+    from paper_2005_12764_gb300 import inputs
+    if args.model == "shan_chen":
+        return inputs.channel_shan_chen()
+    return inputs.channel_droplets()
+
+
+def workload_name(args):
+    if args.model == "shan_chen":
+        return "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, Shan-Chen G_sc = 1.6"
+    return WORKLOAD
+
+
 def cpu_oracle_rate(workload, steps, warm=1):
     """Oracle lattice updates per second on this host (all cores) over `steps` steps."""
     import oracle
@@ -155,8 +171,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2005_12764_gb300 import inputs
-    w = inputs.channel_droplets()
+    w = bench_workload(args)
     N = w.rho_r.size
     import oracle
     nz, ny, nx = w.shape
@@ -172,7 +187,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": N, "storage": "f64 (oracle)"},
+            "config": {"workload": workload_name(args), "nodes": N, "storage": "f64 (oracle)"},
             "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full steps of the {nx}x{ny}x{nz} channel"},
             "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
@@ -242,11 +257,10 @@ def other_workloads(lbm, stream, local, steps=200):
         stream.synchronize()
         return a.elapsed_time(b) / k
 
-    w = inputs.channel_droplets()
+    w = inputs.channel_shan_chen()
     nz, ny, nx = w.shape
-    lat = lbm.Lattice(lbm.make_params(nx, ny, nz, wall_y=1, wall_z=1, tau_r=1.0, g=(1e-6, 0, 0),
-                                      model="shan_chen", G_sc=1.6, stream=stream.cuda_stream))
-    lat.set_fields(0.96 * w.rho_r + 0.02, 0.96 * w.rho_b + 0.02)
+    lat = lbm.Lattice(lbm.make_params(nx, ny, nz, stream=stream.cuda_stream, **w.params))
+    lat.set_fields(w.rho_r, w.rho_b)
     lat.step(10)
     ms = timed(lat, steps)
     _, k_ms, _ = lat.step_timed(20)
@@ -283,7 +297,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build_lib.build()
-    w = inputs.channel_droplets()
+    w = bench_workload(args)
     nz, ny, nx = w.shape
     N = nx * ny * nz
     stream = torch.cuda.Stream()
@@ -379,7 +393,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": N, "storage": args.storage,
+            "config": {"workload": workload_name(args), "nodes": N, "storage": args.storage,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
                              % (2 * Q * C * elem * N / 2 / 1e6)},
@@ -421,6 +435,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--model", default="colour", choices=["colour", "shan_chen"],
+                    help="model of the timed workload (default: the colour-gradient channel)")
     ap.add_argument("--no-models", action="store_true",
                     help="skip the Shan-Chen and sheared-bijel lines")
     args = ap.parse_args()

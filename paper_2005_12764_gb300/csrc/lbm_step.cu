@@ -437,31 +437,24 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                     rho_at(1, slot(pl), rtx, rty) = c;
                 }
             };
-            // prologue: densities of planes zb-1 and zb; lag planes zb-2 .. zb+1
+            // the march starts at plane zb-2: its first two turns only fill the ring with
+            // the densities of zb-1 and zb (one copy of the pull code for the segment);
+            // lag planes zb-2, zb-1 first, then each turn z stores lag plane z+2
             if (G::DEV) {
-                for (int q = -2; q <= 1; ++q) {
+                for (int q = -2; q <= -1; ++q) {
                     lag_fetch(zb + q);
                     lag_commit(zb + q);
                 }
-                lag_fetch(zb + 2);
+                lag_fetch(zb);
                 __syncthreads();
             }
-            fence_proxy_async();
-            issue(0, zb - 1);
-            wait(0);
-            sc_densities(0, zb - 1);
-            __syncthreads();
-            fence_proxy_async();
-            issue(0, zb);
-            wait(0);
-            sc_densities(0, zb);
-            __syncthreads();
             const float g3 = -p.G_sc * (1.0f / 3.0f);
-            for (int z = zb; z < ze; ++z) {
+            for (int z = zb - 2; z < ze; ++z) {
                 // lag plane z+2 goes to the slot of z-2, last read in the previous plane
                 if (G::DEV) lag_commit(z + 2);
                 float vr[Q], vb[Q], rr = 0.f, rb = 0.f;
-                if (owned && !failed) pull_species(0, z, slot(z), otx, oty, vr, vb, rr, rb, true);
+                if (z >= zb && owned && !failed)
+                    pull_species(0, z, slot(z), otx, oty, vr, vb, rr, rb, true);
                 if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
                 __syncthreads();                  // staged plane z consumed
                 fence_proxy_async();
@@ -470,6 +463,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 wait(0);
                 sc_densities(0, z + 1);
                 __syncthreads();                  // densities of plane z+1 in the ring
+                if (z < zb) continue;
                 if (owned && !failed) {
                     const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
                     const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
@@ -509,13 +503,16 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
 
         // one plane of the march: densities of plane z+1 into (nx_f, nx_rr, nx_rb), then
         // the collision of plane z from (cu, cu_rr, cu_rb); A_h is carried in ah_c
+        // (planes zb-2 and zb-1 only fill the ring: the march starts there, so that one
+        // copy of the pull code serves the whole segment)
         auto march = [&](int z, float (&cu)[Q], float cu_rr, float cu_rb, float (&nx_f)[Q],
                          float& nx_rr, float& nx_rb, float& ah_c) {
             // plane z+1 is in the staging buffer (issued after the previous barrier);
             // plane z+2 is issued right after this plane's barrier frees the buffer
             const int bn = 0;
-            const float ah_nxt =
-                (owned && use_nc && z + 1 < ze) ? p.ah[(size_t)(z + 1) * plane + col] : 0.0f;
+            const float ah_nxt = (owned && use_nc && z + 1 >= zb && z + 1 < ze)
+                                     ? p.ah[(size_t)(z + 1) * plane + col]
+                                     : 0.0f;
             // lag plane z+3 goes to the slot of plane z-1, last read before the barrier
             // of the previous plane; the densities of z+1 read planes z .. z+2. It is
             // fetched here and stored after those densities, which hide the latency.
@@ -527,6 +524,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             __syncthreads();
             fence_proxy_async();
             if (z + 2 <= ze) issue(0, z + 2);
+            if (z < zb) {
+                ah_c = ah_nxt;
+                return;
+            }
             if (owned && !failed) {
                 const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
                 const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
@@ -606,37 +607,22 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
 
         float fa[Q], fb[Q];
         float a_rr = 0.f, a_rb = 0.f, b_rr = 0.f, b_rb = 0.f;
-        // A_h of the plane being collided, loaded one iteration ahead
-        float ah_c = (owned && use_nc) ? p.ah[(size_t)zb * plane + col] : 0.0f;
+        float ah_c = 0.0f;   // A_h of the plane being collided, loaded one plane ahead
 
-        // ---- prologue: planes zb-1 and zb (their pulls read lag planes zb-2 .. zb+1;
-        // lag plane zb+2 replaces zb-2 once the pull of zb-1 is done)
+        // ---- lag planes zb-2 .. zb for the densities of zb-1 (each plane z of the march
+        // then stores lag plane z+3 into the slot of z-1), and the copy of plane zb-1
         if (G::DEV) {
-            for (int q = -2; q <= 1; ++q) {
+            for (int q = -2; q <= 0; ++q) {
                 lag_fetch(zb + q);
                 lag_commit(zb + q);
             }
-            lag_fetch(zb + 2);
             __syncthreads();
         }
-        {
-            fence_proxy_async();
-            issue(0, zb - 1);
-            wait(0);
-            densities(0, zb - 1, fb, b_rr, b_rb, false);
-            __syncthreads();
-            if (G::DEV) lag_commit(zb + 2);
-            fence_proxy_async();
-            issue(0, zb);
-            wait(0);
-            densities(0, zb, fa, a_rr, a_rb, true);
-            __syncthreads();
-            fence_proxy_async();
-            issue(0, zb + 1);
-        }
+        fence_proxy_async();
+        issue(0, zb - 1);
 
         // ---- the march: plane z is collided from fa while plane z+1 is pulled into fb
-        for (int z = zb; z < ze; ++z) {
+        for (int z = zb - 2; z < ze; ++z) {
             march(z, fa, a_rr, a_rb, fb, b_rr, b_rb, ah_c);
 #pragma unroll
             for (int i = 0; i < Q; ++i) fa[i] = fb[i];

@@ -120,6 +120,20 @@ def channel_droplets(nx=256, ny=128, nz=64, n_grid=(10, 2, 2), r_range=(6.0, 9.0
                     drops, steps=steps)
 
 
+def channel_shan_chen(G_sc=1.6, fill=0.02, **kw):
+    """The microfluidic-crystal channel (same droplets, walls and body force) for the
+    Shan-Chen model: each species 0.96 of its colour-model density plus `fill`
+    everywhere (a separated Shan-Chen mixture keeps a little of each species in both
+    phases), coupling G_sc, no near-contact force (it belongs to the colour model)."""
+    w = channel_droplets(**kw)
+    params = dict(wall_y=1, wall_z=1, tau_r=w.params["tau_r"], g=w.params["g"],
+                  model="shan_chen", G_sc=G_sc)
+    scale = 1.0 - 2.0 * fill
+    return Workload(w.name.replace("channel", "channel-shan-chen"), w.shape,
+                    scale * w.rho_r + fill, scale * w.rho_b + fill, params, w.droplets,
+                    steps=w.steps)
+
+
 def dense_emulsion(L=512, volume_fraction=0.35, r_range=(6.0, 12.0), seed=1003, sigma=0.01,
                    tau=1.0, beta=0.7, A_nc=0.01, h_min=3.0, kolmogorov_amp=1e-5,
                    max_attempts=10_000_000, steps=2000):
