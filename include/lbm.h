@@ -161,6 +161,25 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u,
  * A_nc == 0. For diagnostics and tests; synchronises the stream.                 */
 lbm_status lbm_get_nc_field(lbm_ctx* ctx, double* ah, int on_device);
 
+/* Droplet census of the current colour field (the dense-emulsion workload reports
+ * the number of droplets and their sizes): the connected components of {phi > 0}
+ * under 26-connectivity (face, edge and corner neighbours), wrapping around periodic
+ * axes and not across walls. *count = number of components; sizes[0 .. min(count,
+ * capacity) - 1] = their node counts in descending order (sizes may be NULL when
+ * capacity is 0). Diagnostic, not part of the time step; needs 8 bytes per node of
+ * staging and at most 2^31 - 1 nodes. Synchronises the stream.                   */
+lbm_status lbm_droplets(lbm_ctx* ctx, long long* count, long long* sizes, long long capacity);
+
+/* Radially averaged structure factor of the current colour field (the gel workload
+ * reports its peak): S(k_b) = sum over modes in shell b of |phi_hat(m)|^2 /
+ * (N * modes in shell b), phi_hat the discrete Fourier transform of phi - mean(phi),
+ * k(m) = 2 pi (m_x/n_x, m_y/n_y, m_z/n_z), shell b = round(|k| / dk),
+ * dk = 2 pi / max(n_x, n_y, n_z), b = 0 .. nbins - 1 (modes beyond are dropped). Writes
+ * S[nbins], and when not NULL k[nbins] = b dk and modes[nbins]. Every axis is treated
+ * as periodic. Single-precision FFT (cuFFT) with FP64 shell sums. Synchronises.  */
+lbm_status lbm_structure_factor(lbm_ctx* ctx, int nbins, double* k, double* S,
+                                long long* modes);
+
 /* Self-check of the near-contact work bound (an implementation device with no
  * counterpart in the paper: the paper does not say how the film is searched).
  * The step kernel marks, for the next step's film measurement, every 2x2x2 block

@@ -68,9 +68,13 @@ def structure_factor(phi, nbins):
     N = phi.size
     F = np.fft.fftn(phi - phi.mean())
     P = (F * np.conj(F)).real
-    mz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
-    my = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
-    mx = np.fft.fftfreq(nx, 1.0 / nx)[None, None, :]
+    def modes(n):
+        m = np.arange(n, dtype=np.float64)
+        m[m >= (n + 1) // 2] -= n           # signed mode indices, FFT order
+        return m
+    mz = modes(nz)[:, None, None]
+    my = modes(ny)[None, :, None]
+    mx = modes(nx)[None, None, :]
     k = 2 * np.pi * np.sqrt((mx / nx) ** 2 + (my / ny) ** 2 + (mz / nz) ** 2)
     dk = 2 * np.pi / max(nx, ny, nz)
     b = np.rint(k / dk).astype(np.int64)

@@ -753,6 +753,11 @@ static lbm_status ensure_stage(lbm_ctx* c, size_t doubles) {
     return LBM_OK;
 }
 
+namespace lbm {
+lbm_status ctx_stage(lbm_ctx* c, size_t doubles) { return ensure_stage(c, doubles); }
+lbm_status ctx_fail(lbm_ctx* c, lbm_status s, const std::string& msg) { return fail(c, s, msg); }
+}  // namespace lbm
+
 template <class F>
 static void dispatch(int storage, F&& fn) {
     if (storage == 0) fn(StoreF32{});

@@ -89,4 +89,8 @@ lbm_status check_errors(lbm_ctx* c);
 int ctx_num_sms(const lbm_ctx* c);
 cudaStream_t ctx_stream(const lbm_ctx* c);
 void set_global_error(const std::string& msg);
+// Device FP64 staging of at least `doubles` values (c->stage; grown on demand, old
+// contents not kept), and recording a failure in the context's error message.
+lbm_status ctx_stage(lbm_ctx* c, size_t doubles);
+lbm_status ctx_fail(lbm_ctx* c, lbm_status s, const std::string& msg);
 }  // namespace lbm

@@ -31,6 +31,7 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
            "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
+           "lbm_droplets", "lbm_structure_factor",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
            "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy",
            "lbm_engine_last_error"]
@@ -105,6 +106,8 @@ def load():
             "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
             "lbm_nc_bound_check": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+            "lbm_droplets": (C.c_int, [_P, C.POINTER(C.c_longlong), _D, C.c_longlong]),
+            "lbm_structure_factor": (C.c_int, [_P, C.c_int, _D, _D, _D]),
             "lbm_get_window": (C.c_int, [_P] + [C.c_int] * 6 + [_D, _D, _D, C.c_int]),
             "lbm_engine_create": (C.c_int, [C.POINTER(EngineParams), C.POINTER(C.c_void_p)]),
             "lbm_engine_submit": (C.c_int, [_P, PP, _D, _D, _D, C.c_longlong,
@@ -316,6 +319,24 @@ class Lattice:
         out = (C.c_longlong * 2)()
         self._check(self._lib.lbm_nc_bound_check(self._h, out))
         return int(out[0]), int(out[1])
+
+    def droplets(self):
+        """(number of droplets, their node counts in descending order): the
+        26-connected components of {phi > 0} of the current colour field."""
+        n = C.c_longlong()
+        self._check(self._lib.lbm_droplets(self._h, C.byref(n), None, 0))
+        sizes = np.zeros(n.value, dtype=np.int64)
+        if n.value:
+            self._check(self._lib.lbm_droplets(self._h, C.byref(n), sizes.ctypes.data, sizes.size))
+        return int(n.value), sizes
+
+    def structure_factor(self, nbins):
+        """(k, S(k), modes per shell) of the current colour field."""
+        k, S = np.zeros(nbins), np.zeros(nbins)
+        m = np.zeros(nbins, dtype=np.int64)
+        self._check(self._lib.lbm_structure_factor(self._h, int(nbins), k.ctypes.data,
+                                                   S.ctypes.data, m.ctypes.data))
+        return k, S, m
 
     def observables(self):
         out = (C.c_double * 8)()

@@ -122,6 +122,14 @@ def test_dense_emulsion_512_full_size(lbm):
     assert np.isfinite(m1[:5]).all()
     # per-species mass: FP32 arithmetic on 1.3e8 nodes, relative drift well below 1e-6
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6
+    # droplet census: random sequential addition lets spheres touch (near the jamming
+    # fraction they form clusters), so it reports clusters; the components cover
+    # exactly the positive nodes
+    n, sizes = g.droplets()
+    phi = g.get_fields()["phi"]
+    print("emulsion 512^3: components", n, "of", len(w.droplets), "placed; largest", sizes[:3])
+    assert 1 <= n <= len(w.droplets)
+    assert sizes.sum() == int((phi > 0).sum())
     g.close()
 
 
@@ -142,6 +150,14 @@ def test_bicontinuous_gel_640_full_size(lbm):
     m1 = g.observables()
     assert np.isfinite(m1[:5]).all()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6
+    # structure factor: every mode is in a shell below 560 (|m| <= sqrt(3) 320), so
+    # the shells sum to the variance of phi (Parseval)
+    k, S, modes = g.structure_factor(560)
+    phi = g.get_fields()["phi"]
+    var = ((phi - phi.mean()) ** 2).sum()
+    assert modes.sum() == phi.size
+    assert abs((S * modes).sum() - var) < 1e-3 * var
+    print("gel 640^3: S(k) peak at k =", k[1 + int(np.argmax(S[1:]))])
     g.close()
 
 
