@@ -539,14 +539,34 @@ static void fill_step_params(lbm_ctx* c) {
     s.zparts = best_k;
     s.chain = 0;
     c->grid = (int)(tiles * best_k);
-    // chain mode when one wave of whole parts would leave SMs unevenly loaded: a
-    // multiple of the tile columns, at most the CTAs resident at once, and at least
-    // 8 planes per CTA
+    s.band_k = s.band_h = 0;
+    // chain mode when one wave of whole parts would leave SMs unevenly loaded: every
+    // CTA slot, with about w = nz tiles / slots planes each: k = slots / tiles bands
+    // of h ~ w planes, one CTA per (band, tile), and the rest shared by the remaining
+    // slots; of h = floor(w), ceil(w) the one whose busiest CTA has fewer planes
+    // (counting about one plane of pipeline fill per tile a CTA starts) is taken.
     const long long units = tiles * p.nz;
-    const long long g = (long long)(S / s.tiles_x) * s.tiles_x;
-    if (tiles < S && g > 0 && units >= 8 * g && tiles * best_k != g) {
-        s.chain = (int)g;
-        c->grid = (int)g;
+    if (tiles < S && units >= 8LL * S && tiles * best_k != S) {
+        const int k = (int)(S / tiles);
+        const double w = (double)units / (double)S;
+        double best_cost = (double)p.nz / best_k + 1.0;   // part mode: one part per CTA
+        for (int h = std::max(1, (int)std::floor(w)); h <= (int)std::ceil(w); ++h) {
+            const int r = p.nz - k * h;
+            const long long R = S - (long long)k * tiles;
+            if (r < 0 || (r > 0 && R <= 0)) continue;
+            double cost = h + 1.0;
+            if (r > 0) {
+                const double rem = (double)r * tiles / (double)R;
+                cost = std::max(cost, rem + std::ceil(rem / r) + 1.0);
+            }
+            if (cost < best_cost) {
+                best_cost = cost;
+                s.band_k = k;
+                s.band_h = h;
+                s.chain = (int)(r > 0 ? S : (long long)k * tiles);
+            }
+        }
+        if (s.chain > 0) c->grid = s.chain;
     }
 }
 
@@ -570,6 +590,7 @@ void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* ou
     if (zparts > 0) {
         s.zparts = zparts;
         s.chain = 0;
+        s.band_k = s.band_h = 0;
     }
     out->in_map = c->tmap[cur];
     out->out_map = c->smap[1 - cur];

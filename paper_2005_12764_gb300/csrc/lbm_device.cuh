@@ -142,8 +142,11 @@ struct StepParams {
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // part mode: z is cut into this many equal parts, one CTA per
                             // (part, tile)
-    int chain;              // chain mode (> 0): this many CTAs share the (tile, plane) units
-                            // equally, each a contiguous run of them in column-major tile order
+    int chain;              // chain mode (> 0): this many CTAs; the first band_k * tiles
+                            // march one tile each over one of band_k bands of band_h planes,
+                            // the others share the planes above equally, each a contiguous
+                            // run of (tile, plane) units in column-major tile order
+    int band_k, band_h;
     void* fout;             // populations after the step
     int* err;               // device error word: 1 = a bounded wait gave up
 };

@@ -31,13 +31,14 @@
 // part-major, so the CTAs resident at the same time work on neighbouring tiles at
 // the same heights: the halo rows one tile stages are the rows its neighbours are
 // reading, and come from L2 rather than HBM.
-// Chain mode (smaller lattices): exactly as many CTAs as fit on the GPU at once
-// share the (tile, plane) units equally, each taking a contiguous run of them in
-// column-major tile order (all planes of tile (0,0), then of (0,1), ...), so a CTA
-// may finish one tile and continue on the next. Every SM then carries the same
-// work, where whole parts per tile would leave some SMs with one CTA and others
-// with two; the CTA count is a multiple of the tile columns, so tiles side by side
-// in x have the same split and are marched at the same heights at the same time.
+// Chain mode (smaller lattices): as many CTAs as fit on the GPU at once, each with
+// the same number of (tile, plane) units. The lattice height is cut into band_k
+// bands of band_h planes, one CTA per (band, tile), and the planes above them,
+// whose units the remaining CTAs share in contiguous runs (column-major tile order,
+// so such a CTA may finish one tile and continue on the next). Every SM then
+// carries the same work, where whole parts per tile would leave some SMs with one
+// CTA and others with two; within a band every tile is marched at the same heights
+// at the same time, so the halo rows neighbours read come from L2.
 #include <cuda.h>
 
 #include <utility>
@@ -191,20 +192,36 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
 
     // work of this CTA: one or more segments, each a tile and a range of planes
     const int ntiles = p.tiles_x * p.tiles_y;
-    long long u_next = 0, u_end = 0;   // chain mode: this CTA's units (tile, plane)
-    if (p.chain > 0) {
-        const long long U = (long long)ntiles * p.nz;
-        u_next = U * cta / p.chain;
-        u_end = U * (cta + 1) / p.chain;
+    // chain mode: CTAs below nfull march one tile over one band of band_h planes;
+    // the others share the units (tile, plane) of the planes from zr up
+    const int nfull = p.band_k * ntiles, zr = p.band_k * p.band_h, nr = p.nz - zr;
+    long long u_next = 0, u_end = 0;   // chain mode: this CTA's units above zr
+    if (p.chain > 0 && cta >= nfull) {
+        const long long U = (long long)ntiles * nr;
+        const long long R = p.chain - nfull;
+        u_next = U * (cta - nfull) / R;
+        u_end = U * (cta - nfull + 1) / R;
     }
     bool part_done = false;
     auto next_segment = [&](int& sx0, int& sy0, int& szb, int& sze) -> bool {
+        if (p.chain > 0 && cta < nfull) {
+            // one band of one tile; consecutive CTAs are neighbours along x, and a
+            // band's CTAs all march at the same heights
+            if (part_done) return false;
+            part_done = true;
+            const int band = cta / ntiles, tile = cta - band * ntiles;
+            szb = band * p.band_h;
+            sze = szb + p.band_h;
+            sx0 = (tile % p.tiles_x) * TX;
+            sy0 = (tile / p.tiles_x) * TY;
+            return true;
+        }
         if (p.chain > 0) {
             // units in column-major tile order: tile t is column t / tiles_y, row
-            // t % tiles_y; planes ascending within a tile
+            // t % tiles_y; planes zr .. nz-1 ascending within a tile
             if (u_next >= u_end) return false;
-            const int t = (int)(u_next / p.nz);
-            szb = (int)(u_next - (long long)t * p.nz);
+            const int t = (int)(u_next / nr);
+            szb = zr + (int)(u_next - (long long)t * nr);
             sze = (int)min((long long)p.nz, (long long)szb + (u_end - u_next));
             u_next += sze - szb;
             const int tx = t / p.tiles_y;

@@ -165,9 +165,9 @@ def test_shan_chen_walls_sliding_forces_unequal_tau(lbm):
 
 
 def test_shan_chen_chain_mode_and_fp16(lbm):
-    # 72 x 44 x 140 runs the step kernel in chain mode (CTAs crossing tiles)
-    shape = (140, 44, 72)
-    drops = [(20.0, 12.0, 30.0, 6.0), (50.0, 30.0, 70.0, 7.0), (60.0, 14.0, 110.0, 8.0)]
+    # 150 x 60 x 64 runs the step kernel in chain mode (CTAs crossing tiles)
+    shape = (64, 60, 150)
+    drops = [(20.0, 12.0, 30.0, 6.0), (50.0, 30.0, 50.0, 7.0), (110.0, 40.0, 20.0, 8.0)]
     fo, fg, _, _ = _sc_pair(lbm, shape, drops, 20, periodic=(True, False, False), G_sc=1.5,
                             wall_y=1, wall_z=1)
     assert_parity(fo, fg)

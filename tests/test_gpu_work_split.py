@@ -1,9 +1,9 @@
 """GPU checks of how the step's work is split and bounded.
 
-- Chain mode of the step kernel (lattices of fewer tiles than the GPU holds CTAs: a
-  CTA's run of (tile, plane) units may end inside one tile and continue on the
-  next) against the FP64 oracle, and bitwise against part mode (the serving
-  engine's split) on the same lattice.
+- Chain mode of the step kernel (lattices of fewer tiles than the GPU holds CTAs:
+  bands of planes one CTA per (band, tile), the planes above shared in runs that may
+  end inside one tile and continue on the next) against the FP64 oracle, and bitwise
+  against part mode (the serving engine's split) on the same lattice.
 - The near-contact ray-bound bit field the step kernel sets for the next step
   (atomic ORs per row of a tile) equals the one a separate kernel computes from the
   same colour field, on odd, even, ragged, walled and periodic lattices.
@@ -31,12 +31,12 @@ def lbm():
 
 
 def test_chain_mode_walls_ragged_near_contact_matches_oracle(lbm):
-    # 72 x 44 x 140: 3 x 6 tiles (ragged in x and y), 2520 (tile, plane) units, so
-    # the step kernel runs in chain mode with ~8 planes per CTA and most CTAs cross
-    # from one tile to the next, including across the z walls.
-    shape = (140, 44, 72)
-    drops = [(20.0, 12.0, 30.0, 6.0), (33.5, 24.0, 31.0, 6.5), (50.0, 30.0, 70.0, 7.0),
-             (60.0, 14.0, 110.0, 8.0), (12.0, 30.0, 95.0, 5.0)]
+    # 150 x 60 x 64: 5 x 8 tiles (ragged in x and y). The step kernel runs in chain
+    # mode: 7 bands of 9 planes (one CTA per band and tile) and the top plane shared
+    # by the 24 remaining CTAs, whose runs cross from one tile to the next.
+    shape = (64, 60, 150)
+    drops = [(20.0, 12.0, 30.0, 6.0), (33.5, 24.0, 31.0, 6.5), (50.0, 30.0, 50.0, 7.0),
+             (110.0, 40.0, 20.0, 8.0), (130.0, 20.0, 55.0, 6.0)]
     rr, rb = inputs.paint_droplets(shape, drops, periodic=(True, False, False))
     kw = dict(wall_y=1, wall_z=1, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0, g=(1e-5, 0, 0))
     nz, ny, nx = shape
@@ -54,9 +54,10 @@ def test_chain_mode_walls_ragged_near_contact_matches_oracle(lbm):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 def test_chain_mode_is_bitwise_part_mode(lbm, storage):
-    # A sheared 96^3 droplet: lbm_step runs chain mode (36 tiles), the serving engine
-    # part mode; every node's update is computed the same way in both.
-    req = dict(id=0, L=96, R=24.0, sigma=0.02, steps=24, sheared=True)
+    # A sheared 128^3 droplet: lbm_step runs chain mode (64 tiles: 4 bands of 27
+    # planes and 20 planes shared by 48 CTAs), the serving engine part mode; every
+    # node's update is computed the same way in both.
+    req = dict(id=0, L=128, R=32.0, sigma=0.02, steps=24, sheared=True)
     p, rr, rb = serving.request_lattice(req, storage)
     g = lbm.Lattice(p)
     g.set_fields(rr, rb)
