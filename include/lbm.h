@@ -311,8 +311,8 @@ lbm_status lbm_engine_create(const lbm_engine_params* p, lbm_engine** out);
 
 /* Queues a request: a lattice with parameters p (p->cuda_stream is ignored) and
  * initial fields as for lbm_set_fields (host arrays, copied; u may be NULL), to be
- * advanced `steps` >= 1 steps. *ticket identifies it (> 0). Requests use the
- * colour-gradient model without near-contact force (LBM_EINVAL otherwise).      */
+ * advanced `steps` >= 1 steps. *ticket identifies it (> 0). Requests of either
+ * model are served; the near-contact force is not (A_nc > 0 gives LBM_EINVAL).   */
 lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, const double* rho_r,
                              const double* rho_b, const double* u, long long steps,
                              long long* ticket);

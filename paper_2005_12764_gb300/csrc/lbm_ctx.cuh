@@ -28,7 +28,7 @@ int step_box_width(int storage);
 int step_ctas_per_sm();
 int step_pad_x(int storage);
 cudaError_t launch_step_batched(const BatchLattice* tab, int nlat, int ctas, int storage,
-                                bool unit_omega, cudaStream_t s);
+                                bool unit_omega, int model, cudaStream_t s);
 cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long cells, int storage,
                                  int num_sms, cudaStream_t s);
 long long ghost_cells(const StepParams& p);

@@ -19,7 +19,7 @@
 using namespace lbm;
 
 namespace lbm {
-cudaError_t prepare_step_batched(int storage, bool unit_omega);
+cudaError_t prepare_step_batched(int storage, bool unit_omega, int model);
 }
 
 namespace {
@@ -42,10 +42,11 @@ struct Request {
     std::vector<double> out_rr, out_rb, out_u, out_phi;
 };
 
-// Lattices of one storage format and relaxation class: one batched launch.
+// Lattices of one storage format, relaxation class and model: one batched launch.
 struct Group {
     int storage = 0;
     bool unit = false;
+    int model = 0;
     std::vector<Request*> members;
     BatchLattice* d_tab[2] = {nullptr, nullptr};   // tables of the next two steps
     std::vector<BatchLattice> h_tab[2];
@@ -96,7 +97,8 @@ void free_groups(lbm_engine* e) {
     e->graph_valid = false;
 }
 
-// Batch composition: sizes, storage and relaxation class of the resident lattices.
+// Batch composition: sizes, storage, relaxation class and model of the resident
+// lattices.
 std::string signature(const lbm_engine* e) {
     std::vector<std::string> parts;
     for (const Request* r : e->resident) {
@@ -105,7 +107,7 @@ std::string signature(const lbm_engine* e) {
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
         parts.push_back(std::to_string(r->p.nx) + "x" + std::to_string(r->p.ny) + "x" +
                         std::to_string(r->p.nz) + "s" + std::to_string(r->p.storage) +
-                        (unit ? "u" : "v"));
+                        (unit ? "u" : "v") + "m" + std::to_string(r->p.model));
     }
     std::sort(parts.begin(), parts.end());
     std::string s;
@@ -122,18 +124,19 @@ cudaError_t build_batch(lbm_engine* e, int T) {
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
         Group* g = nullptr;
         for (Group& x : e->groups)
-            if (x.storage == r->p.storage && x.unit == unit) g = &x;
+            if (x.storage == r->p.storage && x.unit == unit && x.model == r->p.model) g = &x;
         if (!g) {
             e->groups.emplace_back();
             g = &e->groups.back();
             g->storage = r->p.storage;
             g->unit = unit;
+            g->model = r->p.model;
         }
         g->members.push_back(r);
     }
     cudaError_t err = cudaSuccess;
     for (Group& g : e->groups) {
-        err = prepare_step_batched(g.storage, g.unit);
+        err = prepare_step_batched(g.storage, g.unit, g.model);
         if (err != cudaSuccess) return err;
         for (int j = 0; j < 2; ++j) {
             g.h_tab[j].resize(g.members.size());
@@ -169,7 +172,7 @@ cudaError_t build_batch(lbm_engine* e, int T) {
     for (int j = 0; j < 2 && err == cudaSuccess; ++j)
         for (Group& g : e->groups) {
             if (err == cudaSuccess)
-                err = launch_step_batched(g.d_tab[j], (int)g.members.size(), g.ctas, g.storage, g.unit,
+                err = launch_step_batched(g.d_tab[j], (int)g.members.size(), g.ctas, g.storage, g.unit, g.model,
                                           e->stream);
             if (err == cudaSuccess && g.ghost > 0)
                 err = launch_ghost_batched(g.d_tab[j], (int)g.members.size(), g.ghost, g.storage,
@@ -190,7 +193,7 @@ cudaError_t single_step(lbm_engine* e) {
     cudaError_t err = cudaSuccess;
     for (Group& g : e->groups) {
         if (err == cudaSuccess)
-            err = launch_step_batched(g.d_tab[0], (int)g.members.size(), g.ctas, g.storage, g.unit,
+            err = launch_step_batched(g.d_tab[0], (int)g.members.size(), g.ctas, g.storage, g.unit, g.model,
                                       e->stream);
         if (err == cudaSuccess && g.ghost > 0)
             err = launch_ghost_batched(g.d_tab[0], (int)g.members.size(), g.ghost, g.storage,
@@ -327,7 +330,6 @@ extern "C" lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, cons
     if (!p || !rho_r || !rho_b || !ticket) return efail(e, LBM_EINVAL, "p, rho_r, rho_b and ticket are required");
     if (steps < 1) return efail(e, LBM_EINVAL, "steps must be >= 1");
     if (p->A_nc > 0.0) return efail(e, LBM_EINVAL, "engine requests must have A_nc == 0");
-    if (p->model != 0) return efail(e, LBM_EINVAL, "engine requests use the colour-gradient model");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return efail(e, LBM_EINVAL, "nx, ny, nz must be >= 1");
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return efail(e, LBM_ENOMEM, "host allocation failed");

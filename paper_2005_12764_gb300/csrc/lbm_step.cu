@@ -668,7 +668,7 @@ step_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtens
 // Several lattices in one launch: CTA b belongs to the last lattice whose first CTA
 // is <= b. Its parameters are copied to shared memory once; its tensor maps are read
 // from the table (global memory).
-template <class St, bool UnitOmega>
+template <class St, bool UnitOmega, bool SC>
 __global__ void __launch_bounds__(NT, CTAS_PER_SM)
 step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
     __shared__ StepParams sp;
@@ -691,7 +691,7 @@ step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
             dst[i] = src[i];
     }
     __syncthreads();
-    step_body<St, UnitOmega>(sp, &L.in_map, &L.out_map, (int)blockIdx.x - L.cta_begin);
+    step_body<St, UnitOmega, SC>(sp, &L.in_map, &L.out_map, (int)blockIdx.x - L.cta_begin);
 }
 
 // ---------------------------------------------------------------- ghost fill
@@ -1112,45 +1112,63 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
     return cudaErrorInvalidValue;
 }
 
-template <class St, bool U>
+template <class St, bool U, bool SC>
 static cudaError_t launch_batched_tpl(const BatchLattice* tab, int nlat, int ctas, cudaStream_t s) {
-    step_kernel_batched<St, U><<<ctas, NT, Geo<St>::SMEM, s>>>(tab, nlat);
+    step_kernel_batched<St, U, SC><<<ctas, NT, Geo<St, SC>::SMEM, s>>>(tab, nlat);
     return cudaGetLastError();
 }
 
-template <class St, bool U>
+template <class St, bool U, bool SC>
 static cudaError_t prepare_batched_tpl() {
-    return cudaFuncSetAttribute(step_kernel_batched<St, U>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<St>::SMEM);
+    return cudaFuncSetAttribute(step_kernel_batched<St, U, SC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<St, SC>::SMEM);
 }
+
+// Batched kernel of one (storage, relaxation class, model): dispatched over the
+// 12 combinations with a callable that takes the three as template arguments.
+template <class F>
+static cudaError_t batched_dispatch(int storage, bool unit_omega, int model, F&& fn) {
+    const bool sc = model == 1;
+    switch (storage * 4 + (unit_omega ? 2 : 0) + (sc ? 1 : 0)) {
+        case 0: return fn.template operator()<StoreF32, false, false>();
+        case 1: return fn.template operator()<StoreF32, false, true>();
+        case 2: return fn.template operator()<StoreF32, true, false>();
+        case 3: return fn.template operator()<StoreF32, true, true>();
+        case 4: return fn.template operator()<StoreF16, false, false>();
+        case 5: return fn.template operator()<StoreF16, false, true>();
+        case 6: return fn.template operator()<StoreF16, true, false>();
+        case 7: return fn.template operator()<StoreF16, true, true>();
+        case 8: return fn.template operator()<StoreBF16, false, false>();
+        case 9: return fn.template operator()<StoreBF16, false, true>();
+        case 10: return fn.template operator()<StoreBF16, true, false>();
+        case 11: return fn.template operator()<StoreBF16, true, true>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+struct PrepareBatched {
+    template <class St, bool U, bool SC>
+    cudaError_t operator()() const { return prepare_batched_tpl<St, U, SC>(); }
+};
+struct LaunchBatched {
+    const BatchLattice* tab;
+    int nlat, ctas;
+    cudaStream_t s;
+    template <class St, bool U, bool SC>
+    cudaError_t operator()() const { return launch_batched_tpl<St, U, SC>(tab, nlat, ctas, s); }
+};
 
 // Shared-memory attribute of a batched step kernel: set before any launch (and
 // outside stream capture).
-cudaError_t prepare_step_batched(int storage, bool unit_omega) {
-    switch (storage * 2 + (unit_omega ? 1 : 0)) {
-        case 0: return prepare_batched_tpl<StoreF32, false>();
-        case 1: return prepare_batched_tpl<StoreF32, true>();
-        case 2: return prepare_batched_tpl<StoreF16, false>();
-        case 3: return prepare_batched_tpl<StoreF16, true>();
-        case 4: return prepare_batched_tpl<StoreBF16, false>();
-        case 5: return prepare_batched_tpl<StoreBF16, true>();
-    }
-    return cudaErrorInvalidValue;
+cudaError_t prepare_step_batched(int storage, bool unit_omega, int model) {
+    return batched_dispatch(storage, unit_omega, model, PrepareBatched{});
 }
 
 // One launch advancing every lattice of a device table by one step (all lattices of
-// one storage format and relaxation class).
+// one storage format, relaxation class and model).
 cudaError_t launch_step_batched(const BatchLattice* tab, int nlat, int ctas, int storage,
-                                bool unit_omega, cudaStream_t s) {
-    switch (storage * 2 + (unit_omega ? 1 : 0)) {
-        case 0: return launch_batched_tpl<StoreF32, false>(tab, nlat, ctas, s);
-        case 1: return launch_batched_tpl<StoreF32, true>(tab, nlat, ctas, s);
-        case 2: return launch_batched_tpl<StoreF16, false>(tab, nlat, ctas, s);
-        case 3: return launch_batched_tpl<StoreF16, true>(tab, nlat, ctas, s);
-        case 4: return launch_batched_tpl<StoreBF16, false>(tab, nlat, ctas, s);
-        case 5: return launch_batched_tpl<StoreBF16, true>(tab, nlat, ctas, s);
-    }
-    return cudaErrorInvalidValue;
+                                bool unit_omega, int model, cudaStream_t s) {
+    return batched_dispatch(storage, unit_omega, model, LaunchBatched{tab, nlat, ctas, s});
 }
 
 cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long cells, int storage,

@@ -148,10 +148,39 @@ def test_shortest_job_first_admission(lbm):
     assert order[1] == [1, 2, 3, 0]          # shortest (fewest node-steps) first
 
 
-def test_engine_refuses_other_models(lbm):
-    e = lbm.Engine(budget_bytes=1 << 30, max_slots=2)
-    p = lbm.make_params(16, 16, 16, model="shan_chen", G_sc=1.5)
-    rr = np.ones((16, 16, 16))
-    with pytest.raises(lbm.LbmError):
-        e.submit(p, rr, 0 * rr, 5)
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_shan_chen_requests_in_a_mix_are_bitwise_lbm_step(lbm, storage):
+    # Shan-Chen and colour-gradient requests resident together (two batched launches
+    # per step): each result equals the same lattice stepped by plain lbm_step
+    from paper_2005_12764_gb300 import serving
+    reqs = [dict(id=0, L=32, R=8.0, sigma=0.02, steps=30, sheared=False),
+            dict(id=1, L=48, R=12.0, sigma=0.01, steps=40, sheared=True)]
+    L = 40
+    rr, rb = inputs.paint_droplets((L, L, L), [(20.0, 20.0, 20.0, 10.0)])
+    rr, rb = 0.96 * rr + 0.02, 0.96 * rb + 0.02
+    psc = lbm.make_params(L, L, L, model="shan_chen", G_sc=1.6, storage=storage,
+                          kolmogorov_amp=1e-5)
+    e = lbm.Engine(budget_bytes=8 << 30, max_slots=8, chunk_steps=10, autotune=False)
+    tickets = {}
+    for r in reqs:
+        p, a, b = serving.request_lattice(r, storage)
+        tickets[e.submit(p, a, b, r["steps"])] = ("cg", r, p, a, b)
+    tickets[e.submit(psc, rr, rb, 35)] = ("sc", None, psc, rr, rb)
+    done = {}
+    for _ in range(200):
+        e.tick()
+        for t in tickets:
+            if t not in done and e.state(t) == "finished":
+                done[t] = e.result(t)
+        if len(done) == len(tickets):
+            break
     e.close()
+    assert len(done) == len(tickets)
+    for t, (kind, r, p, a, b) in tickets.items():
+        g = lbm.Lattice(p)
+        g.set_fields(a, b)
+        g.step(r["steps"] if r else 35)
+        f = g.get_fields()
+        g.close()
+        for k in ("rho_r", "rho_b", "u", "phi"):
+            assert np.array_equal(f[k], done[t][k]), (kind, k)
