@@ -695,23 +695,20 @@ step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
 }
 
 // ---------------------------------------------------------------- ghost fill
-// Copies the wrapped-around nodes into the ghost columns/rows of periodic axes, for
-// every species and direction (after the state was set, and after each step on
-// lattices too small for the step kernel to write its ghosts itself).
-// ---------------------------------------------------------------- ghost fill
-// Ghost copies of the periodic axes, per block k and plane z:
-//  part 1, one thread per interior row y: x ghosts -2, -1 <- nodes nx-2, nx-1 and
-//          nx, nx+1 <- nodes 0, 1, each side as one aligned pair of elements when
-//          nx is even (two elements otherwise);
-//  part 2 (periodic y only), one thread per element of the ghost rows -2, -1, ny,
-//          ny+1 over x = -2 .. nx+1, from the wrapped node (corners included).
-// Part 1 covers 2Q nz ny rows, part 2 2Q nz 4 (nx + 4) elements. (Writing the whole
-// 32-byte ghost sectors instead of the pairs measured slower.)
+// Ghost copies of the periodic axes, in warp tasks (each task's indices are worked
+// out once; the lanes sweep a row or a column of rows):
+//  part 1, one task per (block k, plane z), lanes over the rows y: x ghosts -2, -1 <-
+//          nodes nx-2, nx-1 and nx, nx+1 <- nodes 0, 1, each side as one aligned pair
+//          of elements when nx is even (two elements otherwise);
+//  part 2 (periodic y only), one task per (k, z, ghost row -2, -1, ny, ny+1), lanes
+//          over x = -2 .. nx+1: each element from the wrapped node (corners included).
+// Part 1 has 2Q nz tasks, part 2 2Q nz 4. (Writing the whole 32-byte ghost sectors
+// instead of the pairs measured no faster: the fill waits on its loads.)
 __host__ __device__ inline long long ghost_part1(const StepParams& p) {
-    return (long long)2 * Q * p.nz * p.ny;
+    return (long long)2 * Q * p.nz;
 }
 __host__ __device__ inline long long ghost_work(const StepParams& p) {
-    return ghost_part1(p) + (p.wall_y ? 0 : (long long)2 * Q * p.nz * 4 * (p.nx + 4));
+    return ghost_part1(p) + (p.wall_y ? 0 : (long long)2 * Q * p.nz * 4);
 }
 
 template <int B> struct PairOf;
@@ -719,69 +716,73 @@ template <> struct PairOf<2> { using type = unsigned int; };
 template <> struct PairOf<4> { using type = unsigned long long; };
 
 template <class St>
-__device__ __forceinline__ void ghost_item(typename St::T* f, const StepParams& p, long long i) {
+__device__ __forceinline__ void ghost_task(typename St::T* f, const StepParams& p, long long t,
+                                           int lane) {
     using T = typename St::T;
     using Pair = typename PairOf<sizeof(T)>::type;
     const long long n1 = ghost_part1(p);
-    if (i < n1) {
-        const int y = (int)(i % p.ny);
-        const long long kz = i / p.ny;
-        const int z = (int)(kz % p.nz), k = (int)(kz / p.nz);
-        T* row = f + (size_t)k * p.P + pidx(p.pitch, p.nyp, p.padx, 0, y, z);   // node x = 0
-        if ((p.nx & 1) == 0 && p.nx >= 2) {
-            // row[-2], row[-1] <- row[nx-2], row[nx-1]; row[nx], row[nx+1] <- row[0], row[1]
-            const Pair a = *reinterpret_cast<const Pair*>(row + p.nx - 2);
-            const Pair b = *reinterpret_cast<const Pair*>(row);
-            *reinterpret_cast<Pair*>(row - 2) = a;
-            *reinterpret_cast<Pair*>(row + p.nx) = b;
-        } else {
-            const T a0 = row[wrap_near(-2, p.nx)], a1 = row[wrap_near(-1, p.nx)];
-            const T b0 = row[wrap_near(p.nx, p.nx)], b1 = row[wrap_near(p.nx + 1, p.nx)];
-            row[-2] = a0;
-            row[-1] = a1;
-            row[p.nx] = b0;
-            row[p.nx + 1] = b1;
+    if (t < n1) {
+        const int k = (int)(t / p.nz), z = (int)(t - (long long)k * p.nz);
+        T* blk = f + (size_t)k * p.P;
+        for (int y = lane; y < p.ny; y += 32) {
+            T* row = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);   // node x = 0
+            if ((p.nx & 1) == 0 && p.nx >= 2) {
+                // row[-2], row[-1] <- row[nx-2], row[nx-1]; row[nx], row[nx+1] <- row[0], row[1]
+                const Pair a = *reinterpret_cast<const Pair*>(row + p.nx - 2);
+                const Pair b = *reinterpret_cast<const Pair*>(row);
+                *reinterpret_cast<Pair*>(row - 2) = a;
+                *reinterpret_cast<Pair*>(row + p.nx) = b;
+            } else {
+                const T a0 = row[wrap_near(-2, p.nx)], a1 = row[wrap_near(-1, p.nx)];
+                const T b0 = row[wrap_near(p.nx, p.nx)], b1 = row[wrap_near(p.nx + 1, p.nx)];
+                row[-2] = a0;
+                row[-1] = a1;
+                row[p.nx] = b0;
+                row[p.nx + 1] = b1;
+            }
         }
         return;
     }
-    const long long j = i - n1;
-    const int w = p.nx + 4;
-    const int x = (int)(j % w) - 2;
-    const long long r1 = j / w;
-    const int r = (int)(r1 % 4);
-    const long long kz = r1 / 4;
-    const int z = (int)(kz % p.nz), k = (int)(kz / p.nz);
+    const long long j = t - n1;
+    const int r = (int)(j & 3);
+    const long long kz = j >> 2;
+    const int k = (int)(kz / p.nz), z = (int)(kz - (long long)k * p.nz);
     const int y = r < 2 ? r - 2 : p.ny + r - 2;
     T* blk = f + (size_t)k * p.P;
-    blk[pidx(p.pitch, p.nyp, p.padx, x, y, z)] =
-        blk[pidx(p.pitch, p.nyp, p.padx, wrap_near(x, p.nx), wrap_near(y, p.ny), z)];
+    T* dst = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);
+    const T* src = blk + pidx(p.pitch, p.nyp, p.padx, 0, wrap_near(y, p.ny), z);
+    for (int x = lane - 2; x < p.nx + 2; x += 32) dst[x] = src[wrap_near(x, p.nx)];
 }
 
 template <class St>
 __global__ void ghost_fill_kernel(typename St::T* f, const StepParams p) {
     grid_dep_wait();
     const long long total = ghost_work(p);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x)
-        ghost_item<St>(f, p, i);
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total;
+         t += nw)
+        ghost_task<St>(f, p, t, lane);
     grid_dep_launch();
 }
 
-// Ghost copies of every lattice of a batch: item i belongs to the last lattice whose
-// first item is <= i.
+// Ghost copies of every lattice of a batch: task t belongs to the last lattice whose
+// first task is <= t.
 template <class St>
 __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nlat,
                                    long long total) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total;
+         t += nw) {
         int lo = 0, hi = nlat - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].ghost_begin <= i) lo = mid;
+            if (tab[mid].ghost_begin <= t) lo = mid;
             else hi = mid - 1;
         }
         const BatchLattice& L = tab[lo];
-        ghost_item<St>(static_cast<typename St::T*>(L.fout), L.p, i - L.ghost_begin);
+        ghost_task<St>(static_cast<typename St::T*>(L.fout), L.p, t - L.ghost_begin, lane);
     }
 }
 
@@ -829,8 +830,9 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
     }
     if (p.ghost_f) {
         const long long total = ghost_work(p);
-        for (long long i = gtid; i < total; i += gthreads)
-            ghost_item<St>(static_cast<typename St::T*>(p.ghost_f), p, i);
+        const long long nw = gthreads >> 5;
+        for (long long t = gtid >> 5; t < total; t += nw)
+            ghost_task<St>(static_cast<typename St::T*>(p.ghost_f), p, t, lane);
     }
     const int cnt = *p.nc_count;
     const int plane = p.nx * p.ny;
@@ -1173,7 +1175,7 @@ cudaError_t launch_step_batched(const BatchLattice* tab, int nlat, int ctas, int
 
 cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long cells, int storage,
                                  int num_sms, cudaStream_t s) {
-    long long blocks = (cells + 255) / 256;
+    long long blocks = (cells + 7) / 8;   // a warp per task, 8 warps per block
     if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     if (blocks < 1) blocks = 1;
     switch (storage) {
@@ -1185,7 +1187,7 @@ cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long ce
     return cudaGetLastError();
 }
 
-// Work items of one lattice's ghost fill.
+// Warp tasks of one lattice's ghost fill.
 long long ghost_cells(const StepParams& p) { return ghost_work(p); }
 
 template <class St>
@@ -1200,7 +1202,7 @@ cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num
     const int threads = 256;
     const size_t cells = (size_t)ghost_work(p);
     if (cells == 0) return cudaSuccess;   // nothing to copy (no launch)
-    size_t blocks = (cells + threads - 1) / threads;
+    size_t blocks = (cells + threads / 32 - 1) / (threads / 32);   // a warp per task
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     switch (storage) {
