@@ -543,14 +543,14 @@ static void fill_step_params(lbm_ctx* c) {
     // chain mode when one wave of whole parts would leave SMs unevenly loaded: every
     // CTA slot, with about w = nz tiles / slots planes each: k = slots / tiles bands
     // of h ~ w planes, one CTA per (band, tile), and the rest shared by the remaining
-    // slots; of h = floor(w), ceil(w) the one whose busiest CTA has fewer planes
-    // (counting about one plane of pipeline fill per tile a CTA starts) is taken.
+    // slots; of h near w the one whose busiest CTA has the fewest planes (counting
+    // about one plane of pipeline fill per tile a CTA starts) is taken.
     const long long units = tiles * p.nz;
     if (tiles < S && units >= 8LL * S && tiles * best_k != S) {
         const int k = (int)(S / tiles);
         const double w = (double)units / (double)S;
         double best_cost = (double)p.nz / best_k + 1.0;   // part mode: one part per CTA
-        for (int h = std::max(1, (int)std::floor(w)); h <= (int)std::ceil(w); ++h) {
+        for (int h = std::max(1, (int)std::floor(w) - 2); h <= (int)std::ceil(w) + 3; ++h) {
             const int r = p.nz - k * h;
             const long long R = S - (long long)k * tiles;
             if (r < 0 || (r > 0 && R <= 0)) continue;

@@ -54,8 +54,8 @@ def test_chain_mode_walls_ragged_near_contact_matches_oracle(lbm):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 def test_chain_mode_is_bitwise_part_mode(lbm, storage):
-    # A sheared 128^3 droplet: lbm_step runs chain mode (64 tiles: 4 bands of 27
-    # planes and 20 planes shared by 48 CTAs), the serving engine part mode; every
+    # A sheared 128^3 droplet: lbm_step runs chain mode (64 tiles: 4 bands of 28
+    # planes and 16 planes shared by 48 CTAs), the serving engine part mode; every
     # node's update is computed the same way in both.
     req = dict(id=0, L=128, R=32.0, sigma=0.02, steps=24, sheared=True)
     p, rr, rb = serving.request_lattice(req, storage)
