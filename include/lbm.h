@@ -317,6 +317,12 @@ lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, const double* r
                              const double* rho_b, const double* u, long long steps,
                              long long* ticket);
 
+/* Withdraws a request: a queued one leaves the queue, a resident one is freed
+ * (after the engine's queued work has drained) and the others go on unchanged, a
+ * finished one's result is dropped. Its state becomes 5 (cancelled). LBM_ESTATE if
+ * its result was taken or it failed or was cancelled already.                  */
+lbm_status lbm_engine_cancel(lbm_engine* e, long long ticket);
+
 /* One round: admit, advance, retire (see above). Writes (any pointer may be NULL)
  * the number of resident lattices after admission, of queued requests left, of
  * requests retired by this tick, and of steps k advanced. Synchronises.          */
@@ -324,7 +330,7 @@ lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued, int* retir
                            int* steps_advanced);
 
 /* State of a request: 0 queued, 1 resident, 2 finished (result ready), 3 result
- * taken, -1 unknown ticket.                                                      */
+ * taken, 4 failed, 5 cancelled, -1 unknown ticket.                               */
 int lbm_engine_state(const lbm_engine* e, long long ticket);
 
 /* Fields of a finished request (host arrays, any may be NULL; layouts as for

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -921,10 +922,15 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, int n) {
     if (!c) return LBM_EINVAL;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    nvtxRangePushA("lbm_step");   // host-side range over the launches of the n steps
     for (int t = 0; t < n; ++t) {
         cudaError_t e = launch_one_step(c, nullptr, nullptr, nullptr);
-        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        if (e != cudaSuccess) {
+            nvtxRangePop();
+            return cuda_fail(c, e, "step launch");
+        }
     }
+    nvtxRangePop();
     return LBM_OK;
 }
 

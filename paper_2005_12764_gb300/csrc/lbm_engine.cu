@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_ctx.cuh"
 
@@ -355,6 +357,10 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
     if (!e) return LBM_EINVAL;
     if (retired) *retired = 0;
     if (steps_advanced) *steps_advanced = 0;
+    struct Range {   // host-side range over the tick (admission, steps, retirement)
+        Range() { nvtxRangePushA("lbm_engine_tick"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     admit(e);
     if (resident) *resident = (int)e->resident.size();
     if (queued) *queued = (int)e->queue.size();
@@ -431,6 +437,42 @@ extern "C" int lbm_engine_state(const lbm_engine* e, long long ticket) {
     if (!e) return -1;
     auto it = e->all.find(ticket);
     return it == e->all.end() ? -1 : it->second->state;
+}
+
+extern "C" lbm_status lbm_engine_cancel(lbm_engine* e, long long ticket) {
+    if (!e) return LBM_EINVAL;
+    auto it = e->all.find(ticket);
+    if (it == e->all.end()) return efail(e, LBM_EINVAL, "unknown ticket");
+    Request* r = it->second.get();
+    switch (r->state) {
+        case 0:   // queued: leaves the queue
+            e->queue.erase(std::remove(e->queue.begin(), e->queue.end(), r), e->queue.end());
+            break;
+        case 1: {   // resident: its lattice is freed once the queued work has drained
+            cudaStreamSynchronize(e->stream);
+            lbm_destroy(r->ctx);
+            r->ctx = nullptr;
+            e->used -= r->bytes;
+            e->resident.erase(std::remove(e->resident.begin(), e->resident.end(), r),
+                              e->resident.end());
+            e->graph_valid = false;
+            free_groups(e);
+            break;
+        }
+        case 2:   // finished: its result is dropped
+            break;
+        default:
+            return efail(e, LBM_ESTATE, "request already taken, failed or cancelled");
+    }
+    std::vector<double>().swap(r->rr);
+    std::vector<double>().swap(r->rb);
+    std::vector<double>().swap(r->u);
+    std::vector<double>().swap(r->out_rr);
+    std::vector<double>().swap(r->out_rb);
+    std::vector<double>().swap(r->out_u);
+    std::vector<double>().swap(r->out_phi);
+    r->state = 5;
+    return LBM_OK;
 }
 
 extern "C" lbm_status lbm_engine_result(lbm_engine* e, long long ticket, double* rho_r,

@@ -33,7 +33,7 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
            "lbm_droplets", "lbm_structure_factor",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
-           "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy",
+           "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy", "lbm_engine_cancel",
            "lbm_engine_last_error"]
 
 
@@ -114,6 +114,7 @@ def load():
                                             C.POINTER(C.c_longlong)]),
             "lbm_engine_tick": (C.c_int, [_P] + [C.POINTER(C.c_int)] * 4),
             "lbm_engine_state": (C.c_int, [_P, C.c_longlong]),
+            "lbm_engine_cancel": (C.c_int, [_P, C.c_longlong]),
             "lbm_engine_result": (C.c_int, [_P, C.c_longlong, _D, _D, _D, _D,
                                             C.POINTER(C.c_longlong)]),
             "lbm_engine_stats": (None, [_P, C.POINTER(C.c_longlong)]),
@@ -366,7 +367,8 @@ class Engine:
     queued, admitted by device memory, advanced together in batched launches and
     retired with their fields copied to host memory."""
 
-    STATES = {0: "queued", 1: "resident", 2: "finished", 3: "taken", 4: "failed", -1: "unknown"}
+    STATES = {0: "queued", 1: "resident", 2: "finished", 3: "taken", 4: "failed", 5: "cancelled",
+              -1: "unknown"}
 
     POLICIES = {"fcfs": 0, "sjf": 1}
 
@@ -408,6 +410,11 @@ class Engine:
         v = [C.c_int() for _ in range(4)]
         self._check(self._lib.lbm_engine_tick(self._h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def cancel(self, ticket):
+        """Withdraw a queued, resident or finished request (its state becomes
+        'cancelled'); the other requests go on unchanged."""
+        self._check(self._lib.lbm_engine_cancel(self._h, int(ticket)))
 
     def state(self, ticket) -> str:
         return self.STATES[self._lib.lbm_engine_state(self._h, int(ticket))]

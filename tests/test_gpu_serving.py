@@ -184,3 +184,44 @@ def test_shan_chen_requests_in_a_mix_are_bitwise_lbm_step(lbm, storage):
         g.close()
         for k in ("rho_r", "rho_b", "u", "phi"):
             assert np.array_equal(f[k], done[t][k]), (kind, k)
+
+
+def test_cancel_queued_and_resident_requests(lbm):
+    # failures handled on the host: a request that can never fit, one withdrawn while
+    # queued, one withdrawn while resident; the others finish bitwise as lbm_step
+    from paper_2005_12764_gb300 import serving
+    reqs = [dict(id=k, L=L, R=L / 4, sigma=0.02, steps=30, sheared=bool(k % 2))
+            for k, L in enumerate((32, 40, 32, 48))]
+    e = lbm.Engine(budget_bytes=200 << 20, max_slots=2, chunk_steps=10, autotune=False)
+    big = lbm.make_params(128, 128, 128, storage="fp16")    # ~440 MB: never fits
+    with pytest.raises(lbm.LbmError):
+        e.submit(big, np.ones(128 ** 3), np.zeros(128 ** 3), 5)
+    tk = []
+    for r in reqs:
+        p, a, b = serving.request_lattice(r, "fp32")
+        tk.append(e.submit(p, a, b, r["steps"]))
+    e.tick()                                  # requests 0, 1 resident; 2, 3 queued
+    assert [e.state(t) for t in tk] == ["resident", "resident", "queued", "queued"]
+    e.cancel(tk[2])                           # queued
+    e.cancel(tk[1])                           # resident, mid-run
+    assert e.state(tk[1]) == e.state(tk[2]) == "cancelled"
+    with pytest.raises(lbm.LbmError):
+        e.cancel(tk[1])
+    for _ in range(50):
+        e.tick()
+        if all(e.state(t) in ("finished", "cancelled") for t in tk):
+            break
+    for k in (0, 3):
+        assert e.state(tk[k]) == "finished"
+        got = e.result(tk[k])
+        p, a, b = serving.request_lattice(reqs[k], "fp32")
+        g = lbm.Lattice(p)
+        g.set_fields(a, b)
+        g.step(reqs[k]["steps"])
+        f = g.get_fields()
+        g.close()
+        for key in ("rho_r", "rho_b", "u", "phi"):
+            assert np.array_equal(got[key], f[key]), (k, key)
+    with pytest.raises(lbm.LbmError):
+        e.result(tk[2])
+    e.close()
