@@ -180,6 +180,13 @@ lbm_status lbm_droplets(lbm_ctx* ctx, long long* count, long long* sizes, long l
 lbm_status lbm_structure_factor(lbm_ctx* ctx, int nbins, double* k, double* S,
                                 long long* modes);
 
+/* Self-test of failure detection without a GPU fault: runs a kernel whose bounded
+ * mbarrier wait (the kind the step kernel uses for its staged copies) can never
+ * complete, so it gives up after a short bound and sets the context's error word.
+ * Returns LBM_ETIMEOUT when that happened as designed, then clears the word: the
+ * context stays usable. (No counterpart in the paper.) Synchronises.            */
+lbm_status lbm_selftest_timeout(lbm_ctx* ctx);
+
 /* Self-check of the near-contact work bound (an implementation device with no
  * counterpart in the paper: the paper does not say how the film is searched).
  * The step kernel marks, for the next step's film measurement, every 2x2x2 block

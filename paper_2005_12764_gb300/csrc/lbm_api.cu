@@ -1065,6 +1065,20 @@ __global__ void count_diff_kernel(const uint32_t* a, const uint32_t* b, long lon
     if (k) atomicAdd(out, k);
 }
 
+extern "C" lbm_status lbm_selftest_timeout(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    CK(c, cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
+    CK(c, launch_wait_selftest(c->err_word, c->stream));
+    const lbm_status st = check_err_word(c);
+    CK(c, cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (st == LBM_ETIMEOUT) {
+        c->err.clear();
+        return LBM_ETIMEOUT;
+    }
+    return st == LBM_OK ? fail(c, LBM_OK, "the bounded wait did not give up") : st;
+}
+
 extern "C" lbm_status lbm_nc_bound_check(lbm_ctx* c, long long out[2]) {
     if (!c || !out) return LBM_EINVAL;
     if (!(c->p.A_nc > 0.0)) return fail(c, LBM_ESTATE, "no near-contact force on this lattice");

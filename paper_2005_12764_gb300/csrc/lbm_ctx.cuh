@@ -19,6 +19,7 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
 cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int storage,
                       int num_sms, cudaStream_t s);
 cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s);
 int step_tile_x();

@@ -135,13 +135,32 @@ __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^24 polls, records the failure
-// in the error word and returns false (the caller then stops).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err) {
-    for (uint32_t it = 0; it < (1u << 24); ++it)
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (2^24 by default),
+// records the failure in the error word and returns false (the caller then stops).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err,
+                                          uint32_t limit = 1u << 24) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     atomicExch(err, 1);
     return false;
+}
+
+// Self-test of the bounded wait: an mbarrier that expects one arrival nobody makes.
+// The wait gives up after `limit` polls and sets the error word; nothing faults,
+// traps or hangs, and the context stays usable.
+__global__ void wait_timeout_kernel(int* err, uint32_t limit) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0u, err, limit);
+}
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s) {
+    wait_timeout_kernel<<<1, 32, 0, s>>>(err, 1u << 16);
+    return cudaGetLastError();
 }
 
 // Programmatic dependent launch: kernels of the time step are launched so that the

@@ -31,7 +31,7 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
            "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
-           "lbm_droplets", "lbm_structure_factor",
+           "lbm_droplets", "lbm_structure_factor", "lbm_selftest_timeout",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
            "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy", "lbm_engine_cancel",
            "lbm_engine_last_error"]
@@ -107,6 +107,7 @@ def load():
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
             "lbm_nc_bound_check": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
             "lbm_droplets": (C.c_int, [_P, C.POINTER(C.c_longlong), _D, C.c_longlong]),
+            "lbm_selftest_timeout": (C.c_int, [_P]),
             "lbm_structure_factor": (C.c_int, [_P, C.c_int, _D, _D, _D]),
             "lbm_get_window": (C.c_int, [_P] + [C.c_int] * 6 + [_D, _D, _D, C.c_int]),
             "lbm_engine_create": (C.c_int, [C.POINTER(EngineParams), C.POINTER(C.c_void_p)]),
@@ -320,6 +321,11 @@ class Lattice:
         out = (C.c_longlong * 2)()
         self._check(self._lib.lbm_nc_bound_check(self._h, out))
         return int(out[0]), int(out[1])
+
+    def selftest_timeout(self) -> int:
+        """Status of the bounded-wait self-test: LBM_ETIMEOUT (-5) when a wait that
+        cannot complete gave up as designed (the context stays usable)."""
+        return int(self._lib.lbm_selftest_timeout(self._h))
 
     def droplets(self):
         """(number of droplets, their node counts in descending order): the

@@ -411,3 +411,23 @@ def test_one_step_full_size_channel_sampled(lbm):
     ga = gr.reshape(19, N)[m][:, nodes].T
     gbb = gb.reshape(19, N)[m][:, nodes].T
     assert np.abs(oa - ga).max() < 1e-6 and np.abs(ob - gbb).max() < 1e-6
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(lbm):
+    # failure detection without a GPU fault: a wait that cannot complete times out,
+    # the host reads LBM_ETIMEOUT, and the same context then steps as if nothing
+    # had happened
+    shape = (16, 16, 32)
+    rr, rb = inputs.paint_droplets(shape, [(16.0, 8.0, 8.0, 5.0)])
+    a = lbm.Lattice(lbm.make_params(32, 16, 16, sigma=0.01))
+    b = lbm.Lattice(lbm.make_params(32, 16, 16, sigma=0.01))
+    for g in (a, b):
+        g.set_fields(rr, rb)
+        g.step(5)
+    assert a.selftest_timeout() == -5
+    for g in (a, b):
+        g.step(5)
+    fa, fb = a.get_pops(), b.get_pops()
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+    a.close()
+    b.close()
