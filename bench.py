@@ -5,7 +5,7 @@ bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigm
 0.02, beta = 0.7, near-contact force A = 0.01 within 3 lu, g_x = 1e-6, FP32 storage.
 One step = one lattice update of every node (one launch of the fused kernel).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16|fp32_q5]
                   [--impl ours|reference] [--model colour|shan_chen] [--no-serving]
                   [--no-models] [--no-cpu-baseline]
 
@@ -15,7 +15,8 @@ buffers (set fields from pinned host memory, K steps, fields back to the host);
 ``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations
 per node, read once and written once) to the measured HBM bandwidth;
 ``fp16_store`` repeats the device-resident measurement with FP16 deviation
-storage; ``serving`` runs the served request stream (256 droplet / sheared-droplet
+storage and ``fp32_q5_store`` with the reduced FP32 form (19 totals and 5 recolouring
+coefficients per node, 2 x 24 x 4 bytes per node and step); ``serving`` runs the served request stream (256 droplet / sheared-droplet
 runs of edge 32-128, Poisson arrivals at 50/s, FP16 storage) through the serving
 engine and reports p50/p99 latency beside aggregate GLUPS; ``shan_chen`` and
 ``sheared_bijel`` give the device-resident GLUPS of the Shan-Chen model on the same
@@ -55,6 +56,14 @@ def kernel_source_hash() -> str:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
+
+
+def bytes_per_node(storage: str) -> int:
+    """Algorithmic HBM bytes of one node and step: every stored value read once and
+    written once (2 x 2Q values, or 2 x (Q + 5) in the reduced FP32 form)."""
+    if storage == "fp32_q5":
+        return 2 * (Q + 5) * 4
+    return 2 * Q * C * (4 if storage == "fp32" else 2)
 
 
 def measured_traffic(storage: str):
@@ -354,8 +363,7 @@ def run_ours(args):
     d2h = 6 * N * 8
 
     # ---- roofline of the step kernel
-    elem = 4 if args.storage == "fp32" else 2
-    alg_bytes = 2 * Q * C * elem * N
+    alg_bytes = bytes_per_node(args.storage) * N
     k_avg = statistics.mean(kern_ms) * 1e-3
     achieved = alg_bytes / k_avg / 1e9
     peak, peak_kind = peaks()
@@ -366,7 +374,7 @@ def run_ours(args):
     launches = args.steps * lat.launches_per_step
     lat.close()
     # the same workload with FP16 deviation storage (device-resident, as `value`)
-    fp16 = None
+    fp16 = q5 = None
     if args.storage == "fp32":
         g16, ms16, k16 = device_resident_glups(lbm, w, "fp16", args.steps, args.warmup, stream, local)
         g16 = replicas.sum_over_ranks(g16, dist if world > 1 else None, f"cuda:{local}")
@@ -374,6 +382,15 @@ def run_ours(args):
         fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
                 "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
                 "algorithmic_bytes_per_launch": alg16}
+        # and with the reduced FP32 form (Q + 5 values per node), against its own
+        # byte model of 192 bytes per node and step
+        g5, ms5, k5 = device_resident_glups(lbm, w, "fp32_q5", args.steps, args.warmup, stream,
+                                            local)
+        g5 = replicas.sum_over_ranks(g5, dist if world > 1 else None, f"cuda:{local}")
+        alg5 = bytes_per_node("fp32_q5") * N
+        q5 = {"value": g5, "unit": "GLUPS", "ms_per_step": ms5, "kernel_ms": k5,
+              "roofline_frac": alg5 / (k5 * 1e-3) / 1e9 / peaks()[0],
+              "algorithmic_bytes_per_launch": alg5, "traffic": measured_traffic("fp32_q5")}
     others = None
     if not args.no_models:
         others = other_workloads(lbm, stream, local)
@@ -396,7 +413,7 @@ def run_ours(args):
             "config": {"workload": workload_name(args), "nodes": N, "storage": args.storage,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
-                             % (2 * Q * C * elem * N / 2 / 1e6)},
+                             % (bytes_per_node(args.storage) * N / 2 / 1e6)},
             "e2e": {"value": e2e, "unit": "GLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "job": "set_fields(host) + K steps + get_fields(host)"},
@@ -414,6 +431,8 @@ def run_ours(args):
         }
         if fp16:
             line["fp16_store"] = fp16
+        if q5:
+            line["fp32_q5_store"] = q5
         if others:
             line.update(others)
         if serving_rep:
@@ -430,7 +449,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp32_q5"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -58,11 +58,25 @@ typedef enum {
  * w_i rho0 (1 + s_k phi)/2 (s_r = +1, s_b = -1), where phi is the colour field of
  * the node that wrote the population, in the step that wrote it: the species'
  * share of the reference rest population w_i rho0 of the total population:
- * the total deviation f_i - w_i rho0 split between the species by colour.      */
+ * the total deviation f_i - w_i rho0 split between the species by colour.
+ *
+ * LBM_STORE_FP32_Q5 is an exact reduced FP32 form of the colour-gradient state:
+ * Q + 5 values per node instead of 2Q (192 instead of 304 bytes moved per node and
+ * step). After recolouring, the two species' populations of a node are
+ *   f^r_i = kappa_r f_i + w_i (c_i . m)/|c_i|,  f^b_i = kappa_b f_i - w_i (c_i . m)/|c_i|,
+ * f_i = f^r_i + f^b_i, kappa_k = rho_k/rho, m = beta (rho_r rho_b/rho) n with n the
+ * unit colour gradient (m = 0 where the gradient vanishes). The form stores the 19
+ * totals f_i and (kappa_r, kappa_b, m); each streamed population is split with the
+ * coefficients of the node it comes from. The Shan-Chen model is refused with it
+ * (its species do not share one population). lbm_get_pops returns the rebuilt
+ * species populations; lbm_set_pops stores a split of the recoloured form exactly
+ * and projects any other split onto that form (kappa_k from the species sums, m
+ * from the first moment of f^r_i - kappa_r f_i).                                   */
 typedef enum {
     LBM_STORE_FP32 = 0,
     LBM_STORE_FP16_DEV = 1,
-    LBM_STORE_BF16_DEV = 2
+    LBM_STORE_BF16_DEV = 2,
+    LBM_STORE_FP32_Q5 = 3
 } lbm_storage;
 
 /* Binary-mixture model (Sec. "Multi-component flows"). LBM_MODEL_COLOUR: the

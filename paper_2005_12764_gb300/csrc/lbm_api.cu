@@ -76,9 +76,21 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
             const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
             const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
             const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-            const float hw = wgt(i) * ref_half;
-            St::store(f, (size_t)i * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
-            St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
+            if constexpr (St::RED) {
+                St::store(f, (size_t)i * P + q, (float)((rr + rb) * e), 0.0f);
+            } else {
+                const float hw = wgt(i) * ref_half;
+                St::store(f, (size_t)i * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
+                St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
+            }
+        }
+        if constexpr (St::RED) {
+            // f^eq is linear in the density: f^eq(rho_k, u) = (rho_k / rho) f^eq(rho, u),
+            // the reduced form with kappa_k = rho_k / rho and m = 0
+            const double rho = rr + rb;
+            St::store(f, (size_t)Q * P + q, (float)(rr / rho), 0.0f);
+            St::store(f, (size_t)(Q + 1) * P + q, (float)(rb / rho), 0.0f);
+            for (int k = 2; k < Q5_AUX; ++k) St::store(f, (size_t)(Q + k) * P + q, 0.0f, 0.0f);
         }
         phi0[n] = ph;
         phi1[n] = ph;
@@ -92,10 +104,27 @@ __device__ inline float ldpop(const typename St::T* f, size_t idx, int i, int k,
                               float ph) {
     return St::load(f, idx, dev_ref(wgt(i) * ref_half, ph, k));
 }
-// Current colour field of node n as the deviation references need it (0 for FP32).
+// Both species' populations of direction i at padded index q (P = elements per
+// block): stored as such, or in the reduced form rebuilt from the total and the
+// node's recolouring coefficients.
+template <class St>
+__device__ inline void ldpair(const typename St::T* f, size_t P, size_t q, int i, float ref_half,
+                              float ph, float& a, float& b) {
+    if constexpr (St::RED) {
+        const float t = __ldg(f + (size_t)i * P + q);
+        const float sh = q5_share(i, __ldg(f + (size_t)(Q + 2) * P + q),
+                                  __ldg(f + (size_t)(Q + 3) * P + q), __ldg(f + (size_t)(Q + 4) * P + q));
+        a = __fmaf_rn(__ldg(f + (size_t)Q * P + q), t, sh);
+        b = __fmaf_rn(__ldg(f + (size_t)(Q + 1) * P + q), t, -sh);
+    } else {
+        a = ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
+        b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
+    }
+}
+// Current colour field of node n as the deviation references need it (0 otherwise).
 template <class St>
 __device__ inline float ref_phi(const float* phi_cur, size_t n) {
-    return St::kind != 0 ? phi_cur[n] : 0.0f;
+    return St::DEV ? phi_cur[n] : 0.0f;
 }
 
 // Fields of the current state. rho_k = sum_i f_i^k of the stored (post-collision)
@@ -114,8 +143,8 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
         float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float a = ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
-            const float b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
+            float a, b;
+            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
             rr += a;
             rb += b;
             jx += cx(i) * (a + b);
@@ -175,8 +204,10 @@ __global__ void densities_kernel(const typename St::T* f, StepParams sp, const f
         float rr = 0.f, rb = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            rr += ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
-            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
+            float a, b;
+            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
+            rr += a;
+            rb += b;
         }
         rho[n] = rr;
         rho[N + n] = rb;
@@ -193,8 +224,10 @@ __global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, const
         const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            fr[(size_t)i * N + n] = ldpop<St>(f, (size_t)i * P + q, i, 0, sp.ref_half, ph);
-            fb[(size_t)i * N + n] = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, sp.ref_half, ph);
+            float a, b;
+            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
+            fr[(size_t)i * N + n] = a;
+            fb[(size_t)i * N + n] = b;
         }
     }
 }
@@ -215,8 +248,10 @@ __global__ void window_kernel(const typename St::T* f, StepParams sp, const floa
         const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int d = 0; d < Q; ++d) {
-            out[(size_t)d * M + m] = ldpop<St>(f, (size_t)d * P + q, d, 0, sp.ref_half, ph);
-            out[(size_t)(Q + d) * M + m] = ldpop<St>(f, (size_t)(Q + d) * P + q, d, 1, sp.ref_half, ph);
+            float a, b;
+            ldpair<St>(f, P, q, d, sp.ref_half, ph, a, b);
+            out[(size_t)d * M + m] = a;
+            out[(size_t)(Q + d) * M + m] = b;
         }
         out[(size_t)2 * Q * M + m] = phi_cur[n];
     }
@@ -230,11 +265,40 @@ __global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const float
          n += (size_t)gridDim.x * blockDim.x) {
         const size_t q = node_pidx(sp, n);
         const float ph = ref_phi<St>(phi_cur, n);
+        if constexpr (St::RED) {
+            // reduced form: totals, kappa_k = rho_k / rho, and m from the first moment
+            // of the red excess d_i = f^r_i - kappa_r f_i: with d_i = w_i (c_i . m)/|c_i|,
+            // sum_i d_i c_i = m sum_i (w_i/|c_i|) c_i c_i = m (1 + sqrt 2)/9. Exact for
+            // every recoloured split (all states the step produces); other splits are
+            // projected onto that form.
+            double rr = 0, rb = 0;
+            for (int i = 0; i < Q; ++i) {
+                rr += fr[(size_t)i * N + n];
+                rb += fb[(size_t)i * N + n];
+            }
+            const double kr = rr / (rr + rb), kb = rb / (rr + rb);
+            double mx = 0, my = 0, mz = 0;
+            for (int i = 0; i < Q; ++i) {
+                const double a = fr[(size_t)i * N + n], t = a + fb[(size_t)i * N + n];
+                const double d = a - kr * t;
+                mx += cx(i) * d;
+                my += cy(i) * d;
+                mz += cz(i) * d;
+                St::store(f, (size_t)i * P + q, (float)t, 0.0f);
+            }
+            const double inv = 9.0 / (1.0 + sqrt(2.0));
+            St::store(f, (size_t)Q * P + q, (float)kr, 0.0f);
+            St::store(f, (size_t)(Q + 1) * P + q, (float)kb, 0.0f);
+            St::store(f, (size_t)(Q + 2) * P + q, (float)(mx * inv), 0.0f);
+            St::store(f, (size_t)(Q + 3) * P + q, (float)(my * inv), 0.0f);
+            St::store(f, (size_t)(Q + 4) * P + q, (float)(mz * inv), 0.0f);
+        } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float hw = wgt(i) * sp.ref_half;
-            St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], dev_ref(hw, ph, 0));
-            St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], dev_ref(hw, ph, 1));
+            for (int i = 0; i < Q; ++i) {
+                const float hw = wgt(i) * sp.ref_half;
+                St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], dev_ref(hw, ph, 0));
+                St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], dev_ref(hw, ph, 1));
+            }
         }
     }
 }
@@ -295,8 +359,9 @@ __global__ void totals_kernel(const typename St::T* f, StepParams sp, const floa
         const float ph = ref_phi<St>(phi_cur, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double a = ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
-            const double b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
+            float af, bf;
+            ldpair<St>(f, P, q, i, ref_half, ph, af, bf);
+            const double a = af, b = bf;
             v[0] += a;
             v[1] += b;
             v[2] += cx(i) * (a + b);
@@ -321,8 +386,10 @@ __global__ void volume_kernel(const typename St::T* f, StepParams sp, const floa
         double rr = 0, rb = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            rr += ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
-            rb += ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
+            float a, b;
+            ldpair<St>(f, P, q, i, ref_half, ph, a, b);
+            rr += a;
+            rb += b;
         }
         v[0] += 0.5 * (1.0 + (rr - rb) / (rr + rb));
     }
@@ -354,9 +421,11 @@ __global__ void pressure_kernel(const typename St::T* f, lbm_params p, StepParam
             const float ph = ref_phi<St>(phi_cur, n);
             double rho = 0;
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                rho += (double)ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph) +
-                       (double)ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
+            for (int i = 0; i < Q; ++i) {
+                float a, b;
+                ldpair<St>(f, P, q, i, ref_half, ph, a, b);
+                rho += (double)a + (double)b;
+            }
             if (r < R - 3.0) {
                 v[0] += rho / 3.0;
                 v[1] += 1;
@@ -409,7 +478,12 @@ int grid_for(size_t n, int num_sms) {
 }  // namespace
 
 // ---------------------------------------------------------------- helpers
-static size_t elem_bytes(int storage) { return storage == 0 ? 4 : 2; }
+static size_t elem_bytes(int storage) { return (storage == 0 || storage == 3) ? 4 : 2; }
+// Population blocks per copy: stored (2Q, or the reduced form's Q totals and five
+// coefficient blocks) and streamed (loaded by the step kernel's tensor copies, with
+// ghost copies on periodic axes).
+static int stored_blocks(int storage) { return storage == 3 ? Q + Q5_AUX : 2 * Q; }
+static int streamed_blocks(int storage) { return storage == 3 ? Q : 2 * Q; }
 
 // Padded population layout: two ghost columns left and right of each row, the row
 // length a multiple of 16 bytes (TMA alignment); two ghost rows above and below.
@@ -440,13 +514,14 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     double hcut = p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min;
     if (p->A_nc > 0.0 && !(hcut > p->h_min)) { why = "h_cut must exceed h_min"; return LBM_EINVAL; }
     if (p->A_nc > 0.0 && hcut > 9.0) { why = "h_cut must be <= 9 (film rays of at most 25 samples)"; return LBM_EINVAL; }
-    if (p->storage < 0 || p->storage > 2) { why = "unknown storage"; return LBM_EINVAL; }
+    if (p->storage < 0 || p->storage > 3) { why = "unknown storage"; return LBM_EINVAL; }
     if (!(std::fabs(p->wall_u) < 0.3)) { why = "|wall_u| must be < 0.3"; return LBM_EINVAL; }
     if (p->wall_u != 0.0 && !p->wall_y) { why = "wall_u needs walls at the y extremes (wall_y)"; return LBM_EINVAL; }
     if (p->model != 0 && p->model != 1) { why = "unknown model"; return LBM_EINVAL; }
     if (p->model == 1 && p->A_nc != 0.0) { why = "the near-contact force belongs to the colour-gradient model"; return LBM_EINVAL; }
+    if (p->model == 1 && p->storage == 3) { why = "the reduced storage form holds recoloured (colour-gradient) states only"; return LBM_EINVAL; }
     if (!std::isfinite(p->G_sc)) { why = "G_sc must be finite"; return LBM_EINVAL; }
-    if ((p->storage != 0) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
+    if ((p->storage == 1 || p->storage == 2) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     return LBM_OK;
@@ -463,7 +538,8 @@ extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     if (!p) return 0;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     const PadLayout L = pad_layout(*p);
-    size_t b = 2 * 2 * Q * L.P * elem_bytes(p->storage) + 2 * N * sizeof(float) + p->ny * sizeof(float);
+    size_t b = 2 * (size_t)stored_blocks(p->storage) * L.P * elem_bytes(p->storage) +
+               2 * N * sizeof(float) + p->ny * sizeof(float);
     if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int4)) + 3 * nc_pos_bytes(*p);
     return b;
 }
@@ -493,6 +569,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.pitch = c->pitch;
     s.nyp = c->nyp;
     s.padx = c->padx;
+    s.ghost_arrays = streamed_blocks(p.storage);
     s.plane_p = (size_t)c->pitch * c->nyp;
     s.P = c->P;
     s.wall_y = p.wall_y ? 1 : 0;
@@ -511,7 +588,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.ah_b3 = (float)b3;
     s.ah_inv = (float)(1.0 / (1.0 - b3));
     s.nsamp = (int)std::floor(2.0 * (hcut + 3.0)) + 1;
-    s.ref_half = p.storage == 0 ? 0.0f : (float)(0.5 * p.rho0);
+    s.ref_half = (p.storage == 1 || p.storage == 2) ? (float)(0.5 * p.rho0) : 0.0f;
     const int tx = step_tile_x(), ty = step_tile_y();
     s.tiles_x = (p.nx + tx - 1) / tx;
     s.tiles_y = (p.ny + ty - 1) / ty;
@@ -636,7 +713,7 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->nyp = L.nyp;
     c->padx = L.padx;
     c->P = L.P;
-    const size_t pop_bytes = 2 * Q * c->P * c->elem;
+    const size_t pop_bytes = (size_t)stored_blocks(p->storage) * c->P * c->elem;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMalloc(ptr, bytes) == cudaSuccess;
     };
@@ -686,8 +763,9 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
     }
-    // TMA descriptors of the two population copies: 4-D [38][nz][nyp][pitch], boxes of
-    // BW x (TY+2) x 1 x 1 elements, zero fill outside
+    // TMA descriptors of the two population copies: 4-D [blocks][nz][nyp][pitch], boxes
+    // of BW x (TY+2) x 1 x 1 elements, zero fill outside; loads cover the streamed
+    // blocks, stores every stored block
     {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -698,18 +776,18 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         }
         auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
         const cuuint64_t dims[4] = {(cuuint64_t)c->pitch, (cuuint64_t)c->nyp, (cuuint64_t)p->nz,
-                                    (cuuint64_t)(2 * Q)};
+                                    (cuuint64_t)streamed_blocks(p->storage)};
         const cuuint64_t strides[3] = {(cuuint64_t)c->pitch * c->elem,
                                        (cuuint64_t)c->pitch * c->nyp * c->elem,
                                        (cuuint64_t)c->P * c->elem};
         const cuuint32_t box[4] = {(cuuint32_t)step_box_width(p->storage), (cuuint32_t)step_box_rows(), 1, 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
-        const CUtensorMapDataType dt = p->storage == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+        const CUtensorMapDataType dt = c->elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT16;
         // store maps end at the interior (x < nx, y < ny), so the tile stores of edge
         // tiles are clipped there and never touch ghost or padding cells
         const cuuint64_t sdims[4] = {(cuuint64_t)(c->padx + p->nx), (cuuint64_t)(2 + p->ny),
-                                     (cuuint64_t)p->nz, (cuuint64_t)(2 * Q)};
+                                     (cuuint64_t)p->nz, (cuuint64_t)stored_blocks(p->storage)};
         const cuuint32_t sbox[4] = {(cuuint32_t)step_tile_x(), (cuuint32_t)step_tile_y(), 1, 1};
         for (int b = 0; b < 2; ++b) {
             CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr,
@@ -784,7 +862,8 @@ template <class F>
 static void dispatch(int storage, F&& fn) {
     if (storage == 0) fn(StoreF32{});
     else if (storage == 1) fn(StoreF16{});
-    else fn(StoreBF16{});
+    else if (storage == 2) fn(StoreBF16{});
+    else fn(StoreQ5{});
 }
 
 extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const double* rho_b,
@@ -1270,14 +1349,15 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
 
 extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
     if (!c) return 0;
-    return 2 * Q * c->P * c->elem + 2 * c->N * sizeof(float) + sizeof(long long);
+    return (size_t)stored_blocks(c->p.storage) * c->P * c->elem + 2 * c->N * sizeof(float) +
+           sizeof(long long);
 }
 
 extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
     if (!c || !host_buf) return LBM_EINVAL;
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
     char* b = (char*)host_buf;
-    const size_t pb = 2 * Q * c->P * c->elem, fb = c->N * sizeof(float);
+    const size_t pb = (size_t)stored_blocks(c->p.storage) * c->P * c->elem, fb = c->N * sizeof(float);
     CK(c, cudaMemcpyAsync(b, c->f[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(b + pb, c->phi[c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(b + pb + fb, c->phi[1 - c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
@@ -1289,7 +1369,7 @@ extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
 extern "C" lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf) {
     if (!c || !host_buf) return LBM_EINVAL;
     const char* b = (const char*)host_buf;
-    const size_t pb = 2 * Q * c->P * c->elem, fb = c->N * sizeof(float);
+    const size_t pb = (size_t)stored_blocks(c->p.storage) * c->P * c->elem, fb = c->N * sizeof(float);
     c->cur = 0;
     c->pc = 0;
     CK(c, cudaMemcpyAsync(c->f[0], b, pb, cudaMemcpyHostToDevice, c->stream));

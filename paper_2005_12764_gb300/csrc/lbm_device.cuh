@@ -64,9 +64,12 @@ __device__ __forceinline__ float dev_ref(float hw, float phi, int k) {
     return k == 0 ? __fmaf_rn(hw, phi, hw) : __fmaf_rn(-hw, phi, hw);
 }
 
+// Each format says whether it stores deviations (DEV) and whether it is the reduced
+// form below (RED).
 struct StoreF32 {
     using T = float;
     static constexpr int kind = 0;
+    static constexpr bool DEV = false, RED = false;
     __device__ __forceinline__ static float load(const T* p, size_t i, float) { return __ldg(p + i); }
     __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
     __device__ __forceinline__ static float cvt(T v, float) { return v; }
@@ -75,6 +78,7 @@ struct StoreF32 {
 struct StoreF16 {
     using T = __half;
     static constexpr int kind = 1;
+    static constexpr bool DEV = true, RED = false;
     __device__ __forceinline__ static float load(const T* p, size_t i, float ref) {
         return __half2float(__ldg(p + i)) + ref;
     }
@@ -87,6 +91,7 @@ struct StoreF16 {
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static constexpr int kind = 2;
+    static constexpr bool DEV = true, RED = false;
     __device__ __forceinline__ static float load(const T* p, size_t i, float ref) {
         return __bfloat162float(__ldg(p + i)) + ref;
     }
@@ -96,6 +101,34 @@ struct StoreBF16 {
     __device__ __forceinline__ static float cvt(T v, float ref) { return __bfloat162float(v) + ref; }
     __device__ __forceinline__ static T enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
 };
+// Reduced FP32 form, Q + 5 arrays instead of 2Q. The recoloured post-collision
+// populations of a node are, per direction,
+//   f^r_i = kappa_r f_i + w_i (c_i . m) / |c_i|,   f^b_i = kappa_b f_i - w_i (c_i . m) / |c_i|,
+// with f_i their sum, kappa_k = rho_k / rho and m = beta (rho_r rho_b / rho) n (n the
+// unit colour gradient, m = 0 where it is undefined). So the total f_i (arrays
+// 0 .. Q-1) and the five numbers kappa_r, kappa_b, m_x, m_y, m_z of the node that
+// wrote them (arrays Q .. Q+4) determine both species exactly; the pull rebuilds
+// each species from the coefficients of the population's source node. (The five
+// arrays hold the node's own coefficients: they are read in place, not streamed.)
+struct StoreQ5 {
+    using T = float;
+    static constexpr int kind = 3;
+    static constexpr bool DEV = false, RED = true;
+    __device__ __forceinline__ static float load(const T* p, size_t i, float) { return __ldg(p + i); }
+    __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
+    __device__ __forceinline__ static float cvt(T v, float) { return v; }
+    __device__ __forceinline__ static T enc(float v, float) { return v; }
+};
+constexpr int Q5_AUX = 5;   // kappa_r, kappa_b, m_x, m_y, m_z
+// Recolouring share w_i (c_i . m) / |c_i| of direction i (0 for the rest direction).
+__device__ __forceinline__ float q5_share(int i, float mx, float my, float mz) {
+    if (csq(i) == 0) return 0.0f;
+    float d = 0.0f;
+    if (cx(i)) d = cx(i) > 0 ? mx : -mx;
+    if (cy(i)) d += cy(i) > 0 ? my : -my;
+    if (cz(i)) d += cz(i) > 0 ? mz : -mz;
+    return (wgt(i) * inv_clen(i)) * d;
+}
 
 // ---------------------------------------------------------------- parameters
 struct StepParams {
@@ -130,6 +163,8 @@ struct StepParams {
     // interior starts padx columns in, 32 bytes), row pitch a multiple of 32 bytes;
     // one [nz][nyp][pitch] block per species/direction
     int pitch, nyp, padx;
+    int ghost_arrays;       // blocks with ghost copies (the streamed ones): 2Q, or Q for the
+                            // reduced form, whose coefficient blocks follow them
     size_t plane_p, P;      // pitch * nyp, plane_p * nz
     int wall_y, wall_z;
     int var_tau;            // 0: omega0 everywhere; 1: mixture rule per node
@@ -578,14 +613,20 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
             si += om1 * ((f[i] - wr) - (qs + qa));
             so += om1 * ((f[o] - wr) - (qs - qa));
         }
-        const float sg = (face ? sg_f : sg_e) * cn;
-        const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
-        const float hw = wgt(i) * refh;
-        const float rf_r = dev_ref(hw, phi, 0), rf_b = dev_ref(hw, phi, 1);
-        emit(i, wrr + (ar * si + sg), rf_r);
-        emit(o, wrr + (ar * so - sg), rf_r);
-        emit(Q + i, wrb + (ab * si - sg), rf_b);
-        emit(Q + o, wrb + (ab * so + sg), rf_b);
+        if constexpr (St::RED) {
+            // reduced form: the total; the species split goes with the coefficients
+            emit(i, wr + si, 0.0f);
+            emit(o, wr + so, 0.0f);
+        } else {
+            const float sg = (face ? sg_f : sg_e) * cn;
+            const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
+            const float hw = wgt(i) * refh;
+            const float rf_r = dev_ref(hw, phi, 0), rf_b = dev_ref(hw, phi, 1);
+            emit(i, wrr + (ar * si + sg), rf_r);
+            emit(o, wrr + (ar * so - sg), rf_r);
+            emit(Q + i, wrb + (ab * si - sg), rf_b);
+            emit(Q + o, wrb + (ab * so + sg), rf_b);
+        }
     }
     {
         constexpr int i = 9;
@@ -593,9 +634,23 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         const float wr = w * rho;
         float si = -wr * U15 - 2.0f * pert_sum;
         if (!UnitOmega) si += om1 * ((f[i] - wr) + wr * usq15);
-        const float hw = w * refh;
-        emit(i, w * rr + ar * si, dev_ref(hw, phi, 0));
-        emit(Q + i, w * rb + ab * si, dev_ref(hw, phi, 1));
+        if constexpr (St::RED) {
+            emit(i, wr + si, 0.0f);
+        } else {
+            const float hw = w * refh;
+            emit(i, w * rr + ar * si, dev_ref(hw, phi, 0));
+            emit(Q + i, w * rb + ab * si, dev_ref(hw, phi, 1));
+        }
+    }
+    if constexpr (St::RED) {
+        // recolouring coefficients: kappa_r, kappa_b and m = seg0 G / |G| (the
+        // recolouring term of direction i is then w_i (c_i . m) / |c_i|)
+        const float mg = seg0 * inv_g;
+        emit(Q, ar, 0.0f);
+        emit(Q + 1, ab, 0.0f);
+        emit(Q + 2, mg * Gx, 0.0f);
+        emit(Q + 3, mg * Gy, 0.0f);
+        emit(Q + 4, mg * Gz, 0.0f);
     }
 }
 

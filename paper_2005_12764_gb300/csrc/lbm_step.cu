@@ -25,6 +25,13 @@
 // global memory. The collision writes the plane's outputs to a shared output tile
 // that one thread stores with 38 TMA tensor copies.
 //
+// Reduced form (Q + 5 blocks: the 19 total populations, then the five recolouring
+// coefficients of the node that wrote them): only the totals are staged by tensor
+// copies; the coefficients of the (TX+4) x (TY+4) source columns of each plane go to
+// a 4-slot ring with plain loads, and each pulled total is split into the two
+// species with the coefficients of its source node. The output tile has Q + 5
+// blocks.
+//
 // Work split, two modes.
 // Part mode (lattices of more tiles than the GPU holds CTAs at once): z is cut into
 // `zparts` equal parts and every CTA marches one part of one tile. CTAs are numbered
@@ -66,17 +73,25 @@ struct Geo {
     static constexpr int BOX_BYTES = BW * SH * (int)sizeof(T);
     static constexpr int IK_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int IKS = IK_BYTES / (int)sizeof(T);             // elements per box slot
-    static constexpr size_t STAGE_BYTES = (size_t)2 * Q * IK_BYTES;
+    // streamed blocks (staged per plane) and stored blocks (output tile): 2Q, or for
+    // the reduced form the Q totals and Q + 5 with the recolouring coefficients
+    static constexpr bool RED = St::RED;
+    static constexpr int NL = RED ? Q : 2 * Q;
+    static constexpr int NS = RED ? Q + Q5_AUX : 2 * Q;
+    static constexpr size_t STAGE_BYTES = (size_t)NL * IK_BYTES;
     // 4-slot ring per plane (tile + ring nodes): the colour field, or for the
     // Shan-Chen model the two species densities
     static constexpr size_t PHI_BYTES = (SC ? 2 : 1) * 4 * SH * SWP * sizeof(float);
     // deviation storage: 4-slot ring of the lagged colour field, (TX+4) x (TY+4) per
     // plane (the sources of the tile and its ring), which decodes the pulled values
-    static constexpr bool DEV = St::kind != 0;
+    // reduced form: the same ring holds the five recolouring coefficients of every
+    // source node, [slot][5][TY+4][TX+4]
+    static constexpr bool DEV = St::DEV;
     static constexpr int LW = TX + 4, LH = TY + 4;
-    static constexpr size_t LAG_BYTES = DEV ? 4 * LH * LW * sizeof(float) : 0;
-    // output tile of a plane, [2Q][TY][TX], stored by tensor copies
-    static constexpr size_t OUT_BYTES = (size_t)2 * Q * TX * TY * sizeof(T);
+    static constexpr size_t LAG_BYTES = DEV ? 4 * LH * LW * sizeof(float)
+                                        : (RED ? 4 * Q5_AUX * LH * LW * sizeof(float) : 0);
+    // output tile of a plane, [NS][TY][TX], stored by tensor copies
+    static constexpr size_t OUT_BYTES = (size_t)NS * TX * TY * sizeof(T);
     static constexpr int STAGES = 1;   // staged planes per CTA
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + OUT_BYTES + PHI_BYTES + LAG_BYTES +
                                    2 * sizeof(unsigned long long);
@@ -183,6 +198,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
     using T = typename St::T;
     using G = Geo<St, SC>;
     constexpr int BW = G::BW, IKS = G::IKS, PADX = G::PADX, HALO = G::HALO, STAGES = G::STAGES;
+    static_assert(!(SC && St::RED), "the reduced form holds recoloured populations only");
+    // a ring of source-node data per plane: the lagged colour field (deviation
+    // storage) or the recolouring coefficients (reduced form)
+    constexpr bool RING = G::DEV || G::RED;
     extern __shared__ __align__(128) unsigned char smem[];
     T* stage0 = reinterpret_cast<T*>(smem);
     T* sout = reinterpret_cast<T*>(smem + STAGES * G::STAGE_BYTES);           // [2Q][TY][TX]
@@ -198,8 +217,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
     const size_t plane = (size_t)p.nx * p.ny;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 2 * Q);   // one arrival per (species, direction) box
-        mbar_init(&bars[1], 2 * Q);
+        mbar_init(&bars[0], G::NL);   // one arrival per staged box
+        mbar_init(&bars[1], G::NL);
         fence_mbar_init();
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(fin_map)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(fout_map)) : "memory");
@@ -281,14 +300,14 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
 
         // ---- staging of plane pl into buffer b: one box per species and direction,
         // taken from source plane pl - c_iz
-        // threads 0..37 each issue the box of one (species, direction) and arrive on
+        // threads 0..NL-1 each issue the box of one (species, direction) and arrive on
         // the barrier (with 0 bytes if the box is not needed)
-        const int my_ik = tid < 2 * Q ? tid : -1;
+        const int my_ik = tid < G::NL ? tid : -1;
         const int my_i = my_ik < Q ? my_ik : my_ik - Q;
         const int my_cy = my_ik >= 0 ? cy(my_i) : 0, my_cz = my_ik >= 0 ? cz(my_i) : 0;
         auto issue = [&](int b, int pl) {
             if (my_ik < 0) return;
-            T* st = stage0 + (size_t)b * (2 * Q * IKS);
+            T* st = stage0 + (size_t)b * (G::NL * IKS);
             const int zs0 = pl - my_cz;
             const bool need = !failed && (!p.wall_z || (pl >= 0 && pl < p.nz)) &&
                               !(p.wall_z && (zs0 < 0 || zs0 >= p.nz));
@@ -311,12 +330,58 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         auto lag_at = [&](int sl, int tx, int ty) -> float& {
             return slag[(sl * G::LH + ty + 2) * G::LW + tx + 2];
         };
+        // reduced form: the five recolouring coefficients (k = 0 .. 4) of source column
+        // (tx, ty) in ring slot sl
+        constexpr int LN = G::LW * G::LH;
+        auto aux_at = [&](int sl, int k, int tx, int ty) -> float& {
+            return slag[((sl * Q5_AUX + k) * G::LH + ty + 2) * G::LW + tx + 2];
+        };
+        // ---- reduced form: pull of the totals of node (tx, ty) of plane pl (wrapped; sc
+        // = ring slot of the unwrapped plane) from staged buffer b, and the species
+        // densities rebuilt from the coefficients of each population's source node: the
+        // node x - c_i, or for a link bounced back at a wall the node itself, whose
+        // population of the opposite direction carries the opposite share
+        auto pull_red = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
+                            float& rb) {
+            const T* st = stage0 + (size_t)b * (G::NL * IKS) + (size_t)(ty + 1) * BW + (tx + HALO);
+            const int gy = y0 + ty;
+            const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
+            const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = st[(size_t)i * IKS - cx(i)];
+            float sr = 0.f, sb = 0.f, d = 0.f;
+            if (!(ylo || yhi || zlo || zhi)) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float* a = &aux_at((sc - cz(i)) & 3, 0, tx - cx(i), ty - cy(i));
+                    sr = __fmaf_rn(a[0], ft[i], sr);
+                    sb = __fmaf_rn(a[LN], ft[i], sb);
+                    d += q5_share(i, a[2 * LN], a[3 * LN], a[4 * LN]);
+                }
+            } else {
+                const size_t self = pidx(p.pitch, p.nyp, PADX, wrap_near(x0 + tx, p.nx), gy, pl);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
+                                     (cz(i) > 0 && zlo) || (cz(i) < 0 && zhi);
+                    if (out) ft[i] = __ldg(fin + (size_t)opp(i) * p.P + self);
+                    const float* a = out ? &aux_at(sc, 0, tx, ty)
+                                         : &aux_at((sc - cz(i)) & 3, 0, tx - cx(i), ty - cy(i));
+                    sr = __fmaf_rn(a[0], ft[i], sr);
+                    sb = __fmaf_rn(a[LN], ft[i], sb);
+                    const float sh = q5_share(i, a[2 * LN], a[3 * LN], a[4 * LN]);
+                    d += out ? -sh : sh;
+                }
+            }
+            rr = sr + d;
+            rb = sb - d;
+        };
         // ---- pull of the two species' populations of node (tx, ty) of plane pl
         // (wrapped; sc = lag-ring slot of the unwrapped plane) from staged buffer b, and
         // their densities; wall_terms adds the sliding-wall terms per species.
         auto pull_species = [&](int b, int pl, int sc, int tx, int ty, float (&vr)[Q],
                                 float (&vb)[Q], float& rr, float& rb, bool wall_terms) {
-            const T* st = stage0 + (size_t)b * (2 * Q * IKS) + (size_t)(ty + 1) * BW + (tx + HALO);
+            const T* st = stage0 + (size_t)b * (G::NL * IKS) + (size_t)(ty + 1) * BW + (tx + HALO);
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
@@ -374,13 +439,19 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // against the colour field its source node had when it wrote it.
         auto pull = [&](int b, int pl, int sc, int tx, int ty, float (&ft)[Q], float& rr,
                         float& rb, bool keep) {
-            float vr[Q], vb[Q];
-            pull_species(b, pl, sc, tx, ty, vr, vb, rr, rb, false);
+            if constexpr (G::RED) {
+                pull_red(b, pl, sc, tx, ty, ft, rr, rb);
+            } else {
+                float vr[Q], vb[Q];
+                pull_species(b, pl, sc, tx, ty, vr, vb, rr, rb, false);
+                if (keep) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) ft[i] = vr[i] + vb[i];
+                }
+            }
             if (keep) {
                 const int gy = y0 + ty;
                 const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) ft[i] = vr[i] + vb[i];
                 if (p.wall_u6 != 0.0f && (ylo || yhi)) {
                     // sliding y-walls: a link back from a wall moving with (+-U, 0, 0)
                     // gains 6 w_i rho c_ix (+-U) (the sum of the two species' shares
@@ -419,7 +490,6 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // ---- lagged colour field of plane pl (deviation storage): element e of the
         // (TX+4) x (TY+4) box, wrapped on periodic axes, clamped at walls (values
         // beyond a wall are never read: those links bounce back)
-        constexpr int LN = G::LW * G::LH;
         auto lag_load = [&](int pl, int e) -> float {
             if (e >= LN) return 0.0f;
             const int r = e / G::LW, c = e - r * G::LW;
@@ -430,14 +500,47 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             return __ldg(p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
         };
         float lag_reg0 = 0.f, lag_reg1 = 0.f;   // plane fetched ahead of its slot store
+        // reduced form: the coefficients of the same (TX+4) x (TY+4) sources of plane
+        // pl (the step's input, read in place), wrapped and clamped the same way
+        float aux_reg[2][Q5_AUX];
+        auto aux_fetch = [&](int pl) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int e = tid + j * NT;
+                if (e >= LN) break;
+                const int r = e / G::LW, c = e - r * G::LW;
+                const int gx = wrap_near(x0 - 2 + c, p.nx);
+                int gy = y0 - 2 + r, gz = pl;
+                gy = p.wall_y ? min(max(gy, 0), p.ny - 1) : wrap_near(gy, p.ny);
+                gz = p.wall_z ? min(max(gz, 0), p.nz - 1) : wrap_near(gz, p.nz);
+                const size_t q = pidx(p.pitch, p.nyp, PADX, gx, gy, gz);
+#pragma unroll
+                for (int k = 0; k < Q5_AUX; ++k) aux_reg[j][k] = __ldg(fin + (size_t)(Q + k) * p.P + q);
+            }
+        };
         auto lag_fetch = [&](int pl) {
-            lag_reg0 = lag_load(pl, tid);
-            lag_reg1 = lag_load(pl, tid + NT);
+            if constexpr (G::RED) {
+                aux_fetch(pl);
+            } else {
+                lag_reg0 = lag_load(pl, tid);
+                lag_reg1 = lag_load(pl, tid + NT);
+            }
         };
         auto lag_commit = [&](int pl) {
-            float* d = slag + (size_t)slot(pl) * LN;
-            d[tid] = lag_reg0;
-            if (tid + NT < LN) d[tid + NT] = lag_reg1;
+            if constexpr (G::RED) {
+                float* d = slag + (size_t)slot(pl) * (Q5_AUX * LN);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int e = tid + j * NT;
+                    if (e >= LN) break;
+#pragma unroll
+                    for (int k = 0; k < Q5_AUX; ++k) d[k * LN + e] = aux_reg[j][k];
+                }
+            } else {
+                float* d = slag + (size_t)slot(pl) * LN;
+                d[tid] = lag_reg0;
+                if (tid + NT < LN) d[tid + NT] = lag_reg1;
+            }
         };
 
         const int gxn = x0 + otx, gyn = y0 + oty;
@@ -529,7 +632,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 fence_proxy_async();
                 __syncthreads();
                 if (tid == 0) {
-                    for (int k = 0; k < 2 * Q; ++k)
+                    for (int k = 0; k < G::NS; ++k)
                         tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
                     bulk_commit();
                 }
@@ -552,10 +655,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             // lag plane z+3 goes to the slot of plane z-1, last read before the barrier
             // of the previous plane; the densities of z+1 read planes z .. z+2. It is
             // fetched here and stored after those densities, which hide the latency.
-            if (G::DEV) lag_fetch(z + 3);
+            if (RING) lag_fetch(z + 3);
             wait(bn);
             densities(bn, z + 1, nx_f, nx_rr, nx_rb, true);
-            if (G::DEV) lag_commit(z + 3);
+            if (RING) lag_commit(z + 3);
             if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
             __syncthreads();
             fence_proxy_async();
@@ -634,7 +737,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
-                for (int k = 0; k < 2 * Q; ++k)
+                for (int k = 0; k < G::NS; ++k)
                     tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
                 bulk_commit();
             }
@@ -645,9 +748,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         float a_rr = 0.f, a_rb = 0.f, b_rr = 0.f, b_rb = 0.f;
         float ah_c = 0.0f;   // A_h of the plane being collided, loaded one plane ahead
 
-        // ---- lag planes zb-2 .. zb for the densities of zb-1 (each plane z of the march
-        // then stores lag plane z+3 into the slot of z-1), and the copy of plane zb-1
-        if (G::DEV) {
+        // ---- lag (or coefficient) planes zb-2 .. zb for the densities of zb-1 (each
+        // plane z of the march then stores plane z+3 into the slot of z-1), and the
+        // copy of plane zb-1
+        if (RING) {
             for (int q = -2; q <= 0; ++q) {
                 lag_fetch(zb + q);
                 lag_commit(zb + q);
@@ -721,13 +825,15 @@ step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
 //          of elements when nx is even (two elements otherwise);
 //  part 2 (periodic y only), one task per (k, z, ghost row -2, -1, ny, ny+1), lanes
 //          over x = -2 .. nx+1: each element from the wrapped node (corners included).
-// Part 1 has 2Q nz tasks, part 2 2Q nz 4. (Writing the whole 32-byte ghost sectors
-// instead of the pairs measured no faster: the fill waits on its loads.)
+// With K = p.ghost_arrays streamed blocks (2Q, or Q in the reduced form: its
+// coefficient blocks are read in place), part 1 has K nz tasks, part 2 K nz 4.
+// (Writing the whole 32-byte ghost sectors instead of the pairs measured no faster:
+// the fill waits on its loads.)
 __host__ __device__ inline long long ghost_part1(const StepParams& p) {
-    return (long long)2 * Q * p.nz;
+    return (long long)p.ghost_arrays * p.nz;
 }
 __host__ __device__ inline long long ghost_work(const StepParams& p) {
-    return ghost_part1(p) + (p.wall_y ? 0 : (long long)2 * Q * p.nz * 4);
+    return ghost_part1(p) + (p.wall_y ? 0 : (long long)p.ghost_arrays * p.nz * 4);
 }
 
 template <int B> struct PairOf;
@@ -1087,8 +1193,10 @@ cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, 
         p.nc_list = scan_list;
         p.nc_count = scan_count;
     }
+    // (the list kernel touches populations only in the ghost fill, which depends on
+    // the element type alone: the reduced form shares the FP32 instance)
     switch (storage) {
-        case 0: return launch_list<StoreF32>(p, num_sms, s);
+        case 0: case 3: return launch_list<StoreF32>(p, num_sms, s);
         case 1: return launch_list<StoreF16>(p, num_sms, s);
         case 2: return launch_list<StoreBF16>(p, num_sms, s);
     }
@@ -1116,9 +1224,13 @@ template <class St>
 static cudaError_t launch_tpl(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
                               int grid, cudaStream_t s) {
     const bool unit = !p.var_tau && p.omega0 == 1.0f;
-    if (p.model == 1)
-        return unit ? launch_tpl3<St, true, true>(p, map, omap, grid, s)
-                    : launch_tpl3<St, false, true>(p, map, omap, grid, s);
+    if constexpr (St::RED) {
+        if (p.model == 1) return cudaErrorInvalidValue;   // refused when the context is made
+    } else {
+        if (p.model == 1)
+            return unit ? launch_tpl3<St, true, true>(p, map, omap, grid, s)
+                        : launch_tpl3<St, false, true>(p, map, omap, grid, s);
+    }
     return unit ? launch_tpl3<St, true, false>(p, map, omap, grid, s)
                 : launch_tpl3<St, false, false>(p, map, omap, grid, s);
 }
@@ -1129,6 +1241,7 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
         case 0: return launch_tpl<StoreF32>(p, map, omap, grid, s);
         case 1: return launch_tpl<StoreF16>(p, map, omap, grid, s);
         case 2: return launch_tpl<StoreBF16>(p, map, omap, grid, s);
+        case 3: return launch_tpl<StoreQ5>(p, map, omap, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1146,7 +1259,8 @@ static cudaError_t prepare_batched_tpl() {
 }
 
 // Batched kernel of one (storage, relaxation class, model): dispatched over the
-// 12 combinations with a callable that takes the three as template arguments.
+// 14 combinations (the reduced form holds no Shan-Chen state) with a callable that
+// takes the three as template arguments.
 template <class F>
 static cudaError_t batched_dispatch(int storage, bool unit_omega, int model, F&& fn) {
     const bool sc = model == 1;
@@ -1163,6 +1277,8 @@ static cudaError_t batched_dispatch(int storage, bool unit_omega, int model, F&&
         case 9: return fn.template operator()<StoreBF16, false, true>();
         case 10: return fn.template operator()<StoreBF16, true, false>();
         case 11: return fn.template operator()<StoreBF16, true, true>();
+        case 12: return fn.template operator()<StoreQ5, false, false>();
+        case 14: return fn.template operator()<StoreQ5, true, false>();
     }
     return cudaErrorInvalidValue;
 }
@@ -1198,7 +1314,7 @@ cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long ce
     if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     if (blocks < 1) blocks = 1;
     switch (storage) {
-        case 0: ghost_fill_batched<StoreF32><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
+        case 0: case 3: ghost_fill_batched<StoreF32><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
         case 1: ghost_fill_batched<StoreF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
         case 2: ghost_fill_batched<StoreBF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
         default: return cudaErrorInvalidValue;
@@ -1225,7 +1341,7 @@ cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num
     const size_t cap = (size_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     switch (storage) {
-        case 0: return launch_ghost_tpl<StoreF32>(f, p, (unsigned)blocks, threads, s);
+        case 0: case 3: return launch_ghost_tpl<StoreF32>(f, p, (unsigned)blocks, threads, s);
         case 1: return launch_ghost_tpl<StoreF16>(f, p, (unsigned)blocks, threads, s);
         case 2: return launch_ghost_tpl<StoreBF16>(f, p, (unsigned)blocks, threads, s);
     }
@@ -1236,8 +1352,12 @@ cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num
 int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
 int step_box_rows() { return SH; }
-int step_box_width(int storage) { return storage == 0 ? Geo<StoreF32>::BW : Geo<StoreF16>::BW; }
-int step_pad_x(int storage) { return storage == 0 ? Geo<StoreF32>::PADX : Geo<StoreF16>::PADX; }
+int step_box_width(int storage) {
+    return (storage == 0 || storage == 3) ? Geo<StoreF32>::BW : Geo<StoreF16>::BW;
+}
+int step_pad_x(int storage) {
+    return (storage == 0 || storage == 3) ? Geo<StoreF32>::PADX : Geo<StoreF16>::PADX;
+}
 int step_ctas_per_sm() { return CTAS_PER_SM; }
 
 }  // namespace lbm

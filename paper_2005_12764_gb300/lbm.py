@@ -19,7 +19,7 @@ import numpy as np
 from . import build_lib
 
 Q = 19
-STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp32_q5": 3}
 MODELS = {"colour": 0, "shan_chen": 1}
 _STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ESTATE",
            -5: "LBM_ETIMEOUT"}

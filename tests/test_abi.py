@@ -45,3 +45,8 @@ def test_footprint_is_reported_without_a_device():
     assert lbm.footprint_bytes(p) >= 2 * 2 * 19 * N * 4
     p16 = lbm.make_params(256, 128, 64, storage="fp16")
     assert lbm.footprint_bytes(p16) < lbm.footprint_bytes(p)
+    # the reduced FP32 form: Q + 5 blocks per copy instead of 2Q
+    p5 = lbm.make_params(256, 128, 64, storage="fp32_q5")
+    full, red = lbm.footprint_bytes(p), lbm.footprint_bytes(p5)
+    assert 2 * 24 * N * 4 <= red < full
+    assert (full - red) >= 2 * (2 * 19 - 24) * N * 4

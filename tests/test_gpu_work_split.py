@@ -52,7 +52,7 @@ def test_chain_mode_walls_ragged_near_contact_matches_oracle(lbm):
     g.close()
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "fp32_q5"])
 def test_chain_mode_is_bitwise_part_mode(lbm, storage):
     # A sheared 128^3 droplet: lbm_step runs chain mode (64 tiles: 4 bands of 28
     # planes and 16 planes shared by 48 CTAs), the serving engine part mode; every
