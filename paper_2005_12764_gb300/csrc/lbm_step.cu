@@ -330,11 +330,19 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         auto lag_at = [&](int sl, int tx, int ty) -> float& {
             return slag[(sl * G::LH + ty + 2) * G::LW + tx + 2];
         };
-        // reduced form: the five recolouring coefficients (k = 0 .. 4) of source column
-        // (tx, ty) in ring slot sl
+        // reduced form: the recolouring coefficients of source column (tx, ty) in ring
+        // slot sl; a slot holds the pairs (kappa_r, kappa_b) [LN] (one 8-byte load),
+        // then m_x, m_y, m_z [LN] each
         constexpr int LN = G::LW * G::LH;
-        auto aux_at = [&](int sl, int k, int tx, int ty) -> float& {
-            return slag[((sl * Q5_AUX + k) * G::LH + ty + 2) * G::LW + tx + 2];
+        struct Coef {
+            float kr, kb;
+            const float* m;   // m_x; m_y, m_z follow at strides of LN
+        };
+        auto coef_at = [&](int sl, int tx, int ty) -> Coef {
+            const float* b = slag + (size_t)sl * (Q5_AUX * LN);
+            const int idx = (ty + 2) * G::LW + tx + 2;
+            const float2 k = reinterpret_cast<const float2*>(b)[idx];
+            return Coef{k.x, k.y, b + 2 * LN + idx};
         };
         // ---- reduced form: pull of the totals of node (tx, ty) of plane pl (wrapped; sc
         // = ring slot of the unwrapped plane) from staged buffer b, and the species
@@ -353,10 +361,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             if (!(ylo || yhi || zlo || zhi)) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const float* a = &aux_at((sc - cz(i)) & 3, 0, tx - cx(i), ty - cy(i));
-                    sr = __fmaf_rn(a[0], ft[i], sr);
-                    sb = __fmaf_rn(a[LN], ft[i], sb);
-                    d += q5_share(i, a[2 * LN], a[3 * LN], a[4 * LN]);
+                    const Coef a = coef_at((sc - cz(i)) & 3, tx - cx(i), ty - cy(i));
+                    sr = __fmaf_rn(a.kr, ft[i], sr);
+                    sb = __fmaf_rn(a.kb, ft[i], sb);
+                    d += q5_share(i, a.m[0], a.m[LN], a.m[2 * LN]);
                 }
             } else {
                 const size_t self = pidx(p.pitch, p.nyp, PADX, wrap_near(x0 + tx, p.nx), gy, pl);
@@ -365,11 +373,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                     const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
                                      (cz(i) > 0 && zlo) || (cz(i) < 0 && zhi);
                     if (out) ft[i] = __ldg(fin + (size_t)opp(i) * p.P + self);
-                    const float* a = out ? &aux_at(sc, 0, tx, ty)
-                                         : &aux_at((sc - cz(i)) & 3, 0, tx - cx(i), ty - cy(i));
-                    sr = __fmaf_rn(a[0], ft[i], sr);
-                    sb = __fmaf_rn(a[LN], ft[i], sb);
-                    const float sh = q5_share(i, a[2 * LN], a[3 * LN], a[4 * LN]);
+                    const Coef a = out ? coef_at(sc, tx, ty)
+                                       : coef_at((sc - cz(i)) & 3, tx - cx(i), ty - cy(i));
+                    sr = __fmaf_rn(a.kr, ft[i], sr);
+                    sb = __fmaf_rn(a.kb, ft[i], sb);
+                    const float sh = q5_share(i, a.m[0], a.m[LN], a.m[2 * LN]);
                     d += out ? -sh : sh;
                 }
             }
@@ -487,43 +495,53 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             }
         };
 
-        // ---- lagged colour field of plane pl (deviation storage): element e of the
-        // (TX+4) x (TY+4) box, wrapped on periodic axes, clamped at walls (values
-        // beyond a wall are never read: those links bounce back)
-        auto lag_load = [&](int pl, int e) -> float {
-            if (e >= LN) return 0.0f;
-            const int r = e / G::LW, c = e - r * G::LW;
-            const int gx = wrap_near(x0 - 2 + c, p.nx);
-            int gy = y0 - 2 + r, gz = pl;
-            gy = p.wall_y ? min(max(gy, 0), p.ny - 1) : wrap_near(gy, p.ny);
-            gz = p.wall_z ? min(max(gz, 0), p.nz - 1) : wrap_near(gz, p.nz);
-            return __ldg(p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
-        };
-        float lag_reg0 = 0.f, lag_reg1 = 0.f;   // plane fetched ahead of its slot store
-        // reduced form: the coefficients of the same (TX+4) x (TY+4) sources of plane
-        // pl (the step's input, read in place), wrapped and clamped the same way
-        float aux_reg[2][Q5_AUX];
-        auto aux_fetch = [&](int pl) {
+        // ---- ring of source-node data of plane pl: element e of the (TX+4) x (TY+4)
+        // box of source columns, wrapped on periodic axes, clamped at walls (values
+        // beyond a wall are never read: those links bounce back). Each thread holds
+        // elements tid and tid + NT; their in-plane offsets are worked out once per
+        // segment: into the unpadded colour field (deviation storage) or into a padded
+        // population block (the reduced form's coefficients), -1 for none.
+        int ring_xy[2] = {-1, -1};
+        if constexpr (RING) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int e = tid + j * NT;
                 if (e >= LN) break;
                 const int r = e / G::LW, c = e - r * G::LW;
                 const int gx = wrap_near(x0 - 2 + c, p.nx);
-                int gy = y0 - 2 + r, gz = pl;
+                int gy = y0 - 2 + r;
                 gy = p.wall_y ? min(max(gy, 0), p.ny - 1) : wrap_near(gy, p.ny);
-                gz = p.wall_z ? min(max(gz, 0), p.nz - 1) : wrap_near(gz, p.nz);
-                const size_t q = pidx(p.pitch, p.nyp, PADX, gx, gy, gz);
+                ring_xy[j] = G::RED ? (gy + 2) * p.pitch + gx + PADX : gy * p.nx + gx;
+            }
+        }
+        auto ring_z = [&](int pl) {
+            return p.wall_z ? min(max(pl, 0), p.nz - 1) : wrap_near(pl, p.nz);
+        };
+        // lagged colour field (deviation storage)
+        auto lag_load = [&](int pl, int j) -> float {
+            if (ring_xy[j] < 0) return 0.0f;
+            return __ldg(p.phi_lag + (size_t)ring_z(pl) * plane + ring_xy[j]);
+        };
+        float lag_reg0 = 0.f, lag_reg1 = 0.f;   // plane fetched ahead of its slot store
+        // reduced form: the coefficients of the same source columns of plane pl (the
+        // step's input, read in place)
+        float aux_reg[2][Q5_AUX];
+        auto aux_fetch = [&](int pl) {
+            const T* base = fin + (size_t)ring_z(pl) * p.plane_p;
 #pragma unroll
-                for (int k = 0; k < Q5_AUX; ++k) aux_reg[j][k] = __ldg(fin + (size_t)(Q + k) * p.P + q);
+            for (int j = 0; j < 2; ++j) {
+                if (ring_xy[j] < 0) break;
+#pragma unroll
+                for (int k = 0; k < Q5_AUX; ++k)
+                    aux_reg[j][k] = __ldg(base + (size_t)(Q + k) * p.P + ring_xy[j]);
             }
         };
         auto lag_fetch = [&](int pl) {
             if constexpr (G::RED) {
                 aux_fetch(pl);
             } else {
-                lag_reg0 = lag_load(pl, tid);
-                lag_reg1 = lag_load(pl, tid + NT);
+                lag_reg0 = lag_load(pl, 0);
+                lag_reg1 = lag_load(pl, 1);
             }
         };
         auto lag_commit = [&](int pl) {
@@ -531,10 +549,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 float* d = slag + (size_t)slot(pl) * (Q5_AUX * LN);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
+                    if (ring_xy[j] < 0) break;
                     const int e = tid + j * NT;
-                    if (e >= LN) break;
+                    reinterpret_cast<float2*>(d)[e] = make_float2(aux_reg[j][0], aux_reg[j][1]);
 #pragma unroll
-                    for (int k = 0; k < Q5_AUX; ++k) d[k * LN + e] = aux_reg[j][k];
+                    for (int k = 2; k < Q5_AUX; ++k) d[k * LN + e] = aux_reg[j][k];
                 }
             } else {
                 float* d = slag + (size_t)slot(pl) * LN;
