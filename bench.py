@@ -382,8 +382,9 @@ def run_ours(args):
         fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
                 "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
                 "algorithmic_bytes_per_launch": alg16}
-        # and with the reduced FP32 form (Q + 5 values per node), against its own
-        # byte model of 192 bytes per node and step
+    if args.storage == "fp32" and args.model == "colour":
+        # and with the reduced FP32 form (Q + 5 values per node; colour-gradient states
+        # only), against its own byte model of 192 bytes per node and step
         g5, ms5, k5 = device_resident_glups(lbm, w, "fp32_q5", args.steps, args.warmup, stream,
                                             local)
         g5 = replicas.sum_over_ranks(g5, dist if world > 1 else None, f"cuda:{local}")
@@ -459,6 +460,8 @@ def main():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the Shan-Chen and sheared-bijel lines")
     args = ap.parse_args()
+    if args.storage == "fp32_q5" and args.model == "shan_chen":
+        ap.error("the reduced storage form holds colour-gradient states only")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
