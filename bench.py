@@ -15,7 +15,7 @@ buffers (set fields from pinned host memory, K steps, fields back to the host);
 ``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations
 per node, read once and written once) to the measured HBM bandwidth;
 ``fp16_store`` repeats the device-resident measurement with FP16 deviation
-storage and ``fp32_q5_store`` with the reduced FP32 form (19 totals and 5 recolouring
+storage (and, inside it, BF16) and ``fp32_q5_store`` with the reduced FP32 form (19 totals and 5 recolouring
 coefficients per node, 2 x 24 x 4 bytes per node and step); ``serving`` runs the served request stream (256 droplet / sheared-droplet
 runs of edge 32-128, Poisson arrivals at 50/s, FP16 storage) through the serving
 engine and reports p50/p99 latency beside aggregate GLUPS; ``shan_chen`` and
@@ -382,6 +382,10 @@ def run_ours(args):
         fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
                 "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
                 "algorithmic_bytes_per_launch": alg16}
+        # BF16 deviation storage beside it (same bytes, 8-bit mantissa)
+        gb, msb, kb = device_resident_glups(lbm, w, "bf16", args.steps, args.warmup, stream, local)
+        gb = replicas.sum_over_ranks(gb, dist if world > 1 else None, f"cuda:{local}")
+        fp16["bf16"] = {"value": gb, "unit": "GLUPS", "ms_per_step": msb, "kernel_ms": kb}
     if args.storage == "fp32" and args.model == "colour":
         # and with the reduced FP32 form (Q + 5 values per node; colour-gradient states
         # only), against its own byte model of 192 bytes per node and step
