@@ -311,8 +311,10 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  *   (the timed steps are real steps of the requests) and remembered.
  * - A request's result does not depend on the other requests or on the schedule:
  *   every node is computed by the same arithmetic in any batch.
- * - Requests with A_nc > 0 are refused (LBM_EINVAL): the near-contact pass is not
- *   batched.
+ * - Requests with A_nc > 0 are served too, but not batched: each such lattice is
+ *   advanced by the same k steps through its own step path (near-contact pass, then
+ *   the step kernel; as lbm_step) on the engine's stream, after the batched launches
+ *   of the tick.
  * An engine is not thread-safe; its calls run on its stream and synchronise it.  */
 typedef struct lbm_engine lbm_engine;
 
@@ -333,7 +335,7 @@ lbm_status lbm_engine_create(const lbm_engine_params* p, lbm_engine** out);
 /* Queues a request: a lattice with parameters p (p->cuda_stream is ignored) and
  * initial fields as for lbm_set_fields (host arrays, copied; u may be NULL), to be
  * advanced `steps` >= 1 steps. *ticket identifies it (> 0). Requests of either
- * model are served; the near-contact force is not (A_nc > 0 gives LBM_EINVAL).   */
+ * model and storage format are served, with or without the near-contact force.    */
 lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, const double* rho_r,
                              const double* rho_b, const double* u, long long steps,
                              long long* ticket);

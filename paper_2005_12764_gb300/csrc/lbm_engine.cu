@@ -2,6 +2,8 @@
 // include/lbm.h): independent lattices resident on the device, admitted by device
 // memory, advanced together by batched launches of the step kernel captured in CUDA
 // graphs, retired as they finish so that queued requests take their place.
+// Lattices with the near-contact force take their own step path (the near-contact
+// pass, then the step kernel, per lattice) on the engine's stream in the same tick.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +58,10 @@ struct Group {
     long long ghost = 0;
 };
 
+// Lattices without the near-contact force are advanced by the batched launches; the
+// others by their own context's step path.
+bool batched(const Request* r) { return !(r->p.A_nc > 0.0); }
+
 // Device memory a resident lattice holds: its context plus the FP64 staging of the
 // host field exchanges (7 doubles per node).
 size_t request_bytes(const lbm_params& p) {
@@ -104,6 +110,7 @@ void free_groups(lbm_engine* e) {
 std::string signature(const lbm_engine* e) {
     std::vector<std::string> parts;
     for (const Request* r : e->resident) {
+        if (!batched(r)) continue;
         BatchLattice b;
         step_params_ahead(r->ctx, 0, 0, &b);
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
@@ -121,6 +128,7 @@ std::string signature(const lbm_engine* e) {
 cudaError_t build_batch(lbm_engine* e, int T) {
     free_groups(e);
     for (Request* r : e->resident) {
+        if (!batched(r)) continue;
         BatchLattice b;
         step_params_ahead(r->ctx, 0, 0, &b);
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
@@ -204,11 +212,19 @@ cudaError_t single_step(lbm_engine* e) {
     return err;
 }
 
+// Record k steps of the batched launches for the lattices they advance.
 void advance_all(lbm_engine* e, long long k) {
     for (Request* r : e->resident) {
+        if (!batched(r)) continue;
         advance_state(r->ctx, k);
         r->steps_done += k;
     }
+}
+
+bool any_batched(const lbm_engine* e) {
+    for (const Request* r : e->resident)
+        if (batched(r)) return true;
+    return false;
 }
 
 // Graph replays of `pairs` x 2 steps, timed with events when ms != nullptr.
@@ -331,7 +347,6 @@ extern "C" lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, cons
     if (!e) return LBM_EINVAL;
     if (!p || !rho_r || !rho_b || !ticket) return efail(e, LBM_EINVAL, "p, rho_r, rho_b and ticket are required");
     if (steps < 1) return efail(e, LBM_EINVAL, "steps must be >= 1");
-    if (p->A_nc > 0.0) return efail(e, LBM_EINVAL, "engine requests must have A_nc == 0");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return efail(e, LBM_EINVAL, "nx, ny, nz must be >= 1");
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return efail(e, LBM_ENOMEM, "host allocation failed");
@@ -373,7 +388,8 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
     if (k >= 2 && (k & 1)) --k;   // the graph runs pairs of steps
     cudaError_t err = cudaSuccess;
     long long done = 0;
-    if (!e->graph_valid) {
+    const bool have_batch = any_batched(e);
+    if (have_batch && !e->graph_valid) {
         const std::string sig = signature(e);
         auto it = e->tuned.find(sig);
         const long long tune_need = (long long)kTuneSteps * (sizeof(kCandidates) / sizeof(int));
@@ -404,7 +420,7 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
             err = build_batch(e, kDefaultT);
         }
     }
-    const long long left = k - done;
+    const long long left = have_batch ? k - done : 0;
     if (err == cudaSuccess && left >= 2) {
         err = replay(e, left / 2, nullptr);
         if (err == cudaSuccess) advance_all(e, left - (left & 1));
@@ -415,6 +431,16 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
             advance_all(e, 1);
             e->graph_valid = false;   // the tables' step parity has flipped
         }
+    }
+    // lattices with the near-contact force: k steps each through the context's own
+    // step path (queued on the engine's stream behind the batched work)
+    for (Request* r : e->resident) {
+        if (batched(r) || err != cudaSuccess) continue;
+        if (lbm_step(r->ctx, (int)k) != LBM_OK) {
+            e->err = std::string("request ") + std::to_string(r->ticket) + ": " + lbm_last_error(r->ctx);
+            return LBM_ECUDA;
+        }
+        r->steps_done += k;
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
     if (err != cudaSuccess) {

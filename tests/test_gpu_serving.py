@@ -225,3 +225,46 @@ def test_cancel_queued_and_resident_requests(lbm):
     with pytest.raises(lbm.LbmError):
         e.result(tk[2])
     e.close()
+
+
+@pytest.mark.parametrize("with_batched", [True, False])
+def test_near_contact_requests_are_served_bitwise_lbm_step(lbm, with_batched):
+    # near-contact requests (two droplets close enough for the film force) take their
+    # own step path in the engine's ticks, beside the batched lattices or alone; each
+    # result equals the same lattice stepped by plain lbm_step
+    from paper_2005_12764_gb300 import serving
+    nc = []
+    for k, (L, gap) in enumerate(((40, 2.0), (48, 3.0))):
+        c, R = L / 2.0, L / 6.0
+        drops = [(c - R - gap / 2, c, c, R), (c + R + gap / 2, c, c, R)]
+        a, b = inputs.paint_droplets((L, L, L), drops)
+        p = lbm.make_params(L, L, L, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0,
+                            storage="fp32" if k == 0 else "fp32_q5")
+        nc.append((p, a, b, 25 + 10 * k))
+    e = lbm.Engine(budget_bytes=8 << 30, max_slots=8, chunk_steps=10, autotune=False)
+    tickets = {}
+    for p, a, b, steps in nc:
+        tickets[e.submit(p, a, b, steps)] = (p, a, b, steps)
+    if with_batched:
+        for r in REQS[:2]:
+            p, a, b = serving.request_lattice(r, "fp32")
+            tickets[e.submit(p, a, b, r["steps"])] = (p, a, b, r["steps"])
+    done = {}
+    for _ in range(200):
+        e.tick()
+        for t in tickets:
+            if t not in done and e.state(t) == "finished":
+                done[t] = e.result(t)
+        if len(done) == len(tickets):
+            break
+    e.close()
+    assert len(done) == len(tickets)
+    for t, (p, a, b, steps) in tickets.items():
+        assert done[t]["info"][0] == steps
+        g = lbm.Lattice(p)
+        g.set_fields(a, b)
+        g.step(steps)
+        f = g.get_fields()
+        g.close()
+        for k in ("rho_r", "rho_b", "u", "phi"):
+            assert np.array_equal(f[k], done[t][k]), (t, k)
