@@ -106,17 +106,29 @@ def _samples(rng, shape, droplets, n_any, n_iface):
     return out
 
 
-def test_dense_emulsion_512_full_size(lbm):
-    w = inputs.dense_emulsion()        # 512^3, volume fraction 0.35, radii 6-12
+_EMULSION = {}
+
+
+def _emulsion():
+    if "w" not in _EMULSION:
+        _EMULSION["w"] = inputs.dense_emulsion()   # 512^3, volume fraction 0.35, radii 6-12
+    return _EMULSION["w"]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp32_q5"])
+def test_dense_emulsion_512_full_size(lbm, storage):
+    # the full FP32 form and the reduced (Q + 5) form, the latter holding 25.8 GB for
+    # the two copies instead of 40.8 GB
+    w = _emulsion()
     assert w.params_extra["achieved_fraction"] > 0.34
     n = w.shape[0]
-    g = lbm.Lattice(lbm.make_params(n, n, n, **w.params))
+    g = lbm.Lattice(lbm.make_params(n, n, n, storage=storage, **w.params))
     g.set_fields(w.rho_r, w.rho_b)
     m0 = g.observables()
     g.step(20)
     samples = _samples(np.random.default_rng(31), w.shape, w.droplets, 6, 10)
     worst, bad = _check_sampled_step(lbm, g, w, samples)
-    print("emulsion 512^3: worst |d f| at samples", worst)
+    print(f"emulsion 512^3 ({storage}): worst |d f| at samples", worst)
     assert bad == 0, worst
     m1 = g.observables()
     assert np.isfinite(m1[:5]).all()
