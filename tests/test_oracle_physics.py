@@ -235,6 +235,48 @@ def test_near_contact_film_thickness_flat_films():
     assert checked >= 4
 
 
+def test_near_contact_strength_oblique_rays_brute_force():
+    # Brute force in 3-D: two smooth droplets (phi = tanh((R - r)/1.5), periodic) on an
+    # oblique line, so the rays run between lattice directions. At every node with
+    # |G| >= 1e-3 the strength must equal the reading restated here with an
+    # independent trilinear sampler (scipy's map_coordinates, periodic): samples at
+    # x - t G/|G|, t = -1, -1/2, ..., h_cut + 2; samples with |phi| <= 1e-5 unsigned;
+    # h between the first downward and the next upward crossing, each located
+    # linearly between consecutive signed samples; A_h(h) of Eq. 11, else 0.
+    from scipy.ndimage import map_coordinates
+    nz, ny, nx = 24, 26, 36
+    drops = [(11.0, 12.3, 11.6, 5.0), (24.2, 14.1, 13.0, 5.5)]     # gap ~2.9 lu
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = -np.ones((nz, ny, nx))
+    for cx, cy, cz, R in drops:
+        d = [((a - c + n / 2) % n) - n / 2 for a, c, n in ((xx, cx, nx), (yy, cy, ny), (zz, cz, nz))]
+        phi = np.maximum(phi, np.tanh((R - np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)) / 1.5))
+    A, hmin, hcut = 0.02, 3.0, 6.0
+    p = oracle.make_params(nx, ny, nz, A_nc=A, h_min=hmin, h_cut=hcut)
+    G = oracle.gradient(p, phi)
+    gm = np.sqrt((G * G).sum(0))
+    ts = -1.0 + 0.5 * np.arange(int(np.floor(2 * (hcut + 3))) + 1)
+    checked = films = 0
+    for z, y, x in zip(*np.nonzero(gm >= 1e-3)):
+        n = -G[:, z, y, x] / gm[z, y, x]
+        coords = np.array([z + ts * n[2], y + ts * n[1], x + ts * n[0]])
+        vals = map_coordinates(phi, coords, order=1, mode="grid-wrap")
+        signed = [(t, v) for t, v in zip(ts, vals) if abs(v) > 1e-5]
+        t_d = t_u = None
+        for (t0, v0), (t1, v1) in zip(signed, signed[1:]):
+            if t_d is None and v0 > 0 > v1:
+                t_d = t0 + (t1 - t0) * v0 / (v0 - v1)
+            elif t_d is not None and v0 < 0 < v1:
+                t_u = t0 + (t1 - t0) * v0 / (v0 - v1)
+                break
+        want = oracle.A_h(t_u - t_d, A, hmin, hcut) if t_u is not None else 0.0
+        got = oracle.nc_strength_node(p, phi, int(x), int(y), int(z))
+        assert abs(got - want) <= 1e-12, (x, y, z, got, want)
+        checked += 1
+        films += want > 0
+    assert checked > 1000 and films >= 20, (checked, films)
+
+
 # ------------------------------------------------------------------ symmetries
 @pytest.mark.parametrize("A_nc", [0.0, 0.01])
 def test_translation_invariance(A_nc):
