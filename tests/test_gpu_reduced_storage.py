@@ -196,3 +196,52 @@ def test_checkpoint_resume_is_bitwise(lbm):
 def test_shan_chen_is_refused(lbm):
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(lbm.make_params(16, 16, 16, storage=Q5, model="shan_chen", G_sc=1.2))
+
+
+def test_zero_steps_returns_set_fields(lbm):
+    # f^eq(rho_k, u) is (rho_k / rho) f^eq(rho, u): the reduced form holds any initial
+    # state exactly up to FP32 rounding
+    shape = (5, 6, 7)
+    rr, rb, u = inputs.random_state(shape, seed=3)
+    g = lbm.Lattice(lbm.make_params(7, 6, 5, storage=Q5))
+    g.set_fields(rr, rb, u)
+    g.step(0)
+    f = g.get_fields()
+    g.close()
+    assert np.abs(f["rho_r"] - rr).max() < 4e-7 and np.abs(f["rho_b"] - rb).max() < 4e-7
+    assert np.abs(f["u"] - u).max() < 1e-7
+
+
+def test_laplace_and_observables_match_the_oracle(lbm):
+    w = inputs.static_droplet(L=32, R=8.0)
+    o = oracle.Lattice(oracle.make_params(32, 32, 32, **w.params))
+    o.set_fields(w.rho_r, w.rho_b)
+    o.step(200)
+    g = lbm.Lattice(lbm.make_params(32, 32, 32, storage=Q5, **w.params))
+    g.set_fields(w.rho_r, w.rho_b)
+    t0 = g.observables()
+    g.step(200)
+    lo, lg = o.laplace((16, 16, 16)), g.laplace((16, 16, 16))
+    assert abs(lg["R_eff"] - lo["R_eff"]) < 1e-4
+    assert abs(lg["dp"] - lo["dp"]) / abs(lo["dp"]) < 1e-3
+    t = g.observables()
+    assert abs(t[0] - t0[0]) / t0[0] < 1e-6 and abs(t[1] - t0[1]) / t0[1] < 1e-6
+    assert np.abs(t[2:5]).max() / (t0[0] + t0[1]) < 1e-7
+    o.close()
+    g.close()
+
+
+def test_window_matches_full_download_with_wrap(lbm):
+    g = lbm.Lattice(lbm.make_params(16, 10, 12, sigma=0.01, storage=Q5))
+    rr, rb = inputs.paint_droplets((12, 10, 16), [(8.0, 5.0, 6.0, 3.5)])
+    g.set_fields(rr, rb)
+    g.step(5)
+    fr, fb, lag = g.get_pops()
+    wr, wb, wl = g.get_window(13, 7, 9, 6, 5, 4)
+    zz = (np.arange(9, 13) % 12)[:, None, None]
+    yy = (np.arange(7, 12) % 10)[None, :, None]
+    xx = (np.arange(13, 19) % 16)[None, None, :]
+    assert np.array_equal(wr.reshape(19, 4, 5, 6), fr[:, zz, yy, xx])
+    assert np.array_equal(wb.reshape(19, 4, 5, 6), fb[:, zz, yy, xx])
+    assert np.array_equal(wl.reshape(4, 5, 6), lag[zz, yy, xx])
+    g.close()
