@@ -664,14 +664,21 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
 // Small-number form as in collide_store: f^eq_i(rho_k, U) = w_i rho_k +
 // w_i rho_k (3 c.U + 4.5 (c.U)^2 - 1.5 U^2), opposite directions sharing terms.
 template <class St, bool UnitOmega, class Emit>
-__device__ __forceinline__ void sc_collide_store(const StepParams& p, const float (&fr)[Q],
-                                                 const float (&fb)[Q], float rr, float rb,
-                                                 float phi, const float (&sr)[3],
-                                                 const float (&sb)[3], float Fx, float Fy,
-                                                 float Fz, const Emit& emit) {
-    const float rho = rr + rb;
-    const float inv_rho = __frcp_rn(rho);
-    float jx = 0.f, jy = 0.f, jz = 0.f;
+__device__ __forceinline__ void sc_collide_moments(const StepParams& p, const float (&fr)[Q],
+                                                   const float (&fb)[Q], float rr, float rb,
+                                                   float jx, float jy, float jz, float phi,
+                                                   const float (&sr)[3], const float (&sb)[3],
+                                                   float Fx, float Fy, float Fz,
+                                                   const Emit& emit);
+
+// Momentum j = sum_i c_i (f^r_i + f^b_i) of the two species' populations, summed in one
+// fixed order (the collision and the moments-only march of the unit-rate case get
+// the same bits).
+__device__ __forceinline__ void sc_momentum(const float (&fr)[Q], const float (&fb)[Q], float& jx,
+                                            float& jy, float& jz) {
+    jx = 0.f;
+    jy = 0.f;
+    jz = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float d = (fr[i] + fb[i]) - (fr[opp(i)] + fb[opp(i)]);
@@ -679,6 +686,32 @@ __device__ __forceinline__ void sc_collide_store(const StepParams& p, const floa
         if (cy(i)) jy += cy(i) > 0 ? d : -d;
         if (cz(i)) jz += cz(i) > 0 ? d : -d;
     }
+}
+
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void sc_collide_store(const StepParams& p, const float (&fr)[Q],
+                                                 const float (&fb)[Q], float rr, float rb,
+                                                 float phi, const float (&sr)[3],
+                                                 const float (&sb)[3], float Fx, float Fy,
+                                                 float Fz, const Emit& emit) {
+    float jx, jy, jz;
+    sc_momentum(fr, fb, jx, jy, jz);
+    sc_collide_moments<St, UnitOmega>(p, fr, fb, rr, rb, jx, jy, jz, phi, sr, sb, Fx, Fy, Fz,
+                                      emit);
+}
+
+// The collision from the node's densities and momentum; the populations fr, fb enter
+// only the non-equilibrium part, which vanishes at unit rate (omega = 1): there the
+// caller may pass any arrays.
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void sc_collide_moments(const StepParams& p, const float (&fr)[Q],
+                                                   const float (&fb)[Q], float rr, float rb,
+                                                   float jx, float jy, float jz, float phi,
+                                                   const float (&sr)[3], const float (&sb)[3],
+                                                   float Fx, float Fy, float Fz,
+                                                   const Emit& emit) {
+    const float rho = rr + rb;
+    const float inv_rho = __frcp_rn(rho);
     const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
     float omega = p.omega0;
     if (!UnitOmega && p.var_tau) {

@@ -571,11 +571,12 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         if constexpr (SC) {
             // ---- Shan-Chen model. The ring holds the species densities of planes
             // z-1, z (and z+1 once pulled); the cohesive force of plane z needs those
-            // of its 18 neighbours. Each species' populations are kept only for the
-            // plane being collided: at the start of plane z the staged buffer holds
-            // plane z; its owned populations are pulled, the buffer is refilled with
-            // plane z+1, whose densities (tile + ring) complete the ring, and plane z
-            // is collided. (Plane z+1 is pulled once more, whole, in its own turn.)
+            // of its 18 neighbours. Away from unit rate each species' populations are
+            // needed by the collision; they are kept only for the plane being collided:
+            // at the start of plane z the staged buffer holds plane z; its owned
+            // populations are pulled, the buffer is refilled with plane z+1, whose
+            // densities (tile + ring) complete the ring, and plane z is collided. (Plane
+            // z+1 is pulled once more, whole, in its own turn.)
             auto rho_at = [&](int k, int sl, int tx, int ty) -> float& {
                 return sphi[((k * 4 + sl) * SH + ty + 1) * SWP + tx + 1];
             };
@@ -595,6 +596,104 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                     rho_at(1, slot(pl), rtx, rty) = c;
                 }
             };
+            // cohesive velocity shifts F^k / rho_k = -G sum_i w_i rho_kbar(x + c_i) c_i of
+            // the owned node of plane z (densities rr, rb) from the ring of planes
+            // z-1 .. z+1: 3 sum_i w_i rho_k(x + c_i) c_i per species, a neighbour beyond
+            // a wall taking the node's own density
+            const float g3 = -p.G_sc * (1.0f / 3.0f);
+            auto sc_shifts = [&](int z, float rr, float rb, float (&sr)[3], float (&sb)[3]) {
+                const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
+                const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
+                float ar[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if (i == 9) continue;
+                    const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
+                                      (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
+                    const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
+                    const float nr = wall ? rr : rho_at(0, sl, otx + cx(i), oty + cy(i));
+                    const float nb = wall ? rb : rho_at(1, sl, otx + cx(i), oty + cy(i));
+                    grad_add(i, nr, ar[0], ar[1], ar[2]);
+                    grad_add(i, nb, ab[0], ab[1], ab[2]);
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    sr[a] = g3 * ab[a];
+                    sb[a] = g3 * ar[a];
+                }
+            };
+            if constexpr (UnitOmega) {
+                // ---- unit rate (omega = 1): the collision needs only each node's
+                // densities and momentum, not its populations, so the march takes the
+                // colour-gradient form: each turn pulls plane z+1 once (tile and ring
+                // densities into the ring, the owned node's densities and momentum into
+                // registers) while the copy of plane z+2 is in flight, then collides z.
+                auto sc_pull = [&](int b, int pl, float& rr, float& rb, float (&j)[3]) {
+                    const bool pvalid = !p.wall_z || (pl >= 0 && pl < p.nz);
+                    if (!pvalid) return;
+                    const int plw = wrap_near(pl, p.nz);
+                    float vr[Q], vb[Q], a, c;
+                    if (owned) {
+                        pull_species(b, plw, slot(pl), otx, oty, vr, vb, rr, rb, true);
+                        sc_momentum(vr, vb, j[0], j[1], j[2]);
+                        rho_at(0, slot(pl), otx, oty) = rr;
+                        rho_at(1, slot(pl), otx, oty) = rb;
+                    }
+                    if (ring) {
+                        pull_species(b, plw, slot(pl), rtx, rty, vr, vb, a, c, false);
+                        rho_at(0, slot(pl), rtx, rty) = a;
+                        rho_at(1, slot(pl), rtx, rty) = c;
+                    }
+                };
+                float c_rr = 0.f, c_rb = 0.f, c_j[3] = {0.f, 0.f, 0.f};
+                float n_rr = 0.f, n_rb = 0.f, n_j[3] = {0.f, 0.f, 0.f};
+                // lag planes zb-2 .. zb (deviation storage), then each turn z stores lag
+                // plane z+3 into the slot of z-1, as in the colour-gradient march
+                if (G::DEV) {
+                    for (int q = -2; q <= 0; ++q) {
+                        lag_fetch(zb + q);
+                        lag_commit(zb + q);
+                    }
+                    __syncthreads();
+                }
+                fence_proxy_async();
+                issue(0, zb - 1);
+                const float none[Q] = {};   // populations: unused at unit rate
+                for (int z = zb - 2; z < ze; ++z) {
+                    if (G::DEV) lag_fetch(z + 3);
+                    wait(0);
+                    sc_pull(0, z + 1, n_rr, n_rb, n_j);
+                    if (G::DEV) lag_commit(z + 3);
+                    if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
+                    __syncthreads();
+                    fence_proxy_async();
+                    if (z + 2 <= ze) issue(0, z + 2);
+                    if (z >= zb) {
+                        if (owned && !failed) {
+                            float sr[3], sb[3];
+                            sc_shifts(z, c_rr, c_rb, sr, sb);
+                            const float phic = colour(c_rr, c_rb);
+                            const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
+                            sc_collide_moments<St, true>(p, none, none, c_rr, c_rb, c_j[0], c_j[1],
+                                                         c_j[2], phic, sr, sb, fx_y, p.gy, p.gz, em);
+                            p.phi_out[(size_t)z * plane + col] = phic;
+                        }
+                        fence_proxy_async();
+                        __syncthreads();
+                        if (tid == 0) {
+                            for (int k = 0; k < G::NS; ++k)
+                                tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k,
+                                             sout + (size_t)k * (TX * TY));
+                            bulk_commit();
+                        }
+                    }
+                    c_rr = n_rr;
+                    c_rb = n_rb;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) c_j[a] = n_j[a];
+                }
+                continue;
+            }
             // the march starts at plane zb-2: its first two turns only fill the ring with
             // the densities of zb-1 and zb (one copy of the pull code for the segment);
             // lag planes zb-2, zb-1 first, then each turn z stores lag plane z+2
@@ -606,7 +705,6 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 lag_fetch(zb);
                 __syncthreads();
             }
-            const float g3 = -p.G_sc * (1.0f / 3.0f);
             for (int z = zb - 2; z < ze; ++z) {
                 // lag plane z+2 goes to the slot of z-2, last read in the previous plane
                 if (G::DEV) lag_commit(z + 2);
@@ -623,25 +721,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 __syncthreads();                  // densities of plane z+1 in the ring
                 if (z < zb) continue;
                 if (owned && !failed) {
-                    const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
-                    const int s0 = slot(z - 1), s1 = slot(z), s2 = slot(z + 1);
-                    // 3 sum_i w_i rho_k(x + c_i) c_i, a neighbour beyond a wall taking
-                    // the node's own density
-                    float ar[3] = {0.f, 0.f, 0.f}, ab[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        if (i == 9) continue;
-                        const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) ||
-                                          (cz(i) < 0 && zlo) || (cz(i) > 0 && zhi);
-                        const int sl = cz(i) < 0 ? s0 : (cz(i) > 0 ? s2 : s1);
-                        const float nr = wall ? rr : rho_at(0, sl, otx + cx(i), oty + cy(i));
-                        const float nb = wall ? rb : rho_at(1, sl, otx + cx(i), oty + cy(i));
-                        grad_add(i, nr, ar[0], ar[1], ar[2]);
-                        grad_add(i, nb, ab[0], ab[1], ab[2]);
-                    }
-                    // cohesive velocity shifts F^k / rho_k = -G sum_i w_i rho_kbar c_i
-                    const float sr[3] = {g3 * ab[0], g3 * ab[1], g3 * ab[2]};
-                    const float sb[3] = {g3 * ar[0], g3 * ar[1], g3 * ar[2]};
+                    float sr[3], sb[3];
+                    sc_shifts(z, rr, rb, sr, sb);
                     const float phic = colour(rr, rb);
                     const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
                     sc_collide_store<St, UnitOmega>(p, vr, vb, rr, rb, phic, sr, sb, fx_y, p.gy,
