@@ -274,9 +274,12 @@ def other_workloads(lbm, stream, local, steps=200):
     ms = timed(lat, steps)
     _, k_ms, _ = lat.step_timed(20)
     lat.close()
+    alg = bytes_per_node("fp32") * nx * ny * nz
     out["shan_chen"] = {"workload": "channel 256x128x64, 40 droplets, walls y/z, G_sc = 1.6, FP32",
                         "value": nx * ny * nz / (ms * 1e-3) / 1e9, "unit": "GLUPS",
-                        "ms_per_step": ms, "kernel_ms": k_ms / 20}
+                        "ms_per_step": ms, "kernel_ms": k_ms / 20,
+                        "roofline_frac": alg / (k_ms / 20 * 1e-3) / 1e9 / peaks()[0],
+                        "algorithmic_bytes_per_launch": alg}
     w = inputs.sheared_bijel()
     nz, ny, nx = w.shape
     lat = lbm.Lattice(lbm.make_params(nx, ny, nz, stream=stream.cuda_stream, **w.params))
