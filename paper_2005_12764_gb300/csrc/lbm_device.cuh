@@ -547,13 +547,13 @@ struct SmemEmit {
     }
 };
 
-template <class St, bool UnitOmega, class Emit>
-__device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
-                                              float rb, float phi, float Gx, float Gy, float Gz,
-                                              float Fx, float Fy, float Fz, const Emit& emit) {
-    const float rho = rr + rb;
-    const float inv_rho = __frcp_rn(rho);
-    float jx = 0.f, jy = 0.f, jz = 0.f;
+// Momentum j = sum_i c_i f_i of the total populations, summed in one fixed order
+// (the collision and the unit-rate march, which carries only the moments, get the
+// same bits).
+__device__ __forceinline__ void cg_momentum(const float (&f)[Q], float& jx, float& jy, float& jz) {
+    jx = 0.f;
+    jy = 0.f;
+    jz = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float d = f[i] - f[opp(i)];
@@ -561,6 +561,33 @@ __device__ __forceinline__ void collide_store(const StepParams& p, const float (
         if (cy(i)) jy += cy(i) > 0 ? d : -d;
         if (cz(i)) jz += cz(i) > 0 ? d : -d;
     }
+}
+
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void collide_moments(const StepParams& p, const float (&f)[Q], float rr,
+                                                float rb, float jx, float jy, float jz, float phi,
+                                                float Gx, float Gy, float Gz, float Fx, float Fy,
+                                                float Fz, const Emit& emit);
+
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void collide_store(const StepParams& p, const float (&f)[Q], float rr,
+                                              float rb, float phi, float Gx, float Gy, float Gz,
+                                              float Fx, float Fy, float Fz, const Emit& emit) {
+    float jx, jy, jz;
+    cg_momentum(f, jx, jy, jz);
+    collide_moments<St, UnitOmega>(p, f, rr, rb, jx, jy, jz, phi, Gx, Gy, Gz, Fx, Fy, Fz, emit);
+}
+
+// The collision from the node's densities and momentum; the total populations f enter
+// only the non-equilibrium part, which vanishes at unit rate (omega = 1): there the
+// caller may pass any array.
+template <class St, bool UnitOmega, class Emit>
+__device__ __forceinline__ void collide_moments(const StepParams& p, const float (&f)[Q], float rr,
+                                                float rb, float jx, float jy, float jz, float phi,
+                                                float Gx, float Gy, float Gz, float Fx, float Fy,
+                                                float Fz, const Emit& emit) {
+    const float rho = rr + rb;
+    const float inv_rho = __frcp_rn(rho);
     const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
     float omega = p.omega0;
     if (!UnitOmega && p.var_tau) {

@@ -758,6 +758,17 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             if (RING) lag_fetch(z + 3);
             wait(bn);
             densities(bn, z + 1, nx_f, nx_rr, nx_rb, true);
+            if constexpr (UnitOmega) {
+                // unit rate: the collision needs only the momentum of the populations,
+                // which is all that is carried to the next turn (in nx_f[0 .. 2])
+                if (owned) {
+                    float jx, jy, jz;
+                    cg_momentum(nx_f, jx, jy, jz);
+                    nx_f[0] = jx;
+                    nx_f[1] = jy;
+                    nx_f[2] = jz;
+                }
+            }
             if (RING) lag_commit(z + 3);
             if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
             __syncthreads();
@@ -820,7 +831,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 }
                 // outputs go to the shared output tile; the tile is stored below
                 const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
-                collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
+                if constexpr (UnitOmega)
+                    collide_moments<St, true>(p, cu, cu_rr, cu_rb, cu[0], cu[1], cu[2], phic, Gx,
+                                              Gy, Gz, Fx, Fy, Fz, em);
+                else
+                    collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
                 p.phi_out[node] = phic;
             }
             if (p.nc_pos_out) {
@@ -862,10 +877,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         issue(0, zb - 1);
 
         // ---- the march: plane z is collided from fa while plane z+1 is pulled into fb
+        // (at unit rate only fa[0 .. 2], the momentum, is carried)
         for (int z = zb - 2; z < ze; ++z) {
             march(z, fa, a_rr, a_rb, fb, b_rr, b_rb, ah_c);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fa[i] = fb[i];
+            for (int i = 0; i < (UnitOmega ? 3 : Q); ++i) fa[i] = fb[i];
             a_rr = b_rr;
             a_rb = b_rb;
         }
