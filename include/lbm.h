@@ -275,6 +275,18 @@ lbm_status lbm_sync(lbm_ctx* ctx);
 /* Bytes of device memory held by a context with these parameters (admission).  */
 size_t lbm_footprint_bytes(const lbm_params* p);
 
+/* Work split the step kernel of a context with these parameters uses on a GPU with
+ * num_sms SMs (host computation, no device needed). The kernel's CTAs own 32 x 8
+ * tiles of (x, y) columns and march along z, two CTAs per SM. out[0] = zparts: part
+ * mode, z cut into this many equal parts, one CTA per (part, tile); out[1] = chain
+ * (> 0: chain mode with this many CTAs, 0: part mode); out[2], out[3] = band_k,
+ * band_h: in chain mode CTAs c < band_k tiles march tile c mod tiles over planes
+ * (c / tiles) band_h ... + band_h - 1, the others share the (tile, plane) units of
+ * planes band_k band_h ... nz - 1 in equal contiguous runs (column-major tile order,
+ * planes ascending within a tile); out[4] = grid (CTAs launched). LBM_EINVAL for
+ * invalid parameters or num_sms < 1.                                              */
+lbm_status lbm_work_split(const lbm_params* p, int num_sms, long long out[5]);
+
 /* Number of steps taken since the last lbm_set_fields.                          */
 long long lbm_steps_taken(const lbm_ctx* ctx);
 

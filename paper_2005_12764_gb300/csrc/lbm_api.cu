@@ -552,6 +552,75 @@ extern "C" void lbm_velocity_set(int c[LBM_Q * 3]) {
     }
 }
 
+// Work split of the step kernel over the GPU's CTA slots (num_sms x CTAs per SM).
+struct WorkSplit {
+    int zparts, chain, band_k, band_h, grid;
+};
+static WorkSplit work_split(const lbm_params& p, int num_sms) {
+    WorkSplit w{1, 0, 0, 0, 1};
+    const int tx = step_tile_x(), ty = step_tile_y();
+    const long long tiles = (long long)((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty);
+    // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
+    // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
+    // pipeline fill), the cost of a part-major launch.
+    const int S = (num_sms > 0 ? num_sms : 1) * step_ctas_per_sm();
+    int best_k = 1;
+    double best = 1e300;
+    for (int k = 1; k <= p.nz && k <= 4096; ++k) {
+        const long long ctas = tiles * k;
+        const long long waves = (ctas + S - 1) / S;
+        const double cost = (double)waves * ((double)p.nz / k + 4.0);
+        if (cost < best * 0.999) {
+            best = cost;
+            best_k = k;
+        }
+    }
+    w.zparts = best_k;
+    w.grid = (int)(tiles * best_k);
+    // chain mode when one wave of whole parts would leave SMs unevenly loaded: every
+    // CTA slot, with about w = nz tiles / slots planes each: k = slots / tiles bands
+    // of h ~ w planes, one CTA per (band, tile), and the rest shared by the remaining
+    // slots; of h near w the one whose busiest CTA has the fewest planes (counting
+    // about one plane of pipeline fill per tile a CTA starts) is taken.
+    const long long units = tiles * p.nz;
+    if (tiles < S && units >= 8LL * S && tiles * best_k != S) {
+        const int k = (int)(S / tiles);
+        const double wsh = (double)units / (double)S;
+        double best_cost = (double)p.nz / best_k + 1.0;   // part mode: one part per CTA
+        for (int h = std::max(1, (int)std::floor(wsh) - 2); h <= (int)std::ceil(wsh) + 3; ++h) {
+            const int r = p.nz - k * h;
+            const long long R = S - (long long)k * tiles;
+            if (r < 0 || (r > 0 && R <= 0)) continue;
+            double cost = h + 1.0;
+            if (r > 0) {
+                const double rem = (double)r * tiles / (double)R;
+                cost = std::max(cost, rem + std::ceil(rem / r) + 1.0);
+            }
+            if (cost < best_cost) {
+                best_cost = cost;
+                w.band_k = k;
+                w.band_h = h;
+                w.chain = (int)(r > 0 ? S : (long long)k * tiles);
+            }
+        }
+        if (w.chain > 0) w.grid = w.chain;
+    }
+    return w;
+}
+
+extern "C" lbm_status lbm_work_split(const lbm_params* p, int num_sms, long long out[5]) {
+    std::string why;
+    if (!out || num_sms < 1) return fail(nullptr, LBM_EINVAL, "out is NULL or num_sms < 1");
+    if (validate(p, why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+    const WorkSplit w = work_split(*p, num_sms);
+    out[0] = w.zparts;
+    out[1] = w.chain;
+    out[2] = w.band_k;
+    out[3] = w.band_h;
+    out[4] = w.grid;
+    return LBM_OK;
+}
+
 static void fill_step_params(lbm_ctx* c) {
     const lbm_params& p = c->p;
     StepParams& s = c->sp;
@@ -598,54 +667,12 @@ static void fill_step_params(lbm_ctx* c) {
     s.nby = (p.ny + 1) / 2;
     s.nbz = (p.nz + 1) / 2;
     s.nbw = (s.nbx + 31) / 32;
-    // z parts: one CTA (one per SM) marches one part of one tile. Pick the number of
-    // parts that minimises waves x (planes per part + 2 halo planes + ~2 planes of
-    // pipeline fill), the cost of a part-major launch.
-    const long long tiles = (long long)s.tiles_x * s.tiles_y;
-    const int S = (c->num_sms > 0 ? c->num_sms : 1) * step_ctas_per_sm();
-    int best_k = 1;
-    double best = 1e300;
-    for (int k = 1; k <= p.nz && k <= 4096; ++k) {
-        const long long ctas = tiles * k;
-        const long long waves = (ctas + S - 1) / S;
-        const double cost = (double)waves * ((double)p.nz / k + 4.0);
-        if (cost < best * 0.999) {
-            best = cost;
-            best_k = k;
-        }
-    }
-    s.zparts = best_k;
-    s.chain = 0;
-    c->grid = (int)(tiles * best_k);
-    s.band_k = s.band_h = 0;
-    // chain mode when one wave of whole parts would leave SMs unevenly loaded: every
-    // CTA slot, with about w = nz tiles / slots planes each: k = slots / tiles bands
-    // of h ~ w planes, one CTA per (band, tile), and the rest shared by the remaining
-    // slots; of h near w the one whose busiest CTA has the fewest planes (counting
-    // about one plane of pipeline fill per tile a CTA starts) is taken.
-    const long long units = tiles * p.nz;
-    if (tiles < S && units >= 8LL * S && tiles * best_k != S) {
-        const int k = (int)(S / tiles);
-        const double w = (double)units / (double)S;
-        double best_cost = (double)p.nz / best_k + 1.0;   // part mode: one part per CTA
-        for (int h = std::max(1, (int)std::floor(w) - 2); h <= (int)std::ceil(w) + 3; ++h) {
-            const int r = p.nz - k * h;
-            const long long R = S - (long long)k * tiles;
-            if (r < 0 || (r > 0 && R <= 0)) continue;
-            double cost = h + 1.0;
-            if (r > 0) {
-                const double rem = (double)r * tiles / (double)R;
-                cost = std::max(cost, rem + std::ceil(rem / r) + 1.0);
-            }
-            if (cost < best_cost) {
-                best_cost = cost;
-                s.band_k = k;
-                s.band_h = h;
-                s.chain = (int)(r > 0 ? S : (long long)k * tiles);
-            }
-        }
-        if (s.chain > 0) c->grid = s.chain;
-    }
+    const WorkSplit w = work_split(p, c->num_sms);
+    s.zparts = w.zparts;
+    s.chain = w.chain;
+    s.band_k = w.band_k;
+    s.band_h = w.band_h;
+    c->grid = w.grid;
 }
 
 // The step kernel's bounded waits record a give-up in a device word; report it.

@@ -29,7 +29,8 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_step_timed", "lbm_launches_per_step",
            "lbm_get_fields", "lbm_get_pops", "lbm_set_pops", "lbm_observables", "lbm_laplace",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
-           "lbm_footprint_bytes", "lbm_steps_taken", "lbm_destroy", "lbm_last_error",
+           "lbm_footprint_bytes", "lbm_work_split", "lbm_steps_taken", "lbm_destroy",
+           "lbm_last_error",
            "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
            "lbm_droplets", "lbm_structure_factor", "lbm_selftest_timeout",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
@@ -100,6 +101,7 @@ def load():
             "lbm_load_state": (C.c_int, [_P, C.c_void_p]),
             "lbm_sync": (C.c_int, [_P]),
             "lbm_footprint_bytes": (C.c_size_t, [PP]),
+            "lbm_work_split": (C.c_int, [PP, C.c_int, C.POINTER(C.c_longlong)]),
             "lbm_steps_taken": (C.c_longlong, [_P]),
             "lbm_destroy": (None, [_P]),
             "lbm_last_error": (C.c_char_p, [_P]),
@@ -170,6 +172,16 @@ def totals_noalloc(pops_ptr: int, n_nodes: int, out_ptr: int, stream=None) -> No
 
 def footprint_bytes(params: Params) -> int:
     return int(load().lbm_footprint_bytes(C.byref(params)))
+
+
+def work_split(params: Params, num_sms: int) -> dict:
+    """The step kernel's work split on a GPU of num_sms SMs (include/lbm.h,
+    lbm_work_split): zparts, chain, band_k, band_h, grid."""
+    out = (C.c_longlong * 5)()
+    rc = load().lbm_work_split(C.byref(params), int(num_sms), out)
+    if rc != 0:
+        raise LbmError(rc, load().lbm_last_error(None).decode())
+    return dict(zip(("zparts", "chain", "band_k", "band_h", "grid"), (int(v) for v in out)))
 
 
 def _is_torch(a):
