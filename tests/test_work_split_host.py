@@ -90,3 +90,16 @@ def test_invalid_arguments_are_refused():
         split(16, 16, 16, 0)
     with pytest.raises(lbm.LbmError):
         split(16, 16, 16, 152, tau_r=0.5)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(storage=7), dict(storage="fp32_q5", model="shan_chen", G_sc=1.2),
+    dict(model="shan_chen", A_nc=0.01), dict(wall_u=0.01), dict(wall_y=1, wall_u=0.5),
+    dict(beta=1.5), dict(sigma=-1.0), dict(A_nc=0.01, h_min=0.0), dict(A_nc=0.01, h_cut=12.0),
+    dict(storage="fp16", rho0=0.0),
+])
+def test_parameter_validation_without_a_device(bad):
+    # the parameter checks of lbm_create run before any device call; lbm_work_split
+    # applies the same checks, so they are testable on the host
+    with pytest.raises(lbm.LbmError):
+        split(16, 16, 16, 152, **bad)
