@@ -1,30 +1,36 @@
 """Benchmark of the fused colour-gradient LB step on GB300.
 
-Default workload: the microfluidic-crystal channel, 256 x 128 x 64 D3Q19 nodes with
-bounce-back walls at the y and z extremes, 40 droplets (radii 6-9, seeded), sigma =
-0.02, beta = 0.7, near-contact force A = 0.01 within 3 lu, g_x = 1e-6, FP32 storage.
-One step = one lattice update of every node (one launch of the fused kernel).
+Default workload: the dense emulsion, 512^3 periodic D3Q19 nodes (134,217,728) with
+random non-overlapping droplets at volume fraction 0.35 (radii 6-12, seeded random
+sequential addition), Kolmogorov forcing F_x = 1e-5 sin(2 pi y / 512), near-contact
+force A = 0.01 within 3 lu, sigma = 0.01, beta = 0.7, tau = 1, FP32 storage. One step =
+one lattice update of every node (the near-contact pass and the fused step kernel).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16|bf16|fp32_q5]
-                  [--impl ours|reference] [--model colour|shan_chen] [--no-serving]
-                  [--no-models] [--no-cpu-baseline]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload emulsion|channel]
+                  [--storage fp32|fp16|bf16|fp32_q5] [--impl ours|reference]
+                  [--model colour|shan_chen] [--no-serving] [--no-models] [--no-cpu-baseline]
 
-Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second)
-over all ranks; ``e2e`` times the same job through the public C-ABI with host
-buffers (set fields from pinned host memory, K steps, fields back to the host);
-``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations
-per node, read once and written once) to the measured HBM bandwidth;
-``fp16_store`` repeats the device-resident measurement with FP16 deviation
-storage (and, inside it, BF16) and ``fp32_q5_store`` with the reduced FP32 form (19 totals and 5 recolouring
-coefficients per node, 2 x 24 x 4 bytes per node and step); ``serving`` runs the served request stream (256 droplet / sheared-droplet
-runs of edge 32-128, Poisson arrivals at 50/s, FP16 storage) through the serving
-engine and reports p50/p99 latency beside aggregate GLUPS; ``shan_chen`` and
-``sheared_bijel`` give the device-resident GLUPS of the Shan-Chen model on the same
-channel and of the sheared-bijel channel with sliding walls; ``cpu_baseline`` times
-the FP64 oracle on the host cores. ``--impl reference`` times the oracle itself on
-the same workload (the method has no other reference implementation). Multi-GPU
-runs are independent replicas: one channel lattice per rank, the request stream
-sharded over the ranks.
+Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second) over
+all ranks, device-resident; the timed K-step loop is repeated until about a second
+has been timed (so that the clock sampler sees it) and the median repeat is
+reported. ``e2e`` times the same job through the public C-ABI with host buffers
+(set fields from pinned host memory, K steps, fields back to the host);
+``roofline`` relates the step kernel's algorithmic bytes (2 x 19 x 2 populations per
+node, read once and written once) to the measured HBM bandwidth; ``fp16_store``
+repeats the device-resident measurement on the same lattice with FP16 deviation
+storage (and, inside it, BF16), ``fp32_q5_store`` with the reduced FP32 form (19
+totals and 5 recolouring coefficients per node); ``gel_640`` times the bicontinuous
+gel quench (640^3, tau = 0.8, 2 % pinning sites, near contact on, FP32) with the
+near-contact pass's share; ``channel`` the microfluidic-crystal channel (256 x 128
+x 64); ``shan_chen`` and ``sheared_bijel`` the Shan-Chen model on the channel and the
+sheared-bijel channel with sliding walls; ``serving`` runs the served request stream
+(256 droplet / sheared-droplet runs of edge 32-128, Poisson arrivals at 50/s, FP16
+storage) through the serving engine and reports p50/p99 latency beside aggregate
+GLUPS; ``cpu_baseline`` times the FP64 oracle on the host cores (all, and one) on a
+bounded sample of the workload. ``--impl reference`` times the oracle itself on that
+sample (the method has no other reference implementation). Multi-GPU runs are
+independent replicas: one lattice per rank, the request stream sharded over the
+ranks.
 """
 from __future__ import annotations
 
@@ -42,9 +48,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & % HBM roofline, FP32 vs FP16-store; served-run p50/p99 latency"
-WORKLOAD = "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, NC on"
 Q, C = 19, 2
 
+WORKLOADS = {
+    "emulsion": "dense emulsion 512^3 periodic, volume fraction 0.35, radii 6-12, "
+                "Kolmogorov F_x = 1e-5 sin(2 pi y/512), NC on (A = 0.01, h_min = 3)",
+    "channel": "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, NC on",
+    "channel_sc": "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, "
+                  "Shan-Chen G_sc = 1.6",
+}
+
+# Bounded sample of a workload for the oracle (CPU baseline, reference arm): a box of
+# the workload's initial fields, stepped as a periodic lattice of its own with the
+# workload's parameters. (nz, ny, nx) of the box.
+CPU_SAMPLE = {"emulsion": (64, 256, 256), "channel": None, "channel_sc": None}
 
 KERNEL_SOURCES = ("lbm_step.cu", "lbm_device.cuh")   # what the step kernel is built from
 
@@ -66,17 +83,22 @@ def bytes_per_node(storage: str) -> int:
     return 2 * Q * C * (4 if storage == "fp32" else 2)
 
 
-def measured_traffic(storage: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def measured_traffic(storage: str, workload: str = "emulsion", nodes: int | None = None):
+    """DRAM bytes per launch of the step kernel on `workload` from the committed ncu
+    summary, if it was taken on the current kernel sources; else None. A line taken on
+    a smaller case of the workload gives bytes per node, scaled to `nodes`."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     want = kernel_source_hash()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and not line.startswith("#") and parts[0] == want and parts[1] == storage:
-            return float(parts[2])
+        if line.startswith("#") or len(parts) < 5:
+            continue
+        h, st, wl, captured_nodes, b = parts[:5]
+        if h == want and st == storage and wl == workload:
+            per_node = float(b) / float(captured_nodes)
+            return per_node * (nodes if nodes is not None else float(captured_nodes))
     return None
 
 
@@ -89,21 +111,89 @@ def peaks():
     return 6800.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms in a thread."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+def match_gpu(uuid: str | None, smi_listing: str, local: int) -> str:
+    """nvidia-smi's -i argument for a torch device: the UUID nvidia-smi lists for it
+    (`smi_listing` = lines "uuid, index" of `nvidia-smi --query-gpu=uuid,index`), since
+    nvidia-smi ignores CUDA_VISIBLE_DEVICES and a local index may name another GPU;
+    the local index when the UUID is unknown or not listed."""
+    if uuid:
+        u = uuid.lower().removeprefix("gpu-")
+        for ln in smi_listing.splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if parts and parts[0].lower().removeprefix("gpu-") == u:
+                return parts[0]
+    return str(local)
 
-    def __init__(self, index):
-        self.index = index
+
+def gpu_selector(local: int) -> str:
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+        r = subprocess.run(["nvidia-smi", "--query-gpu=uuid,index", "--format=csv,noheader"],
+                           capture_output=True, text=True, timeout=10)
+        return match_gpu(str(u) if u is not None else None, r.stdout, local)
+    except Exception:
+        return str(local)
+
+
+CLOCK_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                "clocks_event_reasons.sw_power_cap")
+REASON_NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def parse_clock_line(line: str):
+    parts = [p.strip() for p in line.split(",")]
+    return parts if len(parts) >= 7 else None
+
+
+def summarise_clocks(samples):
+    """Median SM clock, maximum clock and the throttle reasons seen in nvidia-smi
+    samples (lists of the CLOCK_FIELDS columns)."""
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+    def num(s):
+        try:
+            return float(s)
+        except ValueError:
+            return None
+    sm = [v for v in (num(s[0]) for s in samples) if v is not None]
+    mx = [v for v in (num(s[1]) for s in samples) if v is not None]
+    reasons = sorted({REASON_NAMES[k] for s in samples for k in range(4)
+                      if s[3 + k].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+            "samples": len(samples)}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons of one GPU, sampled every 100 ms in a
+    thread, plus one query at entry and one at exit (so a short region still has a
+    record)."""
+
+    def __init__(self, selector):
+        self.sel = selector
         self.samples = []
+        self.edges = []
         self.proc = None
 
+    def _query_once(self):
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", self.sel, f"--query-gpu={CLOCK_FIELDS}",
+                                "--format=csv,noheader,nounits"], capture_output=True,
+                               text=True, timeout=10)
+            s = parse_clock_line(r.stdout.strip().splitlines()[0]) if r.stdout.strip() else None
+            if s:
+                self.edges.append(s)
+        except (FileNotFoundError, OSError, subprocess.TimeoutExpired, IndexError):
+            pass
+
     def __enter__(self):
+        self._query_once()
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", "-i", self.sel, f"--query-gpu={CLOCK_FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -114,9 +204,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 7:
-                self.samples.append(parts)
+            s = parse_clock_line(line)
+            if s:
+                self.samples.append(s)
 
     def __exit__(self, *a):
         if self.proc:
@@ -125,18 +215,13 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        self._query_once()
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4)
-                          if s[3 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        d = summarise_clocks(self.samples if self.samples else self.edges)
+        d["source"] = "100 ms samples" if self.samples else "queries at entry and exit"
+        d["gpu"] = self.sel
+        return d
 
 
 def dist_env():
@@ -146,27 +231,54 @@ def dist_env():
     return rank, world, local
 
 
-def bench_workload(args):
-    """The timed workload: the channel, with the colour-gradient model (default) or the
-    Shan-Chen model (--model shan_chen)."""
-    from paper_2005_12764_gb300 import inputs
+def workload_key(args):
     if args.model == "shan_chen":
+        return "channel_sc"
+    return args.workload
+
+
+def make_workload(key):
+    from paper_2005_12764_gb300 import inputs
+    if key == "emulsion":
+        return inputs.dense_emulsion()
+    if key == "channel_sc":
         return inputs.channel_shan_chen()
     return inputs.channel_droplets()
 
 
-def workload_name(args):
-    if args.model == "shan_chen":
-        return "microfluidic-crystal channel 256x128x64, 40 droplets, walls y/z, Shan-Chen G_sc = 1.6"
-    return WORKLOAD
+def host_cpu():
+    """Host CPU model (lscpu) and core count."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (FileNotFoundError, OSError, subprocess.TimeoutExpired):
+        pass
+    return {"model": model, "cores": os.cpu_count()}
 
 
-def cpu_oracle_rate(workload, steps, warm=1):
-    """Oracle lattice updates per second on this host (all cores) over `steps` steps."""
+def cpu_sample(w, key):
+    """Fields and shape of the oracle's bounded sample of workload w: the whole
+    lattice, or a box of its initial fields (CPU_SAMPLE) stepped as a periodic lattice
+    with the workload's parameters."""
+    box = CPU_SAMPLE.get(key)
+    if box is None:
+        return w.rho_r, w.rho_b, w.shape, "the whole lattice"
+    nz, ny, nx = box
+    rr = w.rho_r[:nz, :ny, :nx].copy()
+    rb = w.rho_b[:nz, :ny, :nx].copy()
+    return rr, rb, box, f"a {nx}x{ny}x{nz} box of its initial fields, periodic"
+
+
+def oracle_rate(rr, rb, shape, params, steps, warm=1):
+    """Oracle lattice updates per second on this host over `steps` steps."""
     import oracle
-    nz, ny, nx = workload.shape
-    lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **workload.params))
-    lat.set_fields(workload.rho_r, workload.rho_b)
+    nz, ny, nx = shape
+    lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **params))
+    lat.set_fields(rr, rb)
     lat.step(warm)
     t0 = time.perf_counter()
     lat.step(steps)
@@ -175,56 +287,106 @@ def cpu_oracle_rate(workload, steps, warm=1):
     return nx * ny * nz * steps / dt, dt
 
 
+def one_core_rate(key, steps):
+    """The oracle on one core: a child process with OMP_NUM_THREADS=1 (the OpenMP
+    runtime of this process already has its thread count)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate-only",
+                        "--workload", key, "--cpu-steps", str(steps)], capture_output=True,
+                       text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_rate_only(args):
+    key = workload_key(args)
+    w = make_workload(key)
+    rr, rb, shape, what = cpu_sample(w, key)
+    rate, dt = oracle_rate(rr, rb, shape, w.params, args.cpu_steps)
+    print(json.dumps({"rate": rate, "dt": dt, "sample": what}), flush=True)
+
+
 def run_reference(args):
-    """The FP64 oracle timed on the host cores, on the same workload and metric."""
+    """The FP64 oracle timed on the host cores, on the same workload and metric (each
+    step on the bounded sample of the workload)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = bench_workload(args)
-    N = w.rho_r.size
+    key = workload_key(args)
+    w = make_workload(key)
+    rr, rb, shape, what = cpu_sample(w, key)
     import oracle
-    nz, ny, nx = w.shape
+    nz, ny, nx = shape
     lat = oracle.Lattice(oracle.make_params(nx, ny, nz, **w.params))
-    lat.set_fields(w.rho_r, w.rho_b)
+    lat.set_fields(rr, rb)
     lat.step(args.warmup)
     t0 = time.perf_counter()
     lat.step(args.steps)
     dt = time.perf_counter() - t0
-    glups = N * args.steps / dt / 1e9
-    cores = os.cpu_count()
+    n = nx * ny * nz
+    glups = n * args.steps / dt / 1e9
+    cpu = host_cpu()
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "nodes": N, "storage": "f64 (oracle)"},
-            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full steps of the {nx}x{ny}x{nz} channel"},
+            "config": {"workload": WORKLOADS[key], "nodes": w.rho_r.size,
+                       "storage": "f64 (oracle)"},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": cpu["cores"],
+                             "cpu": cpu["model"], "kind": "oracle",
+                             "sample": f"{args.steps} steps of {what} ({n} nodes)"},
             "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def device_resident_glups(lbm, w, storage, steps, warmup, stream, local):
-    """GLUPS of `steps` steps queued back to back (CUDA events on the library's
-    stream) and the mean step-kernel time (ms) from the library's own events."""
+def timed_steps(lat, stream, steps, min_total_s=1.0, max_reps=20):
+    """Per-repeat milliseconds of `steps` steps queued back to back (CUDA events on the
+    library's stream, synchronised on both sides), repeated until about min_total_s
+    has been timed."""
+    import torch
+    reps = []
+    total = 0.0
+    while len(reps) < max_reps and (total < min_total_s * 1e3 or len(reps) < 1):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b)
+        reps.append(ms)
+        total += ms
+    return reps
+
+
+def device_resident(lbm, w, storage, steps, warmup, stream, local, pins=None):
+    """GLUPS of `steps` steps queued back to back (median repeat), the mean step-kernel
+    and near-contact pass times (ms, the library's own events), and the lattice's
+    species-mass drift over the run."""
     import torch
     nz, ny, nx = w.shape
     lat = lbm.Lattice(lbm.make_params(nx, ny, nz, storage=storage, stream=stream.cuda_stream,
                                       **w.params))
     lat.set_fields(torch.from_numpy(w.rho_r).to(f"cuda:{local}"),
                    torch.from_numpy(w.rho_b).to(f"cuda:{local}"))
+    if pins is not None:
+        lat.set_pin_mask(torch.from_numpy(pins).to(f"cuda:{local}"))
+    m0 = lat.observables()[:2]
     lat.step(warmup)
     lat.sync()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    lat.step(steps)
-    b.record(stream)
-    stream.synchronize()
-    ms = a.elapsed_time(b)
-    kt = max(5, min(steps, 50))
-    _, step_ms, _ = lat.step_timed(kt)
+    reps = timed_steps(lat, stream, steps, min_total_s=0.5, max_reps=5)
+    ms = statistics.median(reps)
+    kt = max(5, min(steps, 20))
+    nc_ms, step_ms, _ = lat.step_timed(kt)
+    m1 = lat.observables()[:2]
+    taken = lat.steps_taken
     lat.close()
-    return nx * ny * nz * steps / (ms * 1e-3) / 1e9, ms / steps, step_ms / kt
+    drift = [abs(float(m1[k]) - float(m0[k])) / float(m0[k]) for k in range(2)]
+    return {"value": nx * ny * nz * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps,
+            "kernel_ms": step_ms / kt, "near_contact_pass_ms": nc_ms / kt,
+            "mass_drift_rel": {"red": drift[0], "blue": drift[1], "steps": taken}}
 
 
 def serving_run(lbm, rank, world, dist, local):
@@ -250,13 +412,39 @@ def serving_run(lbm, rank, world, dist, local):
             "engine": {k: rep["engine"][k] for k in ("ticks", "peak_bytes", "planes_per_cta")}}
 
 
-def other_workloads(lbm, stream, local, steps=200):
-    """Device-resident GLUPS of two more workloads of the same step: the Shan-Chen
-    model on the channel geometry, and the sheared-bijel channel (1024 x 128 x 128,
-    sliding walls, near contact on) after 300 steps of coarsening from the quench."""
+def other_workloads(lbm, stream, local, key, steps=20, warmup=5):
+    """Device-resident GLUPS of more workloads of the same step: the gel quench at
+    640^3 (FP32), the channel (when it is not the timed workload), the Shan-Chen model
+    on the channel geometry, and the sheared-bijel channel (1024 x 128 x 128, sliding
+    walls, near contact on) after 300 steps of coarsening from the quench."""
     import torch
     from paper_2005_12764_gb300 import inputs
     out = {}
+    hbm = peaks()[0]
+
+    def frac(kernel_ms, nodes, storage="fp32"):
+        return bytes_per_node(storage) * nodes / (kernel_ms * 1e-3) / 1e9 / hbm
+
+    # the bicontinuous gel quench, 640^3, FP32 (two copies, 81 GB)
+    g = inputs.bicontinuous()
+    n = g.rho_r.size
+    d = device_resident(lbm, g, "fp32", steps, warmup, stream, local, pins=g.pins)
+    d.update({"workload": "bicontinuous gel quench 640^3 periodic, phi0 U(+-0.01), 2 % pins, "
+                          "tau = 0.8, sigma = 0.015, A_nc = 0.02, FP32, steps "
+                          f"{warmup + 1}-{warmup + steps} after the quench",
+              "unit": "GLUPS", "nodes": n,
+              "roofline_frac": frac(d["kernel_ms"], n),
+              "near_contact_share": d["near_contact_pass_ms"] / d["ms_per_step"]})
+    out["gel_640"] = d
+    del g
+    if key != "channel":
+        w = inputs.channel_droplets()
+        n = w.rho_r.size
+        d = device_resident(lbm, w, "fp32", 200, 10, stream, local)
+        d.update({"workload": WORKLOADS["channel"], "unit": "GLUPS", "nodes": n,
+                  "roofline_frac": frac(d["kernel_ms"], n),
+                  "traffic": measured_traffic("fp32", "channel", n)})
+        out["channel"] = d
 
     def timed(lat, k):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -271,14 +459,14 @@ def other_workloads(lbm, stream, local, steps=200):
     lat = lbm.Lattice(lbm.make_params(nx, ny, nz, stream=stream.cuda_stream, **w.params))
     lat.set_fields(w.rho_r, w.rho_b)
     lat.step(10)
-    ms = timed(lat, steps)
+    ms = timed(lat, 200)
     _, k_ms, _ = lat.step_timed(20)
     lat.close()
     alg = bytes_per_node("fp32") * nx * ny * nz
     out["shan_chen"] = {"workload": "channel 256x128x64, 40 droplets, walls y/z, G_sc = 1.6, FP32",
                         "value": nx * ny * nz / (ms * 1e-3) / 1e9, "unit": "GLUPS",
                         "ms_per_step": ms, "kernel_ms": k_ms / 20,
-                        "roofline_frac": alg / (k_ms / 20 * 1e-3) / 1e9 / peaks()[0],
+                        "roofline_frac": alg / (k_ms / 20 * 1e-3) / 1e9 / hbm,
                         "algorithmic_bytes_per_launch": alg}
     w = inputs.sheared_bijel()
     nz, ny, nx = w.shape
@@ -302,14 +490,15 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2005_12764_gb300 import build_lib, inputs, lbm, replicas
+    from paper_2005_12764_gb300 import build_lib, lbm, replicas
 
     rank, world, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build_lib.build()
-    w = bench_workload(args)
+    key = workload_key(args)
+    w = make_workload(key)
     nz, ny, nx = w.shape
     N = nx * ny * nz
     stream = torch.cuda.Stream()
@@ -319,6 +508,7 @@ def run_ours(args):
     dev_rb = torch.from_numpy(w.rho_b).to(f"cuda:{local}")
     torch.cuda.synchronize()
     lat.set_fields(dev_rr, dev_rb)
+    del dev_rr, dev_rb
     lat.step(args.warmup)
     lat.sync()
 
@@ -328,24 +518,21 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- device-resident timing: K steps queued back to back, CUDA events on the
-    # stream the kernels run on
+    # stream the kernels run on; the K-step loop is repeated until about a second has
+    # been timed (the clock sampler's 100 ms samples then cover it) and the median
+    # repeat is taken
     barrier()
-    with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        lat.step(args.steps)
-        t_end.record(stream)
-        stream.synchronize()
+    with ClockSampler(gpu_selector(local)) as clk:
+        reps = timed_steps(lat, stream, args.steps, min_total_s=1.0)
     barrier()
-    total_ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist if world > 1 else None,
-                                       f"cuda:{local}")
+    med_ms = statistics.median(reps)
+    total_ms = replicas.max_over_ranks(med_ms, dist if world > 1 else None, f"cuda:{local}")
     ms_per_step = total_ms / args.steps
     glups = world * N * args.steps / (total_ms * 1e-3) / 1e9
     # per-kernel durations (events around each launch, inside the library)
-    kt = max(5, min(args.steps, 50))
+    kt = max(5, min(args.steps, 20))
     nc_ms, step_ms, _ = lat.step_timed(kt)
-    kern_ms = [step_ms / kt]
+    kern_ms = step_ms / kt
     nc_avg_ms = nc_ms / kt
     # ---- end to end through the public API with pinned host buffers
     host_rr = torch.from_numpy(w.rho_r).pin_memory()
@@ -364,64 +551,81 @@ def run_ours(args):
     e2e = world * N * args.steps / e2e_s / 1e9
     h2d = 2 * N * 8
     d2h = 6 * N * 8
+    del host_rr, host_rb, outs
 
     # ---- roofline of the step kernel
     alg_bytes = bytes_per_node(args.storage) * N
-    k_avg = statistics.mean(kern_ms) * 1e-3
-    achieved = alg_bytes / k_avg / 1e9
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic(args.storage)
+    traffic = measured_traffic(args.storage, key, N)
 
     obs = lat.observables()
     finite = bool(np.isfinite(obs[:5]).all())
     launches = args.steps * lat.launches_per_step
     lat.close()
-    # the same workload with FP16 deviation storage (device-resident, as `value`)
+    # the same workload with FP16 / BF16 deviation storage and the reduced FP32 form
+    # (device-resident, as `value`)
     fp16 = q5 = None
-    if args.storage == "fp32":
-        g16, ms16, k16 = device_resident_glups(lbm, w, "fp16", args.steps, args.warmup, stream, local)
-        g16 = replicas.sum_over_ranks(g16, dist if world > 1 else None, f"cuda:{local}")
-        alg16 = 2 * Q * C * 2 * N
-        fp16 = {"value": g16, "unit": "GLUPS", "ms_per_step": ms16, "kernel_ms": k16,
-                "roofline_frac": alg16 / (k16 * 1e-3) / 1e9 / peaks()[0],
-                "algorithmic_bytes_per_launch": alg16}
-        # BF16 deviation storage beside it (same bytes, 8-bit mantissa)
-        gb, msb, kb = device_resident_glups(lbm, w, "bf16", args.steps, args.warmup, stream, local)
-        gb = replicas.sum_over_ranks(gb, dist if world > 1 else None, f"cuda:{local}")
-        fp16["bf16"] = {"value": gb, "unit": "GLUPS", "ms_per_step": msb, "kernel_ms": kb}
-    if args.storage == "fp32" and args.model == "colour":
-        # and with the reduced FP32 form (Q + 5 values per node; colour-gradient states
-        # only), against its own byte model of 192 bytes per node and step
-        g5, ms5, k5 = device_resident_glups(lbm, w, "fp32_q5", args.steps, args.warmup, stream,
-                                            local)
-        g5 = replicas.sum_over_ranks(g5, dist if world > 1 else None, f"cuda:{local}")
+    if args.storage == "fp32" and not args.no_variants:
+        d16 = device_resident(lbm, w, "fp16", args.steps, args.warmup, stream, local)
+        d16["value"] = replicas.sum_over_ranks(d16["value"], dist if world > 1 else None,
+                                               f"cuda:{local}")
+        alg16 = bytes_per_node("fp16") * N
+        d16.update({"unit": "GLUPS",
+                    "roofline_frac": alg16 / (d16["kernel_ms"] * 1e-3) / 1e9 / peak,
+                    "algorithmic_bytes_per_launch": alg16,
+                    "traffic": measured_traffic("fp16", key, N)})
+        fp16 = d16
+        db = device_resident(lbm, w, "bf16", args.steps, args.warmup, stream, local)
+        db["value"] = replicas.sum_over_ranks(db["value"], dist if world > 1 else None,
+                                              f"cuda:{local}")
+        db.update({"unit": "GLUPS",
+                   "roofline_frac": alg16 / (db["kernel_ms"] * 1e-3) / 1e9 / peak})
+        fp16["bf16"] = db
+    if args.storage == "fp32" and args.model == "colour" and not args.no_variants:
+        # the reduced FP32 form (Q + 5 values per node; colour-gradient states only),
+        # against its own byte model of 192 bytes per node and step
+        d5 = device_resident(lbm, w, "fp32_q5", args.steps, args.warmup, stream, local)
+        d5["value"] = replicas.sum_over_ranks(d5["value"], dist if world > 1 else None,
+                                              f"cuda:{local}")
         alg5 = bytes_per_node("fp32_q5") * N
-        q5 = {"value": g5, "unit": "GLUPS", "ms_per_step": ms5, "kernel_ms": k5,
-              "roofline_frac": alg5 / (k5 * 1e-3) / 1e9 / peaks()[0],
-              "algorithmic_bytes_per_launch": alg5, "traffic": measured_traffic("fp32_q5")}
+        d5.update({"unit": "GLUPS",
+                   "roofline_frac": alg5 / (d5["kernel_ms"] * 1e-3) / 1e9 / peak,
+                   "algorithmic_bytes_per_launch": alg5,
+                   "traffic": measured_traffic("fp32_q5", key, N)})
+        q5 = d5
     others = None
     if not args.no_models:
-        others = other_workloads(lbm, stream, local)
+        others = other_workloads(lbm, stream, local, key)
     serving_rep = None
     if not args.no_serving:
         serving_rep = serving_run(lbm, rank, world, dist if world > 1 else None, local)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            rate, dt = cpu_oracle_rate(w, args.cpu_steps)
-            cpu = {"value": rate / 1e9, "unit": "GLUPS", "cores": os.cpu_count(),
+            rr, rb, shape, what = cpu_sample(w, key)
+            n_s = shape[0] * shape[1] * shape[2]
+            rate, dt = oracle_rate(rr, rb, shape, w.params, args.cpu_steps)
+            hc = host_cpu()
+            cpu = {"value": rate / 1e9, "unit": "GLUPS", "cores": hc["cores"], "cpu": hc["model"],
                    "kind": "oracle",
-                   "sample": f"{args.cpu_steps} full FP64 steps of the {nx}x{ny}x{nz} channel "
-                             f"({dt:.1f} s)"}
+                   "sample": f"{args.cpu_steps} FP64 steps of {what} ({n_s} nodes, {dt:.1f} s)"}
+            one = one_core_rate(key, max(1, args.cpu_steps // 10))
+            if one:
+                cpu["one_core"] = {"value": one["rate"] / 1e9, "unit": "GLUPS", "cores": 1,
+                                   "sample": f"{max(1, args.cpu_steps // 10)} FP64 steps of "
+                                             f"{one['sample']} ({one['dt']:.1f} s)"}
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args), "nodes": N, "storage": args.storage,
+            "config": {"workload": WORKLOADS[key], "nodes": N, "storage": args.storage,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
-                             % (bytes_per_node(args.storage) * N / 2 / 1e6)},
+                             % (bytes_per_node(args.storage) * N / 2 / 1e6),
+                       "timed_repeats": len(reps),
+                       "repeat_ms": [round(r, 3) for r in reps]},
             "e2e": {"value": e2e, "unit": "GLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "job": "set_fields(host) + K steps + get_fields(host)"},
@@ -429,7 +633,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "kernel": "step_kernel (fused stream/collide/perturb/recolour)",
-                         "kernel_ms": statistics.mean(kern_ms),
+                         "kernel_ms": kern_ms,
                          "near_contact_pass_ms": nc_avg_ms,
                          "ghost_fill": "written by the near-contact pass (no launch of its own)",
                          "algorithmic_bytes_per_launch": alg_bytes},
@@ -455,23 +659,29 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="emulsion", choices=["emulsion", "channel"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp32_q5"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP16/BF16 and reduced-form lines")
     ap.add_argument("--model", default="colour", choices=["colour", "shan_chen"],
-                    help="model of the timed workload (default: the colour-gradient channel)")
+                    help="model of the timed workload (shan_chen: the channel)")
     ap.add_argument("--no-models", action="store_true",
-                    help="skip the Shan-Chen and sheared-bijel lines")
+                    help="skip the gel, channel, Shan-Chen and sheared-bijel lines")
+    ap.add_argument("--oracle-rate-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.storage == "fp32_q5" and args.model == "shan_chen":
         ap.error("the reduced storage form holds colour-gradient states only")
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.oracle_rate_only:
+        run_oracle_rate_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

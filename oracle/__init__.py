@@ -75,6 +75,8 @@ def _load():
                 "or_recolour": (None, [_D, C.c_double, C.c_double, C.c_double, _D, _D, _D]),
                 "or_A_h": (C.c_double, [C.c_double] * 4),
                 "or_nc_strength_node": (C.c_double, [P, _D, _U8, C.c_long, C.c_long, C.c_long]),
+                "or_nc_strength_node_thr": (C.c_double, [P, _D, _U8, C.c_long, C.c_long,
+                                                         C.c_long, C.c_double, C.c_double]),
                 "or_gradient": (None, [P, _D, _D, _D, _D]),
                 "or_create": (C.c_void_p, [P]),
                 "or_destroy": (None, [C.c_void_p]),
@@ -89,6 +91,8 @@ def _load():
                 "or_get_forces": (None, [C.c_void_p, _D]),
                 "or_totals": (None, [C.c_void_p, _D]),
                 "or_step_nodes": (C.c_int, [P, _D, _D, _D, _U8, C.c_long, _L, _D, _D, _D]),
+                "or_step_nodes_given_ah": (C.c_int, [P, _D, _D, _D, _U8, C.c_long, _L, _D, _D,
+                                                     _D, _D]),
                 "or_laplace": (None, [C.c_void_p, _D, _D]),
             }
             for name, (res, args) in sig.items():
@@ -204,11 +208,24 @@ def nc_strength_node(params: Params, phi_ray, x, y, z, pin=None):
                                        int(z))
 
 
-def step_nodes(params: Params, fr, fb, phi_lag, nodes, pin=None):
+def nc_strength_node_thr(params: Params, phi_ray, x, y, z, band, g_min, pin=None):
+    """nc_strength_node with the reading's two thresholds given: the sign band of a
+    ray sample (1e-5) and the least lagged gradient (1e-3)."""
+    phi_ray = _f64(phi_ray)
+    pin_p = None
+    if pin is not None:
+        pin = np.ascontiguousarray(pin, dtype=np.uint8)
+        pin_p = pin.ctypes.data_as(_U8)
+    return _load().or_nc_strength_node_thr(C.byref(params), _d(phi_ray), pin_p, int(x), int(y),
+                                           int(z), float(band), float(g_min))
+
+
+def step_nodes(params: Params, fr, fb, phi_lag, nodes, pin=None, ah=None):
     """One step evaluated at the listed flat node indices from a given state.
 
     fr, fb: [19, N] post-collision populations; phi_lag: [N] lagged colour field.
-    Returns (fr_new [n,19], fb_new [n,19], F [n,3]).
+    ah: optional near-contact strength of each listed node, used instead of the
+    measured one. Returns (fr_new [n,19], fb_new [n,19], F [n,3]).
     """
     fr = _f64(fr)
     fb = _f64(fb)
@@ -220,8 +237,15 @@ def step_nodes(params: Params, fr, fb, phi_lag, nodes, pin=None):
     if pin is not None:
         pin = np.ascontiguousarray(pin, dtype=np.uint8)
         pin_p = pin.ctypes.data_as(_U8)
-    rc = _load().or_step_nodes(C.byref(params), _d(fr), _d(fb), _d(phi_lag), pin_p, n,
-                               nodes.ctypes.data_as(_L), _d(oa), _d(ob), _d(F))
+    if ah is None:
+        rc = _load().or_step_nodes(C.byref(params), _d(fr), _d(fb), _d(phi_lag), pin_p, n,
+                                   nodes.ctypes.data_as(_L), _d(oa), _d(ob), _d(F))
+    else:
+        ah = _f64(ah).reshape(-1)
+        assert ah.size == n
+        rc = _load().or_step_nodes_given_ah(C.byref(params), _d(fr), _d(fb), _d(phi_lag), pin_p,
+                                            n, nodes.ctypes.data_as(_L), _d(ah), _d(oa),
+                                            _d(ob), _d(F))
     if rc != 0:
         raise ValueError("or_step_nodes needs the lagged near-contact reading")
     return oa, ob, F

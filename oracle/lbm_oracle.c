@@ -403,20 +403,26 @@ static void gradient_node(const or_params* p, const double* phi, long x, long y,
  *    |G'| >= 1e-3 whose nearest pin (within the cube of half-width ceil(h_cut))
  *    lies at distance d gets A_h[d] added.
  * This routine returns the strength A_h at node (x, y, z).                       */
-double or_nc_strength_node(const or_params* p, const double* phi_ray,
-                           const unsigned char* pin, long x, long y, long z) {
+/* The same strength with the two thresholds of the reading as arguments: the
+ * sign band (1e-5 in the reading) and the least lagged gradient (1e-3). Used by
+ * the tests to decide whether a difference between an FP32 evaluation and this
+ * one is a branch taken differently at a threshold (a sample or a gradient within
+ * rounding of it), by evaluating the reading with each threshold moved by the
+ * FP32 rounding bound.                                                          */
+double or_nc_strength_node_thr(const or_params* p, const double* phi_ray,
+                               const unsigned char* pin, long x, long y, long z,
+                               double band, double g_min) {
     lattice_init();
     if (p->A_nc == 0.0) return 0.0;
     double G[3];
     gradient_node(p, phi_ray, x, y, z, G);
     double gm = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-    if (!(gm >= 1e-3) || !isfinite(gm)) return 0.0;   /* non-finite fields: no force */
+    if (!(gm >= g_min) || !isfinite(gm)) return 0.0;   /* non-finite fields: no force */
     double n[3] = {-G[0] / gm, -G[1] / gm, -G[2] / gm};
     int nsamp = (int)floor(2.0 * (p->h_cut + 3.0)) + 1; /* t = -1 ... h_cut + 2 */
-    /* A sample carries a sign only if |phi| > 1e-5 (samples at rounding level of
+    /* A sample carries a sign only if |phi| > band (samples at rounding level of
      * zero are skipped); a crossing lies between the last signed sample and the
      * next one of opposite sign, located by linear interpolation between them.  */
-    const double band = 1e-5;
     double t_a = 0, v_a = 0, t_d = 0, t_u = 0;
     int have_a = 0, have_d = 0, have_u = 0;
     for (int s = 0; s < nsamp && !have_u; ++s) {
@@ -458,6 +464,11 @@ double or_nc_strength_node(const or_params* p, const double* phi_ray,
         if (best >= 0) Ah += or_A_h(best, p->A_nc, p->h_min, p->h_cut);
     }
     return Ah;
+}
+
+double or_nc_strength_node(const or_params* p, const double* phi_ray,
+                           const unsigned char* pin, long x, long y, long z) {
+    return or_nc_strength_node_thr(p, phi_ray, pin, x, y, z, 1e-5, 1e-3);
 }
 
 /* Isotropic colour gradient G(x) = 3 sum_i w_i c_i phi(x + c_i), the stencil form
@@ -831,9 +842,10 @@ void or_totals(const or_state* s, double out[5]) {
  * of the listed nodes to out_r, out_b ([nlist][Q]) and their force to F ([nlist][3]).
  * The near-contact ray needs the current colour field only when nc_lag == 0,
  * which this routine does not support (returns -1).                           */
-int or_step_nodes(const or_params* p, const double* fr, const double* fb,
-                  const double* phi_lag, const unsigned char* pin, long nlist,
-                  const long* list, double* out_r, double* out_b, double* Fout) {
+static int step_nodes_impl(const or_params* p, const double* fr, const double* fb,
+                           const double* phi_lag, const unsigned char* pin, long nlist,
+                           const long* list, const double* ah_given, double* out_r,
+                           double* out_b, double* Fout) {
     lattice_init();
     if (!p->nc_lag && p->A_nc != 0.0) return -1;
     long N = (long)p->nx * p->ny * p->nz;
@@ -894,7 +906,7 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
         double G[3] = {3.0 * g[0], 3.0 * g[1], 3.0 * g[2]};
         double Fb[3], Fn[3], F[3];
         body_force(p, y, Fb);
-        double ah = or_nc_strength_node(p, phi_lag, pin, x, y, z);
+        double ah = ah_given ? ah_given[k] : or_nc_strength_node(p, phi_lag, pin, x, y, z);
         for (int a = 0; a < 3; ++a) Fn[a] = ah * G[a];
         for (int a = 0; a < 3; ++a) F[a] = Fb[a] + Fn[a];
         collide_node(p, gr, gb, rr, rb, G, F, out_r + k * Q, out_b + k * Q);
@@ -902,6 +914,22 @@ int or_step_nodes(const or_params* p, const double* fr, const double* fb,
             for (int a = 0; a < 3; ++a) Fout[3 * k + a] = F[a];
     }
     return 0;
+}
+
+int or_step_nodes(const or_params* p, const double* fr, const double* fb,
+                  const double* phi_lag, const unsigned char* pin, long nlist,
+                  const long* list, double* out_r, double* out_b, double* Fout) {
+    return step_nodes_impl(p, fr, fb, phi_lag, pin, nlist, list, NULL, out_r, out_b, Fout);
+}
+
+/* The same step at the listed nodes with the near-contact strength A_h of each
+ * listed node given (ah[k] for list[k]) instead of measured: the tests use it to
+ * follow a node whose film measurement took the other branch at a threshold.   */
+int or_step_nodes_given_ah(const or_params* p, const double* fr, const double* fb,
+                           const double* phi_lag, const unsigned char* pin, long nlist,
+                           const long* list, const double* ah, double* out_r, double* out_b,
+                           double* Fout) {
+    return step_nodes_impl(p, fr, fb, phi_lag, pin, nlist, list, ah, out_r, out_b, Fout);
 }
 
 /* Laplace-law measurement (static droplet): with phi and rho taken from the state

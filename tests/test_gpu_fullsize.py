@@ -26,6 +26,7 @@ import math
 import numpy as np
 import pytest
 
+import branch_cases
 import oracle
 from paper_2005_12764_gb300 import inputs
 
@@ -69,11 +70,17 @@ def _window_params(params, shape, y_centre):
 
 
 def _check_sampled_step(lbm, g, w, samples, pins=None):
+    """(worst difference, samples whose difference is not a threshold branch, samples
+    that are): a sample whose next-step populations differ from the oracle's by more
+    than 1e-6 passes only if the GPU's A_h there is the oracle's with a threshold of
+    the film measurement moved by its FP32 rounding bound, and the oracle's step with
+    that A_h gives the GPU's populations."""
     m = _map_to_oracle(lbm)
     nz, ny, nx = w.shape
     before = [g.get_window(x - R, y - R, z - R, W, W, W) for (x, y, z) in samples]
+    ah_gpu = g.get_nc_field() if w.params.get("A_nc", 0.0) > 0 else None
     g.step(1)
-    worst, bad = 0.0, 0
+    worst, bad, branches = 0.0, 0, 0
     for (x, y, z), (fr, fb, lag) in zip(samples, before):
         P = _window_params(w.params, w.shape, y)
         pw = None
@@ -88,8 +95,14 @@ def _check_sampled_step(lbm, g, w, samples, pins=None):
         gr, gb, _ = g.get_window(x, y, z, 1, 1, 1)
         d = max(np.abs(oa[0] - gr.reshape(19)[m]).max(), np.abs(ob[0] - gb.reshape(19)[m]).max())
         worst = max(worst, d)
-        bad += d > 1e-6
-    return worst, bad
+        if d > 1e-6:
+            if ah_gpu is not None and branch_cases.step_explained(
+                    P, fr.reshape(19, -1)[m], fb.reshape(19, -1)[m], lag.ravel(), centre,
+                    gr.reshape(19)[m], gb.reshape(19)[m], float(ah_gpu[z, y, x]), pin=pw):
+                branches += 1
+            else:
+                bad += 1
+    return worst, bad, branches
 
 
 def _samples(rng, shape, droplets, n_any, n_iface):
@@ -127,8 +140,8 @@ def test_dense_emulsion_512_full_size(lbm, storage):
     m0 = g.observables()
     g.step(20)
     samples = _samples(np.random.default_rng(31), w.shape, w.droplets, 6, 10)
-    worst, bad = _check_sampled_step(lbm, g, w, samples)
-    print(f"emulsion 512^3 ({storage}): worst |d f| at samples", worst)
+    worst, bad, branches = _check_sampled_step(lbm, g, w, samples)
+    print(f"emulsion 512^3 ({storage}): worst |d f| at samples", worst, "branches", branches)
     assert bad == 0, worst
     m1 = g.observables()
     assert np.isfinite(m1[:5]).all()
@@ -155,10 +168,11 @@ def test_bicontinuous_gel_640_full_size(lbm):
     g.step(10)
     # every node of the noise field lies on an interface
     samples = _samples(np.random.default_rng(32), w.shape, [], 16, 0)
-    worst, bad = _check_sampled_step(lbm, g, w, samples, pins=w.pins)
-    print("gel 640^3: worst |d f| at samples", worst)
-    # a film thickness that sits on a zero crossing may take the other branch in FP32
-    assert bad <= 1, worst
+    worst, bad, branches = _check_sampled_step(lbm, g, w, samples, pins=w.pins)
+    print("gel 640^3: worst |d f| at samples", worst, "branches", branches)
+    # a film measurement with a sample within FP32 rounding of a threshold may take
+    # the other branch in FP32; every other difference fails
+    assert bad == 0, worst
     m1 = g.observables()
     assert np.isfinite(m1[:5]).all()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6
@@ -183,9 +197,9 @@ def test_sheared_bijel_channel_full_size(lbm):
     rng = np.random.default_rng(33)
     samples = [(int(rng.integers(nx)), int(rng.integers(R, ny - R)), int(rng.integers(R, nz - R)))
                for _ in range(16)]
-    worst, bad = _check_sampled_step(lbm, g, w, samples)
-    print("sheared bijel: worst |d f| at samples", worst)
-    assert bad <= 1, worst
+    worst, bad, branches = _check_sampled_step(lbm, g, w, samples)
+    print("sheared bijel: worst |d f| at samples", worst, "branches", branches)
+    assert bad == 0, worst
     m1 = g.observables()
     assert np.isfinite(m1[:5]).all()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-6 and abs(m1[1] - m0[1]) / m0[1] < 1e-6

@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+import branch_cases
 import oracle
 from paper_2005_12764_gb300 import inputs
 
@@ -197,10 +198,17 @@ def test_near_contact_field_matches_oracle_on_dense_emulsion(lbm):
     # FP32 ray positions and interpolation locate a crossing to ~1e-5 lattice units,
     # which moves A_h by up to ~1e-4 of its value on the h^-3 tail
     A = w.params["A_nc"]
-    bad = np.abs(got - want) > 1e-6 * A + 1e-3 * np.abs(want)
-    print("nodes with A_h > 0:", int((want > 0).sum()), "mismatches:", int(bad.sum()))
+    tol = 1e-6 * A + 1e-3 * np.abs(want)
+    bad = np.argwhere(np.abs(got - want) > tol)
+    # every node beyond that must be a threshold branch: the oracle with the sign band
+    # or the gradient threshold moved by its FP32 rounding bound gives the GPU's A_h
+    unexplained = [(z, y, x) for z, y, x in bad
+                   if not branch_cases.ah_explained(op, lag, x, y, z, got[z, y, x],
+                                                    1e-6 * A + 1e-3 * abs(got[z, y, x]))]
+    print("nodes with A_h > 0:", int((want > 0).sum()), "threshold branches:", len(bad))
     assert (want > 0).sum() > 200
-    assert bad.sum() <= max(2, int(1e-4 * want.size)), np.argwhere(bad)[:10]
+    assert not unexplained, unexplained[:10]
+    assert len(bad) <= max(2, int(1e-4 * want.size)), bad[:10]
 
 
 def test_dense_emulsion_near_contact_30_steps(lbm):
@@ -221,20 +229,27 @@ def test_gel_quench_one_step_sampled(lbm):
     g.set_pin_mask(w.pins)
     g.step(20)
     fr, fb, lag = g.get_pops()
+    ah_gpu = g.get_nc_field().ravel()      # A_h the next step measures
     g.step(1)
     gr, gb, _ = g.get_pops()
     m = _map_to_oracle(lbm)
     N = n ** 3
     nodes = np.random.default_rng(4).choice(N, 3000, replace=False)
     P = oracle.make_params(n, n, n, **w.params)
-    oa, ob, _ = oracle.step_nodes(P, fr.reshape(19, N)[m], fb.reshape(19, N)[m], lag.ravel(),
-                                  nodes, pin=w.pins.ravel())
+    fro, fbo, pins = fr.reshape(19, N)[m], fb.reshape(19, N)[m], w.pins.ravel()
+    oa, ob, _ = oracle.step_nodes(P, fro, fbo, lag.ravel(), nodes, pin=pins)
     ga = gr.reshape(19, N)[m][:, nodes].T
     gbb = gb.reshape(19, N)[m][:, nodes].T
-    bad = (np.abs(oa - ga).max(1) > 1e-6) | (np.abs(ob - gbb).max(1) > 1e-6)
-    # a node whose film thickness sits on a zero crossing of phi may take the other
-    # branch in FP32; allow at most 0.5 % of the sampled nodes to differ
-    assert bad.mean() <= 0.005, (bad.sum(), np.abs(oa - ga).max())
+    bad = np.nonzero((np.abs(oa - ga).max(1) > 1e-6) | (np.abs(ob - gbb).max(1) > 1e-6))[0]
+    # a node whose film measurement has a sample (or whose lagged gradient lies)
+    # within FP32 rounding of a threshold may take the other branch in FP32: each
+    # such node must be reproduced by the oracle with that threshold moved by its
+    # rounding bound; any other difference fails
+    unexplained = [int(nodes[k]) for k in bad
+                   if not branch_cases.step_explained(P, fro, fbo, lag.ravel(), int(nodes[k]),
+                                                      ga[k], gbb[k], ah_gpu[nodes[k]], pin=pins)]
+    print("sampled nodes:", len(nodes), "threshold branches:", len(bad))
+    assert not unexplained, (unexplained[:10], np.abs(oa - ga).max())
 
 
 def test_zero_steps_returns_set_fields(lbm):
