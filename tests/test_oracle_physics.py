@@ -170,17 +170,37 @@ def _laplace_ratio(L, R, steps):
 
 def test_laplace_static_droplet_R8_32cube():
     # The static-droplet workload itself: 32^3, R = 8, sigma = 0.01, 500 steps.
-    # Measured: dp / (2 sigma / R_eff) = 1.042 (1.055 when fully relaxed). The excess
-    # is the finite interface width (~4 lu) against R = 8: it falls as R^-2 (next test).
+    # Measured: dp / (2 sigma / R_eff) = 1.042 at 500 steps (a damped pressure
+    # oscillation), 1.0548 once relaxed. The excess over Laplace's law is the
+    # finite interface width (~4 lu) against R = 8; the fit over R below removes it.
     ratio, lap = _laplace_ratio(32, 8.0, 500)
     assert abs(ratio - 1.0) < 0.06, lap
     assert 7.5 < lap["R_eff"] < 8.2
 
 
 @pytest.mark.slow
-def test_laplace_R12_within_three_percent():
-    ratio, lap = _laplace_ratio(48, 12.0, 1500)
-    assert abs(ratio - 1.0) < 0.03, lap
+def test_laplace_fit_over_R():
+    # Laplace's law dp = 2 sigma / R pins the surface-tension constant of the
+    # perturbation (sigma = 2 A / (9 omega)). Relaxed static droplets (L = 4R, run
+    # until dp has settled to 1e-4) of R = 8, 10, 12 give dp R / (2 sigma) = 1.0548,
+    # 1.0319, 1.0191: the excess falls as R^-2.4, the finite interface width against
+    # R. A least-squares fit of dp R / (2 sigma) = s + c / R^2 takes that
+    # discretisation term out; its R -> infinity limit s must be 1 within 3 % (a
+    # factor-2 error in the constant gives 2 or 1/2). Measured s = 0.991.
+    Rs, steps = (8.0, 10.0, 12.0), (2000, 2500, 3000)
+    ratios, reff = [], []
+    for R, n in zip(Rs, steps):
+        ratio, lap = _laplace_ratio(int(4 * R), R, n)
+        assert abs(lap["R_eff"] - R) < 0.1, lap
+        ratios.append(ratio)
+        reff.append(lap["R_eff"])
+    Reff = np.array(reff)
+    A = np.stack([np.ones(3), 1.0 / Reff ** 2], axis=1)
+    (s_inf, c), *_ = np.linalg.lstsq(A, np.array(ratios), rcond=None)
+    print("dp R / (2 sigma):", ratios, "fit: s =", s_inf, "c =", c)
+    assert abs(s_inf - 1.0) < 0.03, (ratios, s_inf, c)
+    assert c > 0 and ratios[0] > ratios[1] > ratios[2]       # the excess decays with R
+    assert abs(ratios[2] - 1.0) < 0.03, ratios               # R = 12 already within 3 %
 
 
 # ------------------------------------------------------------------ near contact
@@ -190,11 +210,18 @@ def _components(phi):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("A_nc,expect", [(0.0, 1), (0.05, 2)])
+@pytest.mark.parametrize("A_nc,expect", [(0.0, 1), (0.001, 1), (0.02, 1), (0.03, 2), (0.05, 2)])
 def test_near_contact_inhibits_merging(A_nc, expect):
-    # Two R = 8 droplets 2 lu apart (sigma = 0.01). Without the near-contact force the
-    # film drains and they merge (N_c = 0); with A = 0.05 (N_c = A dx / sigma = 5) the
-    # film survives. (With this reading the transition lies between N_c = 3 and 5.)
+    # Two R = 8 droplets 2 lu apart (sigma = 0.01), capillary number N_c = A dx / sigma
+    # (Eq. 11 and the paragraph after it: N_c << 1 merges, N_c ~ 1 inhibits merging).
+    # Without the force (N_c = 0) and well below one (N_c = 0.1) the film drains and
+    # the droplets merge; the film survives from N_c = 3 on (checked at 5 as well).
+    # With this reading the transition lies between N_c = 2 (merges) and 3: the
+    # repulsion per unit film area is integral A_h |G| dn = 2 A (phi spans -1 .. 1),
+    # twice the A of a unit-weight delta function, and it competes with the
+    # diffuse-interface attraction of two interfaces 2 lu apart, so the transition
+    # sits at N_c of order one, a few units, as the paper's order-of-magnitude
+    # statement has it.
     shape = (32, 32, 48)
     drops = [(14.0, 16.0, 16.0, 8.0), (34.0, 16.0, 16.0, 8.0)]
     rr, rb = inputs.paint_droplets(shape, drops)
