@@ -830,6 +830,27 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
                 return fail(nullptr, LBM_ECUDA, "cuTensorMapEncodeTiled failed");
             }
         }
+        // the near-contact pass copies cubes of a colour field (3-D, x fastest) with one
+        // tensor copy where the cube lies inside the lattice: rows must be a multiple of
+        // 16 bytes long, and the lattice at least a cube wide
+        if (p->A_nc > 0.0 && p->nx % 4 == 0) {
+            int box[3];
+            nc_cube_box(p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min, box);
+            if (p->nx >= box[0] && p->ny >= box[1] && p->nz >= box[2]) {
+                const cuuint64_t pd[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
+                const cuuint64_t ps[2] = {(cuuint64_t)p->nx * sizeof(float),
+                                          (cuuint64_t)p->nx * p->ny * sizeof(float)};
+                const cuuint32_t pb[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]};
+                const cuuint32_t pe[3] = {1, 1, 1};
+                bool ok = true;
+                for (int b = 0; b < 2 && ok; ++b)
+                    ok = encode(&c->phimap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->phi[b], pd, ps,
+                                pb, pe, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                c->phimap_ok = ok;
+            }
+        }
     }
     fill_step_params(c);
     *out = c;
@@ -988,24 +1009,14 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
     if (nc) {
         s.nc_pos = c->nc_pos[c->pc];
         s.nc_pos_out = c->nc_pos[1 - c->pc];
-        s.cand = c->cand[c->cw];
-        s.cand_count = c->cand_count + c->cw;
-        s.cand_clear = s.cand_count;
-        s.nc_next = c->nc_next + (1 - c->cw);
-        s.nc_next_clear = c->nc_next + c->cw;
+        s.cand = nullptr;
+        s.cand_clear = nullptr;
         s.ghost_f = ghost_cells(s) > 0 ? c->f[c->cur] : nullptr;
-        if (c->nc_scan) {
-            s.nc_list = nullptr;
-            s.nc_count = nullptr;
-        } else {
-            s.nc_list = c->cand[1 - c->cw];
-            s.nc_count = c->cand_count + (1 - c->cw);
-        }
-        // scan mode compacts its candidates into the list slot this pass would
-        // otherwise read (stale after a change of state)
+        // after a change of state the ray-bound bits of the lag field are recomputed
+        if (e == cudaSuccess && c->nc_scan) e = launch_nc_pos(s, c->num_sms, c->stream);
         if (e == cudaSuccess)
-            e = launch_nc(s, c->cand[1 - c->cw], c->cand_count + (1 - c->cw), c->p.storage,
-                          c->num_sms, c->stream);
+            e = launch_nc_block(s, c->phimap[c->pc], c->phimap_ok, c->p.storage, c->num_sms,
+                                c->stream);
     }
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess)
@@ -1073,15 +1084,17 @@ extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[3]) {
 // live step state; its candidates go to the list slot the next step kernel
 // overwrites.
 static cudaError_t diag_pass(lbm_ctx* c, StepParams s) {
-    s.nc_list = nullptr;
-    s.nc_count = nullptr;
     s.nc_pos = c->nc_pos[2];
     s.nc_pos_out = nullptr;
-    s.nc_next = c->nc_next + 2;
-    s.nc_next_clear = nullptr;
+    s.cand = nullptr;
     s.cand_clear = nullptr;
     s.ghost_f = nullptr;
-    return launch_nc(s, c->cand[c->cw], c->cand_count + c->cw, c->p.storage, c->num_sms, c->stream);
+    cudaError_t e = launch_nc_pos(s, c->num_sms, c->stream);
+    const int k = s.phi_lag == c->phi[0] ? 0 : 1;
+    const bool tma = c->phimap_ok && s.phi_lag == c->phi[k];
+    if (e == cudaSuccess)
+        e = launch_nc_block(s, c->phimap[k], tma, c->p.storage, c->num_sms, c->stream);
+    return e;
 }
 
 extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, double* u,

@@ -19,6 +19,9 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
 cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int storage,
                       int num_sms, cudaStream_t s);
 cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
+                            int storage, int num_sms, cudaStream_t s);
+void nc_cube_box(double h_cut, int box[3]);
 cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s);
@@ -46,6 +49,9 @@ struct lbm_ctx {
     size_t P = 0;               // elements per padded [z][y][x] block
     CUtensorMap tmap[2];        // TMA load descriptors of the two population copies
     CUtensorMap smap[2];        // TMA store descriptors (interior only: x < nx, y < ny)
+    CUtensorMap phimap[2];      // TMA load descriptors of the two colour fields (near-contact
+                                // cubes), valid when phimap_ok
+    bool phimap_ok = false;
     void* f[2] = {nullptr, nullptr};
     float* phi[2] = {nullptr, nullptr};
     float* fx_row = nullptr;

@@ -359,8 +359,9 @@ __device__ __forceinline__ bool nc_sample_marked(const StepParams& p, int x, int
     return (w >> (bx & 31)) & 1u;
 }
 
-__device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y, int z, float nx_,
-                                              float ny_, float nz_) {
+// First sample of a ray outside the fluid (p.nsamp if none).
+__device__ __forceinline__ int nc_sample_end(const StepParams& p, int y, int z, float ny_,
+                                             float nz_) {
     int s_end = p.nsamp;
     if (p.wall_y || p.wall_z) {
         const float ylo = (float)-y, yhi = (float)(p.ny - 1 - y);
@@ -387,6 +388,12 @@ __device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y,
             s_end = s + 1;
         }
     }
+    return s_end;
+}
+
+__device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y, int z, float nx_,
+                                              float ny_, float nz_) {
+    const int s_end = nc_sample_end(p, y, z, ny_, nz_);
     for (int s = s_end - 1; s >= 0; --s)
         if (nc_sample_marked(p, x, y, z, nx_, ny_, nz_, s)) return s;
     return -1;

@@ -48,6 +48,7 @@
 // at the same time, so the halo rows neighbours read come from L2.
 #include <cuda.h>
 
+#include <cmath>
 #include <utility>
 
 #include "lbm_device.cuh"
@@ -59,6 +60,12 @@ static_assert(TX == 32, "a warp is one row of a tile (near-contact bits, row sto
 constexpr int CTAS_PER_SM = 2;
 constexpr int SH = TY + 2, SWP = TX + 2;   // staged rows; colour-field ring columns
 constexpr int NRING = 2 * (TX + 2) + 2 * TY;
+// Threads that issue a plane's tensor copies, one copy each: the loads from thread
+// LOAD_T0 on, the stores from STORE_T0 on, in warps that pull no ring node (threads
+// 0 .. NRING-1 do), so that the issue is spread and off the busiest warps.
+constexpr int LOAD_T0 = 96, STORE_T0 = 160;
+static_assert(NRING <= LOAD_T0 && LOAD_T0 + 2 * Q <= STORE_T0 && STORE_T0 + 2 * Q <= NT,
+              "copy-issuing threads");
 
 template <class St, bool SC = false>
 struct Geo {
@@ -215,6 +222,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const size_t plane = (size_t)p.nx * p.ny;
+    // the output block this thread stores per plane (one tensor copy), or -1
+    const int my_st = (tid >= STORE_T0 && tid < STORE_T0 + G::NS) ? tid - STORE_T0 : -1;
 
     if (tid == 0) {
         mbar_init(&bars[0], G::NL);   // one arrival per staged box
@@ -302,7 +311,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // taken from source plane pl - c_iz
         // threads 0..NL-1 each issue the box of one (species, direction) and arrive on
         // the barrier (with 0 bytes if the box is not needed)
-        const int my_ik = tid < G::NL ? tid : -1;
+        const int my_ik = (tid >= LOAD_T0 && tid < LOAD_T0 + G::NL) ? tid - LOAD_T0 : -1;
         const int my_i = my_ik < Q ? my_ik : my_ik - Q;
         const int my_cy = my_ik >= 0 ? cy(my_i) : 0, my_cz = my_ik >= 0 ? cz(my_i) : 0;
         auto issue = [&](int b, int pl) {
@@ -664,7 +673,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                     wait(0);
                     sc_pull(0, z + 1, n_rr, n_rb, n_j);
                     if (G::DEV) lag_commit(z + 3);
-                    if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
+                    if (my_st >= 0) bulk_wait_read();   // the output tile of plane z-1 has been read
                     __syncthreads();
                     fence_proxy_async();
                     if (z + 2 <= ze) issue(0, z + 2);
@@ -680,10 +689,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                         }
                         fence_proxy_async();
                         __syncthreads();
-                        if (tid == 0) {
-                            for (int k = 0; k < G::NS; ++k)
-                                tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k,
-                                             sout + (size_t)k * (TX * TY));
+                        if (my_st >= 0) {
+                            tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, my_st,
+                                         sout + (size_t)my_st * (TX * TY));
                             bulk_commit();
                         }
                     }
@@ -711,7 +719,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 float vr[Q], vb[Q], rr = 0.f, rb = 0.f;
                 if (z >= zb && owned && !failed)
                     pull_species(0, z, slot(z), otx, oty, vr, vb, rr, rb, true);
-                if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
+                if (my_st >= 0) bulk_wait_read();   // the output tile of plane z-1 has been read
                 __syncthreads();                  // staged plane z consumed
                 fence_proxy_async();
                 issue(0, z + 1);
@@ -731,9 +739,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 }
                 fence_proxy_async();
                 __syncthreads();
-                if (tid == 0) {
-                    for (int k = 0; k < G::NS; ++k)
-                        tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
+                if (my_st >= 0) {
+                    tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, my_st, sout + (size_t)my_st * (TX * TY));
                     bulk_commit();
                 }
             }
@@ -770,7 +777,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 }
             }
             if (RING) lag_commit(z + 3);
-            if (tid == 0) bulk_wait_read();   // the output tile of plane z-1 has been read
+            if (my_st >= 0) bulk_wait_read();   // the output tile of plane z-1 has been read
             __syncthreads();
             fence_proxy_async();
             if (z + 2 <= ze) issue(0, z + 2);
@@ -805,15 +812,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 const size_t node = (size_t)z * plane + col;
                 float Fx = fx_y, Fy = p.gy, Fz = p.gz;
                 if (use_nc) {
-                    // near-contact force A_h G, A_h measured by the near-contact pass;
-                    // the entry is consumed (reset to 0) so that only the next pass's
-                    // candidates are nonzero when the next step reads it
+                    // near-contact force A_h G, A_h measured by the near-contact pass
+                    // (which writes every node's A_h)
                     if (ah_c != 0.0f) {
                         Fx += ah_c * Gx;
                         Fy += ah_c * Gy;
                         Fz += ah_c * Gz;
-                        p.ah[node] = 0.0f;
                     }
+                }
+                if (p.cand) {
                     // this node's gradient is the next pass's lagged gradient: list it,
                     // with that gradient, as a candidate if it may reach the 1e-3
                     // threshold there
@@ -851,9 +858,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             // copies have read it
             fence_proxy_async();
             __syncthreads();
-            if (tid == 0) {
-                for (int k = 0; k < G::NS; ++k)
-                    tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, k, sout + (size_t)k * (TX * TY));
+            if (my_st >= 0) {
+                tma_store_4d(fout_map, x0 + PADX, y0 + 2, z, my_st, sout + (size_t)my_st * (TX * TY));
                 bulk_commit();
             }
             ah_c = ah_nxt;
@@ -887,7 +893,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         }
     }
     grid_dep_launch();
-    if (tid == 0) bulk_wait_all();   // output tiles written before the CTA exits
+    if (my_st >= 0) bulk_wait_all();   // output tiles written before the CTA exits
     if (failed) {
         // give copies still in flight into this CTA's shared memory a bounded chance
         // to land before the CTA exits
@@ -1180,6 +1186,425 @@ __global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p)
     grid_dep_launch();
 }
 
+// ---------------------------------------------------------------- near-contact pass, block form
+// A_h of every node from the lagged colour field, one NB_X x NB_Y x NB_Z block of nodes
+// at a time (persistent CTAs, blocks in x-fastest order, so the CTAs resident at one
+// time work on neighbouring blocks and their halos come from L2). The block's lagged
+// field and a halo of H nodes around it -- the farthest trilinear corner a ray of
+// samples up to t = h_cut + 2 reaches is floor(h_cut) + 3 <= H nodes away -- are copied
+// into a shared-memory cube: by one TMA tensor copy where the cube lies inside the
+// lattice (a walled axis may reach past its walls: zero fill, never read), else by
+// asynchronous copies wrapped on periodic axes and clamped at walls. With two cubes
+// the next block's copy is in flight while a block is processed. Then:
+//  1. a bit table over 2 x 2 x 2 blocks of the cube marks where a node of the lagged
+//     field exceeds kPosBand (block b of an axis holds cube nodes 2b .. 2b+2, so the 8
+//     corners of every cell lie in one block): a sample in an unmarked block cannot
+//     carry a positive sign (the ray bound of nc_last_sample, taken from the cube);
+//  2. every node's lagged gradient G' is evaluated there, with the same expression in
+//     the same order as the step kernel's gradient (so the same bits); a node with
+//     |G'| >= 1e-3 whose ray may hold a positive sample is listed, every other node's
+//     A_h is final (0, or its pin term); the list is sorted by the ray's last possibly
+//     positive sample (a counting sort), so the rays a warp marches have similar
+//     lengths;
+//  3. the listed rays are marched, one per thread, with the trilinear corners read
+//     from the cube: the same cells, weights and interpolation order as the
+//     global-memory march, so the same values.
+// Every node's A_h is written (0 where no film is within h_cut): the field needs no
+// clearing between passes and no candidate list. The kernel also clears the next step
+// kernel's ray-bound bits and writes the ghost copies of the step's input populations.
+constexpr int NB_X = 16, NB_Y = 8, NB_Z = 8, NB_NODES = NB_X * NB_Y * NB_Z;
+constexpr int NB_THREADS = 512, NB_PER_THREAD = NB_NODES / NB_THREADS;
+constexpr int NB_BINS = 32;   // ray lengths s_last + 1 <= nsamp <= 25
+static_assert(NB_NODES < (1 << 16), "node index and s_last share one int in the ray list");
+
+template <int H>
+struct NcBlockGeo {
+    static constexpr int HX = (H + 3) / 4 * 4;     // x halo, a multiple of 16 bytes
+    static constexpr int SX = NB_X + 2 * HX, SY = NB_Y + 2 * H, SZ = NB_Z + 2 * H;
+    static constexpr int ROWS = SY * SZ;
+    static constexpr int CHUNKS = SX / 4;          // 16-byte chunks per cube row
+    static constexpr size_t CUBE_BYTES = (size_t)SX * SY * SZ * sizeof(float);
+    // bit table: blocks of 2 x 2 x 2 cube nodes, one 32-bit word of x blocks per (y, z)
+    // block (cell corners reach cube node S - 2, in block S/2 - 1; every S is even)
+    static constexpr int TBX = SX / 2, TBY = SY / 2, TBZ = SZ / 2;
+    static_assert(TBX <= 32, "one word of x blocks");
+    static constexpr size_t TAB_BYTES = (size_t)TBY * TBZ * sizeof(uint32_t);
+    // per cube row, its x blocks holding a node above kPosBand (while the table is
+    // built; the same space then holds the ray list)
+    static constexpr size_t LIST_BYTES =
+        (ROWS > NB_NODES ? ROWS : NB_NODES) * sizeof(uint32_t);
+    static constexpr size_t FIXED = 4 * sizeof(unsigned long long) + TAB_BYTES + LIST_BYTES +
+                                    2 * NB_BINS * sizeof(int) + NB_NODES;
+    static constexpr int NBUF = 2 * CUBE_BYTES + FIXED <= 227 * 1024 ? 2 : 1;
+    static constexpr size_t SMEM = NBUF * CUBE_BYTES + FIXED;
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+// Row of the halo cube along a periodic (wrapped) or walled (clamped) axis.
+__device__ __forceinline__ int halo_index(int a, int n, bool walled) {
+    return walled ? min(max(a, 0), n - 1) : wrap_near(a, n);
+}
+
+// Cell of a ray sample in the cube: ray_cell's corners and fractions, with the corner
+// (ix0, iy0, iz0) as an offset into the cube (whose copies of wrapped nodes make the
+// other corners o + 1, o + SX, o + SX SY away).
+struct CubeCell {
+    int o;
+    float fx, fy, fz;
+};
+template <int H>
+__device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int y0, int z0,
+                                          int lx, int ly, int lz, float ox, float oy, float oz,
+                                          CubeCell& c) {
+    using G = NcBlockGeo<H>;
+    const float flx = floorf(ox), fly = floorf(oy), flz = floorf(oz);
+    c.fx = ox - flx;
+    c.fy = oy - fly;
+    c.fz = oz - flz;
+    const int cx0 = lx + G::HX + (int)flx;
+    int cy0 = ly + H + (int)fly, cz0 = lz + H + (int)flz;
+    if (p.wall_y && y + (int)fly == p.ny - 1) {   // on the last node: the cell below, fy = 1
+        cy0 = p.ny - 2 - y0 + H;
+        c.fy = 1.0f;
+    }
+    if (p.wall_z && z + (int)flz == p.nz - 1) {
+        cz0 = p.nz - 2 - z0 + H;
+        c.fz = 1.0f;
+    }
+    c.o = (cz0 * G::SY + cy0) * G::SX + cx0;
+}
+// Block of the bit table holding the cell of a ray sample (the corner cube_cell
+// finds, halved per axis).
+template <int H>
+__device__ __forceinline__ bool cube_sample_marked(const StepParams& p, const uint32_t* tab, int y,
+                                                   int z, int y0, int z0, int lx, int ly, int lz,
+                                                   float ox, float oy, float oz) {
+    using G = NcBlockGeo<H>;
+    const int ix = (int)floorf(ox), iy = (int)floorf(oy), iz = (int)floorf(oz);
+    int cy0 = ly + H + iy, cz0 = lz + H + iz;
+    if (p.wall_y && y + iy == p.ny - 1) cy0 = p.ny - 2 - y0 + H;
+    if (p.wall_z && z + iz == p.nz - 1) cz0 = p.nz - 2 - z0 + H;
+    return (tab[(cz0 >> 1) * G::TBY + (cy0 >> 1)] >> ((lx + G::HX + ix) >> 1)) & 1u;
+}
+template <int H>
+__device__ __forceinline__ void cube_corners(const float* cube, const CubeCell& c, float (&v)[8]) {
+    using G = NcBlockGeo<H>;
+    const float* b = cube + c.o;
+    v[0] = b[0];
+    v[1] = b[1];
+    v[2] = b[G::SX];
+    v[3] = b[G::SX + 1];
+    v[4] = b[G::SX * G::SY];
+    v[5] = b[G::SX * G::SY + 1];
+    v[6] = b[G::SX * G::SY + G::SX];
+    v[7] = b[G::SX * G::SY + G::SX + 1];
+}
+__device__ __forceinline__ float cube_interp(const CubeCell& c, const float (&v)[8]) {
+    const float c0 = ray_lerp(ray_lerp(v[0], v[1], c.fx), ray_lerp(v[2], v[3], c.fx), c.fy);
+    const float c1 = ray_lerp(ray_lerp(v[4], v[5], c.fx), ray_lerp(v[6], v[7], c.fx), c.fy);
+    return ray_lerp(c0, c1, c.fz);
+}
+
+// Lagged gradient of block node (lx, ly, lz) = lattice node (x, y, z) from the cube: the
+// terms of gradient_global in its order; a neighbour beyond a wall takes the centre value.
+template <int H>
+__device__ __forceinline__ void cube_gradient(const StepParams& p, const float* cube, int x, int y,
+                                              int z, int lx, int ly, int lz, float& Gx, float& Gy,
+                                              float& Gz) {
+    using G = NcBlockGeo<H>;
+    const float* c0 = cube + ((lz + H) * G::SY + (ly + H)) * G::SX + (lx + G::HX);
+    const float phic = c0[0];
+    const bool ylo = p.wall_y && y == 0, yhi = p.wall_y && y == p.ny - 1;
+    const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
+    Gx = Gy = Gz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (i == 9) continue;
+        const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) || (cz(i) < 0 && zlo) ||
+                          (cz(i) > 0 && zhi);
+        const float v = wall ? phic : c0[(cz(i) * G::SY + cy(i)) * G::SX + cx(i)];
+        grad_add(i, v, Gx, Gy, Gz);
+    }
+}
+
+// Origin of block b of the lattice's block grid.
+__device__ __forceinline__ void nc_block_origin(const StepParams& p, long long b, int& x0, int& y0,
+                                                int& z0) {
+    const int bxn = (p.nx + NB_X - 1) / NB_X, byn = (p.ny + NB_Y - 1) / NB_Y;
+    const int bx = (int)(b % bxn);
+    const long long r = b / bxn;
+    x0 = bx * NB_X;
+    y0 = (int)(r % byn) * NB_Y;
+    z0 = (int)(r / byn) * NB_Z;
+}
+
+// Starts the copy of block b's cube into `cube`: one tensor copy by thread 0 (completing
+// on `bar`, which every fill arrives at once, with 0 bytes when not used) or the
+// asynchronous copies of every thread (one commit group per fill, possibly empty).
+template <int H>
+__device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtensorMap* map,
+                                              bool tma_ok, long long b, float* cube,
+                                              unsigned long long* bar) {
+    using G = NcBlockGeo<H>;
+    int x0, y0, z0;
+    nc_block_origin(p, b, x0, y0, z0);
+    const bool inside = tma_ok && x0 >= G::HX && x0 + NB_X + G::HX <= p.nx &&
+                        (p.wall_y || (y0 >= H && y0 + NB_Y + H <= p.ny)) &&
+                        (p.wall_z || (z0 >= H && z0 + NB_Z + H <= p.nz));
+    const int tid = threadIdx.x;
+    if (inside) {
+        if (tid == 0) {
+            mbar_arrive_tx(bar, (uint32_t)G::CUBE_BYTES);
+            tma_load_3d(cube, map, x0 - G::HX, y0 - H, z0 - H, bar);
+        }
+    } else {
+        if (tid == 0) mbar_arrive_tx(bar, 0u);
+        if ((p.nx & 3) == 0) {   // 16-byte chunks then never straddle the periodic seam
+            for (int k = tid; k < G::ROWS * G::CHUNKS; k += NB_THREADS) {
+                const int c = k % G::CHUNKS, row = k / G::CHUNKS;
+                const int ly = row % G::SY, lz = row / G::SY;
+                const int gy = halo_index(y0 - H + ly, p.ny, p.wall_y);
+                const int gz = halo_index(z0 - H + lz, p.nz, p.wall_z);
+                const int gx = wrap_near(x0 - G::HX + 4 * c, p.nx);
+                cp_async16(cube + (size_t)row * G::SX + 4 * c,
+                           p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
+            }
+        } else {
+            for (int k = tid; k < G::ROWS * G::SX; k += NB_THREADS) {
+                const int c = k % G::SX, row = k / G::SX;
+                const int ly = row % G::SY, lz = row / G::SY;
+                const int gy = halo_index(y0 - H + ly, p.ny, p.wall_y);
+                const int gz = halo_index(z0 - H + lz, p.nz, p.wall_z);
+                const int gx = wrap_near(x0 - G::HX + c, p.nx);
+                cp_async4(cube + k, p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+template <class St, int H>
+__global__ void __launch_bounds__(NB_THREADS, 1)
+nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
+    using G = NcBlockGeo<H>;
+    constexpr int NBUF = G::NBUF;
+    extern __shared__ __align__(128) unsigned char nsm[];
+    float* cubes = reinterpret_cast<float*>(nsm);                          // [NBUF][SZ][SY][SX]
+    unsigned char* q = nsm + NBUF * G::CUBE_BYTES;                         // 128-byte aligned
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(q);   // [NBUF], 4 slots
+    uint32_t* tab = reinterpret_cast<uint32_t*>(q + 4 * sizeof(unsigned long long));  // [TBZ][TBY]
+    int* rays = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tab) + G::TAB_BYTES);
+    uint32_t* rowbits = reinterpret_cast<uint32_t*>(rays);                 // [SZ][SY], then the list
+    int* bins = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(rays) + G::LIST_BYTES);
+    int* cursor = bins + NB_BINS;                                          // [NB_BINS] scatter
+    unsigned char* slast = reinterpret_cast<unsigned char*>(cursor + NB_BINS);   // s_last + 1
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&lag_map)) : "memory");
+    }
+    __syncthreads();
+    grid_dep_wait();
+    if (gtid == 0 && p.cand_clear) *p.cand_clear = 0;
+    if (p.nc_pos_out) {
+        const long long words = (long long)p.nbw * p.nby * p.nbz;
+        for (long long i = gtid; i < words; i += gthreads) p.nc_pos_out[i] = 0u;
+    }
+    if (p.ghost_f) {
+        const long long total = ghost_work(p);
+        for (long long t = gtid >> 5; t < total; t += gthreads >> 5)
+            ghost_task<St>(static_cast<typename St::T*>(p.ghost_f), p, t, lane);
+    }
+    const long long nblocks = (long long)((p.nx + NB_X - 1) / NB_X) *
+                              ((p.ny + NB_Y - 1) / NB_Y) * ((p.nz + NB_Z - 1) / NB_Z);
+    const size_t plane = (size_t)p.nx * p.ny;
+    uint32_t parity = 0u;
+    bool failed = false;
+    if (blockIdx.x < nblocks)
+        nc_fill_start<H>(p, &lag_map, tma_ok, blockIdx.x, cubes, &bars[0]);
+    int it = 0;
+    for (long long b = blockIdx.x; b < nblocks; b += gridDim.x, ++it) {
+        const int buf = NBUF == 2 ? (it & 1) : 0;
+        float* cube = cubes + (size_t)buf * (G::CUBE_BYTES / sizeof(float));
+        int x0, y0, z0;
+        nc_block_origin(p, b, x0, y0, z0);
+        const long long bn = b + gridDim.x;
+        if (NBUF == 2) {
+            // the next block's copy into the other cube (consumed in the last iteration)
+            fence_proxy_async();
+            if (bn < nblocks)
+                nc_fill_start<H>(p, &lag_map, tma_ok, bn, cubes + (size_t)(buf ^ 1) *
+                                 (G::CUBE_BYTES / sizeof(float)), &bars[buf ^ 1]);
+            else
+                cp_async_commit();
+            cp_async_wait<1>();   // this block's copies (the next block's may be in flight)
+        } else {
+            if (it > 0) {   // one cube: this block's copy starts once the last one is consumed
+                fence_proxy_async();
+                nc_fill_start<H>(p, &lag_map, tma_ok, b, cube, &bars[0]);
+            }
+            cp_async_wait<0>();
+        }
+        // (a wait that gives up leaves its phase pending: the drain below waits on it)
+        if (mbar_wait(&bars[buf], (parity >> buf) & 1u, p.err)) parity ^= 1u << buf;
+        else failed = true;
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        // ---- 1. the ray-bound table: per cube row, the x blocks (nodes 2b .. 2b+2)
+        // holding a node above kPosBand; then each table word ORs the 3 x 3 rows of its
+        // (y, z) block
+        for (int row = tid; row < G::ROWS; row += NB_THREADS) {
+            const float4* r = reinterpret_cast<const float4*>(cube + (size_t)row * G::SX);
+            uint64_t m = 0;
+#pragma unroll
+            for (int c = 0; c < G::CHUNKS; ++c) {
+                const float4 v = r[c];
+                m |= (uint64_t)((v.x > kPosBand ? 1u : 0u) | (v.y > kPosBand ? 2u : 0u) |
+                                (v.z > kPosBand ? 4u : 0u) | (v.w > kPosBand ? 8u : 0u)) << (4 * c);
+            }
+            const uint64_t c = m | (m >> 1) | (m >> 2);   // bit k: nodes k .. k+2
+            rowbits[row] = even_bits((uint32_t)c) | (even_bits((uint32_t)(c >> 32)) << 16);
+        }
+        if (tid < NB_BINS) bins[tid] = 0;
+        __syncthreads();
+        for (int w = tid; w < G::TBY * G::TBZ; w += NB_THREADS) {
+            const int by = w % G::TBY, bz = w / G::TBY;
+            uint32_t v = 0u;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+                    v |= rowbits[min(2 * bz + dz, G::SZ - 1) * G::SY + min(2 * by + dy, G::SY - 1)];
+            tab[w] = v;
+        }
+        __syncthreads();
+        // ---- 2. gradients, thresholds and ray bounds of the block's nodes; nodes
+        // without a ray to march take their final A_h here
+#pragma unroll
+        for (int j = 0; j < NB_PER_THREAD; ++j) {
+            const int idx = tid + j * NB_THREADS;
+            const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            int s_last = -1;
+            if (x < p.nx && y < p.ny && z < p.nz) {
+                float Gx, Gy, Gz, nx_, ny_, nz_;
+                cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
+                float a = 0.0f;
+                if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
+                    // the last sample inside the fluid whose cell's block is marked
+                    for (int sm = nc_sample_end(p, y, z, ny_, nz_) - 1; sm >= 0; --sm) {
+                        const float t = -1.0f + 0.5f * (float)sm;
+                        if (cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz, t * nx_,
+                                                  t * ny_, t * nz_)) {
+                            s_last = sm;
+                            break;
+                        }
+                    }
+                    if (s_last < 0 && p.pin_d2) {
+                        const unsigned d2 = __ldg(p.pin_d2 + (size_t)z * plane + (size_t)y * p.nx + x);
+                        if (d2 != 255u) a = A_h(p, sqrtf((float)d2));
+                    }
+                }
+                if (s_last < 0) p.ah[(size_t)z * plane + (size_t)y * p.nx + x] = a;
+            }
+            if (s_last >= 0) {   // one atomic per distinct ray length in the warp
+                const unsigned peers = __match_any_sync(__activemask(), s_last);
+                if (lane == __ffs(peers) - 1) atomicAdd(&bins[s_last], __popc(peers));
+            }
+            slast[idx] = (unsigned char)(s_last + 1);
+        }
+        __syncthreads();
+        // counting sort by s_last, longest rays first
+        if (tid < 32) {
+            const int n = tid < NB_BINS ? bins[NB_BINS - 1 - tid] : 0;
+            int incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (tid < NB_BINS) cursor[NB_BINS - 1 - tid] = incl - n;
+            if (tid == 31) bins[0] = incl;   // (bins[] is not read again) total rays
+        }
+        __syncthreads();
+        const int nr = bins[0];
+#pragma unroll
+        for (int j = 0; j < NB_PER_THREAD; ++j) {
+            const int idx = tid + j * NB_THREADS;
+            const int sl = (int)slast[idx] - 1;
+            if (sl >= 0) {
+                const unsigned peers = __match_any_sync(__activemask(), sl);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&cursor[sl], __popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                rays[base + __popc(peers & ((1u << lane) - 1u))] = idx | (sl << 16);
+            }
+        }
+        __syncthreads();
+        // ---- 3. the listed rays, one per thread, corners from the cube
+        for (int k = tid; k < nr; k += NB_THREADS) {
+            const int e = rays[k];
+            const int idx = e & 0xffff, s_last = e >> 16;
+            const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            float Gx, Gy, Gz, nx_, ny_, nz_;
+            cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
+            nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
+            NcMarch mr;
+            float a = 0.0f, v[8];
+            CubeCell cell;
+            int key = -1;
+            for (int s = 0; s <= s_last; ++s) {
+                const float t = -1.0f + 0.5f * (float)s;
+                cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, t * nx_, t * ny_, t * nz_, cell);
+                if (cell.o != key) {
+                    cube_corners<H>(cube, cell, v);
+                    key = cell.o;
+                }
+                if (mr.feed(p, t, cube_interp(cell, v), a)) break;
+            }
+            const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
+            if (p.pin_d2) {
+                const unsigned d2 = __ldg(p.pin_d2 + node);
+                if (d2 != 255u) a += A_h(p, sqrtf((float)d2));
+            }
+            p.ah[node] = a;
+        }
+        __syncthreads();   // the cube, table and ray list are consumed
+    }
+    if (failed) {
+        // give tensor copies still in flight into this CTA's cubes a bounded chance to
+        // land before the CTA exits
+        for (int b = 0; b < NBUF; ++b)
+            for (uint32_t i = 0; i < (1u << 20); ++i)
+                if (mbar_try_wait(&bars[b], (parity >> b) & 1u)) break;
+    }
+    cp_async_wait<0>();
+    grid_dep_launch();
+}
+
 // Scan mode (after the state was set): ah = 0 everywhere, and every node whose
 // lagged gradient may reach the threshold is appended, with that gradient, to the
 // list the list kernel then works on.
@@ -1317,6 +1742,57 @@ cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, 
         case 2: return launch_list<StoreBF16>(p, num_sms, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <class St, int H>
+static cudaError_t launch_block_tpl(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
+                                   int num_sms, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(nc_block_kernel<St, H>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)NcBlockGeo<H>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_block_kernel<St, H>,
+                                                              NB_THREADS, NcBlockGeo<H>::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    return pdl_launch(nc_block_kernel<St, H>, (unsigned)(num_sms * per_sm), NB_THREADS,
+                      NcBlockGeo<H>::SMEM, s, p, lag_map, tma_ok ? 1 : 0);
+}
+
+template <class St>
+static cudaError_t launch_block_st(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
+                                   int num_sms, cudaStream_t s) {
+    // halo: the farthest corner of a ray sample is floor(h_cut) + 3 nodes away
+    const int need = (int)floorf(p.h_cut) + 3;
+    if (need <= 9) return launch_block_tpl<St, 9>(p, lag_map, tma_ok, num_sms, s);
+    if (need <= 12) return launch_block_tpl<St, 12>(p, lag_map, tma_ok, num_sms, s);
+    return cudaErrorInvalidValue;   // h_cut <= 9 is checked when the context is made
+}
+
+cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
+                            int storage, int num_sms, cudaStream_t s) {
+    // (the pass touches populations only in the ghost fill, which depends on the
+    // element type alone: the reduced form shares the FP32 instance)
+    switch (storage) {
+        case 0: case 3: return launch_block_st<StoreF32>(p, lag_map, tma_ok, num_sms, s);
+        case 1: return launch_block_st<StoreF16>(p, lag_map, tma_ok, num_sms, s);
+        case 2: return launch_block_st<StoreBF16>(p, lag_map, tma_ok, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Shape of the cube a tensor copy of the near-contact pass fills (x, y, z extents), for
+// the tensor map of a colour field.
+void nc_cube_box(double h_cut, int box[3]) {
+    const int need = (int)std::floor(h_cut) + 3;
+    const int H = need <= 9 ? 9 : 12;
+    const int HX = (H + 3) / 4 * 4;
+    box[0] = NB_X + 2 * HX;
+    box[1] = NB_Y + 2 * H;
+    box[2] = NB_Z + 2 * H;
 }
 
 template <class St, bool U, bool SC>

@@ -211,6 +211,42 @@ def test_near_contact_field_matches_oracle_on_dense_emulsion(lbm):
     assert len(bad) <= max(2, int(1e-4 * want.size)), bad[:10]
 
 
+@pytest.mark.parametrize("case", ["periodic", "walls"])
+def test_near_contact_field_tensor_copied_cubes(lbm, case):
+    # Lattices large enough that the near-contact pass copies the inner blocks' halo
+    # cubes with one tensor copy (a 16 x 8 x 8 block whose 40 x 26 x 26 cube lies
+    # inside the lattice; on walled axes the cube may reach past the walls) and the
+    # others with element copies wrapped across the periodic seams: every node's A_h
+    # against the oracle's full ray march, threshold branches proven as above.
+    nz, ny, nx = (40, 48, 64) if case == "periodic" else (42, 34, 64)
+    drops = inputs.dense_emulsion(L=64, volume_fraction=0.3, r_range=(4.0, 7.0), seed=12).droplets
+    per = (True, True, True) if case == "periodic" else (True, False, False)
+    drops = [d for d in drops if d[1] < ny - 2 and d[2] < nz - 2]
+    rr, rb = inputs.paint_droplets((nz, ny, nx), drops, periodic=per)
+    kw = dict(sigma=0.01, A_nc=0.01, h_min=3.0, kolmogorov_amp=1e-5)
+    if case == "walls":
+        kw.update(wall_y=1, wall_z=1)
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **kw))
+    g.set_fields(rr, rb)
+    g.step(8)
+    _, _, lag = g.get_pops()
+    got = g.get_nc_field()
+    op = oracle.make_params(nx, ny, nz, **kw)
+    want = np.zeros_like(got)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                want[z, y, x] = oracle.nc_strength_node(op, lag, x, y, z)
+    A = kw["A_nc"]
+    bad = np.argwhere(np.abs(got - want) > 1e-6 * A + 1e-3 * np.abs(want))
+    unexplained = [(z, y, x) for z, y, x in bad
+                   if not branch_cases.ah_explained(op, lag, x, y, z, got[z, y, x],
+                                                    1e-6 * A + 1e-3 * abs(got[z, y, x]))]
+    print(case, "nodes with A_h > 0:", int((want > 0).sum()), "threshold branches:", len(bad))
+    assert (want > 0).sum() > 200
+    assert not unexplained, unexplained[:10]
+
+
 def test_dense_emulsion_near_contact_30_steps(lbm):
     n = 40
     w = inputs.dense_emulsion(L=n, volume_fraction=0.3, r_range=(4.0, 7.0), seed=11)
