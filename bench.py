@@ -7,7 +7,7 @@ force A = 0.01 within 3 lu, sigma = 0.01, beta = 0.7, tau = 1, FP32 storage. One
 one lattice update of every node (the near-contact pass and the fused step kernel).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload emulsion|channel]
-                  [--storage fp32|fp16|bf16|fp32_q5] [--impl ours|reference]
+                  [--storage fp32|fp16|bf16|fp32_q5|fp16_q5] [--impl ours|reference]
                   [--model colour|shan_chen] [--no-serving] [--no-models] [--no-cpu-baseline]
 
 Prints one JSON line. ``value`` is GLUPS (10^9 lattice-node updates per second) over
@@ -19,7 +19,8 @@ reported. ``e2e`` times the same job through the public C-ABI with host buffers
 node, read once and written once) to the measured HBM bandwidth; ``fp16_store``
 repeats the device-resident measurement on the same lattice with FP16 deviation
 storage (and, inside it, BF16), ``fp32_q5_store`` with the reduced FP32 form (19
-totals and 5 recolouring coefficients per node); ``gel_640`` times the bicontinuous
+totals and 5 recolouring coefficients per node), ``fp16_q5_store`` with its FP16
+variant (FP16 totals, exact coefficients); ``gel_640`` times the bicontinuous
 gel quench (640^3, tau = 0.8, 2 % pinning sites, near contact on, FP32) with the
 near-contact pass's share; ``channel`` the microfluidic-crystal channel (256 x 128
 x 64); ``shan_chen`` and ``sheared_bijel`` the Shan-Chen model on the channel and the
@@ -77,9 +78,12 @@ def kernel_source_hash() -> str:
 
 def bytes_per_node(storage: str) -> int:
     """Algorithmic HBM bytes of one node and step: every stored value read once and
-    written once (2 x 2Q values, or 2 x (Q + 5) in the reduced FP32 form)."""
+    written once (2 x 2Q values; in the reduced forms 2 x (Q totals + 5 FP32
+    coefficients), the totals FP32 or FP16)."""
     if storage == "fp32_q5":
         return 2 * (Q + 5) * 4
+    if storage == "fp16_q5":
+        return 2 * (Q * 2 + 5 * 4)
     return 2 * Q * C * (4 if storage == "fp32" else 2)
 
 
@@ -237,10 +241,10 @@ def workload_key(args):
     return args.workload
 
 
-def make_workload(key):
+def make_workload(key, size=512):
     from paper_2005_12764_gb300 import inputs
     if key == "emulsion":
-        return inputs.dense_emulsion()
+        return inputs.dense_emulsion(L=size)
     if key == "channel_sc":
         return inputs.channel_shan_chen()
     return inputs.channel_droplets()
@@ -498,7 +502,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build_lib.build()
     key = workload_key(args)
-    w = make_workload(key)
+    w = make_workload(key, args.size)
     nz, ny, nx = w.shape
     N = nx * ny * nz
     stream = torch.cuda.Stream()
@@ -565,7 +569,7 @@ def run_ours(args):
     lat.close()
     # the same workload with FP16 / BF16 deviation storage and the reduced FP32 form
     # (device-resident, as `value`)
-    fp16 = q5 = None
+    fp16 = q5 = q5h = None
     if args.storage == "fp32" and not args.no_variants:
         d16 = device_resident(lbm, w, "fp16", args.steps, args.warmup, stream, local)
         d16["value"] = replicas.sum_over_ranks(d16["value"], dist if world > 1 else None,
@@ -594,6 +598,16 @@ def run_ours(args):
                    "algorithmic_bytes_per_launch": alg5,
                    "traffic": measured_traffic("fp32_q5", key, N)})
         q5 = d5
+        # and its FP16 variant (FP16 totals, exact FP32 coefficients: 116 bytes per node)
+        dh = device_resident(lbm, w, "fp16_q5", args.steps, args.warmup, stream, local)
+        dh["value"] = replicas.sum_over_ranks(dh["value"], dist if world > 1 else None,
+                                              f"cuda:{local}")
+        algh = bytes_per_node("fp16_q5") * N
+        dh.update({"unit": "GLUPS",
+                   "roofline_frac": algh / (dh["kernel_ms"] * 1e-3) / 1e9 / peak,
+                   "algorithmic_bytes_per_launch": algh,
+                   "traffic": measured_traffic("fp16_q5", key, N)})
+        q5h = dh
     others = None
     if not args.no_models:
         others = other_workloads(lbm, stream, local, key)
@@ -620,7 +634,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[key], "nodes": N, "storage": args.storage,
+            "config": {"workload": WORKLOADS[key] if args.size == 512 or key != "emulsion"
+                       else WORKLOADS[key].replace("512", str(args.size)),
+                       "nodes": N, "storage": args.storage,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
                              % (bytes_per_node(args.storage) * N / 2 / 1e6),
@@ -645,6 +661,8 @@ def run_ours(args):
             line["fp16_store"] = fp16
         if q5:
             line["fp32_q5_store"] = q5
+        if q5h:
+            line["fp16_q5_store"] = q5h
         if others:
             line.update(others)
         if serving_rep:
@@ -656,13 +674,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_study(args):
+    """The workloads' own long runs (not a bench line): `--study emulsion` runs the
+    512^3 emulsion for `--study-steps` steps (2000) in every storage form and reports
+    each form's species-mass drift and droplet census against FP32's; `--study gel`
+    runs the 640^3 gel quench in FP32 and in the FP16 reduced form, reporting GLUPS and
+    the peak of the structure factor S(k, t) every `--every` steps."""
+    import numpy as np
+    import torch
+
+    from paper_2005_12764_gb300 import build_lib, inputs, lbm
+
+    torch.cuda.set_device(0)
+    build_lib.build()
+    stream = torch.cuda.Stream()
+
+    def lattice(w, storage, pins=None):
+        nz, ny, nx = w.shape
+        lat = lbm.Lattice(lbm.make_params(nx, ny, nz, storage=storage,
+                                          stream=stream.cuda_stream, **w.params))
+        lat.set_fields(torch.from_numpy(w.rho_r).cuda(), torch.from_numpy(w.rho_b).cuda())
+        if pins is not None:
+            lat.set_pin_mask(torch.from_numpy(pins).cuda())
+        return lat
+
+    def timed(lat, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(k)
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b)
+
+    out = {"study": args.study, "steps": args.study_steps}
+    if args.study == "emulsion":
+        w = make_workload("emulsion", args.size)
+        N = w.rho_r.size
+        forms = {}
+        for st in ("fp32", "fp16", "bf16", "fp32_q5", "fp16_q5"):
+            lat = lattice(w, st)
+            m0 = lat.observables()[:2]
+            n0, s0 = lat.droplets()
+            ms = timed(lat, args.study_steps)
+            m1 = lat.observables()[:2]
+            n1, s1 = lat.droplets()
+            hist = np.bincount(np.minimum(np.round(np.cbrt(3 * s1 / (4 * np.pi))).astype(int), 40),
+                               minlength=41)
+            forms[st] = {"glups": N * args.study_steps / (ms * 1e-3) / 1e9,
+                         "mass_drift_rel": [abs(float(m1[k] - m0[k])) / float(m0[k]) for k in range(2)],
+                         "droplets_start": n0, "droplets_end": n1,
+                         "radius_histogram_end": hist.tolist(),
+                         "largest_end": [int(v) for v in s1[:3]]}
+            lat.close()
+        ref = forms["fp32"]["radius_histogram_end"]
+        for st, d in forms.items():
+            d["histogram_l1_vs_fp32"] = int(np.abs(np.array(d["radius_histogram_end"]) -
+                                                   np.array(ref)).sum())
+        out.update({"workload": WORKLOADS["emulsion"], "forms": forms})
+    else:
+        w = inputs.bicontinuous()
+        N = w.rho_r.size
+        runs = {}
+        for st in ("fp32", "fp16_q5"):
+            lat = lattice(w, st, w.pins)
+            series, total_ms, done = [], 0.0, 0
+            while done < args.study_steps:
+                k = min(args.every, args.study_steps - done)
+                total_ms += timed(lat, k)
+                done += k
+                kk, S, modes = lat.structure_factor(560)
+                j = 1 + int(np.argmax(S[1:]))
+                series.append({"step": done, "k_peak": float(kk[j]), "S_peak": float(S[j])})
+            runs[st] = {"glups": N * done / (total_ms * 1e-3) / 1e9, "S_peak_vs_t": series}
+            lat.close()
+        out.update({"workload": "bicontinuous gel quench 640^3, 2 % pins, tau = 0.8", "runs": runs})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="emulsion", choices=["emulsion", "channel"])
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp32_q5"])
+    ap.add_argument("--size", type=int, default=512,
+                    help="edge of the emulsion box (smaller cases for profiler captures)")
+    ap.add_argument("--storage", default="fp32",
+                    choices=["fp32", "fp16", "bf16", "fp32_q5", "fp16_q5"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -674,12 +772,18 @@ def main():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the gel, channel, Shan-Chen and sheared-bijel lines")
     ap.add_argument("--oracle-rate-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--study", choices=["emulsion", "gel"],
+                    help="long run of a workload instead of the bench line")
+    ap.add_argument("--study-steps", type=int, default=2000)
+    ap.add_argument("--every", type=int, default=1000)
     args = ap.parse_args()
-    if args.storage == "fp32_q5" and args.model == "shan_chen":
+    if args.storage in ("fp32_q5", "fp16_q5") and args.model == "shan_chen":
         ap.error("the reduced storage form holds colour-gradient states only")
     if args.warmup < 3:
         args.warmup = 3
-    if args.oracle_rate_only:
+    if args.study:
+        run_study(args)
+    elif args.oracle_rate_only:
         run_oracle_rate_only(args)
     elif args.impl == "reference":
         run_reference(args)

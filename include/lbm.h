@@ -71,12 +71,21 @@ typedef enum {
  * (its species do not share one population). lbm_get_pops returns the rebuilt
  * species populations; lbm_set_pops stores a split of the recoloured form exactly
  * and projects any other split onto that form (kappa_k from the species sums, m
- * from the first moment of f^r_i - kappa_r f_i).                                   */
+ * from the first moment of f^r_i - kappa_r f_i).
+ *
+ * LBM_STORE_FP16_Q5 is the same reduced form with the 19 totals stored in FP16 as
+ * deviations f_i - w_i rho0 from the lattice weights (rounded to nearest even; the
+ * total density is close to rho0 in both phases, so the deviation is small), and the
+ * five coefficients kept exact in FP32 (each as two 16-bit arrays: the low and the
+ * high half of its bits), so that the species masses they carry are not rounded:
+ * 2 x (19 x 2 + 5 x 4) = 116 bytes moved per node and step. All arithmetic is FP32,
+ * as in every form.                                                                */
 typedef enum {
     LBM_STORE_FP32 = 0,
     LBM_STORE_FP16_DEV = 1,
     LBM_STORE_BF16_DEV = 2,
-    LBM_STORE_FP32_Q5 = 3
+    LBM_STORE_FP32_Q5 = 3,
+    LBM_STORE_FP16_Q5 = 4
 } lbm_storage;
 
 /* Binary-mixture model (Sec. "Multi-component flows"). LBM_MODEL_COLOUR: the
@@ -112,7 +121,8 @@ typedef struct {
                                 bijel materials". A link that comes back from a moving
                                 wall gains 6 w_i rho c_i.u_w (moving-wall halfway
                                 bounce-back, rho the node's density). |wall_u| < 0.3.  */
-    double rho0;             /* reference density of the FP16/BF16 deviation storage (1)  */
+    double rho0;             /* reference density of the FP16/BF16 deviation storage and of
+                                the FP16 reduced form's totals (1)                        */
     int model;               /* lbm_model: LBM_MODEL_COLOUR (default) or LBM_MODEL_SHAN_CHEN */
     double G_sc;             /* Shan-Chen coupling G_C, > 0 repulsive (Shan-Chen model)    */
     int storage;             /* lbm_storage                                               */
@@ -201,15 +211,6 @@ lbm_status lbm_structure_factor(lbm_ctx* ctx, int nbins, double* k, double* S,
  * context stays usable. (No counterpart in the paper.) Synchronises.            */
 lbm_status lbm_selftest_timeout(lbm_ctx* ctx);
 
-/* Self-check of the near-contact work bound (an implementation device with no
- * counterpart in the paper: the paper does not say how the film is searched).
- * The step kernel marks, for the next step's film measurement, every 2x2x2 block
- * of the block grid (block b = nodes 2b .. 2b+2 per axis) that holds a node with
- * colour field > 0.5e-5. This recomputes that bit field from the current colour
- * field with a separate kernel and compares: out[0] = 32-bit words that differ,
- * out[1] = words compared. LBM_ESTATE unless A_nc > 0 and a step has run since the
- * last change of state. Synchronises the stream.                                 */
-lbm_status lbm_nc_bound_check(lbm_ctx* ctx, long long out[2]);
 
 /* Raw populations as float64 [19][N] per species, in the order of
  * lbm_velocity_set, plus the colour field of the previous step (lag buffer, [N];
@@ -227,6 +228,23 @@ lbm_status lbm_set_pops(lbm_ctx* ctx, const double* f_r, const double* f_b,
  * 39 wx wy wz doubles; synchronises the stream.                                  */
 lbm_status lbm_get_window(lbm_ctx* ctx, int x0, int y0, int z0, int wx, int wy, int wz,
                           double* f_r, double* f_b, double* phi_lag, int on_device);
+
+/* Z-slab domain decomposition (the paper's MPI domain decomposition of the fluid, Sec.
+ * "High-performance LB code for bijel materials"): the stored state of a range of z
+ * planes, copied as stored, so that neighbouring subdomains can exchange halo planes
+ * bitwise in every storage format. The state of plane z is every stored population
+ * block's plane z (ghost cells included) and plane z of the lagged colour field (the
+ * field the next step's near-contact pass reads).
+ * lbm_planes_bytes: bytes of h planes of that state (the buffer of the two calls below),
+ * laid out [stored blocks][h][padded plane] elements, then [h][ny][nx] float32.
+ * lbm_get_planes / lbm_set_planes: planes z0 .. z0+h-1 (0 <= z0, z0 + h <= nz, h >= 1)
+ * into / from `buf`, CUDA device memory the caller owns on the context's device.
+ * Queued on the context's stream, no allocation, no synchronisation. Setting planes
+ * replaces that part of the state; the near-contact pass needs no other state (it
+ * measures every node's film anew each step).                                     */
+size_t lbm_planes_bytes(const lbm_ctx* ctx, int h);
+lbm_status lbm_get_planes(lbm_ctx* ctx, int z0, int h, void* buf);
+lbm_status lbm_set_planes(lbm_ctx* ctx, int z0, int h, const void* buf);
 
 /* FP64 conserved totals of the current state, summed on the device in a fixed
  * order: out = {sum f^r, sum f^b, P_x, P_y, P_z, steps, 0, 0}, P = sum_i c_i f_i.

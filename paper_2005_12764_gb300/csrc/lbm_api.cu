@@ -77,7 +77,8 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
             const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
             const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
             if constexpr (St::RED) {
-                St::store(f, (size_t)i * P + q, (float)((rr + rb) * e), 0.0f);
+                St::store(f, (size_t)i * P + q, (float)((rr + rb) * e),
+                          St::tot_ref(i, 2.0f * ref_half));
             } else {
                 const float hw = wgt(i) * ref_half;
                 St::store(f, (size_t)i * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
@@ -88,9 +89,9 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
             // f^eq is linear in the density: f^eq(rho_k, u) = (rho_k / rho) f^eq(rho, u),
             // the reduced form with kappa_k = rho_k / rho and m = 0
             const double rho = rr + rb;
-            St::store(f, (size_t)Q * P + q, (float)(rr / rho), 0.0f);
-            St::store(f, (size_t)(Q + 1) * P + q, (float)(rb / rho), 0.0f);
-            for (int k = 2; k < Q5_AUX; ++k) St::store(f, (size_t)(Q + k) * P + q, 0.0f, 0.0f);
+            St::store_coef(f, P, q, 0, (float)(rr / rho));
+            St::store_coef(f, P, q, 1, (float)(rb / rho));
+            for (int k = 2; k < Q5_AUX; ++k) St::store_coef(f, P, q, k, 0.0f);
         }
         phi0[n] = ph;
         phi1[n] = ph;
@@ -111,11 +112,10 @@ template <class St>
 __device__ inline void ldpair(const typename St::T* f, size_t P, size_t q, int i, float ref_half,
                               float ph, float& a, float& b) {
     if constexpr (St::RED) {
-        const float t = __ldg(f + (size_t)i * P + q);
-        const float sh = q5_share(i, __ldg(f + (size_t)(Q + 2) * P + q),
-                                  __ldg(f + (size_t)(Q + 3) * P + q), __ldg(f + (size_t)(Q + 4) * P + q));
-        a = __fmaf_rn(__ldg(f + (size_t)Q * P + q), t, sh);
-        b = __fmaf_rn(__ldg(f + (size_t)(Q + 1) * P + q), t, -sh);
+        const float t = St::load(f, (size_t)i * P + q, St::tot_ref(i, 2.0f * ref_half));
+        const float sh = q5_share(i, St::coef(f, P, q, 2), St::coef(f, P, q, 3), St::coef(f, P, q, 4));
+        a = __fmaf_rn(St::coef(f, P, q, 0), t, sh);
+        b = __fmaf_rn(St::coef(f, P, q, 1), t, -sh);
     } else {
         a = ldpop<St>(f, (size_t)i * P + q, i, 0, ref_half, ph);
         b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
@@ -284,14 +284,14 @@ __global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const float
                 mx += cx(i) * d;
                 my += cy(i) * d;
                 mz += cz(i) * d;
-                St::store(f, (size_t)i * P + q, (float)t, 0.0f);
+                St::store(f, (size_t)i * P + q, (float)t, St::tot_ref(i, 2.0f * sp.ref_half));
             }
             const double inv = 9.0 / (1.0 + sqrt(2.0));
-            St::store(f, (size_t)Q * P + q, (float)kr, 0.0f);
-            St::store(f, (size_t)(Q + 1) * P + q, (float)kb, 0.0f);
-            St::store(f, (size_t)(Q + 2) * P + q, (float)(mx * inv), 0.0f);
-            St::store(f, (size_t)(Q + 3) * P + q, (float)(my * inv), 0.0f);
-            St::store(f, (size_t)(Q + 4) * P + q, (float)(mz * inv), 0.0f);
+            St::store_coef(f, P, q, 0, (float)kr);
+            St::store_coef(f, P, q, 1, (float)kb);
+            St::store_coef(f, P, q, 2, (float)(mx * inv));
+            St::store_coef(f, P, q, 3, (float)(my * inv));
+            St::store_coef(f, P, q, 4, (float)(mz * inv));
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -479,11 +479,14 @@ int grid_for(size_t n, int num_sms) {
 
 // ---------------------------------------------------------------- helpers
 static size_t elem_bytes(int storage) { return (storage == 0 || storage == 3) ? 4 : 2; }
+static bool reduced_form(int storage) { return storage == 3 || storage == 4; }
 // Population blocks per copy: stored (2Q, or the reduced form's Q totals and five
 // coefficient blocks) and streamed (loaded by the step kernel's tensor copies, with
 // ghost copies on periodic axes).
-static int stored_blocks(int storage) { return storage == 3 ? Q + Q5_AUX : 2 * Q; }
-static int streamed_blocks(int storage) { return storage == 3 ? Q : 2 * Q; }
+static int stored_blocks(int storage) {
+    return storage == 3 ? Q + StoreQ5::AUX_BLOCKS : (storage == 4 ? Q + StoreQ5H::AUX_BLOCKS : 2 * Q);
+}
+static int streamed_blocks(int storage) { return reduced_form(storage) ? Q : 2 * Q; }
 
 // Padded population layout: two ghost columns left and right of each row, the row
 // length a multiple of 16 bytes (TMA alignment); two ghost rows above and below.
@@ -514,14 +517,14 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     double hcut = p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min;
     if (p->A_nc > 0.0 && !(hcut > p->h_min)) { why = "h_cut must exceed h_min"; return LBM_EINVAL; }
     if (p->A_nc > 0.0 && hcut > 9.0) { why = "h_cut must be <= 9 (film rays of at most 25 samples)"; return LBM_EINVAL; }
-    if (p->storage < 0 || p->storage > 3) { why = "unknown storage"; return LBM_EINVAL; }
+    if (p->storage < 0 || p->storage > 4) { why = "unknown storage"; return LBM_EINVAL; }
     if (!(std::fabs(p->wall_u) < 0.3)) { why = "|wall_u| must be < 0.3"; return LBM_EINVAL; }
     if (p->wall_u != 0.0 && !p->wall_y) { why = "wall_u needs walls at the y extremes (wall_y)"; return LBM_EINVAL; }
     if (p->model != 0 && p->model != 1) { why = "unknown model"; return LBM_EINVAL; }
     if (p->model == 1 && p->A_nc != 0.0) { why = "the near-contact force belongs to the colour-gradient model"; return LBM_EINVAL; }
-    if (p->model == 1 && p->storage == 3) { why = "the reduced storage form holds recoloured (colour-gradient) states only"; return LBM_EINVAL; }
+    if (p->model == 1 && reduced_form(p->storage)) { why = "the reduced storage forms hold recoloured (colour-gradient) states only"; return LBM_EINVAL; }
     if (!std::isfinite(p->G_sc)) { why = "G_sc must be finite"; return LBM_EINVAL; }
-    if ((p->storage == 1 || p->storage == 2) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
+    if ((p->storage == 1 || p->storage == 2 || p->storage == 4) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     return LBM_OK;
@@ -529,10 +532,6 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
 
 // Bytes of the near-contact ray-bound bit field (one bit per 2x2x2 block, rows of
 // 32-bit words along x).
-static size_t nc_pos_bytes(const lbm_params& p) {
-    const size_t nbx = (size_t)(p.nx + 1) / 2;
-    return ((nbx + 31) / 32) * ((p.ny + 1) / 2) * ((p.nz + 1) / 2) * sizeof(uint32_t);
-}
 
 extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     if (!p) return 0;
@@ -540,7 +539,7 @@ extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     const PadLayout L = pad_layout(*p);
     size_t b = 2 * (size_t)stored_blocks(p->storage) * L.P * elem_bytes(p->storage) +
                2 * N * sizeof(float) + p->ny * sizeof(float);
-    if (p->A_nc > 0.0) b += N * (sizeof(float) + 2 * sizeof(int4)) + 3 * nc_pos_bytes(*p);
+    if (p->A_nc > 0.0) b += N * sizeof(float);   // the near-contact strength A_h
     return b;
 }
 
@@ -657,16 +656,12 @@ static void fill_step_params(lbm_ctx* c) {
     s.ah_b3 = (float)b3;
     s.ah_inv = (float)(1.0 / (1.0 - b3));
     s.nsamp = (int)std::floor(2.0 * (hcut + 3.0)) + 1;
-    s.ref_half = (p.storage == 1 || p.storage == 2) ? (float)(0.5 * p.rho0) : 0.0f;
+    s.ref_half = (p.storage == 1 || p.storage == 2 || p.storage == 4) ? (float)(0.5 * p.rho0) : 0.0f;
     const int tx = step_tile_x(), ty = step_tile_y();
     s.tiles_x = (p.nx + tx - 1) / tx;
     s.tiles_y = (p.ny + ty - 1) / ty;
     s.err = c->err_word;
     s.ah = c->ah;
-    s.nbx = (p.nx + 1) / 2;
-    s.nby = (p.ny + 1) / 2;
-    s.nbz = (p.nz + 1) / 2;
-    s.nbw = (s.nbx + 31) / 32;
     const WorkSplit w = work_split(p, c->num_sms);
     s.zparts = w.zparts;
     s.chain = w.chain;
@@ -706,10 +701,8 @@ void advance_state(lbm_ctx* c, long long k) {
     if (k & 1) {
         c->cur ^= 1;
         c->pc ^= 1;
-        c->cw ^= 1;
     }
     c->steps += k;
-    if (k > 0) c->nc_scan = false;
 }
 lbm_status check_errors(lbm_ctx* c) { return check_err_word(c); }
 int ctx_num_sms(const lbm_ctx* c) { return c->num_sms; }
@@ -749,20 +742,7 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
               alloc((void**)&c->phi[1], c->N * sizeof(float)) &&
               alloc((void**)&c->fx_row, p->ny * sizeof(float)) &&
               alloc((void**)&c->err_word, sizeof(int)) &&
-              (p->A_nc > 0.0 ? alloc((void**)&c->ah, c->N * sizeof(float)) &&
-                                   alloc((void**)&c->cand[0], c->N * sizeof(int4)) &&
-                                   alloc((void**)&c->cand[1], c->N * sizeof(int4)) &&
-                                   alloc((void**)&c->cand_count, 2 * sizeof(int)) &&
-                                   alloc((void**)&c->nc_pos[0], 3 * nc_pos_bytes(*p)) &&
-                                   alloc((void**)&c->nc_next, 3 * sizeof(int))
-                               : true);
-    if (ok && p->A_nc > 0.0) {
-        const size_t words = nc_pos_bytes(*p) / sizeof(uint32_t);
-        c->nc_pos[1] = c->nc_pos[0] + words;
-        c->nc_pos[2] = c->nc_pos[0] + 2 * words;
-        ok = cudaMemset(c->nc_next, 0, 3 * sizeof(int)) == cudaSuccess &&
-             cudaMemset(c->cand_count, 0, 2 * sizeof(int)) == cudaSuccess;
-    }
+              (p->A_nc > 0.0 ? alloc((void**)&c->ah, c->N * sizeof(float)) : true);
     c->red_blocks = c->num_sms * 8;
     ok = ok && alloc((void**)&c->red, (size_t)(c->red_blocks + 1) * 8 * sizeof(double));
     ok = ok && cudaMallocHost((void**)&c->red_host, 8 * sizeof(double)) == cudaSuccess;
@@ -870,11 +850,6 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->red);
     cudaFree(c->err_word);
     cudaFree(c->ah);
-    cudaFree(c->cand[0]);
-    cudaFree(c->cand[1]);
-    cudaFree(c->cand_count);
-    cudaFree(c->nc_pos[0]);
-    cudaFree(c->nc_next);
     if (c->red_host) cudaFreeHost(c->red_host);
     delete c;
 }
@@ -911,7 +886,8 @@ static void dispatch(int storage, F&& fn) {
     if (storage == 0) fn(StoreF32{});
     else if (storage == 1) fn(StoreF16{});
     else if (storage == 2) fn(StoreBF16{});
-    else fn(StoreQ5{});
+    else if (storage == 3) fn(StoreQ5{});
+    else fn(StoreQ5H{});
 }
 
 extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const double* rho_b,
@@ -944,7 +920,6 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const doub
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed
     c->steps = 0;
     c->fields_set = true;
-    c->nc_scan = true;
     return LBM_OK;
 }
 
@@ -983,19 +958,14 @@ extern "C" lbm_status lbm_set_pin_mask(lbm_ctx* c, const uint8_t* mask, int on_d
     cudaFree(c->pin_mask);
     c->pin_mask = nullptr;
     fill_step_params(c);
-    c->nc_scan = true;
     return LBM_OK;
 }
 
-// Launches of one time step: the near-contact pass (A_nc > 0), the step kernel and,
-// without near-contact force, the ghost-copy fill of the step's output (with it, the
-// next pass writes those ghost copies).
-// Near-contact bookkeeping: the step kernel of step t lists candidates in cand[cw]
-// and consumes (zeroes) the A_h entries it reads; the pass of step t+1 reads that
-// list and writes A_h only at those nodes. The step kernel also sets the ray-bound
-// bits of its colour field, nc_pos[k] for phi[k], which that pass reads. After any
-// change of state the pass scans every node once instead. Events (optional) bracket
-// the launches: e0 .. e1 pass, e1 .. e2 step kernel, e2 .. e3 ghost fill.
+// Launches of one time step: the near-contact pass (A_nc > 0), which writes every
+// node's A_h from the lagged colour field, the step kernel and, without near-contact
+// force, the ghost-copy fill of the step's output (with it, the next pass writes those
+// ghost copies). Events (optional) bracket the launches: e0 .. e1 pass, e1 .. e2 step
+// kernel, e2 .. e3 ghost fill.
 static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2,
                                    cudaEvent_t e3 = nullptr) {
     StepParams s = c->sp;
@@ -1007,13 +977,7 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
     cudaError_t e = cudaSuccess;
     if (e0) e = cudaEventRecord(e0, c->stream);
     if (nc) {
-        s.nc_pos = c->nc_pos[c->pc];
-        s.nc_pos_out = c->nc_pos[1 - c->pc];
-        s.cand = nullptr;
-        s.cand_clear = nullptr;
         s.ghost_f = ghost_cells(s) > 0 ? c->f[c->cur] : nullptr;
-        // after a change of state the ray-bound bits of the lag field are recomputed
-        if (e == cudaSuccess && c->nc_scan) e = launch_nc_pos(s, c->num_sms, c->stream);
         if (e == cudaSuccess)
             e = launch_nc_block(s, c->phimap[c->pc], c->phimap_ok, c->p.storage, c->num_sms,
                                 c->stream);
@@ -1027,8 +991,6 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
         e = launch_ghost_fill(c->f[1 - c->cur], s, c->p.storage, c->num_sms, c->stream);
     if (e == cudaSuccess && e3) e = cudaEventRecord(e3, c->stream);
     if (e != cudaSuccess) return e;
-    c->nc_scan = false;
-    c->cw ^= 1;
     c->cur ^= 1;
     c->pc ^= 1;
     c->steps++;
@@ -1079,22 +1041,13 @@ extern "C" lbm_status lbm_step_timed(lbm_ctx* c, int n, double out_ms[3]) {
     return check_err_word(c);
 }
 
-// A near-contact pass outside the time step (diagnostics): scan mode on s.phi_lag
-// into s.ah, with the scratch bit field and work counter, touching none of the
-// live step state; its candidates go to the list slot the next step kernel
-// overwrites.
+// A near-contact pass outside the time step (diagnostics): A_h of s.phi_lag into s.ah,
+// touching none of the live step state.
 static cudaError_t diag_pass(lbm_ctx* c, StepParams s) {
-    s.nc_pos = c->nc_pos[2];
-    s.nc_pos_out = nullptr;
-    s.cand = nullptr;
-    s.cand_clear = nullptr;
     s.ghost_f = nullptr;
-    cudaError_t e = launch_nc_pos(s, c->num_sms, c->stream);
     const int k = s.phi_lag == c->phi[0] ? 0 : 1;
     const bool tma = c->phimap_ok && s.phi_lag == c->phi[k];
-    if (e == cudaSuccess)
-        e = launch_nc_block(s, c->phimap[k], tma, c->p.storage, c->num_sms, c->stream);
-    return e;
+    return launch_nc_block(s, c->phimap[k], tma, c->p.storage, c->num_sms, c->stream);
 }
 
 extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, double* u,
@@ -1175,15 +1128,6 @@ extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
     return LBM_OK;
 }
 
-__global__ void count_diff_kernel(const uint32_t* a, const uint32_t* b, long long n,
-                                  unsigned long long* out) {
-    unsigned long long k = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        k += a[i] != b[i];
-    if (k) atomicAdd(out, k);
-}
-
 extern "C" lbm_status lbm_selftest_timeout(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
     CK(c, cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream));
@@ -1196,30 +1140,6 @@ extern "C" lbm_status lbm_selftest_timeout(lbm_ctx* c) {
         return LBM_ETIMEOUT;
     }
     return st == LBM_OK ? fail(c, LBM_OK, "the bounded wait did not give up") : st;
-}
-
-extern "C" lbm_status lbm_nc_bound_check(lbm_ctx* c, long long out[2]) {
-    if (!c || !out) return LBM_EINVAL;
-    if (!(c->p.A_nc > 0.0)) return fail(c, LBM_ESTATE, "no near-contact force on this lattice");
-    if (c->steps == 0 || c->nc_scan)
-        return fail(c, LBM_ESTATE, "no step has run since the last change of state");
-    const long long words = (long long)(nc_pos_bytes(c->p) / sizeof(uint32_t));
-    if (ensure_stage(c, 1) != LBM_OK) return LBM_ENOMEM;
-    StepParams s = c->sp;
-    s.phi_lag = c->phi[c->pc];
-    s.nc_pos = c->nc_pos[2];
-    CK(c, launch_nc_pos(s, c->num_sms, c->stream));
-    unsigned long long* d = reinterpret_cast<unsigned long long*>(c->stage);
-    CK(c, cudaMemsetAsync(d, 0, sizeof(*d), c->stream));
-    count_diff_kernel<<<grid_for((size_t)words, c->num_sms), kThreads, 0, c->stream>>>(
-        c->nc_pos[2], c->nc_pos[c->pc], words, d);
-    CK(c, cudaGetLastError());
-    unsigned long long h = 0;
-    CK(c, cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    out[0] = (long long)h;
-    out[1] = words;
-    return LBM_OK;
 }
 
 extern "C" lbm_status lbm_get_pops(lbm_ctx* c, double* f_r, double* f_b, double* phi_lag,
@@ -1295,6 +1215,44 @@ extern "C" lbm_status lbm_get_window(lbm_ctx* c, int x0, int y0, int z0, int wx,
     return LBM_OK;
 }
 
+// Z-plane ranges of the stored state (slab decomposition): every stored block's
+// planes, then the lagged colour field's, copied as stored.
+extern "C" size_t lbm_planes_bytes(const lbm_ctx* c, int h) {
+    if (!c || h < 1) return 0;
+    const size_t plane_p = (size_t)c->pitch * c->nyp;
+    return (size_t)stored_blocks(c->p.storage) * h * plane_p * c->elem +
+           (size_t)h * c->p.nx * c->p.ny * sizeof(float);
+}
+
+static lbm_status planes_copy(lbm_ctx* c, int z0, int h, void* buf, bool get) {
+    if (!c) return LBM_EINVAL;
+    if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
+    if (!buf) return fail(c, LBM_EINVAL, "buf is NULL");
+    if (h < 1 || z0 < 0 || z0 + h > c->p.nz) return fail(c, LBM_EINVAL, "planes outside the lattice");
+    const size_t plane_p = (size_t)c->pitch * c->nyp;
+    const size_t seg = (size_t)h * plane_p * c->elem;   // bytes per block
+    unsigned char* b = static_cast<unsigned char*>(buf);
+    unsigned char* f = static_cast<unsigned char*>(c->f[c->cur]);
+    const int blocks = stored_blocks(c->p.storage);
+    for (int k = 0; k < blocks; ++k) {
+        unsigned char* blk = f + ((size_t)k * c->P + (size_t)z0 * plane_p) * c->elem;
+        CK(c, cudaMemcpyAsync(get ? b + k * seg : blk, get ? blk : b + k * seg, seg,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const size_t plane = (size_t)c->p.nx * c->p.ny;
+    float* ph = c->phi[c->pc] + (size_t)z0 * plane;
+    unsigned char* pb = b + blocks * seg;
+    CK(c, cudaMemcpyAsync(get ? (void*)pb : (void*)ph, get ? (const void*)ph : (const void*)pb,
+                          (size_t)h * plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    return LBM_OK;
+}
+extern "C" lbm_status lbm_get_planes(lbm_ctx* c, int z0, int h, void* buf) {
+    return planes_copy(c, z0, h, buf, true);
+}
+extern "C" lbm_status lbm_set_planes(lbm_ctx* c, int z0, int h, const void* buf) {
+    return planes_copy(c, z0, h, const_cast<void*>(buf), false);
+}
+
 extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* f_b,
                                    const double* phi_lag, int on_device) {
     if (!c) return LBM_EINVAL;
@@ -1328,7 +1286,6 @@ extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* 
     CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
     c->fields_set = true;
-    c->nc_scan = true;
     return LBM_OK;
 }
 
@@ -1418,7 +1375,6 @@ extern "C" lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf) {
     CK(c, cudaStreamSynchronize(c->stream));
     std::memcpy(&c->steps, b + pb + 2 * fb, sizeof(long long));
     c->fields_set = true;
-    c->nc_scan = true;
     return LBM_OK;
 }
 

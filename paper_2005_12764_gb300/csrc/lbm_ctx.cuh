@@ -16,9 +16,6 @@ namespace lbm {
 cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUtensorMap& omap,
                         int storage, int grid,
                         cudaStream_t s);
-cudaError_t launch_nc(const StepParams& p, int4* scan_list, int* scan_count, int storage,
-                      int num_sms, cudaStream_t s);
-cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
                             int storage, int num_sms, cudaStream_t s);
 void nc_cube_box(double h_cut, int box[3]);
@@ -58,13 +55,6 @@ struct lbm_ctx {
     uint8_t* pin_d2 = nullptr;
     uint8_t* pin_mask = nullptr;
     float* ah = nullptr;        // near-contact strength per node (A_nc > 0)
-    int4* cand[2] = {nullptr, nullptr}; // candidate lists {node, G} (ping-pong) and counters
-    int* cand_count = nullptr;          // [2]
-    uint32_t* nc_pos[3] = {nullptr, nullptr, nullptr}; // ray-bound bit fields: [k] of phi[k],
-                                        // [2] scratch for diagnostic passes
-    int* nc_next = nullptr;             // [3] list-kernel work counters: ping-pong, scratch
-    int cw = 0;                 // list the next step kernel writes
-    bool nc_scan = true;        // next near-contact pass must scan every node
     double* stage = nullptr;    // device FP64 staging, grown on demand
     size_t stage_cap = 0;       // its size in doubles
     double* red = nullptr;      // reduction partials

@@ -74,6 +74,10 @@ struct StoreF32 {
     __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
     __device__ __forceinline__ static float cvt(T v, float) { return v; }
     __device__ __forceinline__ static T enc(float v, float) { return v; }
+    // (the reduced forms' members; unused by the full forms)
+    static constexpr int AUX_BLOCKS = 0;
+    __device__ __forceinline__ static float tot_ref(int, float) { return 0.0f; }
+    __device__ __forceinline__ static float coef(const T*, size_t, size_t, int) { return 0.0f; }
 };
 struct StoreF16 {
     using T = __half;
@@ -87,6 +91,10 @@ struct StoreF16 {
     }
     __device__ __forceinline__ static float cvt(T v, float ref) { return __half2float(v) + ref; }
     __device__ __forceinline__ static T enc(float v, float ref) { return __float2half_rn(v - ref); }
+    // (the reduced forms' members; unused by the full forms)
+    static constexpr int AUX_BLOCKS = 0;
+    __device__ __forceinline__ static float tot_ref(int, float) { return 0.0f; }
+    __device__ __forceinline__ static float coef(const T*, size_t, size_t, int) { return 0.0f; }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
@@ -100,6 +108,10 @@ struct StoreBF16 {
     }
     __device__ __forceinline__ static float cvt(T v, float ref) { return __bfloat162float(v) + ref; }
     __device__ __forceinline__ static T enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
+    // (the reduced forms' members; unused by the full forms)
+    static constexpr int AUX_BLOCKS = 0;
+    __device__ __forceinline__ static float tot_ref(int, float) { return 0.0f; }
+    __device__ __forceinline__ static float coef(const T*, size_t, size_t, int) { return 0.0f; }
 };
 // Reduced FP32 form, Q + 5 arrays instead of 2Q. The recoloured post-collision
 // populations of a node are, per direction,
@@ -110,16 +122,58 @@ struct StoreBF16 {
 // wrote them (arrays Q .. Q+4) determine both species exactly; the pull rebuilds
 // each species from the coefficients of the population's source node. (The five
 // arrays hold the node's own coefficients: they are read in place, not streamed.)
+constexpr int Q5_AUX = 5;   // kappa_r, kappa_b, m_x, m_y, m_z
 struct StoreQ5 {
     using T = float;
     static constexpr int kind = 3;
     static constexpr bool DEV = false, RED = true;
+    static constexpr int AUX_BLOCKS = Q5_AUX;   // blocks holding the five coefficients
     __device__ __forceinline__ static float load(const T* p, size_t i, float) { return __ldg(p + i); }
     __device__ __forceinline__ static void store(T* p, size_t i, float v, float) { p[i] = v; }
     __device__ __forceinline__ static float cvt(T v, float) { return v; }
     __device__ __forceinline__ static T enc(float v, float) { return v; }
+    // reference of the stored total of direction i (rho0_ref = 2 ref_half): none
+    __device__ __forceinline__ static float tot_ref(int, float) { return 0.0f; }
+    // coefficient k of the node at padded index q (P = elements per block)
+    __device__ __forceinline__ static float coef(const T* p, size_t P, size_t q, int k) {
+        return __ldg(p + (size_t)(Q + k) * P + q);
+    }
+    __device__ __forceinline__ static void store_coef(T* p, size_t P, size_t q, int k, float v) {
+        p[(size_t)(Q + k) * P + q] = v;
+    }
 };
-constexpr int Q5_AUX = 5;   // kappa_r, kappa_b, m_x, m_y, m_z
+// Reduced form with FP16 totals, Q + 10 16-bit arrays: the 19 totals as FP16
+// deviations f_i - w_i rho0 from the lattice weights (rounded to nearest even; in both
+// phases the total density is close to rho0, so the deviation is O(|u|, |rho - rho0|)),
+// and the five coefficients kept exact in FP32, each as two 16-bit arrays (low half,
+// then high half of its bits), so that the species masses the coefficients carry are
+// not rounded. 58 bytes per node and copy instead of 96 (FP32 reduced form) or 152
+// (full FP32).
+struct StoreQ5H {
+    using T = __half;
+    static constexpr int kind = 4;
+    static constexpr bool DEV = false, RED = true;
+    static constexpr int AUX_BLOCKS = 2 * Q5_AUX;
+    __device__ __forceinline__ static float load(const T* p, size_t i, float ref) {
+        return __half2float(__ldg(p + i)) + ref;
+    }
+    __device__ __forceinline__ static void store(T* p, size_t i, float v, float ref) {
+        p[i] = __float2half_rn(v - ref);
+    }
+    __device__ __forceinline__ static float cvt(T v, float ref) { return __half2float(v) + ref; }
+    __device__ __forceinline__ static T enc(float v, float ref) { return __float2half_rn(v - ref); }
+    __device__ __forceinline__ static float tot_ref(int i, float rho0) { return wgt(i) * rho0; }
+    __device__ __forceinline__ static float coef(const T* p, size_t P, size_t q, int k) {
+        const unsigned lo = __half_as_ushort(__ldg(p + (size_t)(Q + 2 * k) * P + q));
+        const unsigned hi = __half_as_ushort(__ldg(p + (size_t)(Q + 2 * k + 1) * P + q));
+        return __uint_as_float(lo | (hi << 16));
+    }
+    __device__ __forceinline__ static void store_coef(T* p, size_t P, size_t q, int k, float v) {
+        const unsigned b = __float_as_uint(v);
+        p[(size_t)(Q + 2 * k) * P + q] = __ushort_as_half((unsigned short)(b & 0xffffu));
+        p[(size_t)(Q + 2 * k + 1) * P + q] = __ushort_as_half((unsigned short)(b >> 16));
+    }
+};
 // Recolouring share w_i (c_i . m) / |c_i| of direction i (0 for the rest direction).
 __device__ __forceinline__ float q5_share(int i, float mx, float my, float mz) {
     if (csq(i) == 0) return 0.0f;
@@ -138,21 +192,7 @@ struct StepParams {
     const float* fx_row;    // [ny] x body force per row: g_x + Kolmogorov profile
     const uint8_t* pin_d2;  // [N] squared distance to the nearest pin, 255 = none; or null
     float* ah;              // [N] near-contact strength A_h of this step (A_nc > 0)
-    int4* cand;             // candidates written by the step kernel: nodes with |G| >= 0.9e-3,
-                            // {node, G_x, G_y, G_z} (float bits), G of the step's colour field
-    int* cand_count;        // its length (reset before the step kernel)
-    const int4* nc_list;    // list the near-contact pass works on (null: scan every node)
-    const int* nc_count;
-    uint32_t* nc_pos;       // [nbz][nby][nbw] bits: block (bx, by, bz) of the 2x2x2 block grid
-                            // may hold a node with phi_lag > kPosBand among nodes 2b .. 2b+2
-                            // per axis (bit bx & 31 of word bx >> 5)
-    uint32_t* nc_pos_out;   // the same bits for phi_out: cleared by the near-contact pass and
-                            // set by the step kernel (null: not kept)
-    int* nc_next;           // work counter of the near-contact list kernel (0 on entry)
-    int* nc_next_clear;     // counter the list kernel zeroes for the next pass (or null)
-    int* cand_clear;        // candidate counter the list kernel zeroes for the step kernel
     void* ghost_f;          // populations whose ghost copies the list kernel fills (or null)
-    int nbx, nby, nbz, nbw; // block grid: ceil(n / 2) per axis; nbw = ceil(nbx / 32)
     float gy, gz;
     float wall_u6;          // 6 U of sliding y-walls (+U at y = ny-1/2, -U at y = -1/2), or 0
     int model;              // 0: colour gradient; 1: Shan-Chen
@@ -173,7 +213,8 @@ struct StepParams {
     float sigma, beta;
     float A_nc, h_min, h_cut, ah_b3, ah_inv;  // A_h tail: b3 = (h_min/h_cut)^3, inv = 1/(1-b3)
     int nsamp;              // ray samples t = -1, -1/2, ..., h_cut + 2
-    float ref_half;         // rho0/2 for FP16/BF16 deviation storage, 0 for FP32
+    float ref_half;         // rho0/2 for FP16/BF16 deviation storage and the FP16 reduced
+                            // form (whose totals are stored as f_i - w_i rho0), else 0
     int tiles_x, tiles_y;   // xy tiles of the step kernel
     int zparts;             // part mode: z is cut into this many equal parts, one CTA per
                             // (part, tile)
@@ -267,23 +308,12 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
 //
 // Work bound (exact): an upward crossing needs a positive sample, and a trilinear
 // sample is a convex combination of its 8 corner nodes, so it cannot exceed 1e-5
-// when every corner is <= kPosBand = 1e-5/2. A bit field over 2x2x2 blocks marks
-// where such a corner may be; samples after the last marked one cannot complete a
-// crossing pair, so the march ends there with the same A_h. Most candidate rays
-// (outward from a droplet into the bulk) have no marked sample at all.
+// when every corner is <= kPosBand = 1e-5/2 (the interpolation's roundings add a few
+// ulp of 0.5e-5 at most). A bit table over 2x2x2 blocks marks where such a corner may
+// be; samples after the last marked one cannot complete a crossing pair, so the march
+// ends there with the same A_h.
 constexpr float kSignBand = 1e-5f;
 constexpr float kPosBand = 0.5e-5f;
-
-// Blocks of the bit field that hold node n of an axis of N nodes (nb = ceil(N/2)
-// blocks, block b = nodes 2b, 2b+1, 2b+2): `second` = 0 gives n/2, `second` = 1 the
-// other block holding it, or -1. Even n >= 2 also lie in block n/2 - 1; on a
-// periodic axis the last block wraps over node 0 (and over node 1 when N is odd).
-__device__ __forceinline__ int pos_block(int n, int second, int N, bool periodic, int nb) {
-    if (!second) return n >> 1;
-    if ((n & 1) == 0 && n >= 2) return (n >> 1) - 1;
-    if (periodic && (n == 0 || (n == 1 && (N & 1)))) return nb - 1;
-    return -1;
-}
 
 // Bits 0, 2, .., 30 of v moved to bits 0 .. 15.
 __device__ __forceinline__ uint32_t even_bits(uint32_t v) {
@@ -292,28 +322,6 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t v) {
     v = (v | (v >> 2)) & 0x0F0F0F0Fu;
     v = (v | (v >> 4)) & 0x00FF00FFu;
     return (v | (v >> 8)) & 0x0000FFFFu;
-}
-
-// Marks, in the bit field `bits`, the blocks holding the positive nodes of one row
-// segment: m = bit j set if node (x0 + j, y, z) has phi > kPosBand, x0 even, the
-// segment at most 32 nodes. Lane `which` (0 .. 3) of the calling warp handles the
-// (y, z) block pair (which & 1, which >> 1). The blocks x0/2 .. x0/2 + 15 take their
-// nodes 2b, 2b+1, 2b+2 from the segment (node x0 + 32 belongs to the next segment,
-// which marks it as its own first node); the block before the segment (wrapping
-// at x = 0) holds node x0, and for odd nx node 1 as well.
-__device__ __forceinline__ void mark_pos_row(uint32_t* bits, const StepParams& p, int x0, int y,
-                                             int z, uint32_t m, int which) {
-    const int by = pos_block(y, which & 1, p.ny, !p.wall_y, p.nby);
-    const int bz = pos_block(z, which >> 1, p.nz, !p.wall_z, p.nbz);
-    if (by < 0 || bz < 0) return;
-    uint32_t* row = bits + ((size_t)bz * p.nby + by) * p.nbw;
-    const uint32_t c = even_bits(m | (m >> 1) | (m >> 2));
-    const int b0 = x0 >> 1;
-    if (c) atomicOr(row + (b0 >> 5), c << (b0 & 31));
-    if ((m & 1u) || (x0 == 0 && (p.nx & 1) && (m & 2u))) {
-        const int pb = x0 == 0 ? p.nbx - 1 : b0 - 1;
-        atomicOr(row + (pb >> 5), 1u << (pb & 31));
-    }
 }
 
 // Ray of a candidate: unit direction -G'/|G'|; false when |G'| < 1e-3 or non-finite.
@@ -326,37 +334,6 @@ __device__ __forceinline__ bool nc_ray(float Gx, float Gy, float Gz, float& nx_,
     ny_ = -Gy * inv;
     nz_ = -Gz * inv;
     return true;
-}
-
-// Ray sample positions: cell b = base + floor(o) and fraction o - floor(o) along one
-// axis, for |o| <= h_cut + 2 <= 11. Periodic axes of at least 12 nodes wrap with one
-// conditional add or subtract; shorter ones take the general wrap. On a walled axis
-// the point lies inside the fluid iff -base <= o <= n - 1 - base, i.e. its cell is a
-// fluid node and it does not pass the last node.
-__device__ __forceinline__ int ray_wrap(int b, int n) {
-    if (n >= 12) {
-        b = b < 0 ? b + n : b;
-        return b >= n ? b - n : b;
-    }
-    return wrap_near(b, n);
-}
-
-// Index of the last sample of a ray that may be positive, or -1: the samples
-// inside the fluid are s < s_end (the first sample outside stops the march), and
-// the bit field is scanned from s_end - 1 downwards. A sample on the last node of
-// a walled axis (fraction 0) is looked up in that node's block: its value is that
-// node's, whatever the other corner holds. (Starting the march at the first
-// possibly positive sample instead of t = -1 gives the same A_h, but finding that
-// sample by a forward scan costs more than the samples it saves.)
-__device__ __forceinline__ bool nc_sample_marked(const StepParams& p, int x, int y, int z,
-                                                 float nx_, float ny_, float nz_, int s) {
-    const float t = -1.0f + 0.5f * (float)s;
-    const int ix = ray_wrap(x + (int)floorf(t * nx_), p.nx);
-    const int iy = ray_wrap(y + (int)floorf(t * ny_), p.ny);   // identity on walled axes
-    const int iz = ray_wrap(z + (int)floorf(t * nz_), p.nz);
-    const int bx = ix >> 1;
-    const uint32_t w = __ldg(p.nc_pos + ((iz >> 1) * p.nby + (iy >> 1)) * p.nbw + (bx >> 5));
-    return (w >> (bx & 31)) & 1u;
 }
 
 // First sample of a ray outside the fluid (p.nsamp if none).
@@ -391,90 +368,10 @@ __device__ __forceinline__ int nc_sample_end(const StepParams& p, int y, int z, 
     return s_end;
 }
 
-__device__ __forceinline__ int nc_last_sample(const StepParams& p, int x, int y, int z, float nx_,
-                                              float ny_, float nz_) {
-    const int s_end = nc_sample_end(p, y, z, ny_, nz_);
-    for (int s = s_end - 1; s >= 0; --s)
-        if (nc_sample_marked(p, x, y, z, nx_, ny_, nz_, s)) return s;
-    return -1;
-}
-
-// Trilinear sample of the lagged colour field at node (x, y, z) + offset o, for a
-// point known to lie inside the fluid (as nc_last_sample established). The cell and
-// the weights come from the offset alone (|o| is small), so the point is located to
-// the precision of o, not of x + o; on the last node of a walled axis (fraction 0)
-// the cell below is used with fraction 1, which gives that node's value.
-// Split into the cell (corner indices and fractions), its 8 corner values, and the
-// interpolation, so that a ray can keep the corners while it stays in one cell; the
-// interpolation fixes every rounding (no contraction left to the compiler), so a
-// sample has the same value however it is evaluated.
-struct RayCell {
-    int r00, r01, r10, r11;   // row offsets of the corners (z0 y0, z0 y1, z1 y0, z1 y1)
-    int ix0, ix1;
-    float fx, fy, fz;
-};
-__device__ __forceinline__ void ray_cell(const StepParams& p, int x, int y, int z, float ox,
-                                         float oy, float oz, RayCell& c) {
-    const float flx = floorf(ox), fly = floorf(oy), flz = floorf(oz);
-    c.fx = ox - flx;
-    c.fy = oy - fly;
-    c.fz = oz - flz;
-    int ix0 = x + (int)flx, iy0 = y + (int)fly, iz0 = z + (int)flz;
-    int iy1, iz1;
-    ix0 = ray_wrap(ix0, p.nx);
-    c.ix0 = ix0;
-    c.ix1 = ix0 + 1 == p.nx ? 0 : ix0 + 1;
-    if (p.wall_y) {
-        if (iy0 == p.ny - 1) {
-            iy0 = p.ny - 2;
-            c.fy = 1.0f;
-        }
-        iy1 = iy0 + 1;
-    } else {
-        iy0 = ray_wrap(iy0, p.ny);
-        iy1 = iy0 + 1 == p.ny ? 0 : iy0 + 1;
-    }
-    if (p.wall_z) {
-        if (iz0 == p.nz - 1) {
-            iz0 = p.nz - 2;
-            c.fz = 1.0f;
-        }
-        iz1 = iz0 + 1;
-    } else {
-        iz0 = ray_wrap(iz0, p.nz);
-        iz1 = iz0 + 1 == p.nz ? 0 : iz0 + 1;
-    }
-    c.r00 = (iz0 * p.ny + iy0) * p.nx;
-    c.r01 = (iz0 * p.ny + iy1) * p.nx;
-    c.r10 = (iz1 * p.ny + iy0) * p.nx;
-    c.r11 = (iz1 * p.ny + iy1) * p.nx;
-}
-__device__ __forceinline__ void ray_corners(const StepParams& p, const RayCell& c, float (&v)[8]) {
-    const float* f = p.phi_lag;
-    v[0] = __ldg(f + c.r00 + c.ix0);
-    v[1] = __ldg(f + c.r00 + c.ix1);
-    v[2] = __ldg(f + c.r01 + c.ix0);
-    v[3] = __ldg(f + c.r01 + c.ix1);
-    v[4] = __ldg(f + c.r10 + c.ix0);
-    v[5] = __ldg(f + c.r10 + c.ix1);
-    v[6] = __ldg(f + c.r11 + c.ix0);
-    v[7] = __ldg(f + c.r11 + c.ix1);
-}
+// Linear interpolation (1 - w) a + w b with every rounding fixed (no contraction left
+// to the compiler), so that a ray sample has the same value however it is evaluated.
 __device__ __forceinline__ float ray_lerp(float a, float b, float w) {
     return __fmaf_rn(w, b, __fmul_rn(1.0f - w, a));   // (1 - w) a + w b
-}
-__device__ __forceinline__ float ray_interp(const RayCell& c, const float (&v)[8]) {
-    const float c0 = ray_lerp(ray_lerp(v[0], v[1], c.fx), ray_lerp(v[2], v[3], c.fx), c.fy);
-    const float c1 = ray_lerp(ray_lerp(v[4], v[5], c.fx), ray_lerp(v[6], v[7], c.fx), c.fy);
-    return ray_lerp(c0, c1, c.fz);
-}
-__device__ __forceinline__ float ray_sample(const StepParams& p, int x, int y, int z, float ox,
-                                            float oy, float oz) {
-    RayCell c;
-    ray_cell(p, x, y, z, ox, oy, oz, c);
-    float v[8];
-    ray_corners(p, c, v);
-    return ray_interp(c, v);
 }
 
 // Crossing search along one ray, fed its samples in order (t = -1, -1/2, ...):
@@ -551,6 +448,18 @@ struct SmemEmit {
     typename St::T* tile;        // this node in block 0 of the shared output tile
     __device__ __forceinline__ void operator()(int k, float v, float ref) const {
         tile[k * NT] = St::enc(v, ref);   // NT nodes per block of the tile
+    }
+    // reduced forms: recolouring coefficient k (its block(s) after the Q totals)
+    __device__ __forceinline__ void coef(int k, float v) const {
+        if constexpr (St::RED) {
+            if constexpr (St::AUX_BLOCKS == Q5_AUX) {
+                tile[(Q + k) * NT] = v;
+            } else {
+                const unsigned b = __float_as_uint(v);
+                tile[(Q + 2 * k) * NT] = __ushort_as_half((unsigned short)(b & 0xffffu));
+                tile[(Q + 2 * k + 1) * NT] = __ushort_as_half((unsigned short)(b >> 16));
+            }
+        }
     }
 };
 
@@ -649,8 +558,8 @@ __device__ __forceinline__ void collide_moments(const StepParams& p, const float
         }
         if constexpr (St::RED) {
             // reduced form: the total; the species split goes with the coefficients
-            emit(i, wr + si, 0.0f);
-            emit(o, wr + so, 0.0f);
+            emit(i, wr + si, St::tot_ref(i, 2.0f * refh));
+            emit(o, wr + so, St::tot_ref(o, 2.0f * refh));
         } else {
             const float sg = (face ? sg_f : sg_e) * cn;
             const float wrr = face ? wrr_f : wrr_e, wrb = face ? wrb_f : wrb_e;
@@ -669,7 +578,7 @@ __device__ __forceinline__ void collide_moments(const StepParams& p, const float
         float si = -wr * U15 - 2.0f * pert_sum;
         if (!UnitOmega) si += om1 * ((f[i] - wr) + wr * usq15);
         if constexpr (St::RED) {
-            emit(i, wr + si, 0.0f);
+            emit(i, wr + si, St::tot_ref(i, 2.0f * refh));
         } else {
             const float hw = w * refh;
             emit(i, w * rr + ar * si, dev_ref(hw, phi, 0));
@@ -680,11 +589,11 @@ __device__ __forceinline__ void collide_moments(const StepParams& p, const float
         // recolouring coefficients: kappa_r, kappa_b and m = seg0 G / |G| (the
         // recolouring term of direction i is then w_i (c_i . m) / |c_i|)
         const float mg = seg0 * inv_g;
-        emit(Q, ar, 0.0f);
-        emit(Q + 1, ab, 0.0f);
-        emit(Q + 2, mg * Gx, 0.0f);
-        emit(Q + 3, mg * Gy, 0.0f);
-        emit(Q + 4, mg * Gz, 0.0f);
+        emit.coef(0, ar);
+        emit.coef(1, ab);
+        emit.coef(2, mg * Gx);
+        emit.coef(3, mg * Gy);
+        emit.coef(4, mg * Gz);
     }
 }
 

@@ -84,7 +84,7 @@ struct Geo {
     // the reduced form the Q totals and Q + 5 with the recolouring coefficients
     static constexpr bool RED = St::RED;
     static constexpr int NL = RED ? Q : 2 * Q;
-    static constexpr int NS = RED ? Q + Q5_AUX : 2 * Q;
+    static constexpr int NS = RED ? Q + St::AUX_BLOCKS : 2 * Q;
     static constexpr size_t STAGE_BYTES = (size_t)NL * IK_BYTES;
     // 4-slot ring per plane (tile + ring nodes): the colour field, or for the
     // Shan-Chen model the two species densities
@@ -364,8 +364,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
             const int gy = y0 + ty;
             const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
             const bool zlo = p.wall_z && pl == 0, zhi = p.wall_z && pl == p.nz - 1;
+            const float rho0 = 2.0f * p.ref_half;   // reference of the stored totals
 #pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = st[(size_t)i * IKS - cx(i)];
+            for (int i = 0; i < Q; ++i) ft[i] = St::cvt(st[(size_t)i * IKS - cx(i)], St::tot_ref(i, rho0));
             float sr = 0.f, sb = 0.f, d = 0.f;
             if (!(ylo || yhi || zlo || zhi)) {
 #pragma unroll
@@ -381,7 +382,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 for (int i = 0; i < Q; ++i) {
                     const bool out = (cy(i) > 0 && ylo) || (cy(i) < 0 && yhi) ||
                                      (cz(i) > 0 && zlo) || (cz(i) < 0 && zhi);
-                    if (out) ft[i] = __ldg(fin + (size_t)opp(i) * p.P + self);
+                    if (out) ft[i] = St::load(fin, (size_t)opp(i) * p.P + self, St::tot_ref(opp(i), rho0));
                     const Coef a = out ? coef_at(sc, tx, ty)
                                        : coef_at((sc - cz(i)) & 3, tx - cx(i), ty - cy(i));
                     sr = __fmaf_rn(a.kr, ft[i], sr);
@@ -536,13 +537,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
         // step's input, read in place)
         float aux_reg[2][Q5_AUX];
         auto aux_fetch = [&](int pl) {
-            const T* base = fin + (size_t)ring_z(pl) * p.plane_p;
+            if constexpr (G::RED) {
+                const size_t base = (size_t)ring_z(pl) * p.plane_p;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (ring_xy[j] < 0) break;
+                for (int j = 0; j < 2; ++j) {
+                    if (ring_xy[j] < 0) break;
 #pragma unroll
-                for (int k = 0; k < Q5_AUX; ++k)
-                    aux_reg[j][k] = __ldg(base + (size_t)(Q + k) * p.P + ring_xy[j]);
+                    for (int k = 0; k < Q5_AUX; ++k)
+                        aux_reg[j][k] = St::coef(fin, p.P, base + ring_xy[j], k);
+                }
             }
         };
         auto lag_fetch = [&](int pl) {
@@ -820,22 +823,6 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                         Fz += ah_c * Gz;
                     }
                 }
-                if (p.cand) {
-                    // this node's gradient is the next pass's lagged gradient: list it,
-                    // with that gradient, as a candidate if it may reach the 1e-3
-                    // threshold there
-                    const bool cand = Gx * Gx + Gy * Gy + Gz * Gz >= 0.81e-6f;
-                    const unsigned m = __ballot_sync(__activemask(), cand);
-                    if (cand) {
-                        const int leader = __ffs(m) - 1;
-                        int base = 0;
-                        if (lane == leader) base = atomicAdd(p.cand_count, __popc(m));
-                        base = __shfl_sync(m, base, leader);
-                        p.cand[base + __popc(m & ((1u << lane) - 1u))] =
-                            make_int4((int)node, __float_as_int(Gx), __float_as_int(Gy),
-                                      __float_as_int(Gz));
-                    }
-                }
                 // outputs go to the shared output tile; the tile is stored below
                 const SmemEmit<St, TX * TY> em{sout + oty * TX + otx};
                 if constexpr (UnitOmega)
@@ -844,13 +831,6 @@ __device__ __forceinline__ void step_body(const StepParams& p, const CUtensorMap
                 else
                     collide_store<St, UnitOmega>(p, cu, cu_rr, cu_rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
                 p.phi_out[node] = phic;
-            }
-            if (p.nc_pos_out) {
-                // ray-bound bits of this step's colour field for the next near-contact
-                // pass: one warp is one row of the tile
-                const bool pos = owned && !failed && phi_at(slot(z), otx, oty) > kPosBand;
-                const uint32_t m = __ballot_sync(0xffffffffu, pos);
-                if (m != 0u && lane < 4) mark_pos_row(p.nc_pos_out, p, x0, y0 + oty, z, m, lane);
             }
             // store the output tile of plane z: 2Q tensor copies of TX x TY, clipped by
             // the store map at the lattice edge (to 16 bytes: ghost copies are written
@@ -971,22 +951,41 @@ __device__ __forceinline__ void ghost_task(typename St::T* f, const StepParams& 
     if (t < n1) {
         const int k = (int)(t / p.nz), z = (int)(t - (long long)k * p.nz);
         T* blk = f + (size_t)k * p.P;
-        for (int y = lane; y < p.ny; y += 32) {
-            T* row = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);   // node x = 0
-            if ((p.nx & 1) == 0 && p.nx >= 2) {
-                // row[-2], row[-1] <- row[nx-2], row[nx-1]; row[nx], row[nx+1] <- row[0], row[1]
-                const Pair a = *reinterpret_cast<const Pair*>(row + p.nx - 2);
-                const Pair b = *reinterpret_cast<const Pair*>(row);
-                *reinterpret_cast<Pair*>(row - 2) = a;
-                *reinterpret_cast<Pair*>(row + p.nx) = b;
-            } else {
-                const T a0 = row[wrap_near(-2, p.nx)], a1 = row[wrap_near(-1, p.nx)];
-                const T b0 = row[wrap_near(p.nx, p.nx)], b1 = row[wrap_near(p.nx + 1, p.nx)];
-                row[-2] = a0;
-                row[-1] = a1;
-                row[p.nx] = b0;
-                row[p.nx + 1] = b1;
+        if ((p.nx & 1) == 0 && p.nx >= 2) {
+            // row[-2], row[-1] <- row[nx-2], row[nx-1]; row[nx], row[nx+1] <- row[0], row[1]
+            // (GB rows at a time: every load of a batch is issued before its stores)
+            constexpr int GB = 4;
+            for (int y0 = lane; y0 < p.ny; y0 += 32 * GB) {
+                Pair a[GB], b[GB];
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    const int y = y0 + 32 * g;
+                    if (y < p.ny) {
+                        const T* row = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);
+                        a[g] = *reinterpret_cast<const Pair*>(row + p.nx - 2);
+                        b[g] = *reinterpret_cast<const Pair*>(row);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    const int y = y0 + 32 * g;
+                    if (y < p.ny) {
+                        T* row = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);
+                        *reinterpret_cast<Pair*>(row - 2) = a[g];
+                        *reinterpret_cast<Pair*>(row + p.nx) = b[g];
+                    }
+                }
             }
+            return;
+        }
+        for (int y = lane; y < p.ny; y += 32) {   // odd nx: element by element
+            T* row = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);   // node x = 0
+            const T a0 = row[wrap_near(-2, p.nx)], a1 = row[wrap_near(-1, p.nx)];
+            const T b0 = row[wrap_near(p.nx, p.nx)], b1 = row[wrap_near(p.nx + 1, p.nx)];
+            row[-2] = a0;
+            row[-1] = a1;
+            row[p.nx] = b0;
+            row[p.nx + 1] = b1;
         }
         return;
     }
@@ -998,7 +997,20 @@ __device__ __forceinline__ void ghost_task(typename St::T* f, const StepParams& 
     T* blk = f + (size_t)k * p.P;
     T* dst = blk + pidx(p.pitch, p.nyp, p.padx, 0, y, z);
     const T* src = blk + pidx(p.pitch, p.nyp, p.padx, 0, wrap_near(y, p.ny), z);
-    for (int x = lane - 2; x < p.nx + 2; x += 32) dst[x] = src[wrap_near(x, p.nx)];
+    constexpr int GB = 4;
+    for (int x0 = lane - 2; x0 < p.nx + 2; x0 += 32 * GB) {
+        T v[GB];
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int x = x0 + 32 * g;
+            if (x < p.nx + 2) v[g] = src[wrap_near(x, p.nx)];
+        }
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const int x = x0 + 32 * g;
+            if (x < p.nx + 2) dst[x] = v[g];
+        }
+    }
 }
 
 template <class St>
@@ -1031,159 +1043,6 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
         const BatchLattice& L = tab[lo];
         ghost_task<St>(static_cast<typename St::T*>(L.fout), L.p, t - L.ghost_begin, lane);
     }
-}
-
-// ---------------------------------------------------------------- near-contact pass
-// A_h from the lagged colour field, for the nodes of a candidate list {node, G'}:
-// the list the previous step kernel wrote (lagged gradient >= 0.9e-3, a superset of
-// the nodes where A_h can be nonzero), or, after a change of state, the list the
-// scan kernel below compacts from every node. Every other entry of ah is 0.
-//
-// Warps take 32 candidates at a time from a shared counter (ray lengths vary
-// widely, so the work is handed out as it is done):
-//  1. each lane finds the last sample of its ray that may be positive (the bit
-//     field, scanned from the far end: in a bicontinuous mixture the first lookup
-//     usually settles it);
-//  2. where at least half the rays of the warp need samples (a fine mixture), each
-//     lane marches its own ray and stops as soon as A_h is decided; otherwise, in
-//     rounds of NC_CHUNK samples per ray, the samples the unfinished rays need next
-//     are spread evenly over the lanes and interpolated into shared memory, so a
-//     few long rays do not hold the warp back, and each lane feeds its ray's
-//     crossing search (along a droplet, the march ends at the last possibly
-//     positive sample). Both evaluate every sample with the same arithmetic.
-// Before that, the kernel does the bookkeeping of the step kernel that follows it:
-// it zeroes that kernel's candidate counter and ray-bound bits and the next pass's
-// work counter, and writes the ghost copies of the step's input populations (work
-// that overlaps the rays instead of taking a launch of its own).
-constexpr int NC_THREADS = 256, NC_WARPS = NC_THREADS / 32, NC_CHUNK = 8;
-
-template <class St>
-__global__ void __launch_bounds__(NC_THREADS) nc_list_kernel(const StepParams p) {
-    __shared__ float vals[NC_WARPS][NC_CHUNK][32];   // [sample of the round][ray]
-    __shared__ int rx[NC_WARPS][32], ry[NC_WARPS][32], rz[NC_WARPS][32], rs[NC_WARPS][32];
-    __shared__ int pre[NC_WARPS][33];
-    __shared__ float rnx[NC_WARPS][32], rny[NC_WARPS][32], rnz[NC_WARPS][32];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gthreads = (long long)gridDim.x * blockDim.x;
-    grid_dep_wait();
-    if (gtid == 0) {
-        if (p.cand_clear) *p.cand_clear = 0;
-        if (p.nc_next_clear) *p.nc_next_clear = 0;
-    }
-    if (p.nc_pos_out) {
-        const long long words = (long long)p.nbw * p.nby * p.nbz;
-        for (long long i = gtid; i < words; i += gthreads) p.nc_pos_out[i] = 0u;
-    }
-    if (p.ghost_f) {
-        const long long total = ghost_work(p);
-        const long long nw = gthreads >> 5;
-        for (long long t = gtid >> 5; t < total; t += nw)
-            ghost_task<St>(static_cast<typename St::T*>(p.ghost_f), p, t, lane);
-    }
-    const int cnt = *p.nc_count;
-    const int plane = p.nx * p.ny;
-    for (;;) {
-        int chunk = 0;
-        if (lane == 0) chunk = atomicAdd(p.nc_next, 1);
-        const int k0 = __shfl_sync(0xffffffffu, chunk, 0) * 32;
-        if (k0 >= cnt) break;
-        const int k = k0 + lane;
-        int node = 0, x = 0, y = 0, z = 0, s_last = -1;
-        float nx_ = 0.f, ny_ = 0.f, nz_ = 0.f;
-        bool valid = false;
-        if (k < cnt) {
-            const int4 c = p.nc_list[k];
-            node = c.x;
-            z = node / plane;
-            const int rem = node - z * plane;
-            y = rem / p.nx;
-            x = rem - y * p.nx;
-            valid = nc_ray(__int_as_float(c.y), __int_as_float(c.z), __int_as_float(c.w), nx_,
-                           ny_, nz_);
-            if (valid) s_last = nc_last_sample(p, x, y, z, nx_, ny_, nz_);
-        }
-        rx[wib][lane] = x;
-        ry[wib][lane] = y;
-        rz[wib][lane] = z;
-        rnx[wib][lane] = nx_;
-        rny[wib][lane] = ny_;
-        rnz[wib][lane] = nz_;
-        NcMarch mr;
-        float a = 0.0f;
-        int s0 = 0;                      // next sample of this lane's ray
-        bool active = s_last >= 0;
-        if (__popc(__ballot_sync(0xffffffffu, active)) >= 16) {
-            // most rays of the warp need samples (a fine mixture): each lane marches
-            // its own ray, keeping the cell corners while the ray stays in one cell
-            if (active) {
-                RayCell cell;
-                float v[8];
-                int key = -1;
-                for (int s = 0; s <= s_last; ++s) {
-                    const float t = -1.0f + 0.5f * (float)s;
-                    ray_cell(p, x, y, z, t * nx_, t * ny_, t * nz_, cell);
-                    const int kk = cell.r00 + cell.ix0;   // corner (ix0, iy0, iz0)
-                    if (kk != key) {
-                        ray_corners(p, cell, v);
-                        key = kk;
-                    }
-                    if (mr.feed(p, t, ray_interp(cell, v), a)) break;
-                }
-            }
-            active = false;
-        }
-        while (__any_sync(0xffffffffu, active)) {
-            const int my = active ? min(NC_CHUNK, s_last + 1 - s0) : 0;
-            // exclusive prefix of the sample counts over the warp
-            int incl = my;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            pre[wib][lane + 1] = incl;
-            if (lane == 0) pre[wib][0] = 0;
-            rs[wib][lane] = s0;
-            __syncwarp();
-            for (int task = lane; task < total; task += 32) {
-                // ray r: pre[r] <= task < pre[r + 1]
-                int lo = 0, hi = 31;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (pre[wib][mid] <= task) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int r = lo, j = task - pre[wib][r];
-                const float t = -1.0f + 0.5f * (float)(rs[wib][r] + j);
-                // inside the fluid: established in phase 1
-                vals[wib][j][r] = ray_sample(p, rx[wib][r], ry[wib][r], rz[wib][r],
-                                             t * rnx[wib][r], t * rny[wib][r], t * rnz[wib][r]);
-            }
-            __syncwarp();
-            if (active) {
-                for (int j = 0; j < my; ++j) {
-                    if (mr.feed(p, -1.0f + 0.5f * (float)(s0 + j), vals[wib][j][lane], a)) {
-                        active = false;
-                        break;
-                    }
-                }
-                s0 += my;
-                if (s0 > s_last) active = false;
-            }
-            __syncwarp();
-        }
-        if (valid) {
-            if (p.pin_d2) {
-                const unsigned d2 = __ldg(p.pin_d2 + node);
-                if (d2 != 255u) a += A_h(p, sqrtf((float)d2));
-            }
-            if (a != 0.0f) p.ah[node] = a;
-        }
-        __syncwarp();
-    }
-    grid_dep_launch();
 }
 
 // ---------------------------------------------------------------- near-contact pass, block form
@@ -1289,8 +1148,8 @@ __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int
     }
     c.o = (cz0 * G::SY + cy0) * G::SX + cx0;
 }
-// Block of the bit table holding the cell of a ray sample (the corner cube_cell
-// finds, halved per axis).
+// Whether the block of the bit table holding the cell of a ray sample (the corner
+// cube_cell finds, halved per axis) is marked.
 template <int H>
 __device__ __forceinline__ bool cube_sample_marked(const StepParams& p, const uint32_t* tab, int y,
                                                    int z, int y0, int z0, int lx, int ly, int lz,
@@ -1399,6 +1258,54 @@ __device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtenso
     cp_async_commit();
 }
 
+// One ray of the block pass: node, direction, bound and crossing search, with the
+// corners of its current cell (kept while the ray stays in that cell).
+struct NcRay {
+    int lx, ly, lz, x, y, z, s_last, key;
+    float nx_, ny_, nz_, a;
+    float v[8];
+    NcMarch mr;
+    template <int H>
+    __device__ __forceinline__ void start(const StepParams& p, const float* cube, int e, int x0,
+                                          int y0, int z0) {
+        const int idx = e & 0xffff;
+        s_last = e >> 16;
+        lx = idx % NB_X;
+        ly = (idx / NB_X) % NB_Y;
+        lz = idx / (NB_X * NB_Y);
+        x = x0 + lx;
+        y = y0 + ly;
+        z = z0 + lz;
+        float Gx, Gy, Gz;
+        cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
+        nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
+        a = 0.0f;
+        key = -1;
+    }
+    // Sample s; false once A_h is decided or the bound is passed.
+    template <int H>
+    __device__ __forceinline__ bool advance(const StepParams& p, const float* cube, int y0, int z0,
+                                            int s) {
+        if (s > s_last) return false;
+        const float t = -1.0f + 0.5f * (float)s;
+        CubeCell cell;
+        cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, t * nx_, t * ny_, t * nz_, cell);
+        if (cell.o != key) {
+            cube_corners<H>(cube, cell, v);
+            key = cell.o;
+        }
+        return !mr.feed(p, t, cube_interp(cell, v), a);
+    }
+    __device__ __forceinline__ void finish(const StepParams& p, size_t plane) {
+        const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
+        if (p.pin_d2) {
+            const unsigned d2 = __ldg(p.pin_d2 + node);
+            if (d2 != 255u) a += A_h(p, sqrtf((float)d2));
+        }
+        p.ah[node] = a;
+    }
+};
+
 template <class St, int H>
 __global__ void __launch_bounds__(NB_THREADS, 1)
 nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
@@ -1411,9 +1318,10 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
     uint32_t* tab = reinterpret_cast<uint32_t*>(q + 4 * sizeof(unsigned long long));  // [TBZ][TBY]
     int* rays = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tab) + G::TAB_BYTES);
     uint32_t* rowbits = reinterpret_cast<uint32_t*>(rays);                 // [SZ][SY], then the list
+    // (rays: {node | s_last << 16}, sorted by s_last)
     int* bins = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(rays) + G::LIST_BYTES);
     int* cursor = bins + NB_BINS;                                          // [NB_BINS] scatter
-    unsigned char* slast = reinterpret_cast<unsigned char*>(cursor + NB_BINS);   // s_last + 1
+    unsigned char* slast = reinterpret_cast<unsigned char*>(cursor + NB_BINS);   // [NB_NODES] s_last + 1
     const int tid = threadIdx.x, lane = tid & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
@@ -1424,11 +1332,6 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
     }
     __syncthreads();
     grid_dep_wait();
-    if (gtid == 0 && p.cand_clear) *p.cand_clear = 0;
-    if (p.nc_pos_out) {
-        const long long words = (long long)p.nbw * p.nby * p.nbz;
-        for (long long i = gtid; i < words; i += gthreads) p.nc_pos_out[i] = 0u;
-    }
     if (p.ghost_f) {
         const long long total = ghost_work(p);
         for (long long t = gtid >> 5; t < total; t += gthreads >> 5)
@@ -1563,34 +1466,14 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
             }
         }
         __syncthreads();
-        // ---- 3. the listed rays, one per thread, corners from the cube
+        // ---- 3. the listed rays, one per thread, corners from the cube (kept while a ray
+        // stays in one cell)
         for (int k = tid; k < nr; k += NB_THREADS) {
-            const int e = rays[k];
-            const int idx = e & 0xffff, s_last = e >> 16;
-            const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
-            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            float Gx, Gy, Gz, nx_, ny_, nz_;
-            cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
-            nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
-            NcMarch mr;
-            float a = 0.0f, v[8];
-            CubeCell cell;
-            int key = -1;
-            for (int s = 0; s <= s_last; ++s) {
-                const float t = -1.0f + 0.5f * (float)s;
-                cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, t * nx_, t * ny_, t * nz_, cell);
-                if (cell.o != key) {
-                    cube_corners<H>(cube, cell, v);
-                    key = cell.o;
-                }
-                if (mr.feed(p, t, cube_interp(cell, v), a)) break;
+            NcRay r;
+            r.start<H>(p, cube, rays[k], x0, y0, z0);
+            for (int s = 0; r.advance<H>(p, cube, y0, z0, s); ++s) {
             }
-            const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
-            if (p.pin_d2) {
-                const unsigned d2 = __ldg(p.pin_d2 + node);
-                if (d2 != 255u) a += A_h(p, sqrtf((float)d2));
-            }
-            p.ah[node] = a;
+            r.finish(p, plane);
         }
         __syncthreads();   // the cube, table and ray list are consumed
     }
@@ -1603,77 +1486,6 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
     }
     cp_async_wait<0>();
     grid_dep_launch();
-}
-
-// Scan mode (after the state was set): ah = 0 everywhere, and every node whose
-// lagged gradient may reach the threshold is appended, with that gradient, to the
-// list the list kernel then works on.
-__global__ void nc_scan_kernel(const StepParams p, int4* list, int* count) {
-    const int lane = threadIdx.x & 31;
-    const int N = (int)p.N;
-    const int plane = p.nx * p.ny;
-    const int stride = gridDim.x * blockDim.x;
-    // uniform trip count over the warp, for the ballot
-    for (int base = blockIdx.x * blockDim.x; base < N; base += stride) {
-        const int n = base + (int)threadIdx.x;
-        bool cand = false;
-        float Gx = 0.f, Gy = 0.f, Gz = 0.f;
-        if (n < N) {
-            const int z = n / plane;
-            const int rem = n - z * plane;
-            const int y = rem / p.nx, x = rem - y * p.nx;
-            gradient_global(p, p.phi_lag, x, y, z, Gx, Gy, Gz);
-            cand = Gx * Gx + Gy * Gy + Gz * Gz >= 0.81e-6f;
-            p.ah[n] = 0.0f;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, cand);
-        int b = 0;
-        if (lane == 0 && m) b = atomicAdd(count, __popc(m));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (cand)
-            list[b + __popc(m & ((1u << lane) - 1u))] =
-                make_int4(n, __float_as_int(Gx), __float_as_int(Gy), __float_as_int(Gz));
-    }
-}
-
-// Block bit field of the ray bound: one warp per 32 consecutive x-blocks (one
-// word); a block is marked when one of the nodes 2b .. 2b+2 per axis (wrapped on
-// periodic axes, clipped at walls) has phi_lag > kPosBand. For each of the 3 x 3
-// rows a lane loads the two nodes 2b, 2b+1 of its block (coalesced over the warp)
-// and takes node 2b+2 from the next lane.
-__global__ void nc_pos_kernel(const StepParams p) {
-    const int lane = threadIdx.x & 31;
-    const int words = p.nbw * p.nby * p.nbz;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < words; w += wstride) {
-        const int wx = w % p.nbw;
-        const int by = (w / p.nbw) % p.nby;
-        const int bz = w / (p.nbw * p.nby);
-        const int bx = wx * 32 + lane;
-        const int xa = (2 * bx) % p.nx, xb = (2 * bx + 1) % p.nx, xe = (64 * wx + 64) % p.nx;
-        // all 3 x 3 rows are loaded before any is reduced, so the loads overlap
-        float a[9], b[9], e[9];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            int z = 2 * bz + r / 3, y = 2 * by + r % 3;
-            const bool zin = z < p.nz || !p.wall_z, yin = y < p.ny || !p.wall_y;
-            z = z < p.nz ? z : (z - p.nz) % p.nz;
-            y = y < p.ny ? y : (y - p.ny) % p.ny;
-            const float* row = p.phi_lag + ((size_t)z * p.ny + y) * p.nx;
-            a[r] = zin && yin ? __ldg(row + xa) : -1.0f;
-            b[r] = zin && yin ? __ldg(row + xb) : -1.0f;
-            e[r] = zin && yin && lane == 31 ? __ldg(row + xe) : -1.0f;
-        }
-        float m = -1.0f;   // max over the block's nodes
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            float c = __shfl_down_sync(0xffffffffu, a[r], 1);
-            if (lane == 31) c = e[r];
-            m = fmaxf(m, fmaxf(a[r], fmaxf(b[r], c)));
-        }
-        const unsigned bits = __ballot_sync(0xffffffffu, bx < p.nbx && m > kPosBand);
-        if (lane == 0) p.nc_pos[w] = bits;
-    }
 }
 
 // Launch with programmatic stream serialisation (see grid_dep_wait). (The list and
@@ -1693,55 +1505,6 @@ static cudaError_t pdl_launch(void (*kernel)(KArgs...), unsigned grid, unsigned 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
-// The bit field of p.phi_lag into p.nc_pos, on its own (scan mode, self-checks).
-cudaError_t launch_nc_pos(const StepParams& p, int num_sms, cudaStream_t s) {
-    const long long words = (long long)p.nbw * p.nby * p.nbz;
-    long long g = (words + NC_WARPS - 1) / NC_WARPS;
-    if (g > (long long)num_sms * 16) g = (long long)num_sms * 16;
-    nc_pos_kernel<<<(unsigned)g, NC_THREADS, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-// The near-contact pass. Scan mode (p.nc_list == null, after a change of state):
-// the bit field of the lag field, then the candidate compaction into scan_list /
-// scan_count. Then the list kernel, on as many CTAs as are resident at once (the
-// warps fetch their work from the counter p.nc_next).
-template <class St>
-static cudaError_t launch_list(const StepParams& p, int num_sms, cudaStream_t s) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_list_kernel<St>,
-                                                                      NC_THREADS, 0);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
-    return pdl_launch(nc_list_kernel<St>, (unsigned)(num_sms * per_sm), NC_THREADS, 0, s, p);
-}
-
-cudaError_t launch_nc(const StepParams& p_in, int4* scan_list, int* scan_count, int storage,
-                      int num_sms, cudaStream_t s) {
-    StepParams p = p_in;
-    if (!p.nc_list) {
-        cudaError_t e = launch_nc_pos(p, num_sms, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scan_count, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p.nc_next, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
-        long long gs = ((long long)p.N + NC_THREADS - 1) / NC_THREADS;
-        if (gs > (long long)num_sms * 8) gs = (long long)num_sms * 8;
-        nc_scan_kernel<<<(unsigned)gs, NC_THREADS, 0, s>>>(p, scan_list, scan_count);
-        p.nc_list = scan_list;
-        p.nc_count = scan_count;
-    }
-    // (the list kernel touches populations only in the ghost fill, which depends on
-    // the element type alone: the reduced form shares the FP32 instance)
-    switch (storage) {
-        case 0: case 3: return launch_list<StoreF32>(p, num_sms, s);
-        case 1: return launch_list<StoreF16>(p, num_sms, s);
-        case 2: return launch_list<StoreBF16>(p, num_sms, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 template <class St, int H>
@@ -1778,7 +1541,7 @@ cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, boo
     // element type alone: the reduced form shares the FP32 instance)
     switch (storage) {
         case 0: case 3: return launch_block_st<StoreF32>(p, lag_map, tma_ok, num_sms, s);
-        case 1: return launch_block_st<StoreF16>(p, lag_map, tma_ok, num_sms, s);
+        case 1: case 4: return launch_block_st<StoreF16>(p, lag_map, tma_ok, num_sms, s);
         case 2: return launch_block_st<StoreBF16>(p, lag_map, tma_ok, num_sms, s);
     }
     return cudaErrorInvalidValue;
@@ -1834,6 +1597,7 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
         case 1: return launch_tpl<StoreF16>(p, map, omap, grid, s);
         case 2: return launch_tpl<StoreBF16>(p, map, omap, grid, s);
         case 3: return launch_tpl<StoreQ5>(p, map, omap, grid, s);
+        case 4: return launch_tpl<StoreQ5H>(p, map, omap, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1851,7 +1615,7 @@ static cudaError_t prepare_batched_tpl() {
 }
 
 // Batched kernel of one (storage, relaxation class, model): dispatched over the
-// 14 combinations (the reduced form holds no Shan-Chen state) with a callable that
+// 16 combinations (the reduced forms hold no Shan-Chen state) with a callable that
 // takes the three as template arguments.
 template <class F>
 static cudaError_t batched_dispatch(int storage, bool unit_omega, int model, F&& fn) {
@@ -1871,6 +1635,8 @@ static cudaError_t batched_dispatch(int storage, bool unit_omega, int model, F&&
         case 11: return fn.template operator()<StoreBF16, true, true>();
         case 12: return fn.template operator()<StoreQ5, false, false>();
         case 14: return fn.template operator()<StoreQ5, true, false>();
+        case 16: return fn.template operator()<StoreQ5H, false, false>();
+        case 18: return fn.template operator()<StoreQ5H, true, false>();
     }
     return cudaErrorInvalidValue;
 }
@@ -1907,7 +1673,7 @@ cudaError_t launch_ghost_batched(const BatchLattice* tab, int nlat, long long ce
     if (blocks < 1) blocks = 1;
     switch (storage) {
         case 0: case 3: ghost_fill_batched<StoreF32><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
-        case 1: ghost_fill_batched<StoreF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
+        case 1: case 4: ghost_fill_batched<StoreF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
         case 2: ghost_fill_batched<StoreBF16><<<(unsigned)blocks, 256, 0, s>>>(tab, nlat, cells); break;
         default: return cudaErrorInvalidValue;
     }
@@ -1934,7 +1700,7 @@ cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num
     if (blocks > cap) blocks = cap;
     switch (storage) {
         case 0: case 3: return launch_ghost_tpl<StoreF32>(f, p, (unsigned)blocks, threads, s);
-        case 1: return launch_ghost_tpl<StoreF16>(f, p, (unsigned)blocks, threads, s);
+        case 1: case 4: return launch_ghost_tpl<StoreF16>(f, p, (unsigned)blocks, threads, s);
         case 2: return launch_ghost_tpl<StoreBF16>(f, p, (unsigned)blocks, threads, s);
     }
     return cudaErrorInvalidValue;

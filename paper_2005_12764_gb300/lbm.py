@@ -19,7 +19,7 @@ import numpy as np
 from . import build_lib
 
 Q = 19
-STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp32_q5": 3}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp32_q5": 3, "fp16_q5": 4}
 MODELS = {"colour": 0, "shan_chen": 1}
 _STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_ESTATE",
            -5: "LBM_ETIMEOUT"}
@@ -31,7 +31,8 @@ SYMBOLS = ["lbm_velocity_set", "lbm_create", "lbm_set_fields", "lbm_set_pin_mask
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_sync",
            "lbm_footprint_bytes", "lbm_work_split", "lbm_steps_taken", "lbm_destroy",
            "lbm_last_error",
-           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_nc_bound_check", "lbm_get_window",
+           "lbm_totals_noalloc", "lbm_get_nc_field", "lbm_get_window",
+           "lbm_planes_bytes", "lbm_get_planes", "lbm_set_planes",
            "lbm_droplets", "lbm_structure_factor", "lbm_selftest_timeout",
            "lbm_engine_create", "lbm_engine_submit", "lbm_engine_tick", "lbm_engine_state",
            "lbm_engine_result", "lbm_engine_stats", "lbm_engine_destroy", "lbm_engine_cancel",
@@ -107,7 +108,9 @@ def load():
             "lbm_last_error": (C.c_char_p, [_P]),
             "lbm_totals_noalloc": (C.c_int, [_D, C.c_longlong, _D, C.c_void_p]),
             "lbm_get_nc_field": (C.c_int, [_P, _D, C.c_int]),
-            "lbm_nc_bound_check": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+            "lbm_planes_bytes": (C.c_size_t, [_P, C.c_int]),
+            "lbm_get_planes": (C.c_int, [_P, C.c_int, C.c_int, _D]),
+            "lbm_set_planes": (C.c_int, [_P, C.c_int, C.c_int, _D]),
             "lbm_droplets": (C.c_int, [_P, C.POINTER(C.c_longlong), _D, C.c_longlong]),
             "lbm_selftest_timeout": (C.c_int, [_P]),
             "lbm_structure_factor": (C.c_int, [_P, C.c_int, _D, _D, _D]),
@@ -327,12 +330,20 @@ class Lattice:
         self._check(self._lib.lbm_get_nc_field(self._h, ah.ctypes.data, 0))
         return ah
 
-    def nc_bound_check(self):
-        """(differing words, words) between the step kernel's near-contact ray-bound
-        bit field and one recomputed from the current colour field."""
-        out = (C.c_longlong * 2)()
-        self._check(self._lib.lbm_nc_bound_check(self._h, out))
-        return int(out[0]), int(out[1])
+    def planes_bytes(self, h):
+        """Bytes of h z-planes of the stored state (populations as stored, lagged colour
+        field)."""
+        return int(self._lib.lbm_planes_bytes(self._h, int(h)))
+
+    def get_planes(self, z0, h, buf):
+        """Planes z0 .. z0+h-1 of the stored state into buf (a CUDA uint8 tensor of
+        planes_bytes(h) bytes); queued on the lattice's stream."""
+        assert _is_torch(buf) and buf.is_cuda and buf.numel() * buf.element_size() >= self.planes_bytes(h)
+        self._check(self._lib.lbm_get_planes(self._h, int(z0), int(h), buf.data_ptr()))
+
+    def set_planes(self, z0, h, buf):
+        assert _is_torch(buf) and buf.is_cuda and buf.numel() * buf.element_size() >= self.planes_bytes(h)
+        self._check(self._lib.lbm_set_planes(self._h, int(z0), int(h), buf.data_ptr()))
 
     def selftest_timeout(self) -> int:
         """Status of the bounded-wait self-test: LBM_ETIMEOUT (-5) when a wait that

@@ -18,6 +18,7 @@ def test_byte_models():
     assert bench.bytes_per_node("fp32") == 2 * 19 * 2 * 4 == 304
     assert bench.bytes_per_node("fp16") == bench.bytes_per_node("bf16") == 152
     assert bench.bytes_per_node("fp32_q5") == 2 * (19 + 5) * 4 == 192
+    assert bench.bytes_per_node("fp16_q5") == 2 * (19 * 2 + 5 * 4) == 116
 
 
 def test_traffic_lookup_is_keyed_by_the_kernel_sources():

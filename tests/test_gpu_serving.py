@@ -41,7 +41,7 @@ def _run_alone(lbm, serving, req, storage):
     return out
 
 
-@pytest.mark.parametrize("storage", ["fp16", "fp32", "fp32_q5"])
+@pytest.mark.parametrize("storage", ["fp16", "fp32", "fp32_q5", "fp16_q5"])
 def test_result_is_the_same_alone_in_the_mix_and_by_lbm_step(lbm, storage):
     from paper_2005_12764_gb300 import serving
     alone = {r["id"]: _run_alone(lbm, serving, r, storage) for r in REQS}

@@ -94,6 +94,7 @@ def test_invalid_arguments_are_refused():
 
 @pytest.mark.parametrize("bad", [
     dict(storage=7), dict(storage="fp32_q5", model="shan_chen", G_sc=1.2),
+    dict(storage="fp16_q5", model="shan_chen", G_sc=1.2), dict(storage="fp16_q5", rho0=0.0),
     dict(model="shan_chen", A_nc=0.01), dict(wall_u=0.01), dict(wall_y=1, wall_u=0.5),
     dict(beta=1.5), dict(sigma=-1.0), dict(A_nc=0.01, h_min=0.0), dict(A_nc=0.01, h_cut=12.0),
     dict(storage="fp16", rho0=0.0),
