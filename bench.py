@@ -365,14 +365,15 @@ def timed_steps(lat, stream, steps, min_total_s=1.0, max_reps=20):
     return reps
 
 
-def device_resident(lbm, w, storage, steps, warmup, stream, local, pins=None):
+def device_resident(lbm, w, storage, steps, warmup, stream, local, pins=None, inplace=0):
     """GLUPS of `steps` steps queued back to back (median repeat), the mean step-kernel
-    and near-contact pass times (ms, the library's own events), and the lattice's
+    and near-contact pass times (ms, the library's own events; in place, the step
+    kernel time covers the colour-field and collide passes), and the lattice's
     species-mass drift over the run."""
     import torch
     nz, ny, nx = w.shape
     lat = lbm.Lattice(lbm.make_params(nx, ny, nz, storage=storage, stream=stream.cuda_stream,
-                                      **w.params))
+                                      inplace=inplace, **w.params))
     lat.set_fields(torch.from_numpy(w.rho_r).to(f"cuda:{local}"),
                    torch.from_numpy(w.rho_b).to(f"cuda:{local}"))
     if pins is not None:
@@ -440,6 +441,18 @@ def other_workloads(lbm, stream, local, key, steps=20, warmup=5):
               "roofline_frac": frac(d["kernel_ms"], n),
               "near_contact_share": d["near_contact_pass_ms"] / d["ms_per_step"]})
     out["gel_640"] = d
+    # the same quench with FP16 deviation storage, two copies (39.8 GB) and in place
+    # (one copy, 19.9 GB: two passes per step, the populations read twice)
+    for tag, inplace in (("gel_640_fp16", 0), ("gel_640_fp16_inplace", 1)):
+        d = device_resident(lbm, g, "fp16", steps, warmup, stream, local, pins=g.pins,
+                            inplace=inplace)
+        d.update({"workload": "bicontinuous gel quench 640^3 as above, FP16 deviation storage"
+                              + (", in place (one population copy)" if inplace else ""),
+                  "unit": "GLUPS", "nodes": n,
+                  "roofline_frac": frac(d["kernel_ms"], n, "fp16"),
+                  "pass_bytes_per_node": bytes_per_node("fp16") * (3 if inplace else 2) // 2,
+                  "near_contact_share": d["near_contact_pass_ms"] / d["ms_per_step"]})
+        out[tag] = d
     del g
     if key != "channel":
         w = inputs.channel_droplets()

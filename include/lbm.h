@@ -127,6 +127,14 @@ typedef struct {
     double G_sc;             /* Shan-Chen coupling G_C, > 0 repulsive (Shan-Chen model)    */
     int storage;             /* lbm_storage                                               */
     void* cuda_stream;       /* cudaStream_t to run on, or NULL                           */
+    int inplace;             /* 1 = one population copy, updated in place (AA pattern):
+                                even steps leave a node's post-collision populations at
+                                the node with opposite directions, odd steps at the
+                                downstream neighbours; two passes per step (colour field,
+                                then stream-collide-push), 2/3 of the two-copy memory.
+                                Colour model, storage FP32/FP16/BF16, no sliding walls;
+                                lbm_get_planes/lbm_set_planes and the engine refuse it.
+                                0 = two copies (default).                                */
 } lbm_params;
 
 /* Number of directions and the velocity set used by lbm_get_pops/lbm_set_pops:

@@ -53,6 +53,9 @@ __device__ __forceinline__ size_t node_pidx(const StepParams& sp, size_t n) {
 }
 
 // f_i^k = f_i^eq(rho_k, u), Eq. (2); both colour-field buffers get phi.
+// Direction block a state write of f*_i of a node goes to, at the node's own padded
+// index: i for the two-copy storage; opp(i) (layout 0) with in-place storage.
+__device__ inline int wdir(const StepParams& sp, int i) { return sp.aa_layout < 0 ? i : opp(i); }
 template <class St>
 __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
                                    const double* rho_r, const double* rho_b, const double* u,
@@ -81,8 +84,9 @@ __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
                           St::tot_ref(i, 2.0f * ref_half));
             } else {
                 const float hw = wgt(i) * ref_half;
-                St::store(f, (size_t)i * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
-                St::store(f, (size_t)(Q + i) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
+                const int d = wdir(sp, i);
+                St::store(f, (size_t)d * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
+                St::store(f, (size_t)(Q + d) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
             }
         }
         if constexpr (St::RED) {
@@ -121,6 +125,25 @@ __device__ inline void ldpair(const typename St::T* f, size_t P, size_t q, int i
         b = ldpop<St>(f, (size_t)(Q + i) * P + q, i, 1, ref_half, ph);
     }
 }
+// Both species' populations f*_i of node n (padded index q) of the state: ldpair for
+// the two-copy storage; with in-place storage from the slots the state's layout puts
+// them in (aa_slot).
+template <class St>
+__device__ inline void ldnode(const typename St::T* f, const StepParams& sp, size_t n, size_t q,
+                              int i, float ph, float& a, float& b) {
+    if (sp.aa_layout < 0) {
+        ldpair<St>(f, sp.P, q, i, sp.ref_half, ph, a, b);
+        return;
+    }
+    const size_t plane = (size_t)sp.nx * sp.ny;
+    const int z = (int)(n / plane);
+    const int rem = (int)(n - (size_t)z * plane);
+    const int y = rem / sp.nx, x = rem - y * sp.nx;
+    int dir;
+    const size_t idx = aa_slot(sp, sp.aa_layout, i, x, y, z, dir);
+    a = ldpop<St>(f, (size_t)dir * sp.P + idx, i, 0, sp.ref_half, ph);
+    b = ldpop<St>(f, (size_t)(Q + dir) * sp.P + idx, i, 1, sp.ref_half, ph);
+}
 // Current colour field of node n as the deviation references need it (0 otherwise).
 template <class St>
 __device__ inline float ref_phi(const float* phi_cur, size_t n) {
@@ -144,7 +167,7 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
+            ldnode<St>(f, sp, n, q, i, ph, a, b);
             rr += a;
             rb += b;
             jx += cx(i) * (a + b);
@@ -205,7 +228,7 @@ __global__ void densities_kernel(const typename St::T* f, StepParams sp, const f
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
+            ldnode<St>(f, sp, n, q, i, ph, a, b);
             rr += a;
             rb += b;
         }
@@ -225,7 +248,7 @@ __global__ void pops_to_f64_kernel(const typename St::T* f, StepParams sp, const
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            ldpair<St>(f, P, q, i, sp.ref_half, ph, a, b);
+            ldnode<St>(f, sp, n, q, i, ph, a, b);
             fr[(size_t)i * N + n] = a;
             fb[(size_t)i * N + n] = b;
         }
@@ -249,7 +272,7 @@ __global__ void window_kernel(const typename St::T* f, StepParams sp, const floa
 #pragma unroll
         for (int d = 0; d < Q; ++d) {
             float a, b;
-            ldpair<St>(f, P, q, d, sp.ref_half, ph, a, b);
+            ldnode<St>(f, sp, n, q, d, ph, a, b);
             out[(size_t)d * M + m] = a;
             out[(size_t)(Q + d) * M + m] = b;
         }
@@ -296,8 +319,9 @@ __global__ void f64_to_pops_kernel(typename St::T* f, StepParams sp, const float
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float hw = wgt(i) * sp.ref_half;
-                St::store(f, (size_t)i * P + q, (float)fr[(size_t)i * N + n], dev_ref(hw, ph, 0));
-                St::store(f, (size_t)(Q + i) * P + q, (float)fb[(size_t)i * N + n], dev_ref(hw, ph, 1));
+                const int d = wdir(sp, i);
+                St::store(f, (size_t)d * P + q, (float)fr[(size_t)i * N + n], dev_ref(hw, ph, 0));
+                St::store(f, (size_t)(Q + d) * P + q, (float)fb[(size_t)i * N + n], dev_ref(hw, ph, 1));
             }
         }
     }
@@ -360,7 +384,7 @@ __global__ void totals_kernel(const typename St::T* f, StepParams sp, const floa
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float af, bf;
-            ldpair<St>(f, P, q, i, ref_half, ph, af, bf);
+            ldnode<St>(f, sp, n, q, i, ph, af, bf);
             const double a = af, b = bf;
             v[0] += a;
             v[1] += b;
@@ -387,7 +411,7 @@ __global__ void volume_kernel(const typename St::T* f, StepParams sp, const floa
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            ldpair<St>(f, P, q, i, ref_half, ph, a, b);
+            ldnode<St>(f, sp, n, q, i, ph, a, b);
             rr += a;
             rb += b;
         }
@@ -423,7 +447,7 @@ __global__ void pressure_kernel(const typename St::T* f, lbm_params p, StepParam
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float a, b;
-                ldpair<St>(f, P, q, i, ref_half, ph, a, b);
+                ldnode<St>(f, sp, n, q, i, ph, a, b);
                 rho += (double)a + (double)b;
             }
             if (r < R - 3.0) {
@@ -527,17 +551,24 @@ static lbm_status validate(const lbm_params* p, std::string& why) {
     if ((p->storage == 1 || p->storage == 2 || p->storage == 4) && !(p->rho0 > 0.0)) { why = "rho0 must be > 0 for deviation storage"; return LBM_EINVAL; }
     if (p->wall_y && p->ny < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
     if (p->wall_z && p->nz < 2 && p->A_nc > 0) { why = "walled axis needs >= 2 nodes with A_nc"; return LBM_EINVAL; }
+    if (p->inplace != 0 && p->inplace != 1) { why = "inplace must be 0 or 1"; return LBM_EINVAL; }
+    if (p->inplace && (p->model != 0 || p->storage > 2 || p->wall_u != 0.0)) {
+        why = "in-place storage: colour-gradient model, full storage forms, walls at rest";
+        return LBM_EINVAL;
+    }
+    if (p->inplace && pad_layout(*p).P >= ((size_t)1 << 31)) {
+        why = "in-place storage indexes a padded population block in 31 bits";
+        return LBM_EINVAL;
+    }
     return LBM_OK;
 }
-
-// Bytes of the near-contact ray-bound bit field (one bit per 2x2x2 block, rows of
-// 32-bit words along x).
 
 extern "C" size_t lbm_footprint_bytes(const lbm_params* p) {
     if (!p) return 0;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     const PadLayout L = pad_layout(*p);
-    size_t b = 2 * (size_t)stored_blocks(p->storage) * L.P * elem_bytes(p->storage) +
+    const size_t copies = p->inplace ? 1 : 2;
+    size_t b = copies * (size_t)stored_blocks(p->storage) * L.P * elem_bytes(p->storage) +
                2 * N * sizeof(float) + p->ny * sizeof(float);
     if (p->A_nc > 0.0) b += N * sizeof(float);   // the near-contact strength A_h
     return b;
@@ -661,6 +692,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.tiles_x = (p.nx + tx - 1) / tx;
     s.tiles_y = (p.ny + ty - 1) / ty;
     s.err = c->err_word;
+    s.aa_layout = c->aa ? c->layout : -1;
     s.ah = c->ah;
     const WorkSplit w = work_split(p, c->num_sms);
     s.zparts = w.zparts;
@@ -697,6 +729,19 @@ void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* ou
     out->p = s;
     out->fout = c->f[1 - cur];
 }
+void nc_params_ahead(const lbm_ctx* c, int ahead, NcBatchLattice* out) {
+    const int cur = c->cur ^ (ahead & 1), pc = c->pc ^ (ahead & 1);
+    StepParams s = c->sp;
+    s.fin = c->f[cur];
+    s.fout = c->f[1 - cur];
+    s.phi_lag = c->phi[pc];
+    s.phi_out = c->phi[1 - pc];
+    s.ghost_f = ghost_cells(s) > 0 ? c->f[cur] : nullptr;
+    out->lag_map = c->phimap[pc];
+    out->tma_ok = c->phimap_ok ? 1 : 0;
+    out->p = s;
+}
+double ctx_h_cut(const lbm_ctx* c) { return c->p.h_cut > 0 ? c->p.h_cut : 2.0 * c->p.h_min; }
 void advance_state(lbm_ctx* c, long long k) {
     if (k & 1) {
         c->cur ^= 1;
@@ -737,7 +782,8 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMalloc(ptr, bytes) == cudaSuccess;
     };
-    bool ok = alloc(&c->f[0], pop_bytes) && alloc(&c->f[1], pop_bytes) &&
+    c->aa = p->inplace != 0;
+    bool ok = alloc(&c->f[0], pop_bytes) && (c->aa || alloc(&c->f[1], pop_bytes)) &&
               alloc((void**)&c->phi[0], c->N * sizeof(float)) &&
               alloc((void**)&c->phi[1], c->N * sizeof(float)) &&
               alloc((void**)&c->fx_row, p->ny * sizeof(float)) &&
@@ -796,7 +842,7 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         const cuuint64_t sdims[4] = {(cuuint64_t)(c->padx + p->nx), (cuuint64_t)(2 + p->ny),
                                      (cuuint64_t)p->nz, (cuuint64_t)stored_blocks(p->storage)};
         const cuuint32_t sbox[4] = {(cuuint32_t)step_tile_x(), (cuuint32_t)step_tile_y(), 1, 1};
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < (c->aa ? 0 : 2); ++b) {   // (in-place steps need no tensor maps)
             CUresult r = encode(&c->tmap[b], dt, 4, c->f[b], dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -910,13 +956,17 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const doub
     const int grid = grid_for(N, c->num_sms);
     c->cur = 0;
     c->pc = 0;
+    if (c->aa) {                 // in-place storage starts in the slot layout 0
+        c->layout = 0;
+        c->sp.aa_layout = 0;
+    }
     dispatch(c->p.storage, [&](auto st) {
         using St = decltype(st);
         init_fields_kernel<St><<<grid, kThreads, 0, c->stream>>>(
             (typename St::T*)c->f[0], c->phi[0], c->phi[1], dr, db, du, c->sp);
     });
     CK(c, cudaGetLastError());
-    CK(c, launch_ghost_fill(c->f[0], c->sp, c->p.storage, c->num_sms, c->stream));
+    if (!c->aa) CK(c, launch_ghost_fill(c->f[0], c->sp, c->p.storage, c->num_sms, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed
     c->steps = 0;
     c->fields_set = true;
@@ -975,6 +1025,25 @@ static cudaError_t launch_one_step(lbm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, c
     s.phi_out = c->phi[1 - c->pc];
     const bool nc = c->p.A_nc > 0.0;
     cudaError_t e = cudaSuccess;
+    if (c->aa) {
+        // in place: the pass, then the colour-field and collide passes over the one copy
+        s.fin = s.fout = c->f[0];
+        s.ghost_f = nullptr;
+        if (e0) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess && nc)
+            e = launch_nc_block(s, c->phimap[c->pc], c->phimap_ok, c->p.storage, c->num_sms,
+                                c->stream);
+        if (e == cudaSuccess && e1) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = launch_aa_step(s, c->layout, c->p.storage, c->num_sms, c->stream);
+        if (e == cudaSuccess && e2) e = cudaEventRecord(e2, c->stream);
+        if (e == cudaSuccess && e3) e = cudaEventRecord(e3, c->stream);
+        if (e != cudaSuccess) return e;
+        c->layout ^= 1;
+        c->sp.aa_layout = c->layout;
+        c->pc ^= 1;
+        c->steps++;
+        return cudaSuccess;
+    }
     if (e0) e = cudaEventRecord(e0, c->stream);
     if (nc) {
         s.ghost_f = ghost_cells(s) > 0 ? c->f[c->cur] : nullptr;
@@ -1112,7 +1181,7 @@ extern "C" lbm_status lbm_get_nc_field(lbm_ctx* c, double* ah, int on_device) {
     float* scratch = reinterpret_cast<float*>(c->stage + 6 * N);
     if (c->p.A_nc > 0.0) {
         // measured in scan mode on the current colour field (the next step's lag
-        // field) into scratch; the live A_h buffer and candidate lists are untouched
+        // field) into scratch; the live A_h buffer is untouched
         StepParams s = c->sp;
         s.phi_lag = c->phi[c->pc];
         s.ah = scratch;
@@ -1229,6 +1298,7 @@ static lbm_status planes_copy(lbm_ctx* c, int z0, int h, void* buf, bool get) {
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
     if (!buf) return fail(c, LBM_EINVAL, "buf is NULL");
     if (h < 1 || z0 < 0 || z0 + h > c->p.nz) return fail(c, LBM_EINVAL, "planes outside the lattice");
+    if (c->aa) return fail(c, LBM_EINVAL, "in-place storage keeps a node's populations in its neighbours' planes");
     const size_t plane_p = (size_t)c->pitch * c->nyp;
     const size_t seg = (size_t)h * plane_p * c->elem;   // bytes per block
     unsigned char* b = static_cast<unsigned char*>(buf);
@@ -1260,6 +1330,10 @@ extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* 
     const size_t N = c->N;
     const int grid = grid_for(N, c->num_sms);
     if (!on_device && ensure_stage(c, 2 * Q * N) != LBM_OK) return LBM_ENOMEM;
+    if (c->aa) {                 // in-place storage: the state is written in layout 0
+        c->layout = 0;
+        c->sp.aa_layout = 0;
+    }
     // the colour field first: deviation storage encodes the populations against it
     if (phi_lag) {
         const double* src = phi_lag;
@@ -1283,7 +1357,7 @@ extern "C" lbm_status lbm_set_pops(lbm_ctx* c, const double* f_r, const double* 
             (typename St::T*)c->f[c->cur], c->sp, c->phi[c->pc], dr, db);
     });
     CK(c, cudaGetLastError());
-    CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
+    if (!c->aa) CK(c, launch_ghost_fill(c->f[c->cur], c->sp, c->p.storage, c->num_sms, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
     c->fields_set = true;
     return LBM_OK;
@@ -1347,7 +1421,7 @@ extern "C" lbm_status lbm_laplace(lbm_ctx* c, const double centre[3], double out
 extern "C" size_t lbm_state_bytes(const lbm_ctx* c) {
     if (!c) return 0;
     return (size_t)stored_blocks(c->p.storage) * c->P * c->elem + 2 * c->N * sizeof(float) +
-           sizeof(long long);
+           2 * sizeof(long long);
 }
 
 extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
@@ -1360,6 +1434,8 @@ extern "C" lbm_status lbm_save_state(lbm_ctx* c, void* host_buf) {
     CK(c, cudaMemcpyAsync(b + pb + fb, c->phi[1 - c->pc], fb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     std::memcpy(b + pb + 2 * fb, &c->steps, sizeof(long long));
+    const long long layout = c->aa ? c->layout : -1;   // in-place storage: the state's layout
+    std::memcpy(b + pb + 2 * fb + sizeof(long long), &layout, sizeof(long long));
     return LBM_OK;
 }
 
@@ -1374,6 +1450,13 @@ extern "C" lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf) {
     CK(c, cudaMemcpyAsync(c->phi[1], b + pb + fb, fb, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     std::memcpy(&c->steps, b + pb + 2 * fb, sizeof(long long));
+    long long layout = -1;
+    std::memcpy(&layout, b + pb + 2 * fb + sizeof(long long), sizeof(long long));
+    if ((layout >= 0) != c->aa) return fail(c, LBM_EINVAL, "state saved with the other storage scheme");
+    if (c->aa) {
+        c->layout = (int)layout;
+        c->sp.aa_layout = c->layout;
+    }
     c->fields_set = true;
     return LBM_OK;
 }
@@ -1388,6 +1471,8 @@ extern "C" long long lbm_steps_taken(const lbm_ctx* c) { return c ? c->steps : -
 
 extern "C" int lbm_launches_per_step(const lbm_ctx* c) {
     if (!c) return 0;
+    // in place: the colour-field and collide passes, and the near-contact pass
+    if (c->aa) return c->p.A_nc > 0.0 ? 3 : 2;
     // the fused step, and the near-contact pass (which writes the ghost copies) or
     // the ghost fill
     if (c->p.A_nc > 0.0) return 2;

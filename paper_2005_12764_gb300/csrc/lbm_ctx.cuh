@@ -19,7 +19,15 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
 cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
                             int storage, int num_sms, cudaStream_t s);
 void nc_cube_box(double h_cut, int box[3]);
+cudaError_t launch_nc_batched(const NcBatchLattice* tab, int nlat, long long nblocks,
+                              long long ghost_total, int storage, double h_cut, int num_sms,
+                              cudaStream_t s);
+int nc_halo(double h_cut);
+cudaError_t prepare_nc_batched(int storage, double h_cut);
+long long nc_block_count(const StepParams& p);
 cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
+cudaError_t launch_aa_step(const StepParams& p, int layout, int storage, int num_sms,
+                           cudaStream_t s);
 cudaError_t launch_ghost_fill(void* f, const StepParams& p, int storage, int num_sms,
                               cudaStream_t s);
 int step_tile_x();
@@ -61,6 +69,8 @@ struct lbm_ctx {
     double* red_host = nullptr; // pinned host copy of reduction results
     int red_blocks = 0;
     int cur = 0;                // population copy holding the current state
+    bool aa = false;            // in-place storage: one copy, f[0]
+    int layout = 0;             // its state layout (see aa_slot)
     int pc = 0;                 // phi buffer of the last step (the other one = its lag)
     long long steps = 0;
     bool fields_set = false;
@@ -78,6 +88,10 @@ namespace lbm {
 // context's next one (0 or 1; the state alternates between two buffers), for a
 // lattice without near-contact force, with its z range cut into `zparts` parts.
 void step_params_ahead(const lbm_ctx* c, int ahead, int zparts, BatchLattice* out);
+// The same for the near-contact pass of that step (parameters with the ghost copies of
+// the step's input, tensor map of the lagged colour field).
+void nc_params_ahead(const lbm_ctx* c, int ahead, NcBatchLattice* out);
+double ctx_h_cut(const lbm_ctx* c);
 // Record that `k` steps were run on the context's buffers outside lbm_step.
 void advance_state(lbm_ctx* c, long long k);
 // LBM_ETIMEOUT if a bounded wait in a step kernel gave up (synchronises).

@@ -225,6 +225,9 @@ struct StepParams {
     int band_k, band_h;
     void* fout;             // populations after the step
     int* err;               // device error word: 1 = a bounded wait gave up
+    int aa_layout;          // in-place (AA) storage: where the state's populations are
+                            // (0 or 1, see aa_slot); -1 for the two-copy storage
+    int pad_;
 };
 
 static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
@@ -239,6 +242,18 @@ struct alignas(64) BatchLattice {
     void* fout;
     int cta_begin;
     long long ghost_begin;
+};
+
+// One lattice of a batched near-contact launch: the tensor map of its lagged colour
+// field (and whether the pass may use it), its parameters for the step (lagged field,
+// A_h, the populations whose ghost copies the pass writes), and its first block of
+// nodes and first ghost-copy task in the launch.
+struct alignas(64) NcBatchLattice {
+    CUtensorMap lag_map;
+    StepParams p;
+    long long block_begin;
+    long long ghost_begin;
+    int tma_ok;
 };
 
 // ---------------------------------------------------------------- near-contact force
@@ -265,6 +280,43 @@ __device__ __forceinline__ int wrap_near(int a, int n) {
 // Index of node (x, y, z) in one padded population block (x, y may be ghosts, -2..n+1).
 __host__ __device__ __forceinline__ size_t pidx(int pitch, int nyp, int padx, int x, int y, int z) {
     return ((size_t)z * nyp + (y + 2)) * pitch + (x + padx);
+}
+
+// ---------------------------------------------------------------- in-place (AA) storage
+// One copy of the populations, each slot read and then written by the same node in a
+// step. The state between steps (the post-collision populations f*_i(x) of the last
+// step) sits in one of two layouts, which alternate:
+//  layout 0: f*_i(x) in slot (opp(i), x), the node's own slots, reversed;
+//  layout 1: f*_i(x) in slot (i, x + c_i), streamed already, or in slot (opp(i), x)
+//            when x + c_i lies beyond a wall (the population comes back to x).
+// A step from layout 1 reads a node's post-stream populations f_i(x) from its own
+// slots (i, x) (a link from beyond a wall included) and writes f*_i(x) in layout 0; a
+// step from layout 0 reads f_i(x) = f*_i(x - c_i) from (opp(i), x - c_i) (from (i, x)
+// for a link from beyond a wall) and writes layout 1. Either way every node reads and
+// writes exactly the same slots, so nodes never race.
+// Node (x, y, z) + c_i: false if it lies beyond a wall; else its wrapped coordinates.
+__device__ __forceinline__ bool aa_neighbour(const StepParams& p, int i, int x, int y, int z,
+                                             int& xn, int& yn, int& zn) {
+    yn = y + cy(i);
+    zn = z + cz(i);
+    if ((p.wall_y && (yn < 0 || yn >= p.ny)) || (p.wall_z && (zn < 0 || zn >= p.nz))) return false;
+    xn = wrap_near(x + cx(i), p.nx);
+    yn = wrap_near(yn, p.ny);
+    zn = wrap_near(zn, p.nz);
+    return true;
+}
+// Slot (direction block `dir`, padded index) of f*_i of node (x, y, z) in `layout`.
+__device__ __forceinline__ size_t aa_slot(const StepParams& p, int layout, int i, int x, int y,
+                                          int z, int& dir) {
+    if (layout == 1) {
+        int xn, yn, zn;
+        if (aa_neighbour(p, i, x, y, z, xn, yn, zn)) {
+            dir = i;
+            return pidx(p.pitch, p.nyp, p.padx, xn, yn, zn);
+        }
+    }
+    dir = opp(i);
+    return pidx(p.pitch, p.nyp, p.padx, x, y, z);
 }
 
 // One term 3 w_i c_i v of the isotropic colour gradient (3 w_i = 1/6 for faces, 1/12

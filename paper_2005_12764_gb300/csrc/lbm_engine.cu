@@ -2,8 +2,8 @@
 // include/lbm.h): independent lattices resident on the device, admitted by device
 // memory, advanced together by batched launches of the step kernel captured in CUDA
 // graphs, retired as they finish so that queued requests take their place.
-// Lattices with the near-contact force take their own step path (the near-contact
-// pass, then the step kernel, per lattice) on the engine's stream in the same tick.
+// Lattices with the near-contact force are batched too: their group's step starts
+// with one batched launch of the near-contact pass over all of them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,21 +46,30 @@ struct Request {
     std::vector<double> out_rr, out_rb, out_u, out_phi;
 };
 
-// Lattices of one storage format, relaxation class and model: one batched launch.
+// Lattices of one storage format, relaxation class, model and near-contact class
+// (none, or the halo class of h_cut): one batched launch of the step kernel per step,
+// preceded for near-contact lattices by one batched launch of the near-contact pass
+// (which also writes the ghost copies of their step's input), followed otherwise by
+// one batched ghost-copy fill of the step's output.
 struct Group {
     int storage = 0;
     bool unit = false;
     int model = 0;
+    int nc = 0;          // 0: no near-contact force; else the halo class of the pass
+    double h_cut = 0.0;
     std::vector<Request*> members;
     BatchLattice* d_tab[2] = {nullptr, nullptr};   // tables of the next two steps
     std::vector<BatchLattice> h_tab[2];
+    NcBatchLattice* d_nc[2] = {nullptr, nullptr};  // near-contact tables of those steps
+    std::vector<NcBatchLattice> h_nc[2];
+    long long nc_blocks = 0, nc_ghost = 0;
     int ctas = 0;
     long long ghost = 0;
 };
 
-// Lattices without the near-contact force are advanced by the batched launches; the
-// others by their own context's step path.
-bool batched(const Request* r) { return !(r->p.A_nc > 0.0); }
+int nc_class(const lbm_ctx* c) {
+    return c->p.A_nc > 0.0 ? nc_halo(ctx_h_cut(c)) : 0;
+}
 
 // Device memory a resident lattice holds: its context plus the FP64 staging of the
 // host field exchanges (7 doubles per node).
@@ -98,7 +107,10 @@ lbm_status efail(lbm_engine* e, lbm_status s, const std::string& msg) {
 
 void free_groups(lbm_engine* e) {
     for (Group& g : e->groups)
-        for (int j = 0; j < 2; ++j) cudaFree(g.d_tab[j]);
+        for (int j = 0; j < 2; ++j) {
+            cudaFree(g.d_tab[j]);
+            cudaFree(g.d_nc[j]);
+        }
     e->groups.clear();
     if (e->graph) cudaGraphExecDestroy(e->graph);
     e->graph = nullptr;
@@ -110,13 +122,13 @@ void free_groups(lbm_engine* e) {
 std::string signature(const lbm_engine* e) {
     std::vector<std::string> parts;
     for (const Request* r : e->resident) {
-        if (!batched(r)) continue;
         BatchLattice b;
         step_params_ahead(r->ctx, 0, 0, &b);
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
         parts.push_back(std::to_string(r->p.nx) + "x" + std::to_string(r->p.ny) + "x" +
                         std::to_string(r->p.nz) + "s" + std::to_string(r->p.storage) +
-                        (unit ? "u" : "v") + "m" + std::to_string(r->p.model));
+                        (unit ? "u" : "v") + "m" + std::to_string(r->p.model) + "n" +
+                        std::to_string(nc_class(r->ctx)));
     }
     std::sort(parts.begin(), parts.end());
     std::string s;
@@ -124,29 +136,50 @@ std::string signature(const lbm_engine* e) {
     return s;
 }
 
+// One step of a group with the tables of step j (0 or 1): the batched near-contact
+// pass (near-contact groups), the batched step kernel, and the batched ghost fill
+// (other groups; near-contact groups get their ghost copies from the pass).
+cudaError_t group_step(lbm_engine* e, Group& g, int j) {
+    cudaError_t err = cudaSuccess;
+    if (g.nc)
+        err = launch_nc_batched(g.d_nc[j], (int)g.members.size(), g.nc_blocks, g.nc_ghost, g.storage,
+                                g.h_cut, e->num_sms, e->stream);
+    if (err == cudaSuccess)
+        err = launch_step_batched(g.d_tab[j], (int)g.members.size(), g.ctas, g.storage, g.unit, g.model,
+                                  e->stream);
+    if (err == cudaSuccess && !g.nc && g.ghost > 0)
+        err = launch_ghost_batched(g.d_tab[j], (int)g.members.size(), g.ghost, g.storage, e->num_sms,
+                                   e->stream);
+    return err;
+}
+
 // Tables of the next two steps for block schedule T and the graph replaying them.
 cudaError_t build_batch(lbm_engine* e, int T) {
     free_groups(e);
     for (Request* r : e->resident) {
-        if (!batched(r)) continue;
         BatchLattice b;
         step_params_ahead(r->ctx, 0, 0, &b);
         const bool unit = !b.p.var_tau && b.p.omega0 == 1.0f;
+        const int ncc = nc_class(r->ctx);
         Group* g = nullptr;
         for (Group& x : e->groups)
-            if (x.storage == r->p.storage && x.unit == unit && x.model == r->p.model) g = &x;
+            if (x.storage == r->p.storage && x.unit == unit && x.model == r->p.model && x.nc == ncc)
+                g = &x;
         if (!g) {
             e->groups.emplace_back();
             g = &e->groups.back();
             g->storage = r->p.storage;
             g->unit = unit;
             g->model = r->p.model;
+            g->nc = ncc;
+            g->h_cut = ctx_h_cut(r->ctx);
         }
         g->members.push_back(r);
     }
     cudaError_t err = cudaSuccess;
     for (Group& g : e->groups) {
         err = prepare_step_batched(g.storage, g.unit, g.model);
+        if (err == cudaSuccess && g.nc) err = prepare_nc_batched(g.storage, g.h_cut);
         if (err != cudaSuccess) return err;
         for (int j = 0; j < 2; ++j) {
             g.h_tab[j].resize(g.members.size());
@@ -170,6 +203,26 @@ cudaError_t build_batch(lbm_engine* e, int T) {
             if (err != cudaSuccess) return err;
             err = cudaMemcpyAsync(g.d_tab[j], g.h_tab[j].data(), bytes, cudaMemcpyHostToDevice, e->stream);
             if (err != cudaSuccess) return err;
+            if (!g.nc) continue;
+            // the near-contact pass of the same step: blocks and ghost-copy tasks of
+            // every member, one after the other
+            g.h_nc[j].resize(g.members.size());
+            long long blocks = 0, gtasks = 0;
+            for (size_t i = 0; i < g.members.size(); ++i) {
+                NcBatchLattice& b = g.h_nc[j][i];
+                nc_params_ahead(g.members[i]->ctx, j, &b);
+                b.block_begin = blocks;
+                b.ghost_begin = gtasks;
+                blocks += nc_block_count(b.p);
+                gtasks += b.p.ghost_f ? ghost_cells(b.p) : 0;
+            }
+            g.nc_blocks = blocks;
+            g.nc_ghost = gtasks;
+            const size_t nbytes = g.h_nc[j].size() * sizeof(NcBatchLattice);
+            err = cudaMalloc((void**)&g.d_nc[j], nbytes);
+            if (err != cudaSuccess) return err;
+            err = cudaMemcpyAsync(g.d_nc[j], g.h_nc[j].data(), nbytes, cudaMemcpyHostToDevice, e->stream);
+            if (err != cudaSuccess) return err;
         }
     }
     err = cudaStreamSynchronize(e->stream);
@@ -180,14 +233,8 @@ cudaError_t build_batch(lbm_engine* e, int T) {
     err = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return err;
     for (int j = 0; j < 2 && err == cudaSuccess; ++j)
-        for (Group& g : e->groups) {
-            if (err == cudaSuccess)
-                err = launch_step_batched(g.d_tab[j], (int)g.members.size(), g.ctas, g.storage, g.unit, g.model,
-                                          e->stream);
-            if (err == cudaSuccess && g.ghost > 0)
-                err = launch_ghost_batched(g.d_tab[j], (int)g.members.size(), g.ghost, g.storage,
-                                           e->num_sms, e->stream);
-        }
+        for (Group& g : e->groups)
+            if (err == cudaSuccess) err = group_step(e, g, j);
     cudaError_t end = cudaStreamEndCapture(e->stream, &graph);
     if (err == cudaSuccess) err = end;
     if (err == cudaSuccess) err = cudaGraphInstantiate(&e->graph, graph, 0);
@@ -201,30 +248,17 @@ cudaError_t build_batch(lbm_engine* e, int T) {
 // One step with the step-0 tables, outside the graph (odd remainders).
 cudaError_t single_step(lbm_engine* e) {
     cudaError_t err = cudaSuccess;
-    for (Group& g : e->groups) {
-        if (err == cudaSuccess)
-            err = launch_step_batched(g.d_tab[0], (int)g.members.size(), g.ctas, g.storage, g.unit, g.model,
-                                      e->stream);
-        if (err == cudaSuccess && g.ghost > 0)
-            err = launch_ghost_batched(g.d_tab[0], (int)g.members.size(), g.ghost, g.storage,
-                                       e->num_sms, e->stream);
-    }
+    for (Group& g : e->groups)
+        if (err == cudaSuccess) err = group_step(e, g, 0);
     return err;
 }
 
 // Record k steps of the batched launches for the lattices they advance.
 void advance_all(lbm_engine* e, long long k) {
     for (Request* r : e->resident) {
-        if (!batched(r)) continue;
         advance_state(r->ctx, k);
         r->steps_done += k;
     }
-}
-
-bool any_batched(const lbm_engine* e) {
-    for (const Request* r : e->resident)
-        if (batched(r)) return true;
-    return false;
 }
 
 // Graph replays of `pairs` x 2 steps, timed with events when ms != nullptr.
@@ -348,6 +382,7 @@ extern "C" lbm_status lbm_engine_submit(lbm_engine* e, const lbm_params* p, cons
     if (!p || !rho_r || !rho_b || !ticket) return efail(e, LBM_EINVAL, "p, rho_r, rho_b and ticket are required");
     if (steps < 1) return efail(e, LBM_EINVAL, "steps must be >= 1");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return efail(e, LBM_EINVAL, "nx, ny, nz must be >= 1");
+    if (p->inplace) return efail(e, LBM_EINVAL, "the engine keeps two population copies (inplace = 0)");
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return efail(e, LBM_ENOMEM, "host allocation failed");
     r->p = *p;
@@ -388,7 +423,7 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
     if (k >= 2 && (k & 1)) --k;   // the graph runs pairs of steps
     cudaError_t err = cudaSuccess;
     long long done = 0;
-    const bool have_batch = any_batched(e);
+    const bool have_batch = !e->resident.empty();
     if (have_batch && !e->graph_valid) {
         const std::string sig = signature(e);
         auto it = e->tuned.find(sig);
@@ -431,16 +466,6 @@ extern "C" lbm_status lbm_engine_tick(lbm_engine* e, int* resident, int* queued,
             advance_all(e, 1);
             e->graph_valid = false;   // the tables' step parity has flipped
         }
-    }
-    // lattices with the near-contact force: k steps each through the context's own
-    // step path (queued on the engine's stream behind the batched work)
-    for (Request* r : e->resident) {
-        if (batched(r) || err != cudaSuccess) continue;
-        if (lbm_step(r->ctx, (int)k) != LBM_OK) {
-            e->err = std::string("request ") + std::to_string(r->ticket) + ": " + lbm_last_error(r->ctx);
-            return LBM_ECUDA;
-        }
-        r->steps_done += k;
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
     if (err != cudaSuccess) {

@@ -48,6 +48,7 @@
 // at the same time, so the halo rows neighbours read come from L2.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cmath>
 #include <utility>
 
@@ -919,6 +920,222 @@ step_kernel_batched(const BatchLattice* __restrict__ tab, int nlat) {
     step_body<St, UnitOmega, SC>(sp, &L.in_map, &L.out_map, (int)blockIdx.x - L.cta_begin);
 }
 
+// ---------------------------------------------------------------- in-place (AA) step
+// With in-place storage (one population copy, see aa_slot) a step is two passes over
+// the nodes:
+//  aa_phi_kernel: each node's post-stream species densities from the slots its
+//    populations are in, and its colour field into phi_out (reads only);
+//  aa_collide_kernel: the same densities again, the isotropic gradient of phi_out,
+//    the forces, and the collision of the fused kernel (the same source in the same
+//    order), its outputs written to the node's own slots in the other layout.
+// Work items are row segments of AA_W nodes (x0 .. x0 + AA_W - 1 of row (y, z)), one
+// per CTA at a time, one node per thread: everything that depends on the row (the
+// source and target rows of every direction, wall tests) is the same for the whole
+// CTA, and a thread adds only its wrapped x offset. Both layouts run the same kernels
+// (the layout is an argument), so a state reached in either layout steps on with the
+// same arithmetic. Colour-gradient model, full storage forms (FP32, FP16/BF16 deviations),
+// walls at rest. Bytes per node and step: the populations read twice and written
+// once (1.5x the two-copy step's) for half its memory.
+constexpr int AA_W = 128;
+
+// Node (x, y, z) of a row segment, with the row's index bases.
+struct AaNode {
+    int x, y, z;
+    unsigned self;   // padded index (population blocks; < 2^31, checked at creation)
+    unsigned pself;  // unpadded index (colour fields, A_h)
+};
+// Index offsets of node n + (dx, dy, dz) (|d| <= 1) from n: padded (off) and
+// unpadded (poff), wrapped on periodic axes; false if it lies beyond a wall. The y and
+// z parts depend on the row only (the same for the whole CTA); x adds the lane's part.
+__device__ __forceinline__ bool aa_offset(const StepParams& p, const AaNode& n, int dx, int dy,
+                                          int dz, int& off, int& poff) {
+    const int planeP = p.nyp * p.pitch, plane = p.ny * p.nx;
+    off = 0;
+    poff = 0;
+    if (dz != 0) {
+        const int v = n.z + dz;
+        int w = dz;
+        if (v < 0 || v >= p.nz) {
+            if (p.wall_z) return false;
+            w = v < 0 ? p.nz - 1 : 1 - p.nz;
+        }
+        off += w * planeP;
+        poff += w * plane;
+    }
+    if (dy != 0) {
+        const int v = n.y + dy;
+        int w = dy;
+        if (v < 0 || v >= p.ny) {
+            if (p.wall_y) return false;
+            w = v < 0 ? p.ny - 1 : 1 - p.ny;
+        }
+        off += w * p.pitch;
+        poff += w * p.nx;
+    }
+    if (dx != 0) {
+        const int v = n.x + dx;
+        const int w = v < 0 ? p.nx - 1 : (v >= p.nx ? 1 - p.nx : dx);
+        off += w;
+        poff += w;
+    }
+    return true;
+}
+
+// Post-stream populations f_i(x) = f*_i(x - c_i) of node n (from beyond a wall
+// f*_opp(i)(x)) from the state in layout L, and the species densities. Deviation
+// storage decodes each value against the lagged colour field of the node that wrote
+// it. Every value is loaded before any is decoded (all loads in flight at once).
+template <class St>
+__device__ __forceinline__ void aa_pull(const StepParams& p, int L, const AaNode& n,
+                                        float (&vr)[Q], float (&vb)[Q], float& rr, float& rb) {
+    using T = typename St::T;
+    const T* f = static_cast<const T*>(p.fin);
+    T raw_r[Q], raw_b[Q];
+    float ph[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        // the writer: n - c_i, or n itself for a link from beyond a wall
+        int off, poff;
+        const bool in = aa_offset(p, n, -cx(i), -cy(i), -cz(i), off, poff);
+        unsigned idx = n.self;
+        const T *fr = f + (size_t)i * p.P, *fb = f + (size_t)(Q + i) * p.P;
+        if (L == 0 && in) {           // f*_i of the writer, in its slot (opp(i), writer)
+            idx = n.self + off;
+            fr = f + (size_t)opp(i) * p.P;
+            fb = f + (size_t)(Q + opp(i)) * p.P;
+        }                             // else: the node's own slot (i, x)
+        raw_r[i] = fr[idx];
+        raw_b[i] = fb[idx];
+        if (St::DEV) ph[i] = __ldg(p.phi_lag + (n.pself + (in ? poff : 0)));
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float rf_r = 0.f, rf_b = 0.f;
+        if (St::DEV) {
+            const float hw = wgt(i) * p.ref_half;
+            rf_r = dev_ref(hw, ph[i], 0);
+            rf_b = dev_ref(hw, ph[i], 1);
+        }
+        vr[i] = St::cvt(raw_r[i], rf_r);
+        vb[i] = St::cvt(raw_b[i], rf_b);
+    }
+    rr = sum19(vr);
+    rb = sum19(vb);
+}
+
+// Row segment t of the lattice: first node x0 of row (y, z), for t in [0, rows x
+// segments per row).
+__device__ __forceinline__ void aa_item(const StepParams& p, long long t, int& x0, int& y, int& z) {
+    const int segs = (p.nx + AA_W - 1) / AA_W;
+    const long long r = t / segs;
+    x0 = (int)(t - r * segs) * AA_W;
+    z = (int)(r / p.ny);
+    y = (int)(r - (long long)z * p.ny);
+}
+__host__ __device__ inline long long aa_items(const StepParams& p) {
+    return (long long)p.nz * p.ny * ((p.nx + AA_W - 1) / AA_W);
+}
+
+__device__ __forceinline__ AaNode aa_node(const StepParams& p, int x, int y, int z) {
+    return AaNode{x, y, z, (unsigned)pidx(p.pitch, p.nyp, p.padx, x, y, z),
+                  (unsigned)(((size_t)z * p.ny + y) * p.nx + x)};
+}
+
+template <class St>
+__global__ void __launch_bounds__(AA_W) aa_phi_kernel(const StepParams p, int L) {
+    grid_dep_wait();
+    const long long items = aa_items(p);
+    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
+        int x0, y, z;
+        aa_item(p, t, x0, y, z);
+        const int x = x0 + (int)threadIdx.x;
+        if (x >= p.nx) continue;
+        const AaNode n = aa_node(p, x, y, z);
+        float vr[Q], vb[Q], rr, rb;
+        aa_pull<St>(p, L, n, vr, vb, rr, rb);
+        p.phi_out[n.pself] = colour(rr, rb);
+    }
+    grid_dep_launch();
+}
+
+// Emitter of the collision for in-place storage: output block k (species k / Q,
+// direction k % Q) to the node's slot of that direction in layout LO.
+template <class St>
+struct AaEmit {
+    typename St::T* f;
+    const StepParams* p;
+    AaNode n;
+    int LO;
+    __device__ __forceinline__ void operator()(int k, float v, float ref) const {
+        const int sp = k >= Q ? 1 : 0, i = k - sp * Q;
+        unsigned idx = n.self;
+        typename St::T* fd = f + (size_t)(sp * Q + opp(i)) * p->P;
+        int off, poff;
+        if (LO == 1 && aa_offset(*p, n, cx(i), cy(i), cz(i), off, poff)) {
+            idx = n.self + off;       // (i, x + c_i) unless that lies beyond a wall
+            fd = f + (size_t)(sp * Q + i) * p->P;
+        }
+        fd[idx] = St::enc(v, ref);
+    }
+    __device__ __forceinline__ void coef(int, float) const {}
+};
+
+// Isotropic colour gradient of phi at node n (a neighbour beyond a wall takes the
+// centre value): the terms of gradient_global in the same order.
+__device__ __forceinline__ void aa_gradient(const StepParams& p, const float* phi, const AaNode& n,
+                                            float& Gx, float& Gy, float& Gz) {
+    float v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int off, poff;
+        v[i] = __ldg(phi + (n.pself + (aa_offset(p, n, cx(i), cy(i), cz(i), off, poff) ? poff : 0)));
+    }
+    Gx = Gy = Gz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (i != 9) grad_add(i, v[i], Gx, Gy, Gz);
+}
+
+template <class St, bool UnitOmega>
+__global__ void __launch_bounds__(AA_W) aa_collide_kernel(const StepParams p, int L) {
+    grid_dep_wait();
+    const long long items = aa_items(p);
+    const bool use_nc = p.A_nc > 0.0f;
+    for (long long t = blockIdx.x; t < items; t += gridDim.x) {
+        int x0, y, z;
+        aa_item(p, t, x0, y, z);
+        const int x = x0 + (int)threadIdx.x;
+        if (x >= p.nx) continue;
+        const AaNode n = aa_node(p, x, y, z);
+        float vr[Q], vb[Q], rr, rb;
+        aa_pull<St>(p, L, n, vr, vb, rr, rb);
+        float ft[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ft[i] = vr[i] + vb[i];
+        const float phic = colour(rr, rb);
+        float Gx, Gy, Gz;
+        aa_gradient(p, p.phi_out, n, Gx, Gy, Gz);
+        float Fx = __ldg(p.fx_row + y), Fy = p.gy, Fz = p.gz;
+        if (use_nc) {
+            const float ah = __ldg(p.ah + n.pself);
+            if (ah != 0.0f) {
+                Fx += ah * Gx;
+                Fy += ah * Gy;
+                Fz += ah * Gz;
+            }
+        }
+        const AaEmit<St> em{static_cast<typename St::T*>(p.fout), &p, n, L ^ 1};
+        if constexpr (UnitOmega) {
+            float jx, jy, jz;
+            cg_momentum(ft, jx, jy, jz);
+            collide_moments<St, true>(p, ft, rr, rb, jx, jy, jz, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
+        } else {
+            collide_store<St, false>(p, ft, rr, rb, phic, Gx, Gy, Gz, Fx, Fy, Fz, em);
+        }
+    }
+    grid_dep_launch();
+}
+
 // ---------------------------------------------------------------- ghost fill
 // Ghost copies of the periodic axes, in warp tasks (each task's indices are worked
 // out once; the lanes sweep a row or a column of rows):
@@ -1069,8 +1286,8 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 //     from the cube: the same cells, weights and interpolation order as the
 //     global-memory march, so the same values.
 // Every node's A_h is written (0 where no film is within h_cut): the field needs no
-// clearing between passes and no candidate list. The kernel also clears the next step
-// kernel's ray-bound bits and writes the ghost copies of the step's input populations.
+// clearing between passes and no candidate list. The kernel also writes the ghost
+// copies of the step's input populations (two-copy storage).
 constexpr int NB_X = 16, NB_Y = 8, NB_Z = 8, NB_NODES = NB_X * NB_Y * NB_Z;
 constexpr int NB_THREADS = 512, NB_PER_THREAD = NB_NODES / NB_THREADS;
 constexpr int NB_BINS = 32;   // ray lengths s_last + 1 <= nsamp <= 25
@@ -1306,12 +1523,85 @@ struct NcRay {
     }
 };
 
-template <class St, int H>
-__global__ void __launch_bounds__(NB_THREADS, 1)
-nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
+// Where the blocks of a near-contact launch come from. NcOne: one lattice, its
+// parameters and tensor map in kernel parameter space. NcBatch: the lattices of a
+// batch table (the serving engine's batched launches), global block b belonging to
+// the last lattice whose first block is <= b; a lattice's parameters are copied to
+// shared memory when a cube slot is bound to one of its blocks. bind() is called by
+// every thread of the CTA at the same point.
+struct NcOne {
+    const StepParams* p;
+    const CUtensorMap* map;
+    int tma;
+    __device__ __forceinline__ long long bind(int, long long b) { return b; }
+    __device__ __forceinline__ const StepParams& params(int) const { return *p; }
+    __device__ __forceinline__ const CUtensorMap* lag_map(int) const { return map; }
+    __device__ __forceinline__ int tma_ok(int) const { return tma; }
+    template <class St>
+    __device__ __forceinline__ void ghosts(long long gtid, long long gthreads, int lane) const {
+        if (!p->ghost_f) return;
+        const long long total = ghost_work(*p);
+        for (long long t = gtid >> 5; t < total; t += gthreads >> 5)
+            ghost_task<St>(static_cast<typename St::T*>(p->ghost_f), *p, t, lane);
+    }
+};
+struct NcBatch {
+    const NcBatchLattice* tab;
+    int nlat;
+    long long ghost_total;
+    StepParams* sp;   // [2] in shared memory: the parameters of the lattice bound to a slot
+    int* lat;         // [2] in shared memory: that lattice
+    __device__ __forceinline__ long long bind(int slot, long long b) {
+        __syncthreads();   // the slot's previous parameters are no longer read
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nlat - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tab[mid].block_begin <= b) lo = mid;
+                else hi = mid - 1;
+            }
+            lat[slot] = lo;
+        }
+        __syncthreads();
+        const int l = lat[slot];
+        const int* src = reinterpret_cast<const int*>(&tab[l].p);
+        int* dst = reinterpret_cast<int*>(&sp[slot]);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / sizeof(int)); i += blockDim.x)
+            dst[i] = src[i];
+        __syncthreads();
+        return b - tab[l].block_begin;
+    }
+    __device__ __forceinline__ const StepParams& params(int slot) const { return sp[slot]; }
+    __device__ __forceinline__ const CUtensorMap* lag_map(int slot) const { return &tab[lat[slot]].lag_map; }
+    __device__ __forceinline__ int tma_ok(int slot) const { return tab[lat[slot]].tma_ok; }
+    template <class St>
+    __device__ __forceinline__ void ghosts(long long gtid, long long gthreads, int lane) const {
+        for (long long t = gtid >> 5; t < ghost_total; t += gthreads >> 5) {
+            int lo = 0, hi = nlat - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tab[mid].ghost_begin <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            const NcBatchLattice& L = tab[lo];
+            if (L.p.ghost_f)
+                ghost_task<St>(static_cast<typename St::T*>(L.p.ghost_f), L.p, t - L.ghost_begin, lane);
+        }
+    }
+};
+
+// Blocks of a lattice's block grid.
+__host__ __device__ inline long long nc_blocks(const StepParams& p) {
+    return (long long)((p.nx + NB_X - 1) / NB_X) * ((p.ny + NB_Y - 1) / NB_Y) *
+           ((p.nz + NB_Z - 1) / NB_Z);
+}
+
+// The pass over `nblocks` blocks of `src` (see nc_block_kernel below for what a block
+// does); the CTA takes blocks blockIdx.x, + gridDim.x, ...
+template <class St, int H, class Src>
+__device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsigned char* nsm) {
     using G = NcBlockGeo<H>;
     constexpr int NBUF = G::NBUF;
-    extern __shared__ __align__(128) unsigned char nsm[];
     float* cubes = reinterpret_cast<float*>(nsm);                          // [NBUF][SZ][SY][SX]
     unsigned char* q = nsm + NBUF * G::CUBE_BYTES;                         // 128-byte aligned
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(q);   // [NBUF], 4 slots
@@ -1328,45 +1618,46 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&lag_map)) : "memory");
     }
     __syncthreads();
     grid_dep_wait();
-    if (p.ghost_f) {
-        const long long total = ghost_work(p);
-        for (long long t = gtid >> 5; t < total; t += gthreads >> 5)
-            ghost_task<St>(static_cast<typename St::T*>(p.ghost_f), p, t, lane);
-    }
-    const long long nblocks = (long long)((p.nx + NB_X - 1) / NB_X) *
-                              ((p.ny + NB_Y - 1) / NB_Y) * ((p.nz + NB_Z - 1) / NB_Z);
-    const size_t plane = (size_t)p.nx * p.ny;
+    src.template ghosts<St>(gtid, gthreads, lane);
     uint32_t parity = 0u;
     bool failed = false;
-    if (blockIdx.x < nblocks)
-        nc_fill_start<H>(p, &lag_map, tma_ok, blockIdx.x, cubes, &bars[0]);
+    long long lb[2] = {0, 0};   // local block index of the block bound to each slot
+    if (blockIdx.x < nblocks) {
+        lb[0] = src.bind(0, blockIdx.x);
+        nc_fill_start<H>(src.params(0), src.lag_map(0), src.tma_ok(0), lb[0], cubes, &bars[0]);
+    }
     int it = 0;
     for (long long b = blockIdx.x; b < nblocks; b += gridDim.x, ++it) {
         const int buf = NBUF == 2 ? (it & 1) : 0;
         float* cube = cubes + (size_t)buf * (G::CUBE_BYTES / sizeof(float));
-        int x0, y0, z0;
-        nc_block_origin(p, b, x0, y0, z0);
         const long long bn = b + gridDim.x;
         if (NBUF == 2) {
             // the next block's copy into the other cube (consumed in the last iteration)
             fence_proxy_async();
-            if (bn < nblocks)
-                nc_fill_start<H>(p, &lag_map, tma_ok, bn, cubes + (size_t)(buf ^ 1) *
-                                 (G::CUBE_BYTES / sizeof(float)), &bars[buf ^ 1]);
-            else
+            if (bn < nblocks) {
+                lb[buf ^ 1] = src.bind(buf ^ 1, bn);
+                nc_fill_start<H>(src.params(buf ^ 1), src.lag_map(buf ^ 1), src.tma_ok(buf ^ 1),
+                                 lb[buf ^ 1], cubes + (size_t)(buf ^ 1) * (G::CUBE_BYTES / sizeof(float)),
+                                 &bars[buf ^ 1]);
+            } else {
                 cp_async_commit();
+            }
             cp_async_wait<1>();   // this block's copies (the next block's may be in flight)
         } else {
             if (it > 0) {   // one cube: this block's copy starts once the last one is consumed
                 fence_proxy_async();
-                nc_fill_start<H>(p, &lag_map, tma_ok, b, cube, &bars[0]);
+                lb[0] = src.bind(0, b);
+                nc_fill_start<H>(src.params(0), src.lag_map(0), src.tma_ok(0), lb[0], cube, &bars[0]);
             }
             cp_async_wait<0>();
         }
+        const StepParams& p = src.params(buf);
+        const size_t plane = (size_t)p.nx * p.ny;
+        int x0, y0, z0;
+        nc_block_origin(p, lb[buf], x0, y0, z0);
         // (a wait that gives up leaves its phase pending: the drain below waits on it)
         if (mbar_wait(&bars[buf], (parity >> buf) & 1u, p.err)) parity ^= 1u << buf;
         else failed = true;
@@ -1485,7 +1776,29 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
                 if (mbar_try_wait(&bars[b], (parity >> b) & 1u)) break;
     }
     cp_async_wait<0>();
+}
+
+template <class St, int H>
+__global__ void __launch_bounds__(NB_THREADS, 1)
+nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
+    extern __shared__ __align__(128) unsigned char nsm[];
+    if (threadIdx.x == 0)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&lag_map)) : "memory");
+    NcOne src{&p, &lag_map, tma_ok};
+    nc_block_pass<St, H>(src, nc_blocks(p), nsm);
     grid_dep_launch();
+}
+
+// The near-contact pass of every lattice of a batch table in one launch.
+template <class St, int H>
+__global__ void __launch_bounds__(NB_THREADS, 1)
+nc_block_kernel_batched(const NcBatchLattice* __restrict__ tab, int nlat, long long nblocks,
+                        long long ghost_total) {
+    extern __shared__ __align__(128) unsigned char nsm[];
+    __shared__ StepParams sp[2];
+    __shared__ int lat[2];
+    NcBatch src{tab, nlat, ghost_total, sp, lat};
+    nc_block_pass<St, H>(src, nblocks, nsm);
 }
 
 // Launch with programmatic stream serialisation (see grid_dep_wait). (The list and
@@ -1547,6 +1860,61 @@ cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, boo
     return cudaErrorInvalidValue;
 }
 
+template <class St, int H>
+static cudaError_t launch_block_batched_tpl(const NcBatchLattice* tab, int nlat, long long nblocks,
+                                           long long ghost_total, int num_sms, cudaStream_t s) {
+    if (!tab) {   // preparation only: the shared-memory attribute, outside stream capture
+        return cudaFuncSetAttribute(nc_block_kernel_batched<St, H>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)NcBlockGeo<H>::SMEM);
+    }
+    const long long g = std::min<long long>((long long)num_sms, std::max<long long>(1, nblocks));
+    nc_block_kernel_batched<St, H><<<(unsigned)g, NB_THREADS, NcBlockGeo<H>::SMEM, s>>>(
+        tab, nlat, nblocks, ghost_total);
+    return cudaGetLastError();
+}
+
+template <class St>
+static cudaError_t launch_block_batched_st(const NcBatchLattice* tab, int nlat, long long nblocks,
+                                          long long ghost_total, double h_cut, int num_sms,
+                                          cudaStream_t s) {
+    const int need = (int)std::floor(h_cut) + 3;
+    if (need <= 9) return launch_block_batched_tpl<St, 9>(tab, nlat, nblocks, ghost_total, num_sms, s);
+    if (need <= 12) return launch_block_batched_tpl<St, 12>(tab, nlat, nblocks, ghost_total, num_sms, s);
+    return cudaErrorInvalidValue;
+}
+
+// The near-contact pass of every lattice of a batch table (one storage element type and
+// one halo depth, i.e. h_cut class) in one launch.
+cudaError_t launch_nc_batched(const NcBatchLattice* tab, int nlat, long long nblocks,
+                              long long ghost_total, int storage, double h_cut, int num_sms,
+                              cudaStream_t s) {
+    switch (storage) {
+        case 0: case 3:
+            return launch_block_batched_st<StoreF32>(tab, nlat, nblocks, ghost_total, h_cut, num_sms, s);
+        case 1: case 4:
+            return launch_block_batched_st<StoreF16>(tab, nlat, nblocks, ghost_total, h_cut, num_sms, s);
+        case 2:
+            return launch_block_batched_st<StoreBF16>(tab, nlat, nblocks, ghost_total, h_cut, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Shared-memory attribute of the batched near-contact kernel of one storage element
+// type and halo class: set before any launch (and outside stream capture).
+cudaError_t prepare_nc_batched(int storage, double h_cut) {
+    return launch_nc_batched(nullptr, 0, 0, 0, storage, h_cut, 1, nullptr);
+}
+
+// Halo class of a near-contact pass (lattices sharing it can be batched).
+int nc_halo(double h_cut) {
+    const int need = (int)std::floor(h_cut) + 3;
+    return need <= 9 ? 9 : 12;
+}
+
+// Blocks of nodes of a lattice's near-contact pass.
+long long nc_block_count(const StepParams& p) { return nc_blocks(p); }
+
 // Shape of the cube a tensor copy of the near-contact pass fills (x, y, z extents), for
 // the tensor map of a colour field.
 void nc_cube_box(double h_cut, int box[3]) {
@@ -1600,6 +1968,37 @@ cudaError_t launch_step(const StepParams& p, const CUtensorMap& map, const CUten
         case 4: return launch_tpl<StoreQ5H>(p, map, omap, grid, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <class St>
+static cudaError_t launch_aa_tpl(const StepParams& p, int layout, int num_sms, cudaStream_t s) {
+    // a grid that fills the GPU once (CTAs loop over the row segments)
+    static int per_sm[2] = {0, 0};
+    const bool unit = !p.var_tau && p.omega0 == 1.0f;
+    auto collide = unit ? aa_collide_kernel<St, true> : aa_collide_kernel<St, false>;
+    if (per_sm[unit] == 0) {
+        int a = 0, b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, aa_phi_kernel<St>, AA_W, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, collide, AA_W, 0);
+        if (e != cudaSuccess) return e;
+        per_sm[unit] = std::max(1, std::min(a, b));
+    }
+    const long long items = aa_items(p);
+    const unsigned grid = (unsigned)std::max(1LL, std::min(items, (long long)num_sms * per_sm[unit]));
+    cudaError_t e = pdl_launch(aa_phi_kernel<St>, grid, AA_W, 0, s, p, layout);
+    if (e != cudaSuccess) return e;
+    return pdl_launch(collide, grid, AA_W, 0, s, p, layout);
+}
+
+// One in-place step from state layout `layout` (p.fin == p.fout: the one copy).
+cudaError_t launch_aa_step(const StepParams& p, int layout, int storage, int num_sms,
+                           cudaStream_t s) {
+    switch (storage) {
+        case 0: return launch_aa_tpl<StoreF32>(p, layout, num_sms, s);
+        case 1: return launch_aa_tpl<StoreF16>(p, layout, num_sms, s);
+        case 2: return launch_aa_tpl<StoreBF16>(p, layout, num_sms, s);
+    }
+    return cudaErrorInvalidValue;   // the reduced forms are not stored in place
 }
 
 template <class St, bool U, bool SC>

@@ -59,7 +59,7 @@ class Params(C.Structure):
                 ("A_nc", C.c_double), ("h_min", C.c_double), ("h_cut", C.c_double),
                 ("g", C.c_double * 3), ("kolmogorov_amp", C.c_double), ("wall_u", C.c_double),
                 ("rho0", C.c_double), ("model", C.c_int), ("G_sc", C.c_double),
-                ("storage", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("storage", C.c_int), ("cuda_stream", C.c_void_p), ("inplace", C.c_int)]
 
 
 _lib = None
@@ -143,7 +143,8 @@ def velocity_set() -> np.ndarray:
 
 def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=0.0, beta=0.7,
                 A_nc=0.0, h_min=3.0, h_cut=None, g=(0.0, 0.0, 0.0), kolmogorov_amp=0.0, rho0=1.0,
-                storage="fp32", stream=None, wall_u=0.0, model="colour", G_sc=0.0) -> Params:
+                storage="fp32", stream=None, wall_u=0.0, model="colour", G_sc=0.0,
+                inplace=0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.wall_y, p.wall_z = int(wall_y), int(wall_z)
@@ -161,6 +162,7 @@ def make_params(nx, ny, nz, *, wall_y=0, wall_z=0, tau_r=1.0, tau_b=None, sigma=
     p.G_sc = float(G_sc)
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.cuda_stream = stream
+    p.inplace = int(inplace)
     return p
 
 

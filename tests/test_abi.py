@@ -50,3 +50,7 @@ def test_footprint_is_reported_without_a_device():
     full, red = lbm.footprint_bytes(p), lbm.footprint_bytes(p5)
     assert 2 * 24 * N * 4 <= red < full
     assert (full - red) >= 2 * (2 * 19 - 24) * N * 4
+    # in place: one copy of the populations instead of two
+    pa = lbm.make_params(256, 128, 64, storage="fp16", inplace=1)
+    two, one = lbm.footprint_bytes(p16), lbm.footprint_bytes(pa)
+    assert two - one >= 2 * 19 * N * 2 and one >= 2 * 19 * N * 2

@@ -229,18 +229,23 @@ def test_cancel_queued_and_resident_requests(lbm):
 
 @pytest.mark.parametrize("with_batched", [True, False])
 def test_near_contact_requests_are_served_bitwise_lbm_step(lbm, with_batched):
-    # near-contact requests (two droplets close enough for the film force) take their
-    # own step path in the engine's ticks, beside the batched lattices or alone; each
-    # result equals the same lattice stepped by plain lbm_step
+    # near-contact requests (two droplets close enough for the film force) are batched
+    # like the others: per group (storage, relaxation class, model, halo class of the
+    # film rays) one near-contact launch over all its lattices precedes the batched step
+    # kernel. Each result equals the same lattice stepped by plain lbm_step, beside
+    # batched lattices without the force or alone; several lattices of different sizes
+    # share one near-contact launch (one of them large enough for tensor-copied cubes).
     from paper_2005_12764_gb300 import serving
     nc = []
-    for k, (L, gap) in enumerate(((40, 2.0), (48, 3.0))):
+    cases = ((40, 2.0, "fp32", 3.0), (48, 3.0, "fp32_q5", 3.0), (64, 2.5, "fp32", 3.0),
+             (36, 2.0, "fp32", 3.0), (44, 2.0, "fp16_q5", 3.0), (40, 2.0, "fp32", 2.0))
+    for k, (L, gap, st, hmin) in enumerate(cases):
         c, R = L / 2.0, L / 6.0
         drops = [(c - R - gap / 2, c, c, R), (c + R + gap / 2, c, c, R)]
         a, b = inputs.paint_droplets((L, L, L), drops)
-        p = lbm.make_params(L, L, L, sigma=0.02, beta=0.7, A_nc=0.02, h_min=3.0,
-                            storage="fp32" if k == 0 else "fp32_q5")
-        nc.append((p, a, b, 25 + 10 * k))
+        p = lbm.make_params(L, L, L, sigma=0.02, beta=0.7, A_nc=0.02, h_min=hmin,
+                            storage=st, kolmogorov_amp=1e-4 if k % 2 else 0.0)
+        nc.append((p, a, b, 25 + 10 * (k % 3)))
     e = lbm.Engine(budget_bytes=8 << 30, max_slots=8, chunk_steps=10, autotune=False)
     tickets = {}
     for p, a, b, steps in nc:

@@ -98,9 +98,22 @@ def test_invalid_arguments_are_refused():
     dict(model="shan_chen", A_nc=0.01), dict(wall_u=0.01), dict(wall_y=1, wall_u=0.5),
     dict(beta=1.5), dict(sigma=-1.0), dict(A_nc=0.01, h_min=0.0), dict(A_nc=0.01, h_cut=12.0),
     dict(storage="fp16", rho0=0.0),
+    dict(inplace=1, storage="fp32_q5"), dict(inplace=1, storage="fp16_q5"),
+    dict(inplace=1, model="shan_chen", G_sc=1.2), dict(inplace=1, wall_y=1, wall_u=0.01),
+    dict(inplace=3),
 ])
 def test_parameter_validation_without_a_device(bad):
     # the parameter checks of lbm_create run before any device call; lbm_work_split
     # applies the same checks, so they are testable on the host
     with pytest.raises(lbm.LbmError):
         split(16, 16, 16, 152, **bad)
+
+
+def test_inplace_block_index_limit():
+    # in-place steps index a padded population block in 31 bits: 1290 x 1280 x 1280
+    # FP32 (2.11e9 nodes, 2.16e9 padded positions per block) is refused in place and
+    # accepted with two copies; 640^3 is accepted in place
+    with pytest.raises(lbm.LbmError):
+        split(1290, 1280, 1280, 152, inplace=1)
+    split(1290, 1280, 1280, 152)
+    split(640, 640, 640, 152, inplace=1, storage="fp16")

@@ -55,3 +55,28 @@ def test_totals_without_allocation_rejects_bad_sizes():
         with pytest.raises(lbm.LbmError) as ei:
             lbm.totals_noalloc(pops.data_ptr(), bad, out.data_ptr())
         assert ei.value.status == -1
+
+
+def test_totals_without_allocation_on_3m_nodes_with_a_ragged_last_block():
+    # 3,000,017 nodes: 367 blocks of 8192 nodes, the last one holding 1695; random
+    # FP32 populations summed by torch in FP64 per direction (a different order)
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_12764_gb300 import build_lib, lbm
+    build_lib.build()
+    c = torch.from_numpy(lbm.velocity_set().astype(np.float64)).cuda()     # [19, 3]
+    gen = torch.Generator(device="cuda").manual_seed(2005)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    for n in (3_000_017, 8192 * 5, 1):          # ragged, whole blocks only, one node
+        pops = torch.rand(2 * 19, n, dtype=torch.float32, device="cuda", generator=gen) * 0.1
+        out.fill_(-1.0)
+        lbm.totals_noalloc(pops.data_ptr(), n, out.data_ptr())
+        torch.cuda.synchronize()
+        per_dir = pops.double().sum(dim=1)                               # [38]
+        r, b = per_dir[:19], per_dir[19:]
+        want = torch.cat([r.sum().view(1), b.sum().view(1), ((r + b)[:, None] * c).sum(0)])
+        mass = float(want[0] + want[1])
+        assert torch.allclose(out[:5], want, rtol=1e-12, atol=1e-12 * mass), (n, out[:5], want)
+        assert (out[5:] == -1.0).all()
+        del pops
