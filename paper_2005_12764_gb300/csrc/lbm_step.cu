@@ -1270,8 +1270,9 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 // samples up to t = h_cut + 2 reaches is floor(h_cut) + 3 <= H nodes away -- are copied
 // into a shared-memory cube: by one TMA tensor copy where the cube lies inside the
 // lattice (a walled axis may reach past its walls: zero fill, never read), else by
-// asynchronous copies wrapped on periodic axes and clamped at walls. With two cubes
-// the next block's copy is in flight while a block is processed. Then:
+// asynchronous copies wrapped on periodic axes and clamped at walls. Two CTAs share an
+// SM, one cube each (the halo-9 cube and the tables take 112 KB): while one waits for
+// its copy or at a barrier between the phases below, the other works. Then:
 //  1. a bit table over 2 x 2 x 2 blocks of the cube marks where a node of the lagged
 //     field exceeds kPosBand (block b of an axis holds cube nodes 2b .. 2b+2, so the 8
 //     corners of every cell lie in one block): a sample in an unmarked block cannot
@@ -1286,7 +1287,7 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 //     from the cube: the same cells, weights and interpolation order as the
 //     global-memory march, so the same values.
 // Every node's A_h is written (0 where no film is within h_cut): the field needs no
-// clearing between passes and no candidate list. The kernel also writes the ghost
+// clearing between passes and no candidate list. The kernel first writes the ghost
 // copies of the step's input populations (two-copy storage).
 constexpr int NB_X = 16, NB_Y = 8, NB_Z = 8, NB_NODES = NB_X * NB_Y * NB_Z;
 constexpr int NB_THREADS = 512, NB_PER_THREAD = NB_NODES / NB_THREADS;
@@ -1311,8 +1312,7 @@ struct NcBlockGeo {
         (ROWS > NB_NODES ? ROWS : NB_NODES) * sizeof(uint32_t);
     static constexpr size_t FIXED = 4 * sizeof(unsigned long long) + TAB_BYTES + LIST_BYTES +
                                     2 * NB_BINS * sizeof(int) + NB_NODES;
-    static constexpr int NBUF = 2 * CUBE_BYTES + FIXED <= 227 * 1024 ? 2 : 1;
-    static constexpr size_t SMEM = NBUF * CUBE_BYTES + FIXED;
+    static constexpr size_t SMEM = CUBE_BYTES + FIXED;
 };
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -1475,12 +1475,10 @@ __device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtenso
     cp_async_commit();
 }
 
-// One ray of the block pass: node, direction, bound and crossing search, with the
-// corners of its current cell (kept while the ray stays in that cell).
+// One ray of the block pass: node, direction, bound and crossing search.
 struct NcRay {
-    int lx, ly, lz, x, y, z, s_last, key;
+    int lx, ly, lz, x, y, z, s_last;
     float nx_, ny_, nz_, a;
-    float v[8];
     NcMarch mr;
     template <int H>
     __device__ __forceinline__ void start(const StepParams& p, const float* cube, int e, int x0,
@@ -1497,21 +1495,29 @@ struct NcRay {
         cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
         nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
         a = 0.0f;
-        key = -1;
     }
-    // Sample s; false once A_h is decided or the bound is passed.
+    // The lagged colour field at sample s (t = -1 + s/2), interpolated from the cube.
     template <int H>
-    __device__ __forceinline__ bool advance(const StepParams& p, const float* cube, int y0, int z0,
-                                            int s) {
-        if (s > s_last) return false;
-        const float t = -1.0f + 0.5f * (float)s;
+    __device__ __forceinline__ float value(const StepParams& p, const float* cube, int y0, int z0,
+                                           float t) const {
         CubeCell cell;
         cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, t * nx_, t * ny_, t * nz_, cell);
-        if (cell.o != key) {
-            cube_corners<H>(cube, cell, v);
-            key = cell.o;
+        float v[8];
+        cube_corners<H>(cube, cell, v);
+        return cube_interp(cell, v);
+    }
+    // The march: samples 0 .. s_last in order until A_h is decided, two samples
+    // interpolated per turn (independent work) and fed in order.
+    template <int H>
+    __device__ __forceinline__ void march(const StepParams& p, const float* cube, int y0, int z0) {
+        for (int s = 0; s <= s_last; s += 2) {
+            const float t0 = -1.0f + 0.5f * (float)s, t1 = t0 + 0.5f;
+            const bool two = s + 1 <= s_last;
+            const float v0 = value<H>(p, cube, y0, z0, t0);
+            const float v1 = value<H>(p, cube, y0, z0, two ? t1 : t0);
+            if (mr.feed(p, t0, v0, a)) return;
+            if (!two || mr.feed(p, t1, v1, a)) return;
         }
-        return !mr.feed(p, t, cube_interp(cell, v), a);
     }
     __device__ __forceinline__ void finish(const StepParams& p, size_t plane) {
         const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
@@ -1526,33 +1532,34 @@ struct NcRay {
 // Where the blocks of a near-contact launch come from. NcOne: one lattice, its
 // parameters and tensor map in kernel parameter space. NcBatch: the lattices of a
 // batch table (the serving engine's batched launches), global block b belonging to
-// the last lattice whose first block is <= b; a lattice's parameters are copied to
-// shared memory when a cube slot is bound to one of its blocks. bind() is called by
-// every thread of the CTA at the same point.
+// the last lattice whose first block is <= b; that lattice's parameters are copied to
+// shared memory when the CTA takes the block. bind() is called by every thread of the
+// CTA at the same point. Ghost tasks (the ghost copies of the step's input
+// populations) are numbered over the whole launch.
 struct NcOne {
     const StepParams* p;
     const CUtensorMap* map;
     int tma;
-    __device__ __forceinline__ long long bind(int, long long b) { return b; }
-    __device__ __forceinline__ const StepParams& params(int) const { return *p; }
-    __device__ __forceinline__ const CUtensorMap* lag_map(int) const { return map; }
-    __device__ __forceinline__ int tma_ok(int) const { return tma; }
+    __device__ __forceinline__ long long bind(long long b) { return b; }
+    __device__ __forceinline__ const StepParams& params() const { return *p; }
+    __device__ __forceinline__ const CUtensorMap* lag_map() const { return map; }
+    __device__ __forceinline__ int tma_ok() const { return tma; }
+    __device__ __forceinline__ long long ghost_total() const {
+        return p->ghost_f ? ghost_work(*p) : 0;
+    }
     template <class St>
-    __device__ __forceinline__ void ghosts(long long gtid, long long gthreads, int lane) const {
-        if (!p->ghost_f) return;
-        const long long total = ghost_work(*p);
-        for (long long t = gtid >> 5; t < total; t += gthreads >> 5)
-            ghost_task<St>(static_cast<typename St::T*>(p->ghost_f), *p, t, lane);
+    __device__ __forceinline__ void ghost(long long t, int lane) const {
+        ghost_task<St>(static_cast<typename St::T*>(p->ghost_f), *p, t, lane);
     }
 };
 struct NcBatch {
     const NcBatchLattice* tab;
     int nlat;
-    long long ghost_total;
-    StepParams* sp;   // [2] in shared memory: the parameters of the lattice bound to a slot
-    int* lat;         // [2] in shared memory: that lattice
-    __device__ __forceinline__ long long bind(int slot, long long b) {
-        __syncthreads();   // the slot's previous parameters are no longer read
+    long long gtotal;
+    StepParams* sp;   // in shared memory: the parameters of the lattice of the CTA's block
+    int* lat;         // in shared memory: that lattice
+    __device__ __forceinline__ long long bind(long long b) {
+        __syncthreads();   // the previous block's parameters are no longer read
         if (threadIdx.x == 0) {
             int lo = 0, hi = nlat - 1;
             while (lo < hi) {
@@ -1560,33 +1567,32 @@ struct NcBatch {
                 if (tab[mid].block_begin <= b) lo = mid;
                 else hi = mid - 1;
             }
-            lat[slot] = lo;
+            *lat = lo;
         }
         __syncthreads();
-        const int l = lat[slot];
+        const int l = *lat;
         const int* src = reinterpret_cast<const int*>(&tab[l].p);
-        int* dst = reinterpret_cast<int*>(&sp[slot]);
+        int* dst = reinterpret_cast<int*>(sp);
         for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / sizeof(int)); i += blockDim.x)
             dst[i] = src[i];
         __syncthreads();
         return b - tab[l].block_begin;
     }
-    __device__ __forceinline__ const StepParams& params(int slot) const { return sp[slot]; }
-    __device__ __forceinline__ const CUtensorMap* lag_map(int slot) const { return &tab[lat[slot]].lag_map; }
-    __device__ __forceinline__ int tma_ok(int slot) const { return tab[lat[slot]].tma_ok; }
+    __device__ __forceinline__ const StepParams& params() const { return *sp; }
+    __device__ __forceinline__ const CUtensorMap* lag_map() const { return &tab[*lat].lag_map; }
+    __device__ __forceinline__ int tma_ok() const { return tab[*lat].tma_ok; }
+    __device__ __forceinline__ long long ghost_total() const { return gtotal; }
     template <class St>
-    __device__ __forceinline__ void ghosts(long long gtid, long long gthreads, int lane) const {
-        for (long long t = gtid >> 5; t < ghost_total; t += gthreads >> 5) {
-            int lo = 0, hi = nlat - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (tab[mid].ghost_begin <= t) lo = mid;
-                else hi = mid - 1;
-            }
-            const NcBatchLattice& L = tab[lo];
-            if (L.p.ghost_f)
-                ghost_task<St>(static_cast<typename St::T*>(L.p.ghost_f), L.p, t - L.ghost_begin, lane);
+    __device__ __forceinline__ void ghost(long long t, int lane) const {
+        int lo = 0, hi = nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].ghost_begin <= t) lo = mid;
+            else hi = mid - 1;
         }
+        const NcBatchLattice& L = tab[lo];
+        if (L.p.ghost_f)
+            ghost_task<St>(static_cast<typename St::T*>(L.p.ghost_f), L.p, t - L.ghost_begin, lane);
     }
 };
 
@@ -1601,10 +1607,9 @@ __host__ __device__ inline long long nc_blocks(const StepParams& p) {
 template <class St, int H, class Src>
 __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsigned char* nsm) {
     using G = NcBlockGeo<H>;
-    constexpr int NBUF = G::NBUF;
-    float* cubes = reinterpret_cast<float*>(nsm);                          // [NBUF][SZ][SY][SX]
-    unsigned char* q = nsm + NBUF * G::CUBE_BYTES;                         // 128-byte aligned
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(q);   // [NBUF], 4 slots
+    float* cube = reinterpret_cast<float*>(nsm);                           // [SZ][SY][SX]
+    unsigned char* q = nsm + G::CUBE_BYTES;                                // 128-byte aligned
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(q);    // (4 slots, 1 used)
     uint32_t* tab = reinterpret_cast<uint32_t*>(q + 4 * sizeof(unsigned long long));  // [TBZ][TBY]
     int* rays = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tab) + G::TAB_BYTES);
     uint32_t* rowbits = reinterpret_cast<uint32_t*>(rays);                 // [SZ][SY], then the list
@@ -1613,53 +1618,34 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
     int* cursor = bins + NB_BINS;                                          // [NB_BINS] scatter
     unsigned char* slast = reinterpret_cast<unsigned char*>(cursor + NB_BINS);   // [NB_NODES] s_last + 1
     const int tid = threadIdx.x, lane = tid & 31;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
-    const long long gthreads = (long long)gridDim.x * blockDim.x;
     if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     grid_dep_wait();
-    src.template ghosts<St>(gtid, gthreads, lane);
+    // the ghost copies first, every warp of the launch on its share of the tasks (many
+    // independent scattered accesses in flight at once)
+    {
+        const long long gtotal = src.ghost_total(), gwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        for (long long t = ((long long)blockIdx.x * blockDim.x + tid) >> 5; t < gtotal; t += gwarps)
+            src.template ghost<St>(t, lane);
+    }
     uint32_t parity = 0u;
     bool failed = false;
-    long long lb[2] = {0, 0};   // local block index of the block bound to each slot
-    if (blockIdx.x < nblocks) {
-        lb[0] = src.bind(0, blockIdx.x);
-        nc_fill_start<H>(src.params(0), src.lag_map(0), src.tma_ok(0), lb[0], cubes, &bars[0]);
-    }
-    int it = 0;
-    for (long long b = blockIdx.x; b < nblocks; b += gridDim.x, ++it) {
-        const int buf = NBUF == 2 ? (it & 1) : 0;
-        float* cube = cubes + (size_t)buf * (G::CUBE_BYTES / sizeof(float));
-        const long long bn = b + gridDim.x;
-        if (NBUF == 2) {
-            // the next block's copy into the other cube (consumed in the last iteration)
-            fence_proxy_async();
-            if (bn < nblocks) {
-                lb[buf ^ 1] = src.bind(buf ^ 1, bn);
-                nc_fill_start<H>(src.params(buf ^ 1), src.lag_map(buf ^ 1), src.tma_ok(buf ^ 1),
-                                 lb[buf ^ 1], cubes + (size_t)(buf ^ 1) * (G::CUBE_BYTES / sizeof(float)),
-                                 &bars[buf ^ 1]);
-            } else {
-                cp_async_commit();
-            }
-            cp_async_wait<1>();   // this block's copies (the next block's may be in flight)
-        } else {
-            if (it > 0) {   // one cube: this block's copy starts once the last one is consumed
-                fence_proxy_async();
-                lb[0] = src.bind(0, b);
-                nc_fill_start<H>(src.params(0), src.lag_map(0), src.tma_ok(0), lb[0], cube, &bars[0]);
-            }
-            cp_async_wait<0>();
-        }
-        const StepParams& p = src.params(buf);
+    for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        // (the cube's reads of the last block precede this copy into it: the barrier
+        // that ended that block, then the proxy fence)
+        fence_proxy_async();
+        const long long lb = src.bind(b);
+        nc_fill_start<H>(src.params(), src.lag_map(), src.tma_ok(), lb, cube, bar);
+        cp_async_wait<0>();
+        const StepParams& p = src.params();
         const size_t plane = (size_t)p.nx * p.ny;
         int x0, y0, z0;
-        nc_block_origin(p, lb[buf], x0, y0, z0);
+        nc_block_origin(p, lb, x0, y0, z0);
         // (a wait that gives up leaves its phase pending: the drain below waits on it)
-        if (mbar_wait(&bars[buf], (parity >> buf) & 1u, p.err)) parity ^= 1u << buf;
+        if (mbar_wait(bar, parity, p.err)) parity ^= 1u;
         else failed = true;
         if (__syncthreads_or(failed)) {
             failed = true;
@@ -1706,12 +1692,17 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
                 cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
                 float a = 0.0f;
                 if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
-                    // the last sample inside the fluid whose cell's block is marked
-                    for (int sm = nc_sample_end(p, y, z, ny_, nz_) - 1; sm >= 0; --sm) {
-                        const float t = -1.0f + 0.5f * (float)sm;
-                        if (cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz, t * nx_,
-                                                  t * ny_, t * nz_)) {
-                            s_last = sm;
+                    // the last sample inside the fluid whose cell's block is marked (two
+                    // samples per turn: independent lookups; the sample before s = 0
+                    // lies 1.5 units from the node, inside the cube, and is not used)
+                    for (int sm = nc_sample_end(p, y, z, ny_, nz_) - 1; sm >= 0; sm -= 2) {
+                        const float t0 = -1.0f + 0.5f * (float)sm, t1 = t0 - 0.5f;
+                        const bool m0 = cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz,
+                                                              t0 * nx_, t0 * ny_, t0 * nz_);
+                        const bool m1 = cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz,
+                                                              t1 * nx_, t1 * ny_, t1 * nz_);
+                        if (m0 || (m1 && sm >= 1)) {
+                            s_last = m0 ? sm : sm - 1;
                             break;
                         }
                     }
@@ -1757,29 +1748,26 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
             }
         }
         __syncthreads();
-        // ---- 3. the listed rays, one per thread, corners from the cube (kept while a ray
-        // stays in one cell)
+        // ---- 3. the listed rays, one per thread, corners from the cube
         for (int k = tid; k < nr; k += NB_THREADS) {
             NcRay r;
             r.start<H>(p, cube, rays[k], x0, y0, z0);
-            for (int s = 0; r.advance<H>(p, cube, y0, z0, s); ++s) {
-            }
+            r.march<H>(p, cube, y0, z0);
             r.finish(p, plane);
         }
         __syncthreads();   // the cube, table and ray list are consumed
     }
     if (failed) {
-        // give tensor copies still in flight into this CTA's cubes a bounded chance to
+        // give a tensor copy still in flight into this CTA's cube a bounded chance to
         // land before the CTA exits
-        for (int b = 0; b < NBUF; ++b)
-            for (uint32_t i = 0; i < (1u << 20); ++i)
-                if (mbar_try_wait(&bars[b], (parity >> b) & 1u)) break;
+        for (uint32_t i = 0; i < (1u << 20); ++i)
+            if (mbar_try_wait(bar, parity)) break;
     }
     cp_async_wait<0>();
 }
 
 template <class St, int H>
-__global__ void __launch_bounds__(NB_THREADS, 1)
+__global__ void __launch_bounds__(NB_THREADS, 2)
 nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
     extern __shared__ __align__(128) unsigned char nsm[];
     if (threadIdx.x == 0)
@@ -1791,13 +1779,13 @@ nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map,
 
 // The near-contact pass of every lattice of a batch table in one launch.
 template <class St, int H>
-__global__ void __launch_bounds__(NB_THREADS, 1)
+__global__ void __launch_bounds__(NB_THREADS, 2)
 nc_block_kernel_batched(const NcBatchLattice* __restrict__ tab, int nlat, long long nblocks,
                         long long ghost_total) {
     extern __shared__ __align__(128) unsigned char nsm[];
-    __shared__ StepParams sp[2];
-    __shared__ int lat[2];
-    NcBatch src{tab, nlat, ghost_total, sp, lat};
+    __shared__ StepParams sp;
+    __shared__ int lat;
+    NcBatch src{tab, nlat, ghost_total, &sp, &lat};
     nc_block_pass<St, H>(src, nblocks, nsm);
 }
 
@@ -1863,12 +1851,18 @@ cudaError_t launch_nc_block(const StepParams& p, const CUtensorMap& lag_map, boo
 template <class St, int H>
 static cudaError_t launch_block_batched_tpl(const NcBatchLattice* tab, int nlat, long long nblocks,
                                            long long ghost_total, int num_sms, cudaStream_t s) {
+    static int per_sm = 0;
     if (!tab) {   // preparation only: the shared-memory attribute, outside stream capture
-        return cudaFuncSetAttribute(nc_block_kernel_batched<St, H>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)NcBlockGeo<H>::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(nc_block_kernel_batched<St, H>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)NcBlockGeo<H>::SMEM);
+        if (e == cudaSuccess && per_sm == 0)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_block_kernel_batched<St, H>,
+                                                              NB_THREADS, NcBlockGeo<H>::SMEM);
+        return e;
     }
-    const long long g = std::min<long long>((long long)num_sms, std::max<long long>(1, nblocks));
+    const long long g = std::min<long long>((long long)num_sms * std::max(1, per_sm),
+                                            std::max<long long>(1, nblocks));
     nc_block_kernel_batched<St, H><<<(unsigned)g, NB_THREADS, NcBlockGeo<H>::SMEM, s>>>(
         tab, nlat, nblocks, ghost_total);
     return cudaGetLastError();
