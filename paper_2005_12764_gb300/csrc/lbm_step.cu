@@ -1271,28 +1271,21 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 // into a shared-memory cube: by one TMA tensor copy where the cube lies inside the
 // lattice (a walled axis may reach past its walls: zero fill, never read), else by
 // asynchronous copies wrapped on periodic axes and clamped at walls. Two CTAs share an
-// SM, one cube each (the halo-9 cube and the tables take 112 KB): while one waits for
+// SM, one cube each (the halo-9 cube and the ray list take 110 KB): while one waits for
 // its copy or at a barrier between the phases below, the other works. Then:
-//  1. a bit table over 2 x 2 x 2 blocks of the cube marks where a node of the lagged
-//     field exceeds kPosBand (block b of an axis holds cube nodes 2b .. 2b+2, so the 8
-//     corners of every cell lie in one block): a sample in an unmarked block cannot
-//     carry a positive sign (the ray bound of nc_last_sample, taken from the cube);
-//  2. every node's lagged gradient G' is evaluated there, with the same expression in
-//     the same order as the step kernel's gradient (so the same bits); a node with
-//     |G'| >= 1e-3 whose ray may hold a positive sample is listed, every other node's
-//     A_h is final (0, or its pin term); the list is sorted by the ray's last possibly
-//     positive sample (a counting sort), so the rays a warp marches have similar
-//     lengths;
-//  3. the listed rays are marched, one per thread, with the trilinear corners read
-//     from the cube: the same cells, weights and interpolation order as the
-//     global-memory march, so the same values.
+//  1. every node's lagged gradient G' is evaluated in the cube, with the same
+//     expression in the same order as the step kernel's gradient (so the same bits); a
+//     node with |G'| >= 1e-3 is listed, every other node's A_h is final (0);
+//  2. the listed rays, one per thread: every sample is interpolated from the cube (the
+//     same cells, weights and interpolation order as the oracle's definition, in FP32)
+//     and classified by sign, all samples of every ray in turn, so that the lanes of a
+//     warp stay together; A_h follows from the sign masks and the four samples around
+//     the two crossings (NcRay::measure).
 // Every node's A_h is written (0 where no film is within h_cut): the field needs no
 // clearing between passes and no candidate list. The kernel first writes the ghost
 // copies of the step's input populations (two-copy storage).
 constexpr int NB_X = 16, NB_Y = 8, NB_Z = 8, NB_NODES = NB_X * NB_Y * NB_Z;
 constexpr int NB_THREADS = 512, NB_PER_THREAD = NB_NODES / NB_THREADS;
-constexpr int NB_BINS = 32;   // ray lengths s_last + 1 <= nsamp <= 25
-static_assert(NB_NODES < (1 << 16), "node index and s_last share one int in the ray list");
 
 template <int H>
 struct NcBlockGeo {
@@ -1301,17 +1294,8 @@ struct NcBlockGeo {
     static constexpr int ROWS = SY * SZ;
     static constexpr int CHUNKS = SX / 4;          // 16-byte chunks per cube row
     static constexpr size_t CUBE_BYTES = (size_t)SX * SY * SZ * sizeof(float);
-    // bit table: blocks of 2 x 2 x 2 cube nodes, one 32-bit word of x blocks per (y, z)
-    // block (cell corners reach cube node S - 2, in block S/2 - 1; every S is even)
-    static constexpr int TBX = SX / 2, TBY = SY / 2, TBZ = SZ / 2;
-    static_assert(TBX <= 32, "one word of x blocks");
-    static constexpr size_t TAB_BYTES = (size_t)TBY * TBZ * sizeof(uint32_t);
-    // per cube row, its x blocks holding a node above kPosBand (while the table is
-    // built; the same space then holds the ray list)
-    static constexpr size_t LIST_BYTES =
-        (ROWS > NB_NODES ? ROWS : NB_NODES) * sizeof(uint32_t);
-    static constexpr size_t FIXED = 4 * sizeof(unsigned long long) + TAB_BYTES + LIST_BYTES +
-                                    2 * NB_BINS * sizeof(int) + NB_NODES;
+    // the mbarrier (4 slots), the list of the block's rays and its length
+    static constexpr size_t FIXED = 4 * sizeof(unsigned long long) + (NB_NODES + 4) * sizeof(int);
     static constexpr size_t SMEM = CUBE_BYTES + FIXED;
 };
 
@@ -1364,19 +1348,6 @@ __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int
         c.fz = 1.0f;
     }
     c.o = (cz0 * G::SY + cy0) * G::SX + cx0;
-}
-// Whether the block of the bit table holding the cell of a ray sample (the corner
-// cube_cell finds, halved per axis) is marked.
-template <int H>
-__device__ __forceinline__ bool cube_sample_marked(const StepParams& p, const uint32_t* tab, int y,
-                                                   int z, int y0, int z0, int lx, int ly, int lz,
-                                                   float ox, float oy, float oz) {
-    using G = NcBlockGeo<H>;
-    const int ix = (int)floorf(ox), iy = (int)floorf(oy), iz = (int)floorf(oz);
-    int cy0 = ly + H + iy, cz0 = lz + H + iz;
-    if (p.wall_y && y + iy == p.ny - 1) cy0 = p.ny - 2 - y0 + H;
-    if (p.wall_z && z + iz == p.nz - 1) cz0 = p.nz - 2 - z0 + H;
-    return (tab[(cz0 >> 1) * G::TBY + (cy0 >> 1)] >> ((lx + G::HX + ix) >> 1)) & 1u;
 }
 template <int H>
 __device__ __forceinline__ void cube_corners(const float* cube, const CubeCell& c, float (&v)[8]) {
@@ -1475,16 +1446,13 @@ __device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtenso
     cp_async_commit();
 }
 
-// One ray of the block pass: node, direction, bound and crossing search.
+// One ray of the block pass: node, direction, and A_h from its samples.
 struct NcRay {
-    int lx, ly, lz, x, y, z, s_last;
+    int lx, ly, lz, x, y, z, s_end;
     float nx_, ny_, nz_, a;
-    NcMarch mr;
     template <int H>
-    __device__ __forceinline__ void start(const StepParams& p, const float* cube, int e, int x0,
+    __device__ __forceinline__ void start(const StepParams& p, const float* cube, int idx, int x0,
                                           int y0, int z0) {
-        const int idx = e & 0xffff;
-        s_last = e >> 16;
         lx = idx % NB_X;
         ly = (idx / NB_X) % NB_Y;
         lz = idx / (NB_X * NB_Y);
@@ -1494,9 +1462,10 @@ struct NcRay {
         float Gx, Gy, Gz;
         cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
         nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
+        s_end = nc_sample_end(p, y, z, ny_, nz_);
         a = 0.0f;
     }
-    // The lagged colour field at sample s (t = -1 + s/2), interpolated from the cube.
+    // The lagged colour field at the sample at t, interpolated from the cube.
     template <int H>
     __device__ __forceinline__ float value(const StepParams& p, const float* cube, int y0, int z0,
                                            float t) const {
@@ -1506,18 +1475,48 @@ struct NcRay {
         cube_corners<H>(cube, cell, v);
         return cube_interp(cell, v);
     }
-    // The march: samples 0 .. s_last in order until A_h is decided, two samples
-    // interpolated per turn (independent work) and fed in order.
+    // A_h of the film along the ray: the march of NcMarch over samples 0 .. s_end - 1,
+    // evaluated from the samples' sign classes. Samples within kSignBand of zero carry
+    // no sign and are skipped. The downward crossing is at the first negative sample j
+    // whose previous signed sample jp is positive; the upward one at the first positive
+    // sample k after j, whose previous signed sample kp is negative. The march stops
+    // with A_h = 0 at a signed sample m between j and k with t_m - t_d >= h_cut, i.e.
+    // when kp != j and t_kp - t_d >= h_cut; otherwise A_h = A_h(t_u - t_d), each
+    // crossing located by linear interpolation between its two samples (the same
+    // expressions as the march: the same bits).
     template <int H>
-    __device__ __forceinline__ void march(const StepParams& p, const float* cube, int y0, int z0) {
-        for (int s = 0; s <= s_last; s += 2) {
-            const float t0 = -1.0f + 0.5f * (float)s, t1 = t0 + 0.5f;
-            const bool two = s + 1 <= s_last;
-            const float v0 = value<H>(p, cube, y0, z0, t0);
-            const float v1 = value<H>(p, cube, y0, z0, two ? t1 : t0);
-            if (mr.feed(p, t0, v0, a)) return;
-            if (!two || mr.feed(p, t1, v1, a)) return;
+    __device__ __forceinline__ void measure(const StepParams& p, const float* cube, int y0, int z0) {
+        uint32_t P = 0u, N = 0u;
+#pragma unroll 4
+        for (int s = 0; s < s_end; ++s) {
+            const float v = value<H>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
+            P |= (v > kSignBand ? 1u : 0u) << s;
+            N |= (v < -kSignBand ? 1u : 0u) << s;
         }
+        const uint32_t S = P | N;
+        int jp = -1, j = -1;
+        for (uint32_t m = S, prev = 32u; m != 0u; m &= m - 1u) {
+            const uint32_t i = (uint32_t)(__ffs((int)m) - 1);
+            if (prev < 32u && ((P >> prev) & 1u) && ((N >> i) & 1u)) {
+                jp = (int)prev;
+                j = (int)i;
+                break;
+            }
+            prev = i;
+        }
+        if (j < 0) return;
+        const uint32_t later = P & ~((2u << j) - 1u);   // positive samples after j
+        if (later == 0u) return;
+        const int k = __ffs((int)later) - 1;
+        const int kp = 31 - __clz((int)(S & ((1u << k) - 1u)));
+        const float t_jp = -1.0f + 0.5f * (float)jp, t_j = -1.0f + 0.5f * (float)j;
+        const float v_jp = value<H>(p, cube, y0, z0, t_jp), v_j = value<H>(p, cube, y0, z0, t_j);
+        const float t_d = t_jp + (t_j - t_jp) * v_jp / (v_jp - v_j);
+        const float t_kp = -1.0f + 0.5f * (float)kp, t_k = -1.0f + 0.5f * (float)k;
+        if (kp != j && t_kp - t_d >= p.h_cut) return;
+        const float v_kp = value<H>(p, cube, y0, z0, t_kp), v_k = value<H>(p, cube, y0, z0, t_k);
+        const float t_u = t_kp + (t_k - t_kp) * v_kp / (v_kp - v_k);
+        a = A_h(p, t_u - t_d);
     }
     __device__ __forceinline__ void finish(const StepParams& p, size_t plane) {
         const size_t node = (size_t)z * plane + (size_t)y * p.nx + x;
@@ -1610,13 +1609,8 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
     float* cube = reinterpret_cast<float*>(nsm);                           // [SZ][SY][SX]
     unsigned char* q = nsm + G::CUBE_BYTES;                                // 128-byte aligned
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(q);    // (4 slots, 1 used)
-    uint32_t* tab = reinterpret_cast<uint32_t*>(q + 4 * sizeof(unsigned long long));  // [TBZ][TBY]
-    int* rays = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(tab) + G::TAB_BYTES);
-    uint32_t* rowbits = reinterpret_cast<uint32_t*>(rays);                 // [SZ][SY], then the list
-    // (rays: {node | s_last << 16}, sorted by s_last)
-    int* bins = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(rays) + G::LIST_BYTES);
-    int* cursor = bins + NB_BINS;                                          // [NB_BINS] scatter
-    unsigned char* slast = reinterpret_cast<unsigned char*>(cursor + NB_BINS);   // [NB_NODES] s_last + 1
+    int* rays = reinterpret_cast<int*>(q + 4 * sizeof(unsigned long long));   // [NB_NODES] listed nodes
+    int* nrays = rays + NB_NODES;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -1651,111 +1645,50 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
             failed = true;
             break;
         }
-        // ---- 1. the ray-bound table: per cube row, the x blocks (nodes 2b .. 2b+2)
-        // holding a node above kPosBand; then each table word ORs the 3 x 3 rows of its
-        // (y, z) block
-        for (int row = tid; row < G::ROWS; row += NB_THREADS) {
-            const float4* r = reinterpret_cast<const float4*>(cube + (size_t)row * G::SX);
-            uint64_t m = 0;
-#pragma unroll
-            for (int c = 0; c < G::CHUNKS; ++c) {
-                const float4 v = r[c];
-                m |= (uint64_t)((v.x > kPosBand ? 1u : 0u) | (v.y > kPosBand ? 2u : 0u) |
-                                (v.z > kPosBand ? 4u : 0u) | (v.w > kPosBand ? 8u : 0u)) << (4 * c);
-            }
-            const uint64_t c = m | (m >> 1) | (m >> 2);   // bit k: nodes k .. k+2
-            rowbits[row] = even_bits((uint32_t)c) | (even_bits((uint32_t)(c >> 32)) << 16);
-        }
-        if (tid < NB_BINS) bins[tid] = 0;
+        // ---- 1. gradients and thresholds of the block's nodes: a node with |G'| >= 1e-3
+        // and a first sample inside the fluid is listed; every other node's A_h is final
+        // (0, or its pin term when it has a ray of no samples)
+        if (tid == 0) *nrays = 0;
         __syncthreads();
-        for (int w = tid; w < G::TBY * G::TBZ; w += NB_THREADS) {
-            const int by = w % G::TBY, bz = w / G::TBY;
-            uint32_t v = 0u;
-#pragma unroll
-            for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-                    v |= rowbits[min(2 * bz + dz, G::SZ - 1) * G::SY + min(2 * by + dy, G::SY - 1)];
-            tab[w] = v;
-        }
-        __syncthreads();
-        // ---- 2. gradients, thresholds and ray bounds of the block's nodes; nodes
-        // without a ray to march take their final A_h here
 #pragma unroll
         for (int j = 0; j < NB_PER_THREAD; ++j) {
             const int idx = tid + j * NB_THREADS;
             const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
             const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            int s_last = -1;
+            bool listed = false;
             if (x < p.nx && y < p.ny && z < p.nz) {
                 float Gx, Gy, Gz, nx_, ny_, nz_;
                 cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
                 float a = 0.0f;
                 if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
-                    // the last sample inside the fluid whose cell's block is marked (two
-                    // samples per turn: independent lookups; the sample before s = 0
-                    // lies 1.5 units from the node, inside the cube, and is not used)
-                    for (int sm = nc_sample_end(p, y, z, ny_, nz_) - 1; sm >= 0; sm -= 2) {
-                        const float t0 = -1.0f + 0.5f * (float)sm, t1 = t0 - 0.5f;
-                        const bool m0 = cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz,
-                                                              t0 * nx_, t0 * ny_, t0 * nz_);
-                        const bool m1 = cube_sample_marked<H>(p, tab, y, z, y0, z0, lx, ly, lz,
-                                                              t1 * nx_, t1 * ny_, t1 * nz_);
-                        if (m0 || (m1 && sm >= 1)) {
-                            s_last = m0 ? sm : sm - 1;
-                            break;
-                        }
-                    }
-                    if (s_last < 0 && p.pin_d2) {
+                    listed = nc_sample_end(p, y, z, ny_, nz_) > 0;
+                    if (!listed && p.pin_d2) {
                         const unsigned d2 = __ldg(p.pin_d2 + (size_t)z * plane + (size_t)y * p.nx + x);
                         if (d2 != 255u) a = A_h(p, sqrtf((float)d2));
                     }
                 }
-                if (s_last < 0) p.ah[(size_t)z * plane + (size_t)y * p.nx + x] = a;
+                if (!listed) p.ah[(size_t)z * plane + (size_t)y * p.nx + x] = a;
             }
-            if (s_last >= 0) {   // one atomic per distinct ray length in the warp
-                const unsigned peers = __match_any_sync(__activemask(), s_last);
-                if (lane == __ffs(peers) - 1) atomicAdd(&bins[s_last], __popc(peers));
-            }
-            slast[idx] = (unsigned char)(s_last + 1);
+            // (one atomic per warp)
+            const unsigned m = __ballot_sync(0xffffffffu, listed);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(nrays, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (listed) rays[base + __popc(m & ((1u << lane) - 1u))] = idx;
         }
         __syncthreads();
-        // counting sort by s_last, longest rays first
-        if (tid < 32) {
-            const int n = tid < NB_BINS ? bins[NB_BINS - 1 - tid] : 0;
-            int incl = n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            if (tid < NB_BINS) cursor[NB_BINS - 1 - tid] = incl - n;
-            if (tid == 31) bins[0] = incl;   // (bins[] is not read again) total rays
-        }
-        __syncthreads();
-        const int nr = bins[0];
-#pragma unroll
-        for (int j = 0; j < NB_PER_THREAD; ++j) {
-            const int idx = tid + j * NB_THREADS;
-            const int sl = (int)slast[idx] - 1;
-            if (sl >= 0) {
-                const unsigned peers = __match_any_sync(__activemask(), sl);
-                const int leader = __ffs(peers) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&cursor[sl], __popc(peers));
-                base = __shfl_sync(peers, base, leader);
-                rays[base + __popc(peers & ((1u << lane) - 1u))] = idx | (sl << 16);
-            }
-        }
-        __syncthreads();
-        // ---- 3. the listed rays, one per thread, corners from the cube
+        const int nr = *nrays;
+        // ---- 2. the listed rays, one per thread: the sign class of every sample (all
+        // rays of a lattice without walls have the same samples, so the lanes of a warp
+        // stay together), then A_h from the sign masks and the samples around the two
+        // crossings, interpolated again
         for (int k = tid; k < nr; k += NB_THREADS) {
             NcRay r;
             r.start<H>(p, cube, rays[k], x0, y0, z0);
-            r.march<H>(p, cube, y0, z0);
+            r.measure<H>(p, cube, y0, z0);
             r.finish(p, plane);
         }
-        __syncthreads();   // the cube, table and ray list are consumed
+        __syncthreads();   // the cube and the ray list are consumed
     }
     if (failed) {
         // give a tensor copy still in flight into this CTA's cube a bounded chance to
