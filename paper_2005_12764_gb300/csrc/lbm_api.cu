@@ -693,6 +693,7 @@ static void fill_step_params(lbm_ctx* c) {
     s.tiles_y = (p.ny + ty - 1) / ty;
     s.err = c->err_word;
     s.aa_layout = c->aa ? c->layout : -1;
+    s.nc_seg = nc_segment_blocks(p.nx, p.ny, p.nz, c->num_sms);
     s.ah = c->ah;
     const WorkSplit w = work_split(p, c->num_sms);
     s.zparts = w.zparts;
@@ -856,13 +857,14 @@ extern "C" lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
                 return fail(nullptr, LBM_ECUDA, "cuTensorMapEncodeTiled failed");
             }
         }
-        // the near-contact pass copies cubes of a colour field (3-D, x fastest) with one
-        // tensor copy where the cube lies inside the lattice: rows must be a multiple of
-        // 16 bytes long, and the lattice at least a cube wide
+        // the near-contact pass copies the planes of its halo cubes from a colour field
+        // (3-D, x fastest) with one tensor copy per plane where the cube lies inside the
+        // lattice in x and y: rows must be a multiple of 16 bytes long, and the lattice
+        // at least a cube wide in x and y
         if (p->A_nc > 0.0 && p->nx % 4 == 0) {
             int box[3];
             nc_cube_box(p->h_cut > 0 ? p->h_cut : 2.0 * p->h_min, box);
-            if (p->nx >= box[0] && p->ny >= box[1] && p->nz >= box[2]) {
+            if (p->nx >= box[0] && p->ny >= box[1]) {
                 const cuuint64_t pd[3] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
                 const cuuint64_t ps[2] = {(cuuint64_t)p->nx * sizeof(float),
                                           (cuuint64_t)p->nx * p->ny * sizeof(float)};

@@ -25,6 +25,7 @@ cudaError_t launch_nc_batched(const NcBatchLattice* tab, int nlat, long long nbl
 int nc_halo(double h_cut);
 cudaError_t prepare_nc_batched(int storage, double h_cut);
 long long nc_block_count(const StepParams& p);
+int nc_segment_blocks(int nx, int ny, int nz, int num_sms);
 cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 cudaError_t launch_aa_step(const StepParams& p, int layout, int storage, int num_sms,
                            cudaStream_t s);

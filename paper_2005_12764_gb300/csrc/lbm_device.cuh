@@ -227,7 +227,7 @@ struct StepParams {
     int* err;               // device error word: 1 = a bounded wait gave up
     int aa_layout;          // in-place (AA) storage: where the state's populations are
                             // (0 or 1, see aa_slot); -1 for the two-copy storage
-    int pad_;
+    int nc_seg;             // near-contact pass: blocks per z segment of a block column
 };
 
 static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");

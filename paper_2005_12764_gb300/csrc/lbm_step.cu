@@ -1264,15 +1264,19 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 
 // ---------------------------------------------------------------- near-contact pass, block form
 // A_h of every node from the lagged colour field, one NB_X x NB_Y x NB_Z block of nodes
-// at a time (persistent CTAs, blocks in x-fastest order, so the CTAs resident at one
-// time work on neighbouring blocks and their halos come from L2). The block's lagged
-// field and a halo of H nodes around it -- the farthest trilinear corner a ray of
-// samples up to t = h_cut + 2 reaches is floor(h_cut) + 3 <= H nodes away -- are copied
-// into a shared-memory cube: by one TMA tensor copy where the cube lies inside the
-// lattice (a walled axis may reach past its walls: zero fill, never read), else by
-// asynchronous copies wrapped on periodic axes and clamped at walls. Two CTAs share an
-// SM, one cube each (the halo-9 cube and the ray list take 110 KB): while one waits for
-// its copy or at a barrier between the phases below, the other works. Then:
+// at a time. A work item is a column of blocks (bx, by) and a segment of up to nc_seg
+// consecutive blocks along z (persistent CTAs, items in x-fastest order, so that the
+// CTAs resident at one time work on neighbouring columns and their halos come from L2).
+// The block's lagged field and a halo of H nodes around it -- the farthest trilinear
+// corner a ray of samples up to t = h_cut + 2 reaches is floor(h_cut) + 3 <= H nodes
+// away -- sit in a shared-memory cube, kept as a ring of SZ planes along z: the first
+// block of a segment copies all of its planes, every later block only the NB_Z planes
+// that enter its window (a third of the copying). Each plane is one TMA tensor copy
+// where the cube lies inside the lattice in x and y (a walled y axis may reach past its
+// walls: zero fill, never read), else asynchronous copies wrapped on periodic axes and
+// clamped at walls. Two CTAs share an SM, one cube each (the halo-9 cube and the ray
+// list take 112 KB): while one waits for its copy or at a barrier between the phases
+// below, the other works. Then:
 //  1. every node's lagged gradient G' is evaluated in the cube, with the same
 //     expression in the same order as the step kernel's gradient (so the same bits); a
 //     node with |G'| >= 1e-3 is listed, every other node's A_h is final (0);
@@ -1293,7 +1297,10 @@ struct NcBlockGeo {
     static constexpr int SX = NB_X + 2 * HX, SY = NB_Y + 2 * H, SZ = NB_Z + 2 * H;
     static constexpr int ROWS = SY * SZ;
     static constexpr int CHUNKS = SX / 4;          // 16-byte chunks per cube row
-    static constexpr size_t CUBE_BYTES = (size_t)SX * SY * SZ * sizeof(float);
+    // floats per cube plane (SY rows of SX), padded so that every plane starts on a
+    // 128-byte boundary (the destination of a tensor copy)
+    static constexpr int PLANE = (SX * SY + 31) / 32 * 32;
+    static constexpr size_t CUBE_BYTES = (size_t)PLANE * SZ * sizeof(float);
     // the mbarrier (4 slots), the list of the block's rays and its length
     static constexpr size_t FIXED = 4 * sizeof(unsigned long long) + (NB_NODES + 4) * sizeof(int);
     static constexpr size_t SMEM = CUBE_BYTES + FIXED;
@@ -1321,17 +1328,27 @@ __device__ __forceinline__ int halo_index(int a, int n, bool walled) {
     return walled ? min(max(a, 0), n - 1) : wrap_near(a, n);
 }
 
+// Ring slot of window plane k (0 <= k < 2 SZ) of a block whose window starts in slot
+// zbase: the cube keeps the SZ planes of a block's window in a ring along z, so that
+// the next block of the same column reuses the SZ - NB_Z planes they share.
+template <int H>
+__device__ __forceinline__ int ring_slot(int zbase, int k) {
+    const int r = zbase + k;
+    return r >= NcBlockGeo<H>::SZ ? r - NcBlockGeo<H>::SZ : r;
+}
+
 // Cell of a ray sample in the cube: ray_cell's corners and fractions, with the corner
-// (ix0, iy0, iz0) as an offset into the cube (whose copies of wrapped nodes make the
-// other corners o + 1, o + SX, o + SX SY away).
+// (ix0, iy0, iz0) as offsets into the cube's ring: o0 in the plane of iz0, o1 in the
+// plane of iz0 + 1 (the cube's copies of wrapped nodes make the other corners 1, SX
+// and SX + 1 further on).
 struct CubeCell {
-    int o;
+    int o0, o1;
     float fx, fy, fz;
 };
 template <int H>
 __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int y0, int z0,
-                                          int lx, int ly, int lz, float ox, float oy, float oz,
-                                          CubeCell& c) {
+                                          int lx, int ly, int lz, int zbase, float ox, float oy,
+                                          float oz, CubeCell& c) {
     using G = NcBlockGeo<H>;
     const float flx = floorf(ox), fly = floorf(oy), flz = floorf(oz);
     c.fx = ox - flx;
@@ -1347,20 +1364,23 @@ __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int
         cz0 = p.nz - 2 - z0 + H;
         c.fz = 1.0f;
     }
-    c.o = (cz0 * G::SY + cy0) * G::SX + cx0;
+    const int r = cy0 * G::SX + cx0;
+    c.o0 = ring_slot<H>(zbase, cz0) * G::PLANE + r;
+    c.o1 = ring_slot<H>(zbase, cz0 + 1) * G::PLANE + r;
 }
 template <int H>
 __device__ __forceinline__ void cube_corners(const float* cube, const CubeCell& c, float (&v)[8]) {
     using G = NcBlockGeo<H>;
-    const float* b = cube + c.o;
-    v[0] = b[0];
-    v[1] = b[1];
-    v[2] = b[G::SX];
-    v[3] = b[G::SX + 1];
-    v[4] = b[G::SX * G::SY];
-    v[5] = b[G::SX * G::SY + 1];
-    v[6] = b[G::SX * G::SY + G::SX];
-    v[7] = b[G::SX * G::SY + G::SX + 1];
+    const float* b0 = cube + c.o0;
+    const float* b1 = cube + c.o1;
+    v[0] = b0[0];
+    v[1] = b0[1];
+    v[2] = b0[G::SX];
+    v[3] = b0[G::SX + 1];
+    v[4] = b1[0];
+    v[5] = b1[1];
+    v[6] = b1[G::SX];
+    v[7] = b1[G::SX + 1];
 }
 __device__ __forceinline__ float cube_interp(const CubeCell& c, const float (&v)[8]) {
     const float c0 = ray_lerp(ray_lerp(v[0], v[1], c.fx), ray_lerp(v[2], v[3], c.fx), c.fy);
@@ -1372,11 +1392,14 @@ __device__ __forceinline__ float cube_interp(const CubeCell& c, const float (&v)
 // terms of gradient_global in its order; a neighbour beyond a wall takes the centre value.
 template <int H>
 __device__ __forceinline__ void cube_gradient(const StepParams& p, const float* cube, int x, int y,
-                                              int z, int lx, int ly, int lz, float& Gx, float& Gy,
-                                              float& Gz) {
+                                              int z, int lx, int ly, int lz, int zbase, float& Gx,
+                                              float& Gy, float& Gz) {
     using G = NcBlockGeo<H>;
-    const float* c0 = cube + ((lz + H) * G::SY + (ly + H)) * G::SX + (lx + G::HX);
-    const float phic = c0[0];
+    const int r = (ly + H) * G::SX + (lx + G::HX);
+    const float* pm = cube + ring_slot<H>(zbase, lz + H - 1) * G::PLANE + r;
+    const float* p0 = cube + ring_slot<H>(zbase, lz + H) * G::PLANE + r;
+    const float* pp = cube + ring_slot<H>(zbase, lz + H + 1) * G::PLANE + r;
+    const float phic = p0[0];
     const bool ylo = p.wall_y && y == 0, yhi = p.wall_y && y == p.ny - 1;
     const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
     Gx = Gy = Gz = 0.0f;
@@ -1385,61 +1408,70 @@ __device__ __forceinline__ void cube_gradient(const StepParams& p, const float* 
         if (i == 9) continue;
         const bool wall = (cy(i) < 0 && ylo) || (cy(i) > 0 && yhi) || (cz(i) < 0 && zlo) ||
                           (cz(i) > 0 && zhi);
-        const float v = wall ? phic : c0[(cz(i) * G::SY + cy(i)) * G::SX + cx(i)];
+        const float* pl = cz(i) < 0 ? pm : (cz(i) > 0 ? pp : p0);
+        const float v = wall ? phic : pl[cy(i) * G::SX + cx(i)];
         grad_add(i, v, Gx, Gy, Gz);
     }
 }
 
-// Origin of block b of the lattice's block grid.
-__device__ __forceinline__ void nc_block_origin(const StepParams& p, long long b, int& x0, int& y0,
-                                                int& z0) {
+// Work item t of a lattice's near-contact pass: block column (bx, by) and the blocks
+// bz0 .. bz1-1 of its segment along z.
+__device__ __forceinline__ void nc_item(const StepParams& p, long long t, int& bx, int& by, int& bz0,
+                                        int& bz1) {
     const int bxn = (p.nx + NB_X - 1) / NB_X, byn = (p.ny + NB_Y - 1) / NB_Y;
-    const int bx = (int)(b % bxn);
-    const long long r = b / bxn;
-    x0 = bx * NB_X;
-    y0 = (int)(r % byn) * NB_Y;
-    z0 = (int)(r / byn) * NB_Z;
+    const int bzn = (p.nz + NB_Z - 1) / NB_Z, seg = p.nc_seg > 0 ? p.nc_seg : 1;
+    bx = (int)(t % bxn);
+    const long long r = t / bxn;
+    by = (int)(r % byn);
+    bz0 = (int)(r / byn) * seg;
+    bz1 = min(bzn, bz0 + seg);
 }
 
-// Starts the copy of block b's cube into `cube`: one tensor copy by thread 0 (completing
-// on `bar`, which every fill arrives at once, with 0 bytes when not used) or the
-// asynchronous copies of every thread (one commit group per fill, possibly empty).
+// Starts the copy of window planes k0 .. SZ-1 of the block at (x0, y0, z0) into their
+// ring slots: one tensor copy per plane by thread 0 (completing on `bar`, which thread
+// 0 arrives at once per fill, with 0 bytes when it is not used) where the cube lies
+// inside the lattice in x and y (a walled y axis may reach past its walls: zero fill,
+// never read), else the asynchronous copies of every thread, wrapped on periodic axes
+// and clamped at walls (one commit group per fill). Planes beyond a z wall are clamped
+// (never read).
 template <int H>
-__device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtensorMap* map,
-                                              bool tma_ok, long long b, float* cube,
-                                              unsigned long long* bar) {
+__device__ __forceinline__ void nc_fill_planes(const StepParams& p, const CUtensorMap* map,
+                                               bool tma_ok, int x0, int y0, int z0, int k0,
+                                               int zbase, float* cube, unsigned long long* bar) {
     using G = NcBlockGeo<H>;
-    int x0, y0, z0;
-    nc_block_origin(p, b, x0, y0, z0);
     const bool inside = tma_ok && x0 >= G::HX && x0 + NB_X + G::HX <= p.nx &&
-                        (p.wall_y || (y0 >= H && y0 + NB_Y + H <= p.ny)) &&
-                        (p.wall_z || (z0 >= H && z0 + NB_Z + H <= p.nz));
+                        (p.wall_y || (y0 >= H && y0 + NB_Y + H <= p.ny));
     const int tid = threadIdx.x;
     if (inside) {
         if (tid == 0) {
-            mbar_arrive_tx(bar, (uint32_t)G::CUBE_BYTES);
-            tma_load_3d(cube, map, x0 - G::HX, y0 - H, z0 - H, bar);
+            // (each copy delivers SY rows of SX values: a plane without its padding)
+            mbar_arrive_tx(bar, (uint32_t)((G::SZ - k0) * G::SX * G::SY * sizeof(float)));
+            for (int k = k0; k < G::SZ; ++k)
+                tma_load_3d(cube + (size_t)ring_slot<H>(zbase, k) * G::PLANE, map, x0 - G::HX,
+                            y0 - H, halo_index(z0 - H + k, p.nz, p.wall_z), bar);
         }
     } else {
         if (tid == 0) mbar_arrive_tx(bar, 0u);
+        const int rows = (G::SZ - k0) * G::SY;
         if ((p.nx & 3) == 0) {   // 16-byte chunks then never straddle the periodic seam
-            for (int k = tid; k < G::ROWS * G::CHUNKS; k += NB_THREADS) {
-                const int c = k % G::CHUNKS, row = k / G::CHUNKS;
-                const int ly = row % G::SY, lz = row / G::SY;
+            for (int e = tid; e < rows * G::CHUNKS; e += NB_THREADS) {
+                const int c = e % G::CHUNKS, row = e / G::CHUNKS;
+                const int ly = row % G::SY, k = k0 + row / G::SY;
                 const int gy = halo_index(y0 - H + ly, p.ny, p.wall_y);
-                const int gz = halo_index(z0 - H + lz, p.nz, p.wall_z);
+                const int gz = halo_index(z0 - H + k, p.nz, p.wall_z);
                 const int gx = wrap_near(x0 - G::HX + 4 * c, p.nx);
-                cp_async16(cube + (size_t)row * G::SX + 4 * c,
+                cp_async16(cube + (size_t)ring_slot<H>(zbase, k) * G::PLANE + ly * G::SX + 4 * c,
                            p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
             }
         } else {
-            for (int k = tid; k < G::ROWS * G::SX; k += NB_THREADS) {
-                const int c = k % G::SX, row = k / G::SX;
-                const int ly = row % G::SY, lz = row / G::SY;
+            for (int e = tid; e < rows * G::SX; e += NB_THREADS) {
+                const int c = e % G::SX, row = e / G::SX;
+                const int ly = row % G::SY, k = k0 + row / G::SY;
                 const int gy = halo_index(y0 - H + ly, p.ny, p.wall_y);
-                const int gz = halo_index(z0 - H + lz, p.nz, p.wall_z);
+                const int gz = halo_index(z0 - H + k, p.nz, p.wall_z);
                 const int gx = wrap_near(x0 - G::HX + c, p.nx);
-                cp_async4(cube + k, p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
+                cp_async4(cube + (size_t)ring_slot<H>(zbase, k) * G::PLANE + ly * G::SX + c,
+                          p.phi_lag + ((size_t)gz * p.ny + gy) * p.nx + gx);
             }
         }
     }
@@ -1448,11 +1480,12 @@ __device__ __forceinline__ void nc_fill_start(const StepParams& p, const CUtenso
 
 // One ray of the block pass: node, direction, and A_h from its samples.
 struct NcRay {
-    int lx, ly, lz, x, y, z, s_end;
+    int lx, ly, lz, x, y, z, s_end, zb;
     float nx_, ny_, nz_, a;
     template <int H>
     __device__ __forceinline__ void start(const StepParams& p, const float* cube, int idx, int x0,
-                                          int y0, int z0) {
+                                          int y0, int z0, int zbase) {
+        zb = zbase;
         lx = idx % NB_X;
         ly = (idx / NB_X) % NB_Y;
         lz = idx / (NB_X * NB_Y);
@@ -1460,7 +1493,7 @@ struct NcRay {
         y = y0 + ly;
         z = z0 + lz;
         float Gx, Gy, Gz;
-        cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
+        cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, zb, Gx, Gy, Gz);
         nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
         s_end = nc_sample_end(p, y, z, ny_, nz_);
         a = 0.0f;
@@ -1470,7 +1503,7 @@ struct NcRay {
     __device__ __forceinline__ float value(const StepParams& p, const float* cube, int y0, int z0,
                                            float t) const {
         CubeCell cell;
-        cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, t * nx_, t * ny_, t * nz_, cell);
+        cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, zb, t * nx_, t * ny_, t * nz_, cell);
         float v[8];
         cube_corners<H>(cube, cell, v);
         return cube_interp(cell, v);
@@ -1595,16 +1628,17 @@ struct NcBatch {
     }
 };
 
-// Blocks of a lattice's block grid.
+// Work items of a lattice's near-contact pass: block columns x segments of nc_seg blocks.
 __host__ __device__ inline long long nc_blocks(const StepParams& p) {
+    const int seg = p.nc_seg > 0 ? p.nc_seg : 1, bzn = (p.nz + NB_Z - 1) / NB_Z;
     return (long long)((p.nx + NB_X - 1) / NB_X) * ((p.ny + NB_Y - 1) / NB_Y) *
-           ((p.nz + NB_Z - 1) / NB_Z);
+           ((bzn + seg - 1) / seg);
 }
 
 // The pass over `nblocks` blocks of `src` (see nc_block_kernel below for what a block
 // does); the CTA takes blocks blockIdx.x, + gridDim.x, ...
 template <class St, int H, class Src>
-__device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsigned char* nsm) {
+__device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsigned char* nsm) {
     using G = NcBlockGeo<H>;
     float* cube = reinterpret_cast<float*>(nsm);                           // [SZ][SY][SX]
     unsigned char* q = nsm + G::CUBE_BYTES;                                // 128-byte aligned
@@ -1627,68 +1661,77 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nblocks, unsig
     }
     uint32_t parity = 0u;
     bool failed = false;
-    for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        // (the cube's reads of the last block precede this copy into it: the barrier
-        // that ended that block, then the proxy fence)
-        fence_proxy_async();
-        const long long lb = src.bind(b);
-        nc_fill_start<H>(src.params(), src.lag_map(), src.tma_ok(), lb, cube, bar);
-        cp_async_wait<0>();
+    for (long long item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        const long long li = src.bind(item);
         const StepParams& p = src.params();
         const size_t plane = (size_t)p.nx * p.ny;
-        int x0, y0, z0;
-        nc_block_origin(p, lb, x0, y0, z0);
-        // (a wait that gives up leaves its phase pending: the drain below waits on it)
-        if (mbar_wait(bar, parity, p.err)) parity ^= 1u;
-        else failed = true;
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
-        }
-        // ---- 1. gradients and thresholds of the block's nodes: a node with |G'| >= 1e-3
-        // and a first sample inside the fluid is listed; every other node's A_h is final
-        // (0, or its pin term when it has a ray of no samples)
-        if (tid == 0) *nrays = 0;
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < NB_PER_THREAD; ++j) {
-            const int idx = tid + j * NB_THREADS;
-            const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
-            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            bool listed = false;
-            if (x < p.nx && y < p.ny && z < p.nz) {
-                float Gx, Gy, Gz, nx_, ny_, nz_;
-                cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, Gx, Gy, Gz);
-                float a = 0.0f;
-                if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
-                    listed = nc_sample_end(p, y, z, ny_, nz_) > 0;
-                    if (!listed && p.pin_d2) {
-                        const unsigned d2 = __ldg(p.pin_d2 + (size_t)z * plane + (size_t)y * p.nx + x);
-                        if (d2 != 255u) a = A_h(p, sqrtf((float)d2));
-                    }
-                }
-                if (!listed) p.ah[(size_t)z * plane + (size_t)y * p.nx + x] = a;
+        int bx, by, bz0, bz1;
+        nc_item(p, li, bx, by, bz0, bz1);
+        const int x0 = bx * NB_X, y0 = by * NB_Y;
+        int zbase = 0;   // ring slot of the current block's first window plane
+        for (int bz = bz0; bz < bz1; ++bz) {
+            const int z0 = bz * NB_Z;
+            // the first block of the segment copies its whole window, every later one the
+            // NB_Z planes that enter it (into the slots of the planes that left); (a ring
+            // slot's reads of the last block precede the copy into it: the barrier that
+            // ended that block, then the proxy fence)
+            fence_proxy_async();
+            nc_fill_planes<H>(p, src.lag_map(), src.tma_ok(), x0, y0, z0, bz == bz0 ? 0 : G::SZ - NB_Z,
+                              zbase, cube, bar);
+            cp_async_wait<0>();
+            // (a wait that gives up leaves its phase pending: the drain below waits on it)
+            if (mbar_wait(bar, parity, p.err)) parity ^= 1u;
+            else failed = true;
+            if (__syncthreads_or(failed)) {
+                failed = true;
+                break;
             }
-            // (one atomic per warp)
-            const unsigned m = __ballot_sync(0xffffffffu, listed);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(nrays, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (listed) rays[base + __popc(m & ((1u << lane) - 1u))] = idx;
+            // ---- 1. gradients and thresholds of the block's nodes: a node with |G'| >= 1e-3
+            // and a first sample inside the fluid is listed; every other node's A_h is final
+            // (0, or its pin term when it has a ray of no samples)
+            if (tid == 0) *nrays = 0;
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < NB_PER_THREAD; ++j) {
+                const int idx = tid + j * NB_THREADS;
+                const int lx = idx % NB_X, ly = (idx / NB_X) % NB_Y, lz = idx / (NB_X * NB_Y);
+                const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+                bool listed = false;
+                if (x < p.nx && y < p.ny && z < p.nz) {
+                    float Gx, Gy, Gz, nx_, ny_, nz_;
+                    cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, zbase, Gx, Gy, Gz);
+                    float a = 0.0f;
+                    if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
+                        listed = nc_sample_end(p, y, z, ny_, nz_) > 0;
+                        if (!listed && p.pin_d2) {
+                            const unsigned d2 = __ldg(p.pin_d2 + (size_t)z * plane + (size_t)y * p.nx + x);
+                            if (d2 != 255u) a = A_h(p, sqrtf((float)d2));
+                        }
+                    }
+                    if (!listed) p.ah[(size_t)z * plane + (size_t)y * p.nx + x] = a;
+                }
+                // (one atomic per warp)
+                const unsigned m = __ballot_sync(0xffffffffu, listed);
+                int base = 0;
+                if (lane == 0 && m) base = atomicAdd(nrays, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (listed) rays[base + __popc(m & ((1u << lane) - 1u))] = idx;
+            }
+            __syncthreads();
+            const int nr = *nrays;
+            // ---- 2. the listed rays, one per thread: the sign class of every sample (all
+            // rays of a lattice without walls have the same samples, so the lanes of a warp
+            // stay together), then A_h from the sign masks and the samples around the two
+            // crossings, interpolated again
+            for (int k = tid; k < nr; k += NB_THREADS) {
+                NcRay r;
+                r.start<H>(p, cube, rays[k], x0, y0, z0, zbase);
+                r.measure<H>(p, cube, y0, z0);
+                r.finish(p, plane);
+            }
+            __syncthreads();   // the cube and the ray list are consumed
+            zbase = ring_slot<H>(zbase, NB_Z);   // the next block's window starts NB_Z planes up
         }
-        __syncthreads();
-        const int nr = *nrays;
-        // ---- 2. the listed rays, one per thread: the sign class of every sample (all
-        // rays of a lattice without walls have the same samples, so the lanes of a warp
-        // stay together), then A_h from the sign masks and the samples around the two
-        // crossings, interpolated again
-        for (int k = tid; k < nr; k += NB_THREADS) {
-            NcRay r;
-            r.start<H>(p, cube, rays[k], x0, y0, z0);
-            r.measure<H>(p, cube, y0, z0);
-            r.finish(p, plane);
-        }
-        __syncthreads();   // the cube and the ray list are consumed
     }
     if (failed) {
         // give a tensor copy still in flight into this CTA's cube a bounded chance to
@@ -1842,15 +1885,25 @@ int nc_halo(double h_cut) {
 // Blocks of nodes of a lattice's near-contact pass.
 long long nc_block_count(const StepParams& p) { return nc_blocks(p); }
 
-// Shape of the cube a tensor copy of the near-contact pass fills (x, y, z extents), for
-// the tensor map of a colour field.
+// Shape of the box a tensor copy of the near-contact pass fills (x, y, z extents: one
+// plane of a halo cube), for the tensor map of a colour field.
 void nc_cube_box(double h_cut, int box[3]) {
     const int need = (int)std::floor(h_cut) + 3;
     const int H = need <= 9 ? 9 : 12;
     const int HX = (H + 3) / 4 * 4;
     box[0] = NB_X + 2 * HX;
     box[1] = NB_Y + 2 * H;
-    box[2] = NB_Z + 2 * H;
+    box[2] = 1;
+}
+
+// Blocks per z segment of a block column in the near-contact pass: up to 8 (a block's
+// window then shares all but NB_Z of its planes with the last one's), fewer where the
+// lattice has too few columns for about four work items per CTA (two CTAs per SM).
+int nc_segment_blocks(int nx, int ny, int nz, int num_sms) {
+    const long long cols = (long long)((nx + NB_X - 1) / NB_X) * ((ny + NB_Y - 1) / NB_Y);
+    const long long bzn = (nz + NB_Z - 1) / NB_Z;
+    const long long want = 8LL * std::max(1, num_sms);
+    return (int)std::max<long long>(1, std::min<long long>({8LL, bzn, cols * bzn / want}));
 }
 
 template <class St, bool U, bool SC>
