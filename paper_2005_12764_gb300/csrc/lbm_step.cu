@@ -1345,7 +1345,7 @@ struct CubeCell {
     int o0, o1;
     float fx, fy, fz;
 };
-template <int H>
+template <int H, bool W>
 __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int y0, int z0,
                                           int lx, int ly, int lz, int zbase, float ox, float oy,
                                           float oz, CubeCell& c) {
@@ -1356,11 +1356,11 @@ __device__ __forceinline__ void cube_cell(const StepParams& p, int y, int z, int
     c.fz = oz - flz;
     const int cx0 = lx + G::HX + (int)flx;
     int cy0 = ly + H + (int)fly, cz0 = lz + H + (int)flz;
-    if (p.wall_y && y + (int)fly == p.ny - 1) {   // on the last node: the cell below, fy = 1
+    if (W && p.wall_y && y + (int)fly == p.ny - 1) {   // on the last node: the cell below, fy = 1
         cy0 = p.ny - 2 - y0 + H;
         c.fy = 1.0f;
     }
-    if (p.wall_z && z + (int)flz == p.nz - 1) {
+    if (W && p.wall_z && z + (int)flz == p.nz - 1) {
         cz0 = p.nz - 2 - z0 + H;
         c.fz = 1.0f;
     }
@@ -1390,7 +1390,7 @@ __device__ __forceinline__ float cube_interp(const CubeCell& c, const float (&v)
 
 // Lagged gradient of block node (lx, ly, lz) = lattice node (x, y, z) from the cube: the
 // terms of gradient_global in its order; a neighbour beyond a wall takes the centre value.
-template <int H>
+template <int H, bool W>
 __device__ __forceinline__ void cube_gradient(const StepParams& p, const float* cube, int x, int y,
                                               int z, int lx, int ly, int lz, int zbase, float& Gx,
                                               float& Gy, float& Gz) {
@@ -1400,8 +1400,8 @@ __device__ __forceinline__ void cube_gradient(const StepParams& p, const float* 
     const float* p0 = cube + ring_slot<H>(zbase, lz + H) * G::PLANE + r;
     const float* pp = cube + ring_slot<H>(zbase, lz + H + 1) * G::PLANE + r;
     const float phic = p0[0];
-    const bool ylo = p.wall_y && y == 0, yhi = p.wall_y && y == p.ny - 1;
-    const bool zlo = p.wall_z && z == 0, zhi = p.wall_z && z == p.nz - 1;
+    const bool ylo = W && p.wall_y && y == 0, yhi = W && p.wall_y && y == p.ny - 1;
+    const bool zlo = W && p.wall_z && z == 0, zhi = W && p.wall_z && z == p.nz - 1;
     Gx = Gy = Gz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -1482,7 +1482,7 @@ __device__ __forceinline__ void nc_fill_planes(const StepParams& p, const CUtens
 struct NcRay {
     int lx, ly, lz, x, y, z, s_end, zb;
     float nx_, ny_, nz_, a;
-    template <int H>
+    template <int H, bool W>
     __device__ __forceinline__ void start(const StepParams& p, const float* cube, int idx, int x0,
                                           int y0, int z0, int zbase) {
         zb = zbase;
@@ -1493,17 +1493,17 @@ struct NcRay {
         y = y0 + ly;
         z = z0 + lz;
         float Gx, Gy, Gz;
-        cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, zb, Gx, Gy, Gz);
+        cube_gradient<H, W>(p, cube, x, y, z, lx, ly, lz, zb, Gx, Gy, Gz);
         nc_ray(Gx, Gy, Gz, nx_, ny_, nz_);
         s_end = nc_sample_end(p, y, z, ny_, nz_);
         a = 0.0f;
     }
     // The lagged colour field at the sample at t, interpolated from the cube.
-    template <int H>
+    template <int H, bool W>
     __device__ __forceinline__ float value(const StepParams& p, const float* cube, int y0, int z0,
                                            float t) const {
         CubeCell cell;
-        cube_cell<H>(p, y, z, y0, z0, lx, ly, lz, zb, t * nx_, t * ny_, t * nz_, cell);
+        cube_cell<H, W>(p, y, z, y0, z0, lx, ly, lz, zb, t * nx_, t * ny_, t * nz_, cell);
         float v[8];
         cube_corners<H>(cube, cell, v);
         return cube_interp(cell, v);
@@ -1517,12 +1517,12 @@ struct NcRay {
     // when kp != j and t_kp - t_d >= h_cut; otherwise A_h = A_h(t_u - t_d), each
     // crossing located by linear interpolation between its two samples (the same
     // expressions as the march: the same bits).
-    template <int H>
+    template <int H, bool W>
     __device__ __forceinline__ void measure(const StepParams& p, const float* cube, int y0, int z0) {
         uint32_t P = 0u, N = 0u;
 #pragma unroll 4
         for (int s = 0; s < s_end; ++s) {
-            const float v = value<H>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
+            const float v = value<H, W>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
             P |= (v > kSignBand ? 1u : 0u) << s;
             N |= (v < -kSignBand ? 1u : 0u) << s;
         }
@@ -1543,11 +1543,11 @@ struct NcRay {
         const int k = __ffs((int)later) - 1;
         const int kp = 31 - __clz((int)(S & ((1u << k) - 1u)));
         const float t_jp = -1.0f + 0.5f * (float)jp, t_j = -1.0f + 0.5f * (float)j;
-        const float v_jp = value<H>(p, cube, y0, z0, t_jp), v_j = value<H>(p, cube, y0, z0, t_j);
+        const float v_jp = value<H, W>(p, cube, y0, z0, t_jp), v_j = value<H, W>(p, cube, y0, z0, t_j);
         const float t_d = t_jp + (t_j - t_jp) * v_jp / (v_jp - v_j);
         const float t_kp = -1.0f + 0.5f * (float)kp, t_k = -1.0f + 0.5f * (float)k;
         if (kp != j && t_kp - t_d >= p.h_cut) return;
-        const float v_kp = value<H>(p, cube, y0, z0, t_kp), v_k = value<H>(p, cube, y0, z0, t_k);
+        const float v_kp = value<H, W>(p, cube, y0, z0, t_kp), v_k = value<H, W>(p, cube, y0, z0, t_k);
         const float t_u = t_kp + (t_k - t_kp) * v_kp / (v_kp - v_k);
         a = A_h(p, t_u - t_d);
     }
@@ -1637,7 +1637,7 @@ __host__ __device__ inline long long nc_blocks(const StepParams& p) {
 
 // The pass over `nblocks` blocks of `src` (see nc_block_kernel below for what a block
 // does); the CTA takes blocks blockIdx.x, + gridDim.x, ...
-template <class St, int H, class Src>
+template <class St, int H, bool W, class Src>
 __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsigned char* nsm) {
     using G = NcBlockGeo<H>;
     float* cube = reinterpret_cast<float*>(nsm);                           // [SZ][SY][SX]
@@ -1699,7 +1699,7 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
                 bool listed = false;
                 if (x < p.nx && y < p.ny && z < p.nz) {
                     float Gx, Gy, Gz, nx_, ny_, nz_;
-                    cube_gradient<H>(p, cube, x, y, z, lx, ly, lz, zbase, Gx, Gy, Gz);
+                    cube_gradient<H, W>(p, cube, x, y, z, lx, ly, lz, zbase, Gx, Gy, Gz);
                     float a = 0.0f;
                     if (nc_ray(Gx, Gy, Gz, nx_, ny_, nz_)) {
                         listed = nc_sample_end(p, y, z, ny_, nz_) > 0;
@@ -1725,8 +1725,8 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
             // crossings, interpolated again
             for (int k = tid; k < nr; k += NB_THREADS) {
                 NcRay r;
-                r.start<H>(p, cube, rays[k], x0, y0, z0, zbase);
-                r.measure<H>(p, cube, y0, z0);
+                r.start<H, W>(p, cube, rays[k], x0, y0, z0, zbase);
+                r.measure<H, W>(p, cube, y0, z0);
                 r.finish(p, plane);
             }
             __syncthreads();   // the cube and the ray list are consumed
@@ -1742,14 +1742,14 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
     cp_async_wait<0>();
 }
 
-template <class St, int H>
+template <class St, int H, bool W>
 __global__ void __launch_bounds__(NB_THREADS, 2)
 nc_block_kernel(const StepParams p, const __grid_constant__ CUtensorMap lag_map, int tma_ok) {
     extern __shared__ __align__(128) unsigned char nsm[];
     if (threadIdx.x == 0)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&lag_map)) : "memory");
     NcOne src{&p, &lag_map, tma_ok};
-    nc_block_pass<St, H>(src, nc_blocks(p), nsm);
+    nc_block_pass<St, H, W>(src, nc_blocks(p), nsm);
     grid_dep_launch();
 }
 
@@ -1762,7 +1762,7 @@ nc_block_kernel_batched(const NcBatchLattice* __restrict__ tab, int nlat, long l
     __shared__ StepParams sp;
     __shared__ int lat;
     NcBatch src{tab, nlat, ghost_total, &sp, &lat};
-    nc_block_pass<St, H>(src, nblocks, nsm);
+    nc_block_pass<St, H, true>(src, nblocks, nsm);
 }
 
 // Launch with programmatic stream serialisation (see grid_dep_wait). (The list and
@@ -1784,21 +1784,21 @@ static cudaError_t pdl_launch(void (*kernel)(KArgs...), unsigned grid, unsigned 
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <class St, int H>
+template <class St, int H, bool W>
 static cudaError_t launch_block_tpl(const StepParams& p, const CUtensorMap& lag_map, bool tma_ok,
                                    int num_sms, cudaStream_t s) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(nc_block_kernel<St, H>,
+        cudaError_t e = cudaFuncSetAttribute(nc_block_kernel<St, H, W>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)NcBlockGeo<H>::SMEM);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_block_kernel<St, H>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc_block_kernel<St, H, W>,
                                                               NB_THREADS, NcBlockGeo<H>::SMEM);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    return pdl_launch(nc_block_kernel<St, H>, (unsigned)(num_sms * per_sm), NB_THREADS,
+    return pdl_launch(nc_block_kernel<St, H, W>, (unsigned)(num_sms * per_sm), NB_THREADS,
                       NcBlockGeo<H>::SMEM, s, p, lag_map, tma_ok ? 1 : 0);
 }
 
@@ -1807,8 +1807,14 @@ static cudaError_t launch_block_st(const StepParams& p, const CUtensorMap& lag_m
                                    int num_sms, cudaStream_t s) {
     // halo: the farthest corner of a ray sample is floor(h_cut) + 3 nodes away
     const int need = (int)floorf(p.h_cut) + 3;
-    if (need <= 9) return launch_block_tpl<St, 9>(p, lag_map, tma_ok, num_sms, s);
-    if (need <= 12) return launch_block_tpl<St, 12>(p, lag_map, tma_ok, num_sms, s);
+    // (lattices without walls take the instances without the wall tests)
+    const bool w = p.wall_y || p.wall_z;
+    if (need <= 9)
+        return w ? launch_block_tpl<St, 9, true>(p, lag_map, tma_ok, num_sms, s)
+                 : launch_block_tpl<St, 9, false>(p, lag_map, tma_ok, num_sms, s);
+    if (need <= 12)
+        return w ? launch_block_tpl<St, 12, true>(p, lag_map, tma_ok, num_sms, s)
+                 : launch_block_tpl<St, 12, false>(p, lag_map, tma_ok, num_sms, s);
     return cudaErrorInvalidValue;   // h_cut <= 9 is checked when the context is made
 }
 
@@ -1896,14 +1902,14 @@ void nc_cube_box(double h_cut, int box[3]) {
     box[2] = 1;
 }
 
-// Blocks per z segment of a block column in the near-contact pass: up to 8 (a block's
-// window then shares all but NB_Z of its planes with the last one's), fewer where the
+// Blocks per z segment of a block column in the near-contact pass: up to 16 (a block's
+// window shares all but NB_Z of its planes with the last one's), fewer where the
 // lattice has too few columns for about four work items per CTA (two CTAs per SM).
 int nc_segment_blocks(int nx, int ny, int nz, int num_sms) {
     const long long cols = (long long)((nx + NB_X - 1) / NB_X) * ((ny + NB_Y - 1) / NB_Y);
     const long long bzn = (nz + NB_Z - 1) / NB_Z;
     const long long want = 8LL * std::max(1, num_sms);
-    return (int)std::max<long long>(1, std::min<long long>({8LL, bzn, cols * bzn / want}));
+    return (int)std::max<long long>(1, std::min<long long>({16LL, bzn, cols * bzn / want}));
 }
 
 template <class St, bool U, bool SC>
