@@ -77,6 +77,8 @@ def _load():
                 "or_nc_strength_node": (C.c_double, [P, _D, _U8, C.c_long, C.c_long, C.c_long]),
                 "or_nc_strength_node_thr": (C.c_double, [P, _D, _U8, C.c_long, C.c_long,
                                                          C.c_long, C.c_double, C.c_double]),
+                "or_nc_strength_node_g": (C.c_double, [P, _D, _U8, C.c_long, C.c_long, C.c_long,
+                                                       C.c_double, C.c_double, _D]),
                 "or_gradient": (None, [P, _D, _D, _D, _D]),
                 "or_create": (C.c_void_p, [P]),
                 "or_destroy": (None, [C.c_void_p]),
@@ -218,6 +220,19 @@ def nc_strength_node_thr(params: Params, phi_ray, x, y, z, band, g_min, pin=None
         pin_p = pin.ctypes.data_as(_U8)
     return _load().or_nc_strength_node_thr(C.byref(params), _d(phi_ray), pin_p, int(x), int(y),
                                            int(z), float(band), float(g_min))
+
+
+def nc_strength_node_g(params: Params, phi_ray, x, y, z, G, band=1e-5, g_min=1e-3, pin=None):
+    """nc_strength_node_thr with the lagged gradient G' = (Gx, Gy, Gz) at the node given
+    instead of evaluated from phi_ray."""
+    phi_ray = _f64(phi_ray)
+    g = np.ascontiguousarray(G, dtype=np.float64)
+    pin_p = None
+    if pin is not None:
+        pin = np.ascontiguousarray(pin, dtype=np.uint8)
+        pin_p = pin.ctypes.data_as(_U8)
+    return _load().or_nc_strength_node_g(C.byref(params), _d(phi_ray), pin_p, int(x), int(y),
+                                         int(z), float(band), float(g_min), _d(g))
 
 
 def step_nodes(params: Params, fr, fb, phi_lag, nodes, pin=None, ah=None):

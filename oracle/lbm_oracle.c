@@ -409,13 +409,29 @@ static void gradient_node(const or_params* p, const double* phi, long x, long y,
  * one is a branch taken differently at a threshold (a sample or a gradient within
  * rounding of it), by evaluating the reading with each threshold moved by the
  * FP32 rounding bound.                                                          */
+/* The same strength with the lagged gradient G' at the node given (Gin) instead of
+ * evaluated from phi_ray: the tests move it by the FP32 rounding bound of its
+ * stencil sum, to tell a ray direction rounded differently in FP32 (which moves the
+ * samples, hence the crossings) from a wrong value.                             */
+double or_nc_strength_node_g(const or_params* p, const double* phi_ray,
+                             const unsigned char* pin, long x, long y, long z,
+                             double band, double g_min, const double* Gin);
+
 double or_nc_strength_node_thr(const or_params* p, const double* phi_ray,
                                const unsigned char* pin, long x, long y, long z,
                                double band, double g_min) {
     lattice_init();
-    if (p->A_nc == 0.0) return 0.0;
     double G[3];
     gradient_node(p, phi_ray, x, y, z, G);
+    return or_nc_strength_node_g(p, phi_ray, pin, x, y, z, band, g_min, G);
+}
+
+double or_nc_strength_node_g(const or_params* p, const double* phi_ray,
+                             const unsigned char* pin, long x, long y, long z,
+                             double band, double g_min, const double* Gin) {
+    lattice_init();
+    if (p->A_nc == 0.0) return 0.0;
+    const double G[3] = {Gin[0], Gin[1], Gin[2]};
     double gm = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
     if (!(gm >= g_min) || !isfinite(gm)) return 0.0;   /* non-finite fields: no force */
     double n[3] = {-G[0] / gm, -G[1] / gm, -G[2] / gm};

@@ -20,6 +20,15 @@ A_h reproduces the GPU's populations). The bounds:
   1 per lattice unit moves the value by at most as much. Bound: 3e-6.
 - |G'|: 18 FP32 terms of magnitude <= 1/6, summed with FMAs, and a square root:
   within 5e-7. Bound: 1e-6.
+
+The same rounding moves the ray: each component of G' (10 FMA terms) is within 1e-6
+of its FP64 value, so where |G'| is small (it is >= 1e-3) the FP32 direction may
+turn by up to about 1e-6/|G'|, the samples far along the ray move with it, and with
+them the crossings and h. Such a difference is accepted only if the GPU's A_h lies
+within the comparison's tolerance of the range of the oracle's A_h over the
+gradients G' + (+-1e-6, +-1e-6, +-1e-6) (away from threshold branches A_h is
+continuous in the direction, so every value between two of those is reached by a
+gradient in that box).
 """
 from __future__ import annotations
 
@@ -42,6 +51,16 @@ def ah_variants(P, lag, x, y, z, pin=None):
 def ah_explained(P, lag, x, y, z, got, tol, pin=None) -> bool:
     """True if some threshold variant of the oracle's A_h is within tol of got."""
     return any(abs(v - got) <= tol for v in ah_variants(P, lag, x, y, z, pin))
+
+
+def ah_direction_explained(P, lag, x, y, z, got, tol, G, pin=None) -> bool:
+    """True if got lies within tol of the range of the oracle's A_h over the lagged
+    gradients G + (+-D_GRAD, +-D_GRAD, +-D_GRAD) (G = the FP64 gradient at the node)."""
+    vals = [oracle.nc_strength_node_g(P, lag, x, y, z,
+                                      (G[0] + sx * D_GRAD, G[1] + sy * D_GRAD, G[2] + sz * D_GRAD),
+                                      pin=pin)
+            for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+    return min(vals) - tol <= got <= max(vals) + tol
 
 
 def step_explained(P, fr, fb, lag, node, got_r, got_b, ah_gpu, tol=1e-6, pin=None):

@@ -93,9 +93,9 @@ BOUND_CASES = {
 @pytest.mark.parametrize("case", sorted(BOUND_CASES))
 def test_near_contact_pass_on_odd_ragged_lattices(lbm, case):
     # The near-contact pass works in 16 x 8 x 8 blocks with halo cubes (wrapped at
-    # periodic seams, clamped at walls) and bounds each ray by a cube-local bit table:
-    # on odd, ragged, walled and periodic lattices every node's A_h equals the
-    # oracle's full ray march, after several steps (threshold branches proven).
+    # periodic seams, clamped at walls): on odd, ragged, walled and periodic lattices
+    # every node's A_h equals the oracle's full ray march, after several steps
+    # (threshold branches proven).
     import branch_cases
     c = BOUND_CASES[case]
     shape = c["shape"]
@@ -124,4 +124,60 @@ def test_near_contact_pass_on_odd_ragged_lattices(lbm, case):
                             1e-6 * kw["A_nc"] + 1e-3 * abs(got[z, y, x])), (steps, x, y, z)
                     seen += want > 0
     assert seen > 50
+    g.close()
+
+
+SEGMENT_CASES = [("periodic", dict(h_min=3.0)), ("periodic_halo12", dict(h_min=4.0, h_cut=8.0)),
+                 ("walls_halo12", dict(h_min=3.0, h_cut=9.0, wall_y=1, wall_z=1))]
+
+
+@pytest.mark.parametrize("case", range(len(SEGMENT_CASES)), ids=[c[0] for c in SEGMENT_CASES])
+def test_near_contact_pass_column_segments(lbm, case):
+    # A lattice with enough block columns that the pass walks segments of several
+    # blocks along z (its halo cube a ring of planes, each later block copying only the
+    # planes that enter its window), with the halo-9 and halo-12 cubes (h_cut <= 6,
+    # h_cut up to 9), periodic and walled: A_h at 40,000 random nodes and at up to
+    # 40,000 nodes where the GPU measured a film equals the oracle's ray march
+    # (threshold branches and ray directions rounded in FP32 proven).
+    import branch_cases
+    import torch
+    name, extra = SEGMENT_CASES[case]
+    nz, ny, nx = 128, 128, 256
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cols, bzn = (nx // 16) * (ny // 8), nz // 8
+    assert min(16, bzn, cols * bzn // (8 * sms)) > 1      # segments of more than one block
+    rng = np.random.default_rng(40 + case)
+    drops = [(float(rng.uniform(0, nx)), float(rng.uniform(0, ny)), float(rng.uniform(0, nz)),
+              float(rng.uniform(5.0, 8.0))) for _ in range(420)]
+    walls = bool(extra.get("wall_y"))
+    rr, rb = inputs.paint_droplets((nz, ny, nx), drops, periodic=(True, not walls, not walls))
+    kw = dict(sigma=0.02, beta=0.7, A_nc=0.02, **extra)
+    g = lbm.Lattice(lbm.make_params(nx, ny, nz, **kw))
+    g.set_fields(rr, rb)
+    g.step(3)
+    _, _, lag = g.get_pops()
+    got = g.get_nc_field()
+    op = oracle.make_params(nx, ny, nz, **kw)
+    films = np.argwhere(got > 0)
+    assert len(films) > 1000
+    pick = rng.choice(len(films), size=min(len(films), 40000), replace=False)
+    nodes = [tuple(v) for v in films[pick]]
+    nodes += [(int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx)))
+              for _ in range(40000)]
+    lag = np.ascontiguousarray(lag, dtype=np.float64)
+    G = oracle.gradient(op, lag)
+    turned = 0
+    for (z, y, x) in nodes:
+        want = oracle.nc_strength_node(op, lag, x, y, z)
+        tol = 1e-6 * kw["A_nc"] + 1e-3 * abs(want)
+        if abs(got[z, y, x] - want) > tol:
+            tg = 1e-6 * kw["A_nc"] + 1e-3 * abs(got[z, y, x])
+            if branch_cases.ah_explained(op, lag, x, y, z, got[z, y, x], tg):
+                continue
+            # (a ray direction rounded differently in FP32, at a small |G'|)
+            assert branch_cases.ah_direction_explained(op, lag, x, y, z, got[z, y, x], tg,
+                                                       G[:, z, y, x]), \
+                (name, x, y, z, got[z, y, x], want)
+            turned += 1
+    assert turned <= 1e-3 * len(nodes), turned
     g.close()
