@@ -60,39 +60,48 @@ template <class St>
 __global__ void init_fields_kernel(typename St::T* f, float* phi0, float* phi1,
                                    const double* rho_r, const double* rho_b, const double* u,
                                    StepParams sp) {
-    const size_t N = sp.N, P = sp.P;
+    // (node indices in 32 bits: a lattice has fewer than 2^31 nodes)
+    const unsigned N = (unsigned)sp.N, plane = (unsigned)sp.nx * (unsigned)sp.ny;
+    const size_t P = sp.P;
     const float ref_half = sp.ref_half;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
-         n += (size_t)gridDim.x * blockDim.x) {
-        const size_t q = node_pidx(sp, n);
+    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const unsigned z = n / plane, rem = n - z * plane;
+        const unsigned y = rem / (unsigned)sp.nx, x = rem - y * (unsigned)sp.nx;
+        const size_t q = pidx(sp.pitch, sp.nyp, sp.padx, (int)x, (int)y, (int)z);
         const double rr = rho_r[n], rb = rho_b[n];
-        double ux = 0, uy = 0, uz = 0;
+        float ux = 0.f, uy = 0.f, uz = 0.f;
         if (u) {
-            ux = u[n];
-            uy = u[N + n];
-            uz = u[2 * N + n];
+            ux = (float)u[n];
+            uy = (float)u[N + n];
+            uz = (float)u[2 * (size_t)N + n];
         }
-        const double usq = ux * ux + uy * uy + uz * uz;
+        const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
         const float ph = (float)((rr - rb) / (rr + rb));
+        // f_i = rho_k w_i (1 + d_i), d_i = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u^2: rho_k w_i per
+        // weight class in FP64, rounded once, and the small correction d_i in FP32 (the
+        // result within an FP32 unit of the FP64 value rounded)
+        const float wr[3] = {(float)(rr * (1.0 / 3.0)), (float)(rr * (1.0 / 18.0)), (float)(rr * (1.0 / 36.0))};
+        const float wb[3] = {(float)(rb * (1.0 / 3.0)), (float)(rb * (1.0 / 18.0)), (float)(rb * (1.0 / 36.0))};
+        const double rho = rr + rb;
+        const float wt[3] = {(float)(rho * (1.0 / 3.0)), (float)(rho * (1.0 / 18.0)), (float)(rho * (1.0 / 36.0))};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-            const double w = csq(i) == 0 ? 1.0 / 3.0 : (csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
-            const double e = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+            const float d = cu * (3.0f + 4.5f * cu) - usq15;
+            const int c = csq(i);
             if constexpr (St::RED) {
-                St::store(f, (size_t)i * P + q, (float)((rr + rb) * e),
+                St::store(f, (size_t)i * P + q, __fmaf_rn(wt[c], d, wt[c]),
                           St::tot_ref(i, 2.0f * ref_half));
             } else {
                 const float hw = wgt(i) * ref_half;
-                const int d = wdir(sp, i);
-                St::store(f, (size_t)d * P + q, (float)(rr * e), dev_ref(hw, ph, 0));
-                St::store(f, (size_t)(Q + d) * P + q, (float)(rb * e), dev_ref(hw, ph, 1));
+                const int dd = wdir(sp, i);
+                St::store(f, (size_t)dd * P + q, __fmaf_rn(wr[c], d, wr[c]), dev_ref(hw, ph, 0));
+                St::store(f, (size_t)(Q + dd) * P + q, __fmaf_rn(wb[c], d, wb[c]), dev_ref(hw, ph, 1));
             }
         }
         if constexpr (St::RED) {
             // f^eq is linear in the density: f^eq(rho_k, u) = (rho_k / rho) f^eq(rho, u),
             // the reduced form with kappa_k = rho_k / rho and m = 0
-            const double rho = rr + rb;
             St::store_coef(f, P, q, 0, (float)(rr / rho));
             St::store_coef(f, P, q, 1, (float)(rb / rho));
             for (int k = 2; k < Q5_AUX; ++k) St::store_coef(f, P, q, k, 0.0f);
@@ -158,10 +167,13 @@ template <class St>
 __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int have_force,
                                      const float* phi_now, const float* sc_rho, double* rho_r,
                                      double* rho_b, double* u, double* phi) {
-    const size_t N = sp.N, P = sp.P;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
-         n += (size_t)gridDim.x * blockDim.x) {
-        const size_t q = node_pidx(sp, n);
+    // (node indices in 32 bits: a lattice has fewer than 2^31 nodes)
+    const unsigned N = (unsigned)sp.N, plane = (unsigned)sp.nx * (unsigned)sp.ny;
+    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const unsigned zu = n / plane, rem = n - zu * plane;
+        const unsigned yu = rem / (unsigned)sp.nx;
+        const int x = (int)(rem - yu * (unsigned)sp.nx), y = (int)yu, z = (int)zu;
+        const size_t q = pidx(sp.pitch, sp.nyp, sp.padx, x, y, z);
         const float ph = ref_phi<St>(phi_now, n);
         float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -174,7 +186,6 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
             jy += cy(i) * (a + b);
             jz += cz(i) * (a + b);
         }
-        const int x = (int)(n % sp.nx), y = (int)((n / sp.nx) % sp.ny), z = (int)(n / ((size_t)sp.nx * sp.ny));
         float Fx = 0.f, Fy = 0.f, Fz = 0.f;
         if (have_force) {
             Fx = sp.fx_row[y];
@@ -203,13 +214,13 @@ __global__ void export_fields_kernel(const typename St::T* f, StepParams sp, int
                 Fz += rr * (g3 * Sb[2]) + rb * (g3 * Sr[2]);
             }
         }
-        const double rho = (double)rr + (double)rb;
         if (rho_r) rho_r[n] = rr;
         if (rho_b) rho_b[n] = rb;
         if (u) {
-            u[n] = ((double)jx - 0.5 * Fx) / rho;
-            u[N + n] = ((double)jy - 0.5 * Fy) / rho;
-            u[2 * N + n] = ((double)jz - 0.5 * Fz) / rho;
+            const double inv_rho = 1.0 / ((double)rr + (double)rb);
+            u[n] = ((double)jx - 0.5 * Fx) * inv_rho;
+            u[N + n] = ((double)jy - 0.5 * Fy) * inv_rho;
+            u[2 * (size_t)N + n] = ((double)jz - 0.5 * Fz) * inv_rho;
         }
         if (phi) phi[n] = phi_now[n];
     }
@@ -945,7 +956,9 @@ extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const doub
     const size_t N = c->N;
     const double *dr = rho_r, *db = rho_b, *du = u;
     if (!on_device) {
-        if (ensure_stage(c, 5 * c->N) != LBM_OK) return LBM_ENOMEM;
+        // (sized for lbm_get_fields too, the usual next host exchange, so that the
+        // buffer is not freed and allocated again there)
+        if (ensure_stage(c, 7 * c->N) != LBM_OK) return LBM_ENOMEM;
         CK(c, cudaMemcpyAsync(c->stage, rho_r, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemcpyAsync(c->stage + N, rho_b, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         dr = c->stage;
