@@ -152,7 +152,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out);
 /* Initial state: f_i^k = f_i^eq(rho_k, u) of Eq. (2) per species, with u the
  * common velocity ([3][N], NULL = 0); both colour-field buffers are set to
  * (rho_r - rho_b)/(rho_r + rho_b). rho_r + rho_b must be > 0 at every node.
- * Resets the step counter.                                                     */
+ * Resets the step counter. on_device = 0: host arrays; pinned host memory mapped
+ * into the device's address space (cudaHostAlloc) is read by the kernel directly,
+ * other host memory is copied through a device staging buffer first (allocated on
+ * first use, 7 doubles per node). Returns after the host arrays have been read.  */
 lbm_status lbm_set_fields(lbm_ctx* ctx, const double* rho_r, const double* rho_b,
                           const double* u, int on_device);
 
@@ -177,13 +180,15 @@ lbm_status lbm_step_timed(lbm_ctx* ctx, int n, double out_ms[3]);
 
 /* Kernel launches one lbm_step makes per time step: the fused step, and either the
  * ghost-copy fill of the periodic axes (A_nc == 0) or the near-contact pass, which
- * writes those ghost copies too (A_nc > 0; the first step after a change of state
- * adds the ray-bound field and a candidate scan).                              */
+ * writes those ghost copies too (A_nc > 0). In place (inplace = 1): the colour-field
+ * and collide passes, and the near-contact pass when A_nc > 0.                   */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 
 /* Fields of the last step (any pointer may be NULL): rho_r, rho_b, phi [N] and the
  * physical velocity u = (j + F/2)/rho of the EDM scheme, [3][N]. Before the first
- * step, the fields that were set. Synchronises the stream.                      */
+ * step, the fields that were set. Synchronises the stream. on_device = 0: host
+ * arrays, written by the kernel directly when they are all pinned host memory
+ * mapped into the device's address space, else through the staging buffer.      */
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u,
                           double* phi, int on_device);
 

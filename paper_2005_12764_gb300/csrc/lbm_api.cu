@@ -949,13 +949,47 @@ static void dispatch(int storage, F&& fn) {
     else fn(StoreQ5H{});
 }
 
+// Device address of a host buffer that kernels may read and write directly (pinned host
+// memory mapped into the device's address space, e.g. from cudaHostAlloc), else null.
+static void* mapped_host(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+// The device addresses of the given (non-null) host buffers when every one of them is
+// mapped; false otherwise (the buffers then go through the staging buffer).
+static bool map_all(const void* const* host, void** dev, int n) {
+    for (int k = 0; k < n; ++k) {
+        dev[k] = nullptr;
+        if (host[k] && !(dev[k] = mapped_host(host[k]))) return false;
+    }
+    return true;
+}
+
 extern "C" lbm_status lbm_set_fields(lbm_ctx* c, const double* rho_r, const double* rho_b,
                                      const double* u, int on_device) {
     if (!c) return LBM_EINVAL;
     if (!rho_r || !rho_b) return fail(c, LBM_EINVAL, "rho_r and rho_b are required");
     const size_t N = c->N;
     const double *dr = rho_r, *db = rho_b, *du = u;
+    // host buffers mapped into the device's address space are read by the kernel
+    // directly; any other host buffer is copied to the staging buffer first
+    bool staged = !on_device;
     if (!on_device) {
+        const void* hp[3] = {rho_r, rho_b, u};
+        void* dv[3];
+        if (map_all(hp, dv, 3)) {
+            dr = static_cast<const double*>(dv[0]);
+            db = static_cast<const double*>(dv[1]);
+            du = static_cast<const double*>(dv[2]);
+            staged = false;
+        }
+    }
+    if (staged) {
         // (sized for lbm_get_fields too, the usual next host exchange, so that the
         // buffer is not freed and allocated again there)
         if (ensure_stage(c, 7 * c->N) != LBM_OK) return LBM_ENOMEM;
@@ -1140,7 +1174,21 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
     if (!c->fields_set) return fail(c, LBM_ESTATE, "lbm_set_fields has not been called");
     const size_t N = c->N;
     double *dr = rho_r, *db = rho_b, *du = u, *dp = phi;
+    // host buffers mapped into the device's address space are written by the export
+    // kernel directly (no staging copy); any other host buffer goes through staging
+    bool staged = !on_device;
     if (!on_device) {
+        const void* hp[4] = {rho_r, rho_b, u, phi};
+        void* dv[4];
+        if (map_all(hp, dv, 4)) {
+            dr = static_cast<double*>(dv[0]);
+            db = static_cast<double*>(dv[1]);
+            du = static_cast<double*>(dv[2]);
+            dp = static_cast<double*>(dv[3]);
+            staged = false;
+        }
+    }
+    if (staged) {
         if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
         dr = rho_r ? c->stage : nullptr;
         db = rho_b ? c->stage + N : nullptr;
@@ -1151,18 +1199,18 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
     s.phi_lag = c->phi[1 - c->pc];   // the lag field the last step's rays read
     const int grid = grid_for(N, c->num_sms);
     if (c->steps > 0 && c->p.A_nc > 0.0) {
-        // A_h of the last step, re-measured on its lag field in scan mode into scratch
-        // space after the staged fields (the live A_h buffer is left untouched)
-        if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
-        s.ah = reinterpret_cast<float*>(c->stage + 6 * N);
+        // A_h of the last step, re-measured on its lag field, into the A_h buffer: every
+        // step's near-contact pass writes all of it before the step reads it, so between
+        // steps it holds nothing the state depends on
+        s.ah = c->ah;
         CK(c, diag_pass(c, s));
     }
     float* sc_rho = nullptr;
     if (c->steps > 0 && c->p.model == 1 && u) {
-        // densities of the last step for its cohesive forces, in the scratch space
-        // after the staged fields (2N floats)
-        if (ensure_stage(c, 7 * N) != LBM_OK) return LBM_ENOMEM;
-        sc_rho = reinterpret_cast<float*>(c->stage + 6 * N);
+        // densities of the last step for its cohesive forces (2N floats), in scratch
+        // space after the staged fields, or at the start of the staging buffer
+        if (ensure_stage(c, staged ? 7 * N : N) != LBM_OK) return LBM_ENOMEM;
+        sc_rho = reinterpret_cast<float*>(c->stage + (staged ? 6 * N : 0));
         dispatch(c->p.storage, [&](auto st) {
             using St = decltype(st);
             densities_kernel<St><<<grid, kThreads, 0, c->stream>>>(
@@ -1176,7 +1224,7 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, double* rho_r, double* rho_b, d
             dr, db, du, dp);
     });
     CK(c, cudaGetLastError());
-    if (!on_device) {
+    if (staged) {
         if (rho_r) CK(c, cudaMemcpyAsync(rho_r, dr, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (rho_b) CK(c, cudaMemcpyAsync(rho_b, db, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (u) CK(c, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
