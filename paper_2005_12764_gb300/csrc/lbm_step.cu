@@ -1286,8 +1286,10 @@ __global__ void ghost_fill_batched(const BatchLattice* __restrict__ tab, int nla
 //     warp stay together; A_h follows from the sign masks and the four samples around
 //     the two crossings (NcRay::measure).
 // Every node's A_h is written (0 where no film is within h_cut): the field needs no
-// clearing between passes and no candidate list. The kernel first writes the ghost
-// copies of the step's input populations (two-copy storage).
+// clearing between passes and no candidate list. The kernel also writes the ghost
+// copies of the step's input populations (two-copy storage): a warp with no ray left
+// in a block's last round takes one ghost task, and the CTA's remaining tasks follow
+// its last block.
 constexpr int NB_X = 16, NB_Y = 8, NB_Z = 8, NB_NODES = NB_X * NB_Y * NB_Z;
 constexpr int NB_THREADS = 512, NB_PER_THREAD = NB_NODES / NB_THREADS;
 
@@ -1650,15 +1652,23 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
         mbar_init(bar, 1);
         fence_mbar_init();
     }
+    // ghost tasks of this CTA: blockIdx.x + j gridDim.x for j = 0, 1, ...; a warp that
+    // has no ray left in a block takes the next one (its scattered accesses then overlap
+    // the other warps' rays), and all warps take the rest after the last block
+    int* gnext = nrays + 3;
+    if (tid == 0) *gnext = 0;
     __syncthreads();
     grid_dep_wait();
-    // the ghost copies first, every warp of the launch on its share of the tasks (many
-    // independent scattered accesses in flight at once)
-    {
-        const long long gtotal = src.ghost_total(), gwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-        for (long long t = ((long long)blockIdx.x * blockDim.x + tid) >> 5; t < gtotal; t += gwarps)
-            src.template ghost<St>(t, lane);
-    }
+    const long long gtotal = src.ghost_total();
+    auto ghost_next = [&]() {
+        int j = 0;
+        if (lane == 0) j = atomicAdd(gnext, 1);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
+        if (t >= gtotal) return false;
+        src.template ghost<St>(t, lane);
+        return true;
+    };
     uint32_t parity = 0u;
     bool failed = false;
     for (long long item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
@@ -1729,6 +1739,9 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
                 r.measure<H, W>(p, cube, y0, z0);
                 r.finish(p, plane);
             }
+            // (a warp without a ray in the last round: one ghost task)
+            if ((tid & ~31) + NB_THREADS * ((nr + NB_THREADS - 1) / NB_THREADS - 1) >= nr || nr == 0)
+                ghost_next();
             __syncthreads();   // the cube and the ray list are consumed
             zbase = ring_slot<H>(zbase, NB_Z);   // the next block's window starts NB_Z planes up
         }
@@ -1740,6 +1753,8 @@ __device__ __forceinline__ void nc_block_pass(Src& src, long long nitems, unsign
             if (mbar_try_wait(bar, parity)) break;
     }
     cp_async_wait<0>();
+    while (ghost_next()) {
+    }
 }
 
 template <class St, int H, bool W>
