@@ -38,6 +38,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -85,6 +86,45 @@ def bytes_per_node(storage: str) -> int:
     if storage == "fp16_q5":
         return 2 * (Q * 2 + 5 * 4)
     return 2 * Q * C * (4 if storage == "fp32" else 2)
+
+
+# Algorithmic FP32 work of the near-contact pass (Eq. 11 as read: a film measured along
+# -G'/|G'| by trilinear samples of the lagged colour field), in flops:
+NC_FLOPS_NODE = 45     # the lagged gradient G' (18 multiply-adds) and |G'|, the unit ray
+NC_FLOPS_SAMPLE = 27   # a sample: t n' (3 mul), the cell fractions (3 sub), 7 lerps x 3
+NC_FLOPS_RAY = 20      # the two crossings (linear interpolation) and A_h[h]
+FP32_LANES_PER_SM = 128
+
+
+def nc_flops(nodes: int, listed: int, nsamp: int) -> int:
+    """Flops of one near-contact pass: every node's gradient, and every listed node's
+    ray (|G'| >= 1e-3) of nsamp samples with its two crossings."""
+    return nodes * NC_FLOPS_NODE + listed * (nsamp * NC_FLOPS_SAMPLE + NC_FLOPS_RAY)
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 (non-tensor) peak: SMs x FP32 lanes x 2 flops (a multiply-add) x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def listed_nodes_periodic(phi, g_min: float = 1e-3) -> int:
+    """Nodes of a periodic lattice whose isotropic colour gradient (3 w_i = 1/6 faces,
+    1/12 edges) has |G| >= g_min: those the near-contact pass gives a ray (a torch
+    tensor [nz, ny, nx], on any device)."""
+    import torch
+    G = [torch.zeros_like(phi) for _ in range(3)]
+    for cz in (-1, 0, 1):
+        for cy in (-1, 0, 1):
+            for cx in (-1, 0, 1):
+                n = abs(cx) + abs(cy) + abs(cz)
+                if n == 0 or n == 3:
+                    continue
+                w3 = 1.0 / 6.0 if n == 1 else 1.0 / 12.0
+                v = torch.roll(phi, shifts=(-cz, -cy, -cx), dims=(0, 1, 2))
+                for a, c in enumerate((cx, cy, cz)):
+                    if c:
+                        G[a] += (w3 * c) * v
+    return int(((G[0] ** 2 + G[1] ** 2 + G[2] ** 2).sqrt() >= g_min).sum().item())
 
 
 def measured_traffic(storage: str, workload: str = "emulsion", nodes: int | None = None):
@@ -551,6 +591,13 @@ def run_ours(args):
     nc_ms, step_ms, _ = lat.step_timed(kt)
     kern_ms = step_ms / kt
     nc_avg_ms = nc_ms / kt
+    # nodes the near-contact pass gives a ray, on the lagged field those steps read
+    listed = None
+    if w.params.get("A_nc", 0.0) > 0 and not (w.params.get("wall_y") or w.params.get("wall_z")):
+        phi_dev = torch.empty(w.shape, dtype=torch.float64, device=f"cuda:{local}")
+        lat.get_fields({"phi": phi_dev})
+        listed = listed_nodes_periodic(phi_dev)
+        del phi_dev
     # ---- end to end through the public API with pinned host buffers
     host_rr = torch.from_numpy(w.rho_r).pin_memory()
     host_rb = torch.from_numpy(w.rho_b).pin_memory()
@@ -670,6 +717,21 @@ def run_ours(args):
             "clocks": clk.summary(),
             "finite": finite,
         }
+        if listed is not None:
+            # the near-contact pass takes most of the step on this workload; it is bound by
+            # instruction issue and latency (ALU), not by HBM
+            h_cut = w.params.get("h_cut") or 2.0 * w.params.get("h_min", 3.0)
+            nsamp = int(math.floor(2.0 * (h_cut + 3.0))) + 1
+            fl = nc_flops(N, listed, nsamp)
+            mhz = line["clocks"].get("sm_max_mhz") or 2070.0
+            ach = fl / (nc_avg_ms * 1e-3) / 1e12
+            pk = fp32_peak_tflops(float(mhz))
+            line["near_contact_roofline"] = {
+                "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "kernel": "nc_block_kernel (near-contact film measurement, with the ghost copies)",
+                "kernel_ms": nc_avg_ms, "flops_per_launch": fl, "listed_fraction": listed / N,
+                "samples_per_ray": nsamp,
+                "peak_source": f"152 SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz} MHz"}
         if fp16:
             line["fp16_store"] = fp16
         if q5:

@@ -95,3 +95,20 @@ def test_reduced_form_with_shan_chen_is_refused_on_the_command_line():
                         "--model", "shan_chen"], capture_output=True, text=True, timeout=120,
                        cwd=ROOT)
     assert r.returncode != 0 and "colour-gradient" in r.stderr
+
+
+def test_near_contact_work_model():
+    # the near-contact roofline: nodes with a ray counted like the oracle's gradient
+    # threshold, the flop model and the FP32 peak from unit counts and clock
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2005_12764_gb300 import inputs
+    shape = (12, 16, 20)
+    rr, rb = inputs.paint_droplets(shape, [(8.0, 8.0, 6.0, 4.0), (15.0, 6.0, 6.0, 3.5)])
+    phi = (rr - rb) / (rr + rb)
+    G = oracle.gradient(oracle.make_params(20, 16, 12), phi)
+    want = int((np.sqrt((G ** 2).sum(axis=0)) >= 1e-3).sum())
+    assert bench.listed_nodes_periodic(torch.from_numpy(phi)) == want > 0
+    assert bench.nc_flops(100, 10, 19) == 100 * 45 + 10 * (19 * 27 + 20)
+    assert abs(bench.fp32_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
