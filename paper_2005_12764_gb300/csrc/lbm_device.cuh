@@ -357,26 +357,9 @@ __device__ __forceinline__ void gradient_global(const StepParams& p, const float
 // zero crossing and the next upward one, each located by linear interpolation
 // between consecutive signed samples; a ray that leaves the fluid through a wall
 // stops there. Pinning sites add A_h[d], d the distance to the nearest pin.
-//
-// Work bound (exact): an upward crossing needs a positive sample, and a trilinear
-// sample is a convex combination of its 8 corner nodes, so it cannot exceed 1e-5
-// when every corner is <= kPosBand = 1e-5/2 (the interpolation's roundings add a few
-// ulp of 0.5e-5 at most). A bit table over 2x2x2 blocks marks where such a corner may
-// be; samples after the last marked one cannot complete a crossing pair, so the march
-// ends there with the same A_h.
 constexpr float kSignBand = 1e-5f;
-constexpr float kPosBand = 0.5e-5f;
 
-// Bits 0, 2, .., 30 of v moved to bits 0 .. 15.
-__device__ __forceinline__ uint32_t even_bits(uint32_t v) {
-    v &= 0x55555555u;
-    v = (v | (v >> 1)) & 0x33333333u;
-    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
-    v = (v | (v >> 4)) & 0x00FF00FFu;
-    return (v | (v >> 8)) & 0x0000FFFFu;
-}
-
-// Ray of a candidate: unit direction -G'/|G'|; false when |G'| < 1e-3 or non-finite.
+// Ray of a node: unit direction -G'/|G'|; false when |G'| < 1e-3 or non-finite.
 __device__ __forceinline__ bool nc_ray(float Gx, float Gy, float Gz, float& nx_, float& ny_,
                                        float& nz_) {
     const float gm = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);

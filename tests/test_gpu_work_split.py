@@ -4,9 +4,9 @@
   bands of planes one CTA per (band, tile), the planes above shared in runs that may
   end inside one tile and continue on the next) against the FP64 oracle, and bitwise
   against part mode (the serving engine's split) on the same lattice.
-- The near-contact pass (blocks of nodes with halo cubes, a cube-local ray bound) on
-  odd, even, ragged, walled and periodic lattices: every node's A_h against the
-  oracle.
+- The near-contact pass (blocks of nodes with halo cubes, kept as rings of planes
+  along block columns) on odd, even, ragged, walled and periodic lattices, with the
+  halo-9 and halo-12 cubes: A_h against the oracle.
 """
 import numpy as np
 import pytest
