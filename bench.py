@@ -559,7 +559,8 @@ def run_ours(args):
     nz, ny, nx = w.shape
     N = nx * ny * nz
     stream = torch.cuda.Stream()
-    P = lbm.make_params(nx, ny, nz, storage=args.storage, stream=stream.cuda_stream, **w.params)
+    P = lbm.make_params(nx, ny, nz, storage=args.storage, stream=stream.cuda_stream,
+                        inplace=1 if args.inplace else 0, **w.params)
     lat = lbm.Lattice(P)
     dev_rr = torch.from_numpy(w.rho_r).to(f"cuda:{local}")
     dev_rb = torch.from_numpy(w.rho_b).to(f"cuda:{local}")
@@ -697,6 +698,7 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[key] if args.size == 512 or key != "emulsion"
                        else WORKLOADS[key].replace("512", str(args.size)),
                        "nodes": N, "storage": args.storage,
+                       "inplace": bool(args.inplace),
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (%.0f MB of populations per copy)"
                              % (bytes_per_node(args.storage) * N / 2 / 1e6),
@@ -837,6 +839,9 @@ def main():
     ap.add_argument("--storage", default="fp32",
                     choices=["fp32", "fp16", "bf16", "fp32_q5", "fp16_q5"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inplace", action="store_true",
+                    help="one population copy updated in place (kernel_ms then covers the "
+                         "colour-field and collide passes)")
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
