@@ -1522,11 +1522,20 @@ struct NcRay {
     template <int H, bool W>
     __device__ __forceinline__ void measure(const StepParams& p, const float* cube, int y0, int z0) {
         uint32_t P = 0u, N = 0u;
+        if (s_end == 19) {   // (h_cut = 6, no wall on the ray: every sample unrolled)
+#pragma unroll
+            for (int s = 0; s < 19; ++s) {
+                const float v = value<H, W>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
+                P |= (v > kSignBand ? 1u : 0u) << s;
+                N |= (v < -kSignBand ? 1u : 0u) << s;
+            }
+        } else {
 #pragma unroll 4
-        for (int s = 0; s < s_end; ++s) {
-            const float v = value<H, W>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
-            P |= (v > kSignBand ? 1u : 0u) << s;
-            N |= (v < -kSignBand ? 1u : 0u) << s;
+            for (int s = 0; s < s_end; ++s) {
+                const float v = value<H, W>(p, cube, y0, z0, -1.0f + 0.5f * (float)s);
+                P |= (v > kSignBand ? 1u : 0u) << s;
+                N |= (v < -kSignBand ? 1u : 0u) << s;
+            }
         }
         const uint32_t S = P | N;
         int jp = -1, j = -1;
