@@ -384,3 +384,23 @@ def test_step_nodes_matches_full_step():
     oa, ob, F = oracle.step_nodes(p, fr.reshape(19, -1), fb.reshape(19, -1), lag.ravel(), nodes)
     assert np.array_equal(oa, gr.reshape(19, -1)[:, nodes].T)
     assert np.array_equal(ob, gb.reshape(19, -1)[:, nodes].T)
+
+
+def test_near_contact_with_the_gradient_given_is_the_same_strength():
+    # the oracle entry that takes the lagged gradient as given (used to bound the FP32
+    # rounding of the ray direction) returns the pinned strength when given the node's
+    # own gradient, and moves continuously with it
+    from paper_2005_12764_gb300 import inputs
+    shape = (12, 16, 24)
+    rr, rb = inputs.paint_droplets(shape, [(7.0, 8.0, 6.0, 4.5), (16.5, 8.0, 6.0, 4.5)])
+    phi = (rr - rb) / (rr + rb)
+    P = oracle.make_params(24, 16, 12, A_nc=0.02, h_min=3.0)
+    G = oracle.gradient(P, phi)
+    seen = 0
+    for (z, y, x) in [(6, 8, 11), (6, 8, 12), (6, 8, 10), (5, 7, 11), (6, 9, 13), (2, 2, 2)]:
+        want = oracle.nc_strength_node(P, phi, x, y, z)
+        assert oracle.nc_strength_node_g(P, phi, x, y, z, G[:, z, y, x]) == want
+        near = oracle.nc_strength_node_g(P, phi, x, y, z, G[:, z, y, x] * (1 + 1e-9))
+        assert abs(near - want) <= 1e-6 * max(1e-3, abs(want))
+        seen += want > 0
+    assert seen >= 2
